@@ -1,0 +1,141 @@
+"""Geometric multigrid V-cycle and preconditioned CG.
+
+Test infrastructure only (see the package docstring).
+
+V-cycle: Alg. 1 with m_pre = m_post = 1 (Sec. 2.4).  The coarse level is
+solved exactly (dense Cholesky); the paper uses a Chebyshev iteration to a
+relative accuracy of 1e-8 there (Sec. 2.4), which it does not specify further,
+so the exact solve is the reading taken.  Pre-smoothing visits the colors in
+order and post-smoothing in reverse order, so that with multiplicative
+smoothers the V-cycle is symmetric and CG applies (the paper uses GMRES for
+multiplicative smoothers; that is a different outer method, not implemented).
+
+PCG: standard preconditioned conjugate gradients from x_0 = 0, stopped when
+||r_k||_2 <= rtol ||r_0||_2 (Sec. 2.4: relative residual reduction 1e-8).
+
+Fractional iterations (Sec. 2.4): nu_frac = nu - 1 + log(e_{nu-1}/tol) /
+log(e_{nu-1}/e_nu) with tol = rtol e_0, here with e the residual norm (the
+paper uses the energy norm of the error for CG; the residual-based value is
+labelled as such where reported).
+
+Pins (tests/test_oracle_multigrid.py): the PCG solution matches a direct
+sparse solve to the residual tolerance; the V-cycle operator is symmetric for
+the additive and the symmetrically ordered multiplicative smoothers; on T_0
+the V-cycle is the exact coarse solve; the fractional count reproduces
+hand-computed values.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+from . import schwarz
+from .mesh import TensorMesh
+from .sipg import SIPG
+from .transfer import prolongation_matrix
+
+
+class Hierarchy:
+    """Levels 0..L of a nested Cartesian mesh hierarchy with SIPG matrices,
+    transfers and local solvers.
+
+    smoother: 'ACS' (additive cells), 'AVS' (additive vertex patches),
+              'MCS' (multiplicative cells, red-black),
+              'MVS' (multiplicative vertex patches, 2^(d+1) colors)."""
+
+    def __init__(self, coarse_widths, k, nlevels, smoother="AVS", omega=None,
+                 gamma_hat=1.0, penalty_poly="paper"):
+        self.k = k
+        self.smoother = smoother
+        self.omega = omega if omega is not None else default_omega(smoother, len(coarse_widths))
+        self.meshes = [TensorMesh(coarse_widths)]
+        for _ in range(nlevels - 1):
+            self.meshes.append(self.meshes[-1].refine())
+        self.sipg = [SIPG(m, k, gamma_hat, penalty_poly) for m in self.meshes]
+        self.A = [s.assemble() for s in self.sipg]
+        self.P = [None] + [prolongation_matrix(self.meshes[l - 1], self.meshes[l], k)
+                           for l in range(1, nlevels)]
+        self.coarse_chol = sla.cho_factor(self.A[0].toarray())
+        self.solvers, self.colors = [None], [None]
+        for l in range(1, nlevels):
+            mesh, A = self.meshes[l], self.A[l]
+            nloc = self.sipg[l].nloc
+            if smoother in ("ACS", "MCS"):
+                patches = schwarz.cell_patches(mesh)
+                cols = [schwarz.color_multiplicative_cell(m) for m, _ in patches]
+            else:
+                patches = schwarz.vertex_patches(mesh)
+                f = (schwarz.color_additive_vertex if smoother == "AVS"
+                     else schwarz.color_multiplicative_vertex)
+                cols = [f(v) for v, _ in patches]
+            A_csr = A.tocsr()
+            def local(cells, A_csr=A_csr, nloc=nloc):
+                idx = schwarz.patch_dofs(cells, nloc)
+                return A_csr[idx][:, idx]
+            self.solvers.append(schwarz.LocalSolvers(patches, nloc, local))
+            self.colors.append(cols)
+
+    @property
+    def nlevels(self):
+        return len(self.meshes)
+
+    def smooth(self, l, x, b, post):
+        if self.smoother in ("ACS", "AVS"):
+            return schwarz.additive_smoother(self.A[l], b, x, self.solvers[l], self.omega)
+        return schwarz.multiplicative_smoother(self.A[l], b, x, self.solvers[l], self.colors[l],
+                                               self.omega, reverse=post)
+
+    def vcycle(self, l, x, b):
+        """Alg. 1, MG_l(x, b)."""
+        if l == 0:
+            return sla.cho_solve(self.coarse_chol, b)
+        x = self.smooth(l, x, b, post=False)
+        b_c = self.P[l].T @ (b - self.A[l] @ x)
+        e_c = self.vcycle(l - 1, np.zeros_like(b_c), b_c)
+        x = x + self.P[l] @ e_c
+        x = self.smooth(l, x, b, post=True)
+        return x
+
+    def precondition(self, r):
+        L = self.nlevels - 1
+        return self.vcycle(L, np.zeros_like(r), r)
+
+
+def default_omega(smoother, d):
+    """Relaxation defaults of Sec. 2.4: 0.7 for ACS, 1 for MCS and MVS; the
+    additive vertex patch smoother needs omega < 2^-d (Sec. 2.4)."""
+    return {"ACS": 0.7, "MCS": 1.0, "MVS": 1.0, "AVS": 0.5 ** d}[smoother]
+
+
+def pcg(A, b, precondition, rtol=1e-8, maxit=500):
+    """Preconditioned CG from x_0 = 0.  Returns (x, iterations, residual norm
+    history [||r_0||, ||r_1||, ...], converged)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = precondition(r)
+    p = z.copy()
+    rz = r @ z
+    hist = [np.linalg.norm(r)]
+    if hist[0] == 0.0:
+        return x, 0, hist, True
+    for it in range(1, maxit + 1):
+        q = A @ p
+        alpha = rz / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        hist.append(np.linalg.norm(r))
+        if hist[-1] <= rtol * hist[0]:
+            return x, it, hist, True
+        z = precondition(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit, hist, False
+
+
+def fractional_iterations(hist, rtol):
+    """Sec. 2.4: nu_frac = nu - 1 + log(e_{nu-1}/tol) / log(e_{nu-1}/e_nu),
+    tol = rtol e_0, nu the first step with e_nu <= tol."""
+    tol = rtol * hist[0]
+    for nu in range(1, len(hist)):
+        if hist[nu] <= tol:
+            return nu - 1 + np.log(hist[nu - 1] / tol) / np.log(hist[nu - 1] / hist[nu])
+    return float("nan")

@@ -1,0 +1,46 @@
+"""Pins for oracle.multigrid (Alg. 1, Sec. 2.4)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.multigrid import Hierarchy, fractional_iterations, pcg
+
+
+def coarse(d, n=2):
+    return [np.full(n, 1.0 / n)] * d
+
+
+@pytest.mark.parametrize("smoother", ["ACS", "AVS", "MCS", "MVS"])
+def test_pcg_solution_matches_direct_solve(smoother):
+    H = Hierarchy(coarse(2), k=2, nlevels=3, smoother=smoother)
+    rng = np.random.default_rng(11)
+    A = H.A[-1]
+    b = rng.uniform(-1, 1, A.shape[0])
+    x, it, hist, ok = pcg(A, b, H.precondition, rtol=1e-10, maxit=200)
+    assert ok
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    assert it < 40
+
+
+@pytest.mark.parametrize("smoother", ["ACS", "AVS", "MCS", "MVS"])
+def test_vcycle_is_symmetric(smoother):
+    H = Hierarchy(coarse(2), k=1, nlevels=3, smoother=smoother)
+    N = H.A[-1].shape[0]
+    B = np.column_stack([H.precondition(e) for e in np.eye(N)])
+    assert np.abs(B - B.T).max() <= 1e-11 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_vcycle_on_coarse_level_is_exact():
+    H = Hierarchy(coarse(3), k=2, nlevels=1, smoother="AVS")
+    b = np.random.default_rng(3).uniform(-1, 1, H.A[0].shape[0])
+    x = H.precondition(b)
+    assert np.abs(H.A[0] @ x - b).max() < 1e-11
+
+
+def test_fractional_iterations_hand_values():
+    # e = 1, 0.1, 0.01, 1e-3 ... ; rtol = 10^-2.5 -> nu = 3, frac = 2 + log(1e-2/10^-2.5)/log(10) = 2.5
+    hist = [1.0, 0.1, 0.01, 1e-3, 1e-4]
+    assert np.isclose(fractional_iterations(hist, 10 ** -2.5), 2.5)
+    assert np.isclose(fractional_iterations(hist, 1e-3), 3.0)
