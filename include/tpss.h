@@ -1,0 +1,214 @@
+/*
+ * tpss.h -- C ABI of the GB300 tensor-product Schwarz smoother library.
+ *
+ * Method: Witte, Arndt, Kanschat, "Fast tensor product Schwarz smoothers for
+ * high-order discontinuous Galerkin methods".  Geometric multigrid for the
+ * symmetric interior penalty (SIPG) discretization of -Laplace(u) = f with
+ * discontinuous Q_k elements on Cartesian tensor grids (Sec. 2.1), smoothed by
+ * cell or vertex-patch Schwarz methods (Sec. 2.3) whose local solvers are
+ * applied by fast diagonalization (Sec. 3.2).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Vectors are DEVICE pointers owned by the caller, contiguous, in the DoF
+ *   layout of eq. discFEspace / eq. multiindex: cells lexicographic with the
+ *   first direction fastest, then the (k+1)^d Gauss-Lobatto nodal values of a
+ *   cell, first direction fastest.  A batch of `nrhs` vectors is stored one
+ *   after another (vector r starts at offset r * ndofs(level)).
+ * - Double-precision entry points take double*; the `_f32` entry points take
+ *   float* and require patches set up with an FP32, TF32 or BF16 precision.
+ * - All work is issued asynchronously on the stream given to tpss_create;
+ *   only calls that return host values (documented) synchronize it.
+ * - The library allocates its own device memory (1D tables, eigenpairs,
+ *   per-level scratch vectors) in tpss_create / tpss_setup_patches /
+ *   tpss_mg_setup and frees it in the matching destroy call.  It never frees
+ *   caller memory.
+ * - Return value: TPSS_OK (0) on success, a negative code on a hard error
+ *   (nothing or only part of the work was done), a positive code for a soft
+ *   outcome (TPSS_ENOTCONV: the iteration stopped at maxit).  Arguments are
+ *   checked on the host before any launch.  tpss_last_error() returns a
+ *   thread-local message for the last failing call.
+ * - No exceptions cross this boundary and there is no global mutable state
+ *   other than the thread-local error message.
+ */
+#ifndef TPSS_H
+#define TPSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPSS_OK = 0,
+  TPSS_ENOTCONV = 1,     /* iteration reached maxit without meeting rtol */
+  TPSS_EINVAL = -1,      /* invalid argument (checked on the host) */
+  TPSS_ECUDA = -2,       /* a CUDA call failed */
+  TPSS_ENOMEM = -3,      /* device allocation failed */
+  TPSS_EBREAKDOWN = -4,  /* NaN/Inf residual or p^T A p <= 0 in CG */
+  TPSS_ETIMEOUT = -5,    /* a bounded device-side wait expired */
+  TPSS_ENUMERIC = -6     /* setup produced a non-positive definite 1D problem */
+} tpss_status;
+
+typedef enum { TPSS_CELL = 0, TPSS_VERTEX_PATCH = 1 } tpss_patch_kind;
+
+/* Arithmetic of the smoother's mode contractions.  FP64 is the plain form;
+ * FP32 runs them on the FP32 pipe; TF32 and BF16 run them on tensor cores with
+ * FP32 accumulation.  The 1D eigenproblems are always solved in FP64. */
+typedef enum { TPSS_FP64 = 0, TPSS_FP32 = 1, TPSS_TF32 = 2, TPSS_BF16 = 3 } tpss_precision;
+
+/* Polynomial factor P(k) of the penalty gamma_e = gamma_hat P(k) (1/h+ + 1/h-)
+ * (eq. penalty): the paper's k(k+1), or (k+1)^2. */
+typedef enum { TPSS_PENALTY_PAPER = 0, TPSS_PENALTY_KP1SQ = 1 } tpss_penalty_poly;
+
+/* Problem description (Sec. 2.1).  The coarsest mesh T_0 is the tensor grid
+ * with ncells[t] cells of widths widths[t][0..ncells[t]-1] in direction t
+ * (lower corner at the origin); level l bisects T_0 l times. */
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int degree;               /* k, 1 <= k <= 7 */
+  int ncells[3];            /* cells per direction on level 0 (ncells[2] ignored for dim 2) */
+  const double* widths[3];  /* HOST arrays, copied during tpss_create */
+  int nlevels;              /* >= 1; level nlevels-1 is the finest */
+  double gamma_hat;         /* penalty prefactor, 1 on Cartesian meshes (eq. penalty) */
+  int penalty_poly;         /* tpss_penalty_poly */
+} tpss_problem_desc;
+
+typedef struct tpss_ctx tpss_ctx;
+typedef struct tpss_patches tpss_patches;
+
+/* Create a context: copies the description, runs the 1D setup kernels (Gauss-
+ * Lobatto basis, Gauss rules, per-direction 1D mass/stiffness/face matrices of
+ * eq. 1Dstiffnessmass - eq. 1Dsipg for every level) on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream) and allocates per-level
+ * scratch.  Synchronizes the stream before returning. */
+tpss_status tpss_create(const tpss_problem_desc* desc, void* cuda_stream, tpss_ctx** out);
+tpss_status tpss_destroy(tpss_ctx* ctx);
+
+/* Number of DoFs and cells per direction of a level (host values). */
+tpss_status tpss_level_info(const tpss_ctx* ctx, int level, int64_t* ndofs, int ncells[3]);
+
+/* Thread-local message describing the last error of this thread ("" if none). */
+const char* tpss_last_error(void);
+
+/* ---------------------------------------------------------------- setup --
+ * Fast diagonalization setup of the local solvers of one level (Sec. 3.2):
+ * for every direction t and every subdomain position along t, the 1D matrices
+ * A^(t), M^(t) of eq. 1Dsipg (cells, n = k+1) or eq. 1DsipgVP (vertex patches,
+ * n = 2(k+1)) and the generalized eigenproblem of eq. generalizedEVP,
+ * Z^T A Z = Lambda, Z^T M Z = I, solved in FP64 on the device (Cholesky of M,
+ * cyclic Jacobi on L^{-1} A L^{-T}).  Also builds the colorings (additive:
+ * none for cells, 2^d parity colors for vertex patches; multiplicative:
+ * red-black for cells, 2^(d+1) colors for vertex patches, Sec. 2.3) and the
+ * per-subdomain table 1/(lambda_i + lambda_j + lambda_l) of eq. fastinverse.
+ * Level must be >= 0; vertex patches need >= 2 cells per direction.
+ * Returns TPSS_ENUMERIC if some 1D problem is not positive definite.
+ * Synchronizes the stream. */
+tpss_status tpss_setup_patches(tpss_ctx* ctx, int level, int kind, int precision,
+                               tpss_patches** out);
+tpss_status tpss_patches_destroy(tpss_patches* patches);
+
+/* Host-side description of a patch set: 1D size n, subdomain positions per
+ * direction, number of subdomains, number of multiplicative colors. */
+tpss_status tpss_patches_info(const tpss_patches* patches, int* n, int npos[3],
+                              int64_t* nsub, int* ncolors_mult);
+
+/* Copy the FP64 1D data of direction t at position pos to HOST arrays (each
+ * may be NULL): A and M (n*n, row-major, test index first), Z (n*n row-major,
+ * column j = eigenvector j) and lambda (n).  Synchronizes the stream. */
+tpss_status tpss_patches_eigendata(const tpss_patches* patches, int t, int pos,
+                                   double* A, double* M, double* Z, double* lambda);
+
+/* Set the number of colors of the multiplicative vertex-patch sweep: 0 or
+ * 2^(d+1) = the face-conflict-free coloring of Sec. 2.3 (default), or 2^d =
+ * the parity coloring only (same-color patches then share faces, so the sweep
+ * is not eq. multschwarz1 in any order). */
+tpss_status tpss_patches_set_mult_colors(tpss_patches* patches, int ncolors);
+
+/* ------------------------------------------------------------- smoothers --
+ * Additive Schwarz smoother, Alg. 2 with the damping of eq. additiveschwarz:
+ *   r = b - A x;   x <- x + omega * sum_j R_j^T A_j^{-1} R_j r
+ * with A_j^{-1} = Z Lambda^{-1} Z^T applied by sum factorization
+ * (eq. fastinverse, eq. eigenvectormatvec).  If x_is_zero != 0 the input
+ * values of x are ignored, r = b and no operator is applied.  b and x hold
+ * nrhs vectors of ndofs(level) each.  Overlapping vertex patches are
+ * processed color by color, so the result is deterministic. */
+tpss_status tpss_smooth_additive(tpss_patches* patches, double omega, int nrhs,
+                                 const double* b, double* x, int x_is_zero);
+tpss_status tpss_smooth_additive_f32(tpss_patches* patches, float omega, int nrhs,
+                                     const float* b, float* x, int x_is_zero);
+
+/* Multiplicative Schwarz smoother, Alg. 3 with eq. coloredschwarz: for each
+ * color c (in increasing order, or decreasing if reverse_colors != 0):
+ *   r = b - A x;   x <- x + omega * sum_{j in J_c} R_j^T A_j^{-1} R_j r. */
+tpss_status tpss_smooth_multiplicative(tpss_patches* patches, double omega, int reverse_colors,
+                                       int nrhs, const double* b, double* x);
+
+/* ------------------------------------------------------------- operators --
+ * Matrix-free SIPG operator Au = A_l u (eq. bfsipg) by sum factorization over
+ * the Kronecker form of Sec. 3.2 (cell mass and stiffness matrices plus the
+ * rank-2 face couplings between neighbouring cells).  u and Au must not alias. */
+tpss_status tpss_apply_operator(tpss_ctx* ctx, int level, int nrhs, const double* u, double* Au);
+tpss_status tpss_apply_operator_f32(tpss_ctx* ctx, int level, int nrhs, const float* u, float* Au);
+
+/* r = b - A_l x (r may alias b, not x). */
+tpss_status tpss_residual(tpss_ctx* ctx, int level, int nrhs, const double* b, const double* x,
+                          double* r);
+
+/* Level transfers of Sec. 2.2 between `fine_level` and fine_level-1:
+ * prolongation = embedding of V_{l-1} in V_l (fine += I^up coarse) and
+ * restriction = its transpose (coarse = I^down fine). */
+tpss_status tpss_prolongate_add(tpss_ctx* ctx, int fine_level, int nrhs, const double* coarse,
+                                double* fine);
+tpss_status tpss_restrict(tpss_ctx* ctx, int fine_level, int nrhs, const double* fine,
+                          double* coarse);
+
+/* Right-hand side of eq. sipg on a level, integrated with k+2 Gauss points per
+ * direction.  kind 0: f = d pi^2 prod_t sin(pi x_t), g = 0 (exact solution
+ * prod_t sin(pi x_t) on the unit cube); kind 1: the three-Gaussian solution of
+ * Sec. 2.4 read as u = sum_i exp(-|x - x_i|^2 / sigma^2) / (sqrt(2 pi) sigma),
+ * sigma = 1/3, with f = -Laplace(u) and g = u. */
+tpss_status tpss_assemble_rhs(tpss_ctx* ctx, int level, int kind, double* b);
+
+/* ------------------------------------------------------------- multigrid --
+ * Smoother choice for the V-cycle of Alg. 1 (m_pre = m_post = 1). */
+typedef enum { TPSS_ACS = 0, TPSS_AVS = 1, TPSS_MCS = 2, TPSS_MVS = 3 } tpss_smoother_kind;
+
+typedef struct {
+  int smoother;        /* tpss_smoother_kind */
+  double omega;        /* relaxation parameter of eq. additiveschwarz / eq. coloredschwarz */
+  int precision;       /* tpss_precision of the V-cycle (FP64, or FP32/TF32/BF16: the
+                          whole V-cycle then runs in FP32 with these contractions) */
+  int mult_colors;     /* 0 = default (2^(d+1) for MVS), else as tpss_patches_set_mult_colors */
+  int flexible_cg;     /* 1: Polak-Ribiere beta in tpss_pcg_solve (use with inexact V-cycles) */
+} tpss_mg_params;
+
+/* Build smoothers on levels 1..L and the coarse solver on level 0 (the level 0
+ * matrix assembled by applying the operator to unit vectors and inverted by
+ * Gauss-Jordan elimination on the device; this replaces the paper's
+ * Chebyshev coarse iteration by an exact solve).  Synchronizes the stream. */
+tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params);
+
+/* One V-cycle of Alg. 1 on the finest level with x_L = 0 on entry:
+ * x = MG_L(0, b).  b and x are finest-level FP64 vectors (one right-hand side). */
+tpss_status tpss_vcycle(tpss_ctx* ctx, const double* b, double* x);
+
+/* Exact coarse solve x = A_0^{-1} b on level 0 (after tpss_mg_setup). */
+tpss_status tpss_coarse_solve(tpss_ctx* ctx, const double* b, double* x);
+
+/* Preconditioned CG (Sec. 2.4) on the finest level with one V-cycle as
+ * preconditioner, from x = 0, stopped at ||r_k||_2 <= rtol ||r_0||_2 or after
+ * maxit iterations.  On return *iters and *rel_res are host values; if
+ * res_hist != NULL, the residual norms ||r_0||..||r_iters|| are written to it
+ * (host array of at least maxit+1 doubles).  Synchronizes the stream once per
+ * iteration to test convergence.  Returns TPSS_ENOTCONV at maxit and
+ * TPSS_EBREAKDOWN on a NaN/Inf or non-positive curvature. */
+tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
+                           int* iters, double* rel_res, double* res_hist);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPSS_H */

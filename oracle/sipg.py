@@ -40,6 +40,15 @@ from .mesh import dofs_per_cell, local_multi_indices
 SQRT2 = np.sqrt(2.0)
 
 
+def _wsum(W, trial, test):
+    """B[j, i] = sum_q W[q] sum_r trial[q, i, r] test[q, j, r]: the quadrature
+    sum of a bilinear integrand (test index first), as matrix products."""
+    out = 0.0
+    for r in range(trial.shape[2]):
+        out = out + (test[:, :, r].T * W) @ trial[:, :, r]
+    return out
+
+
 def penalty_factor(k, penalty_poly):
     if penalty_poly == "paper":
         return float(k * (k + 1))
@@ -74,23 +83,24 @@ class SIPG:
     def _cell_tables(self, h):
         """Values Phi[Q, I], gradients G[Q, I, t] and weights W[Q] of the
         d-dimensional Gauss rule on a cell with widths h (physical gradients:
-        d/dx_t = (1/h_t) d/dxhat_t)."""
-        d, n, nq = self.d, self.k + 1, len(self.qx)
-        qmulti = list(itertools.product(range(nq), repeat=d))
-        Phi = np.ones((len(qmulti), self.nloc))
-        G = np.ones((len(qmulti), self.nloc, d))
-        W = np.ones(len(qmulti))
-        for Q, qm in enumerate(qmulti):
+        d/dx_t = (1/h_t) d/dxhat_t).  Each entry is the product over the
+        directions of 1D values, evaluated point by point (vectorized over the
+        points Q and basis functions I)."""
+        d, nq = self.d, len(self.qx)
+        qm = np.array(list(itertools.product(range(nq), repeat=d)))   # [Q, d]
+        im = np.array(self.multi)                                     # [I, d]
+        vals = [self.V[np.ix_(qm[:, t], im[:, t])] for t in range(d)]  # [Q, I] per direction
+        ders = [self.D[np.ix_(qm[:, t], im[:, t])] / h[t] for t in range(d)]
+        Phi = np.ones((len(qm), len(im)))
+        for t in range(d):
+            Phi = Phi * vals[t]
+        G = np.ones((len(qm), len(im), d))
+        for s in range(d):
             for t in range(d):
-                W[Q] *= self.qw[qm[t]] * h[t]
-            for I, im in enumerate(self.multi):
-                for t in range(d):
-                    Phi[Q, I] *= self.V[qm[t], im[t]]
-                    for s in range(d):
-                        if s == t:
-                            G[Q, I, s] *= self.D[qm[t], im[t]] / h[t]
-                        else:
-                            G[Q, I, s] *= self.V[qm[t], im[t]]
+                G[:, :, s] *= ders[t] if t == s else vals[t]
+        W = np.ones(len(qm))
+        for t in range(d):
+            W = W * self.qw[qm[:, t]] * h[t]
         return Phi, G, W
 
     def _face_tables(self, h, t, side):
@@ -99,23 +109,28 @@ class SIPG:
         of the (d-1)-dimensional Gauss rule over the face."""
         d, nq = self.d, len(self.qx)
         others = [s for s in range(d) if s != t]
-        qmulti = list(itertools.product(range(nq), repeat=d - 1))
-        P = np.ones((len(qmulti), self.nloc))
-        G = np.ones((len(qmulti), self.nloc, d))
-        W = np.ones(len(qmulti))
-        for Q, qm in enumerate(qmulti):
-            for a, s in enumerate(others):
-                W[Q] *= self.qw[qm[a]] * h[s]
-            for I, im in enumerate(self.multi):
-                for s in range(d):
-                    if s == t:
-                        val, der = self.Vend[side, im[s]], self.Dend[side, im[s]] / h[s]
-                    else:
-                        a = others.index(s)
-                        val, der = self.V[qm[a], im[s]], self.D[qm[a], im[s]] / h[s]
-                    P[Q, I] *= val
-                    for r in range(d):
-                        G[Q, I, r] *= der if r == s else val
+        qm = np.array(list(itertools.product(range(nq), repeat=d - 1))).reshape(-1, d - 1)  # [Q, d-1]
+        im = np.array(self.multi)
+        nQ = len(qm)
+        vals, ders = [], []
+        for s in range(d):
+            if s == t:
+                vals.append(np.tile(self.Vend[side, im[:, s]], (nQ, 1)))
+                ders.append(np.tile(self.Dend[side, im[:, s]] / h[s], (nQ, 1)))
+            else:
+                a = others.index(s)
+                vals.append(self.V[np.ix_(qm[:, a], im[:, s])])
+                ders.append(self.D[np.ix_(qm[:, a], im[:, s])] / h[s])
+        P = np.ones((nQ, len(im)))
+        for s in range(d):
+            P = P * vals[s]
+        G = np.ones((nQ, len(im), d))
+        for r in range(d):
+            for s in range(d):
+                G[:, :, r] *= ders[s] if s == r else vals[s]
+        W = np.ones(nQ)
+        for a, s in enumerate(others):
+            W = W * self.qw[qm[:, a]] * h[s]
         return P, G, W
 
     # ---------------------------------------------------------- local blocks
@@ -124,7 +139,7 @@ class SIPG:
         key = tuple(h)
         if key not in self._cell_cache:
             _, G, W = self._cell_tables(h)
-            self._cell_cache[key] = np.einsum("q,qis,qjs->ji", W, G, G)
+            self._cell_cache[key] = _wsum(W, G, G)
         return self._cell_cache[key]
 
     def interior_face_blocks(self, hL, hR, t):
@@ -152,9 +167,7 @@ class SIPG:
                 vn = val[S][:, :, None] * normal[S][None, None, :] / SQRT2   # [Q, iota, r]
                 gu = grad[T] / SQRT2
                 gv = grad[S] / SQRT2
-                B = (gam * np.einsum("q,qir,qjr->ji", W, un, vn)
-                     - np.einsum("q,qir,qjr->ji", W, gu, vn)
-                     - np.einsum("q,qir,qjr->ji", W, un, gv))
+                B = gam * _wsum(W, un, vn) - _wsum(W, gu, vn) - _wsum(W, un, gv)
                 blocks[(S, T)] = B
         self._face_cache[key] = blocks
         return blocks
@@ -171,9 +184,7 @@ class SIPG:
         n = np.zeros(self.d)
         n[t] = 1.0 if side == 1 else -1.0
         un = P[:, :, None] * n[None, None, :]
-        B = (gam * np.einsum("q,qir,qjr->ji", W, un, un)
-             - np.einsum("q,qir,qjr->ji", W, G, un)
-             - np.einsum("q,qir,qjr->ji", W, un, G))
+        B = gam * _wsum(W, un, un) - _wsum(W, G, un) - _wsum(W, un, G)
         self._face_cache[key] = B
         return B
 

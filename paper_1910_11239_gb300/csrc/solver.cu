@@ -1,0 +1,590 @@
+// Multigrid V-cycle (Alg. 1), exact coarse solve, preconditioned CG (Sec. 2.4)
+// and the right-hand side of eq. sipg.
+//
+// Coarse level: the level-0 matrix is assembled by applying the matrix-free
+// operator to the unit vectors (batched as right-hand sides) and inverted in
+// place by Gauss-Jordan elimination without pivoting (the matrix is SPD);
+// the coarse solve is then one dense matrix-vector product.  The paper uses a
+// Chebyshev iteration preconditioned by the additive cell smoother there; an
+// exact solve is the reading taken here.
+//
+// CG: all scalars (alpha, beta, inner products) stay on the device; partial
+// sums per block are reduced by a second single-block kernel in a fixed
+// order, so results are deterministic.  The host reads ||r||^2 and p^T A p
+// once per iteration to test convergence and breakdown.
+#include <algorithm>
+#include <cmath>
+
+#include "tpss_internal.cuh"
+
+namespace tpss {
+
+template <typename T>
+tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T* x, int x_is_zero);
+template <typename T>
+tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int nrhs, const T* b, T* x);
+
+struct MGState {
+  tpss_mg_params params{};
+  int mixed = 0;                         // 1: V-cycle in FP32
+  std::vector<tpss_patches*> patches;    // per level, [0] unused
+  int64_t n0 = 0;
+  double* coarse_inv = nullptr;          // [n0][n0]
+  std::vector<double*> b64, x64;         // per level right-hand side / solution
+  std::vector<float*> b32, x32;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr;
+  double* gj_tmp = nullptr;              // 2 n0
+};
+
+void destroy_mg(tpss_ctx* ctx) {
+  MGState* mg = ctx->mg;
+  if (!mg) return;
+  for (auto* P : mg->patches)
+    if (P) tpss_patches_destroy(P);
+  dfree(mg->coarse_inv);
+  dfree(mg->gj_tmp);
+  for (auto* v : mg->b64) dfree(v);
+  for (auto* v : mg->x64) dfree(v);
+  for (auto* v : mg->b32) dfree(v);
+  for (auto* v : mg->x32) dfree(v);
+  dfree(mg->r); dfree(mg->z); dfree(mg->p); dfree(mg->q); dfree(mg->zold);
+  delete mg;
+  ctx->mg = nullptr;
+}
+
+// ------------------------------------------------------------- reductions
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocksMax = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double ws[32];
+  v = warp_sum(v);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) ws[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) / 32;
+  v = threadIdx.x < nw ? ws[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+
+__global__ void dot_partial_kernel(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                                   double* __restrict__ partials) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void dot_final_kernel(const double* __restrict__ partials, int nb, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partials[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+static tpss_status dot(tpss_ctx* ctx, const double* x, const double* y, int64_t n, double* out) {
+  int nb = (int)std::min<int64_t>((n + kRedThreads * 4 - 1) / (kRedThreads * 4), kRedBlocksMax);
+  if (nb < 1) nb = 1;
+  dot_partial_kernel<<<nb, kRedThreads, 0, ctx->stream>>>(x, y, n, ctx->d_partials);
+  dot_final_kernel<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d_partials, nb, out);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+// scalars: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 r.zold, 5 rr0
+__global__ void cg_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                             const double* __restrict__ q, int64_t n, const double* __restrict__ s) {
+  const double alpha = s[0] / s[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+
+__global__ void cg_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                            const double* __restrict__ s, int flexible) {
+  const double beta = (s[3] - (flexible ? s[4] : 0.0)) / s[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void cg_shift_kernel(double* s) { s[0] = s[3]; }
+
+template <typename S, typename D>
+__global__ void copy_convert_kernel(const S* __restrict__ a, D* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = static_cast<D>(a[i]);
+}
+
+static int grid_for(tpss_ctx* ctx, int64_t n) {
+  int64_t b = (n + 255) / 256;
+  const int64_t cap = (int64_t)ctx->num_sms * 8;
+  return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// ----------------------------------------------------------- coarse solve
+__global__ void unit_vectors_kernel(double* __restrict__ E, int64_t n, int64_t c0, int ncols) {
+  const int64_t total = n * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e / n, row = e % n;
+    E[e] = (row == c0 + col) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void gj_save_kernel(const double* __restrict__ A, int64_t n, int64_t j, double* __restrict__ tmp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    tmp[i] = A[i * n + j];       // column j
+    tmp[n + i] = A[j * n + i];   // row j
+  }
+}
+
+__global__ void gj_update_kernel(double* __restrict__ A, int64_t n, int64_t j, const double* __restrict__ tmp) {
+  const double p = tmp[j];
+  const double ip = 1.0 / p;
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, l = e % n;
+    double v;
+    if (i == j && l == j) v = ip;
+    else if (i == j) v = tmp[n + l] * ip;
+    else if (l == j) v = -tmp[i] * ip;
+    else v = A[e] - tmp[i] * tmp[n + l] * ip;
+    A[e] = v;
+  }
+}
+
+// y = Ainv b, one warp per row, FP64 accumulation; S/D input/output types.
+template <typename S, typename D>
+__global__ void dense_mv_kernel(const double* __restrict__ A, const S* __restrict__ b, D* __restrict__ y, int64_t n) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int64_t c = lane; c < n; c += 32) s = fma(A[row * n + c], (double)b[c], s);
+  s = warp_sum(s);
+  if (lane == 0) y[row] = (D)s;
+}
+
+static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
+  const Level& L0 = ctx->levels[0];
+  const int64_t n = L0.ndofs;
+  mg->n0 = n;
+  TPSS_REQUIRE(n <= 16384, "tpss_mg_setup: coarse level too large for the dense coarse solver");
+  TPSS_TRY(dalloc_t(&mg->coarse_inv, (size_t)n * n));
+  TPSS_TRY(dalloc_t(&mg->gj_tmp, (size_t)2 * n));
+  // assemble A_0 column blocks: A_0 e_c for c in [c0, c0 + nc)
+  const int chunk = (int)std::min<int64_t>(n, 256);
+  double* E = nullptr;
+  TPSS_TRY(dalloc_t(&E, (size_t)n * chunk));
+  for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+    const int nc = (int)std::min<int64_t>(chunk, n - c0);
+    unit_vectors_kernel<<<grid_for(ctx, n * nc), 256, 0, ctx->stream>>>(E, n, c0, nc);
+    tpss_status st = apply_operator_t<double>(ctx, 0, nc, E, mg->coarse_inv + c0 * n, nullptr);
+    if (st != TPSS_OK) {
+      dfree(E);
+      return st;
+    }
+  }
+  // columns were written as rows (A_0 symmetric): coarse_inv holds A_0
+  cudaStreamSynchronize(ctx->stream);
+  dfree(E);
+  for (int64_t j = 0; j < n; ++j) {
+    gj_save_kernel<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(mg->coarse_inv, n, j, mg->gj_tmp);
+    gj_update_kernel<<<grid_for(ctx, n * n), 256, 0, ctx->stream>>>(mg->coarse_inv, n, j, mg->gj_tmp);
+  }
+  TPSS_CHECK_LAUNCH();
+  TPSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TPSS_OK;
+}
+
+template <typename S, typename D>
+static tpss_status coarse_apply(tpss_ctx* ctx, MGState* mg, const S* b, D* x) {
+  const int64_t n = mg->n0;
+  const int threads = 256;
+  const int64_t blocks = (n * 32 + threads - 1) / threads;
+  dense_mv_kernel<S, D><<<(unsigned)blocks, threads, 0, ctx->stream>>>(mg->coarse_inv, b, x, n);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+// ---------------------------------------------------------------- V-cycle
+template <typename T>
+static std::vector<T*>& bvec(MGState* mg);
+template <>
+std::vector<double*>& bvec<double>(MGState* mg) { return mg->b64; }
+template <>
+std::vector<float*>& bvec<float>(MGState* mg) { return mg->b32; }
+template <typename T>
+static std::vector<T*>& xvec(MGState* mg);
+template <>
+std::vector<double*>& xvec<double>(MGState* mg) { return mg->x64; }
+template <>
+std::vector<float*>& xvec<float>(MGState* mg) { return mg->x32; }
+template <typename T>
+static T* resid(Level& L);
+template <>
+double* resid<double>(Level& L) { return L.t64[4]; }
+template <>
+float* resid<float>(Level& L) { return L.t32[4]; }
+
+template <typename T>
+static tpss_status smooth(tpss_ctx* ctx, MGState* mg, int l, const T* b, T* x, bool x_zero, bool post) {
+  tpss_patches* P = mg->patches[l];
+  const int kind = mg->params.smoother;
+  const T omega = (T)mg->params.omega;
+  if (kind == TPSS_ACS || kind == TPSS_AVS) return smooth_additive_t<T>(P, omega, 1, b, x, x_zero ? 1 : 0);
+  if (x_zero) TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)ctx->levels[l].ndofs * sizeof(T), ctx->stream));
+  return smooth_multiplicative_t<T>(P, omega, post ? 1 : 0, 1, b, x);
+}
+
+// x_l = MG_l(0, b_l) (Alg. 1); b, x are level-l vectors.
+template <typename T>
+static tpss_status vcycle_t(tpss_ctx* ctx, MGState* mg, int l, const T* b, T* x) {
+  if (l == 0) return coarse_apply<T, T>(ctx, mg, b, x);
+  Level& L = ctx->levels[l];
+  TPSS_TRY(smooth<T>(ctx, mg, l, b, x, true, false));                       // pre-smoothing
+  T* r = resid<T>(L);
+  TPSS_TRY(apply_operator_t<T>(ctx, l, 1, x, r, b));                        // r = b - A x
+  T* bc = bvec<T>(mg)[l - 1];
+  T* xc = xvec<T>(mg)[l - 1];
+  TPSS_TRY(restrict_t<T>(ctx, l, 1, r, bc));                                 // restriction
+  TPSS_TRY(vcycle_t<T>(ctx, mg, l - 1, bc, xc));                             // recursion
+  TPSS_TRY(prolongate_add_t<T>(ctx, l, 1, xc, x));                          // prolongation
+  TPSS_TRY(smooth<T>(ctx, mg, l, b, x, false, true));                       // post-smoothing
+  return TPSS_OK;
+}
+
+// z = B r on the finest level (FP64 in and out; FP32 inside when mixed)
+static tpss_status precondition(tpss_ctx* ctx, MGState* mg, const double* r, double* z) {
+  const int L = ctx->nlevels - 1;
+  const int64_t n = ctx->levels[L].ndofs;
+  if (!mg->mixed) return vcycle_t<double>(ctx, mg, L, r, z);
+  float* bf = mg->b32[L];
+  float* xf = mg->x32[L];
+  copy_convert_kernel<double, float><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(r, bf, n);
+  TPSS_TRY(vcycle_t<float>(ctx, mg, L, bf, xf));
+  copy_convert_kernel<float, double><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(xf, z, n);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+// ------------------------------------------------------------ right-hand side
+// kind 0: f = d pi^2 prod sin(pi x_t), g = 0;  kind 1: Gaussian bells (Sec. 2.4)
+struct RhsArgs {
+  const Basis1D* B;
+  const double* w[3];
+  int nc[3];
+  int dim;
+  int kind;
+  double gpk;   // gamma_hat * P(k)
+  double* b;
+};
+
+__device__ double bells_u(const double* x, int dim, double* lap) {
+  // u = 1/(sqrt(2 pi) sigma) sum_i exp(-|x - x_i|^2 / sigma^2); lap = Laplace(u)
+  const double sigma = 1.0 / 3.0, s2 = sigma * sigma;
+  const double c = 1.0 / (sqrt(2.0 * 3.14159265358979323846) * sigma);
+  const double src[3][3] = {{0.0, 0.0, 0.0}, {0.25, 0.85, 0.85}, {0.6, 0.4, 0.4}};
+  double u = 0.0, l = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double r2 = 0.0;
+    for (int t = 0; t < dim; ++t) r2 += (x[t] - src[i][t]) * (x[t] - src[i][t]);
+    const double e = exp(-r2 / s2);
+    u += e;
+    l += e * (4.0 * r2 / (s2 * s2) - 2.0 * dim / s2);
+  }
+  *lap = c * l;
+  return c * u;
+}
+
+__global__ void rhs_kernel(RhsArgs a) {
+  extern __shared__ double sm[];
+  const Basis1D* B = a.B;
+  const int n1 = B->n1, nq = B->nq_rhs, dim = a.dim;
+  const int64_t cell = blockIdx.x;
+  int cm[3] = {0, 0, 0};
+  int64_t rest = cell;
+  for (int t = 0; t < dim; ++t) {
+    cm[t] = (int)(rest % a.nc[t]);
+    rest /= a.nc[t];
+  }
+  double lo[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  for (int t = 0; t < dim; ++t) {
+    double s = 0.0;
+    for (int c = 0; c < cm[t]; ++c) s += a.w[t][c];
+    lo[t] = s;
+    h[t] = a.w[t][cm[t]];
+  }
+  const int nqd = dim == 3 ? nq * nq * nq : nq * nq;
+  const int nloc = dim == 3 ? n1 * n1 * n1 : n1 * n1;
+  double* F = sm;             // nq^d
+  double* G = F + nqd;        // workspace nq^d
+  double* H = G + nqd;
+  double jac = 1.0;
+  for (int t = 0; t < dim; ++t) jac *= h[t];
+  for (int e = threadIdx.x; e < nqd; e += blockDim.x) {
+    const int q0 = e % nq, q1 = (e / nq) % nq, q2 = dim == 3 ? e / (nq * nq) : 0;
+    const int qq[3] = {q0, q1, q2};
+    double x[3] = {0, 0, 0}, wt = jac;
+    for (int t = 0; t < dim; ++t) {
+      x[t] = lo[t] + h[t] * B->xr[qq[t]];
+      wt *= B->wr[qq[t]];
+    }
+    double f;
+    if (a.kind == 0) {
+      const double pi = 3.14159265358979323846;
+      f = dim * pi * pi;
+      for (int t = 0; t < dim; ++t) f *= sin(pi * x[t]);
+    } else {
+      double lap;
+      bells_u(x, dim, &lap);
+      f = -lap;
+    }
+    F[e] = wt * f;
+  }
+  __syncthreads();
+  // sum factorization: contract q0 -> i0, q1 -> i1, (q2 -> i2) with Vr[q][i]
+  const double* Vr = B->Vr;
+  if (dim == 3) {
+    for (int e = threadIdx.x; e < n1 * nq * nq; e += blockDim.x) {
+      const int i0 = e % n1, q1 = (e / n1) % nq, q2 = e / (n1 * nq);
+      double s = 0.0;
+      for (int q0 = 0; q0 < nq; ++q0) s += Vr[q0 * n1 + i0] * F[q0 + nq * (q1 + nq * q2)];
+      G[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n1 * n1 * nq; e += blockDim.x) {
+      const int i0 = e % n1, i1 = (e / n1) % n1, q2 = e / (n1 * n1);
+      double s = 0.0;
+      for (int q1 = 0; q1 < nq; ++q1) s += Vr[q1 * n1 + i1] * G[i0 + n1 * (q1 + nq * q2)];
+      H[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+      const int i2 = e / (n1 * n1);
+      double s = 0.0;
+      for (int q2 = 0; q2 < nq; ++q2) s += Vr[q2 * n1 + i2] * H[(e % (n1 * n1)) + n1 * n1 * q2];
+      G[e] = s;
+    }
+  } else {
+    for (int e = threadIdx.x; e < n1 * nq; e += blockDim.x) {
+      const int i0 = e % n1, q1 = e / n1;
+      double s = 0.0;
+      for (int q0 = 0; q0 < nq; ++q0) s += Vr[q0 * n1 + i0] * F[q0 + nq * q1];
+      G[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+      const int i0 = e % n1, i1 = e / n1;
+      double s = 0.0;
+      for (int q1 = 0; q1 < nq; ++q1) s += Vr[q1 * n1 + i1] * G[i0 + n1 * q1];
+      H[e] = s;
+    }
+  }
+  __syncthreads();
+  const double* res = dim == 3 ? G : H;
+  // boundary terms int (gamma g v - g n.grad v) for kind 1
+  for (int e = threadIdx.x; e < nloc; e += blockDim.x) {
+    double v = res[e];
+    if (a.kind == 1) {
+      const int ii[3] = {e % n1, (e / n1) % n1, dim == 3 ? e / (n1 * n1) : 0};
+      for (int t = 0; t < dim; ++t)
+        for (int side = 0; side < 2; ++side) {
+          const bool bnd = side == 0 ? cm[t] == 0 : cm[t] == a.nc[t] - 1;
+          if (!bnd) continue;
+          const double gam = a.gpk * 2.0 / h[t];
+          const double nsign = side == 1 ? 1.0 : -1.0;
+          const double phit = (ii[t] == (side == 1 ? n1 - 1 : 0)) ? 1.0 : 0.0;
+          const double dphit = (side == 1 ? B->d1[ii[t]] : B->d0[ii[t]]) / h[t];
+          const int o1 = t == 0 ? 1 : 0, o2 = t == 2 ? 1 : 2;
+          const int nq2 = dim == 3 ? nq : 1;
+          for (int qa = 0; qa < nq; ++qa)
+            for (int qb = 0; qb < nq2; ++qb) {
+              double x[3];
+              x[t] = lo[t] + h[t] * side;
+              x[o1] = lo[o1] + h[o1] * B->xr[qa];
+              double wt = B->wr[qa] * h[o1];
+              double other = Vr[qa * n1 + ii[o1]];
+              if (dim == 3) {
+                x[o2] = lo[o2] + h[o2] * B->xr[qb];
+                wt *= B->wr[qb] * h[o2];
+                other *= Vr[qb * n1 + ii[o2]];
+              }
+              double lap;
+              const double g = bells_u(x, dim, &lap);
+              v += wt * g * other * (gam * phit - nsign * dphit);
+            }
+        }
+    }
+    a.b[cell * nloc + e] = v;
+  }
+}
+
+}  // namespace tpss
+
+using namespace tpss;
+
+extern "C" tpss_status tpss_assemble_rhs(tpss_ctx* ctx, int level, int kind, double* b) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b, "tpss_assemble_rhs: null argument");
+  TPSS_REQUIRE(level >= 0 && level < ctx->nlevels, "tpss_assemble_rhs: level out of range");
+  TPSS_REQUIRE(kind == 0 || kind == 1, "tpss_assemble_rhs: kind must be 0 or 1");
+  const Level& L = ctx->levels[level];
+  RhsArgs a{};
+  a.B = ctx->d_basis;
+  for (int t = 0; t < 3; ++t) {
+    a.w[t] = L.d_widths[t];
+    a.nc[t] = L.nc[t];
+  }
+  a.dim = ctx->dim;
+  a.kind = kind;
+  a.gpk = ctx->gamma_hat * (ctx->penalty_poly == TPSS_PENALTY_KP1SQ ? (double)(ctx->n1 * ctx->n1)
+                                                                    : (double)(ctx->k * ctx->n1));
+  a.b = b;
+  const int nq = ctx->n1 + 1;
+  const size_t smem = 3 * (size_t)(ctx->dim == 3 ? nq * nq * nq : nq * nq) * sizeof(double);
+  rhs_kernel<<<(unsigned)L.ncells, 128, smem, ctx->stream>>>(a);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params) {
+  clear_error();
+  TPSS_REQUIRE(ctx && params, "tpss_mg_setup: null argument");
+  TPSS_REQUIRE(params->smoother >= TPSS_ACS && params->smoother <= TPSS_MVS, "tpss_mg_setup: unknown smoother");
+  TPSS_REQUIRE(params->precision >= TPSS_FP64 && params->precision <= TPSS_BF16, "tpss_mg_setup: unknown precision");
+  TPSS_REQUIRE(params->omega > 0.0 && std::isfinite(params->omega), "tpss_mg_setup: omega must be positive");
+  const bool vertex = params->smoother == TPSS_AVS || params->smoother == TPSS_MVS;
+  if (vertex)
+    for (int l = 1; l < ctx->nlevels; ++l)
+      for (int t = 0; t < ctx->dim; ++t)
+        TPSS_REQUIRE(ctx->levels[l].nc[t] >= 2, "tpss_mg_setup: vertex patches need >= 2 cells per direction");
+  destroy_mg(ctx);
+  MGState* mg = new MGState();
+  ctx->mg = mg;
+  mg->params = *params;
+  mg->mixed = params->precision != TPSS_FP64;
+  const int L = ctx->nlevels;
+  mg->patches.assign(L, nullptr);
+  mg->b64.assign(L, nullptr);
+  mg->x64.assign(L, nullptr);
+  mg->b32.assign(L, nullptr);
+  mg->x32.assign(L, nullptr);
+  tpss_status st = TPSS_OK;
+  auto fail = [&](tpss_status s) {
+    destroy_mg(ctx);
+    return s;
+  };
+  for (int l = 1; l < L; ++l) {
+    if ((st = create_patches(ctx, l, vertex ? TPSS_VERTEX_PATCH : TPSS_CELL, params->precision,
+                             &mg->patches[l])) != TPSS_OK)
+      return fail(st);
+    if (params->mult_colors != 0 && (params->smoother == TPSS_MVS || params->smoother == TPSS_MCS))
+      if ((st = tpss_patches_set_mult_colors(mg->patches[l], params->mult_colors)) != TPSS_OK) return fail(st);
+    if ((st = ensure_level_scratch(ctx, l, 1)) != TPSS_OK) return fail(st);
+  }
+  if ((st = ensure_level_scratch(ctx, 0, 1)) != TPSS_OK) return fail(st);
+  for (int l = 0; l < L; ++l) {
+    const size_t n = (size_t)ctx->levels[l].ndofs;
+    if ((st = dalloc_t(&mg->b64[l], n)) != TPSS_OK) return fail(st);
+    if ((st = dalloc_t(&mg->x64[l], n)) != TPSS_OK) return fail(st);
+    if ((st = dalloc_t(&mg->b32[l], n)) != TPSS_OK) return fail(st);
+    if ((st = dalloc_t(&mg->x32[l], n)) != TPSS_OK) return fail(st);
+  }
+  const size_t nf = (size_t)ctx->levels[L - 1].ndofs;
+  if ((st = dalloc_t(&mg->r, nf)) != TPSS_OK) return fail(st);
+  if ((st = dalloc_t(&mg->z, nf)) != TPSS_OK) return fail(st);
+  if ((st = dalloc_t(&mg->p, nf)) != TPSS_OK) return fail(st);
+  if ((st = dalloc_t(&mg->q, nf)) != TPSS_OK) return fail(st);
+  if ((st = dalloc_t(&mg->zold, nf)) != TPSS_OK) return fail(st);
+  if ((st = coarse_setup(ctx, mg)) != TPSS_OK) return fail(st);
+  TPSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TPSS_OK;
+}
+
+extern "C" tpss_status tpss_vcycle(tpss_ctx* ctx, const double* b, double* x) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && x, "tpss_vcycle: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_vcycle: call tpss_mg_setup first");
+  TPSS_REQUIRE(b != x, "tpss_vcycle: b and x must not alias");
+  return precondition(ctx, ctx->mg, b, x);
+}
+
+extern "C" tpss_status tpss_coarse_solve(tpss_ctx* ctx, const double* b, double* x) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && x, "tpss_coarse_solve: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_coarse_solve: call tpss_mg_setup first");
+  TPSS_REQUIRE(b != x, "tpss_coarse_solve: b and x must not alias");
+  return coarse_apply<double, double>(ctx, ctx->mg, b, x);
+}
+
+extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
+                                      int* iters, double* rel_res, double* res_hist) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && x && iters && rel_res, "tpss_pcg_solve: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_pcg_solve: call tpss_mg_setup first");
+  TPSS_REQUIRE(rtol > 0.0 && maxit >= 1, "tpss_pcg_solve: rtol must be > 0 and maxit >= 1");
+  MGState* mg = ctx->mg;
+  const int L = ctx->nlevels - 1;
+  const int64_t n = ctx->levels[L].ndofs;
+  cudaStream_t s = ctx->stream;
+  double* sc = ctx->d_scalars;
+  const int g = grid_for(ctx, n);
+  *iters = 0;
+  *rel_res = 1.0;
+  TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 5));
+  double h[8];
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(h, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+  const double rr0 = h[5];
+  if (res_hist) res_hist[0] = std::sqrt(rr0);
+  if (!std::isfinite(rr0)) {
+    set_error("tpss_pcg_solve: right-hand side is not finite");
+    return TPSS_EBREAKDOWN;
+  }
+  if (rr0 == 0.0) {
+    *rel_res = 0.0;
+    return TPSS_OK;
+  }
+  TPSS_TRY(precondition(ctx, mg, mg->r, mg->z));
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->p, mg->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TPSS_TRY(dot(ctx, mg->r, mg->z, n, sc + 0));
+  const bool flex = mg->params.flexible_cg != 0;
+  for (int it = 1; it <= maxit; ++it) {
+    TPSS_TRY(apply_operator_t<double>(ctx, L, 1, mg->p, mg->q, nullptr));
+    TPSS_TRY(dot(ctx, mg->p, mg->q, n, sc + 1));
+    cg_xr_kernel<<<g, 256, 0, s>>>(x, mg->r, mg->p, mg->q, n, sc);
+    TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 2));
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(h, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    const double rel = std::sqrt(std::max(h[2], 0.0) / rr0);
+    if (res_hist) res_hist[it] = std::sqrt(std::max(h[2], 0.0));
+    *iters = it;
+    *rel_res = rel;
+    if (!std::isfinite(h[1]) || !(h[1] > 0.0) || !std::isfinite(h[2])) {
+      set_error("tpss_pcg_solve: breakdown (p^T A p <= 0 or non-finite residual)");
+      return TPSS_EBREAKDOWN;
+    }
+    if (rel <= rtol) return TPSS_OK;
+    if (flex) std::swap(mg->z, mg->zold);
+    TPSS_TRY(precondition(ctx, mg, mg->r, mg->z));
+    TPSS_TRY(dot(ctx, mg->r, mg->z, n, sc + 3));
+    if (flex) TPSS_TRY(dot(ctx, mg->r, mg->zold, n, sc + 4));
+    cg_p_kernel<<<g, 256, 0, s>>>(mg->p, mg->z, n, sc, flex ? 1 : 0);
+    cg_shift_kernel<<<1, 1, 0, s>>>(sc);
+    TPSS_CHECK_LAUNCH();
+  }
+  set_error("tpss_pcg_solve: not converged within maxit");
+  return TPSS_ENOTCONV;
+}

@@ -1,0 +1,188 @@
+// Internal declarations of the tensor-product Schwarz smoother library.
+//
+// Layout conventions (all device arrays):
+//  * DoF vectors: cell-major (cells lexicographic, x fastest), then the
+//    (k+1)^d nodal values of the cell, x fastest (eq. discFEspace, eq. multiindex).
+//  * 1D matrices: row-major n x n with the TEST index first, so that
+//    (A u)_i = sum_j A[i*n + j] u_j.
+//  * Patch tensors: n^d values, patch-local 1D index p_t = c_t (k+1) + i_t with
+//    c_t in {0,1} the cell of the patch along t (vertex patches, Sec. 3.2) or
+//    p_t = i_t (cells).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tpss.h"
+
+namespace tpss {
+
+constexpr int kMaxDegree = 7;
+constexpr int kMaxN1 = kMaxDegree + 1;    // (k+1)
+constexpr int kMaxNP = 2 * kMaxN1;        // 2(k+1): vertex patch 1D size
+constexpr int kMaxNQ = kMaxN1 + 1;        // Gauss points of the right-hand side rule
+
+// thread-local message for tpss_last_error()
+void set_error(const std::string& msg);
+void clear_error();
+
+#define TPSS_CHECK_CUDA(call)                                                         \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      ::tpss::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+      return TPSS_ECUDA;                                                              \
+    }                                                                                 \
+  } while (0)
+
+#define TPSS_CHECK_LAUNCH()                                                           \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess) {                                                          \
+      ::tpss::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));     \
+      return TPSS_ECUDA;                                                              \
+    }                                                                                 \
+  } while (0)
+
+#define TPSS_REQUIRE(cond, msg)                                                       \
+  do {                                                                                \
+    if (!(cond)) {                                                                    \
+      ::tpss::set_error(msg);                                                         \
+      return TPSS_EINVAL;                                                             \
+    }                                                                                 \
+  } while (0)
+
+#define TPSS_TRY(expr)                                                                \
+  do {                                                                                \
+    tpss_status s_ = (expr);                                                          \
+    if (s_ < 0) return s_;                                                            \
+  } while (0)
+
+// 1D reference data on [0,1], computed on the device by setup_basis_kernel.
+struct Basis1D {
+  int k, n1, nq_rhs;
+  double nodes[kMaxN1];                 // Gauss-Lobatto points
+  double xq[kMaxN1], wq[kMaxN1];        // (k+1)-point Gauss rule
+  double xr[kMaxNQ], wr[kMaxNQ];        // (k+2)-point Gauss rule (right-hand side)
+  double Vr[kMaxNQ * kMaxN1];           // Vr[q*n1+i] = phi_i(xr_q)
+  double d0[kMaxN1], d1[kMaxN1];        // phi_i'(0), phi_i'(1)
+  double Mhat[kMaxN1 * kMaxN1];         // sum_q wq phi_i phi_j
+  double Lhat[kMaxN1 * kMaxN1];         // sum_q wq phi_i' phi_j'
+  double Pc[2][kMaxN1 * kMaxN1];        // Pc[s][i*n1+j] = phi_j((x_i + s)/2)
+  int status;                           // 0 ok, else Newton failed to converge
+};
+
+// Number of face-coupling coefficients stored per cell position:
+// {cR0, cR1, cRd, cL0, cL1, cLd} (see operator.cu for their meaning).
+constexpr int kFaceCoef = 6;
+
+// Per-level 1D operator data for one scalar type.
+template <typename T>
+struct LevelOps {
+  T* M[3] = {nullptr, nullptr, nullptr};     // [nc][n1*n1]   M_t(c) = h_c Mhat
+  T* A[3] = {nullptr, nullptr, nullptr};     // [nc][n1*n1]   A_t(c) of eq. 1Dsipg
+  T* F[3] = {nullptr, nullptr, nullptr};     // [nc][kFaceCoef]
+  T* d0 = nullptr;                           // [n1]
+  T* d1 = nullptr;                           // [n1]
+  T* Pc = nullptr;                           // [2][n1*n1]
+  T* Vr = nullptr;                           // unused for float
+};
+
+struct Level {
+  int nc[3] = {1, 1, 1};
+  int64_t ncells = 0;
+  int64_t ndofs = 0;
+  std::vector<double> widths[3];             // host copies
+  double* d_widths[3] = {nullptr, nullptr, nullptr};
+  LevelOps<double> op64;
+  LevelOps<float> op32;
+  // scratch: operator intermediates and residual, nrhs_cap right-hand sides
+  int nrhs_cap = 0;
+  double* t64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  float* t32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+struct MGState;
+
+}  // namespace tpss
+
+struct tpss_ctx {
+  int dim = 0, k = 0, n1 = 0, nloc = 0, nlevels = 0;
+  double gamma_hat = 1.0;
+  int penalty_poly = 0;
+  cudaStream_t stream = nullptr;
+  tpss::Basis1D* d_basis = nullptr;
+  tpss::Basis1D h_basis{};
+  std::vector<tpss::Level> levels;
+  tpss::MGState* mg = nullptr;
+  double* d_scalars = nullptr;               // small device scratch for reductions
+  double* d_partials = nullptr;
+  int num_sms = 0;
+};
+
+struct tpss_patches {
+  tpss_ctx* ctx = nullptr;
+  int level = 0, kind = 0, precision = 0;
+  int n = 0;                       // 1D subdomain size
+  int npos[3] = {1, 1, 1};         // positions per direction
+  int64_t nsub = 0;                // number of subdomains
+  double* d_A[3] = {nullptr, nullptr, nullptr};   // [npos][n*n]
+  double* d_M[3] = {nullptr, nullptr, nullptr};
+  double* d_Z[3] = {nullptr, nullptr, nullptr};
+  double* d_lam[3] = {nullptr, nullptr, nullptr}; // [npos][n]
+  float* d_Z32[3] = {nullptr, nullptr, nullptr};
+  float* d_lam32[3] = {nullptr, nullptr, nullptr};
+  double* d_inv = nullptr;         // [nsub][n^d] 1/(sum of lambdas), FP64 path
+  // colorings: packed positions (p_x | p_y << 10 | p_z << 20) grouped by color
+  int* d_add_list = nullptr;
+  std::vector<int> add_offsets;    // ncolors_add + 1
+  int* d_mul_list = nullptr;
+  std::vector<int> mul_offsets;    // ncolors_mul + 1
+  int mul_colors_default = 0;
+  int* d_mul8_list = nullptr;      // alternative 2^d-color multiplicative list (vertex)
+  std::vector<int> mul8_offsets;
+  int mul_colors_active = 0;
+};
+
+namespace tpss {
+
+inline int pack_pos(int px, int py, int pz) { return px | (py << 10) | (pz << 20); }
+__host__ __device__ inline int unpack_x(int v) { return v & 1023; }
+__host__ __device__ inline int unpack_y(int v) { return (v >> 10) & 1023; }
+__host__ __device__ inline int unpack_z(int v) { return (v >> 20) & 1023; }
+
+// device allocation helpers (return TPSS_ENOMEM with a message)
+tpss_status dalloc(void** p, size_t bytes);
+template <typename T>
+tpss_status dalloc_t(T** p, size_t count) {
+  return dalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+void dfree(void* p);
+
+// ---- operator.cu
+template <typename T>
+tpss_status apply_operator_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out,
+                             const T* rhs_for_residual);
+tpss_status ensure_level_scratch(tpss_ctx* ctx, int level, int nrhs);
+
+// ---- smoother.cu
+template <typename T>
+tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs,
+                       const T* r, T* x, cudaStream_t s);
+
+// ---- transfer.cu
+template <typename T>
+tpss_status prolongate_add_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* coarse, T* fine);
+template <typename T>
+tpss_status restrict_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* fine, T* coarse);
+
+// ---- setup.cu
+tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tpss_patches** out);
+
+// ---- solver.cu
+void destroy_mg(tpss_ctx* ctx);
+
+}  // namespace tpss

@@ -1,0 +1,261 @@
+"""Thin Python binding of the C ABI in include/tpss.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library libtpss.so; this module only
+converts torch tensors to device pointers and checks shapes/dtypes.  If the
+library is missing, importing works but the first call raises -- there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtpss.so")
+
+TPSS_OK, TPSS_ENOTCONV = 0, 1
+STATUS_NAMES = {0: "TPSS_OK", 1: "TPSS_ENOTCONV", -1: "TPSS_EINVAL", -2: "TPSS_ECUDA", -3: "TPSS_ENOMEM",
+                -4: "TPSS_EBREAKDOWN", -5: "TPSS_ETIMEOUT", -6: "TPSS_ENUMERIC"}
+CELL, VERTEX_PATCH = 0, 1
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
+PENALTY_PAPER, PENALTY_KP1SQ = 0, 1
+ACS, AVS, MCS, MVS = 0, 1, 2, 3
+SMOOTHERS = {"ACS": ACS, "AVS": AVS, "MCS": MCS, "MVS": MVS}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+
+
+class TpssError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("ncells", ctypes.c_int * 3),
+                ("widths", ctypes.POINTER(ctypes.c_double) * 3), ("nlevels", ctypes.c_int),
+                ("gamma_hat", ctypes.c_double), ("penalty_poly", ctypes.c_int)]
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
+                ("mult_colors", ctypes.c_int), ("flexible_cg", ctypes.c_int)]
+
+
+_lib = None
+
+# exported symbols and their argument types (c_void_p = device or host pointer)
+_VP, _I, _D, _F, _I64P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "tpss_create": [ctypes.POINTER(ProblemDesc), _VP, ctypes.POINTER(_VP)],
+    "tpss_destroy": [_VP],
+    "tpss_level_info": [_VP, _I, _I64P, ctypes.POINTER(ctypes.c_int)],
+    "tpss_last_error": [],
+    "tpss_setup_patches": [_VP, _I, _I, _I, ctypes.POINTER(_VP)],
+    "tpss_patches_destroy": [_VP],
+    "tpss_patches_info": [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _I64P,
+                          ctypes.POINTER(ctypes.c_int)],
+    "tpss_patches_eigendata": [_VP, _I, _I, _VP, _VP, _VP, _VP],
+    "tpss_patches_set_mult_colors": [_VP, _I],
+    "tpss_smooth_additive": [_VP, _D, _I, _VP, _VP, _I],
+    "tpss_smooth_additive_f32": [_VP, _F, _I, _VP, _VP, _I],
+    "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
+    "tpss_apply_operator": [_VP, _I, _I, _VP, _VP],
+    "tpss_apply_operator_f32": [_VP, _I, _I, _VP, _VP],
+    "tpss_residual": [_VP, _I, _I, _VP, _VP, _VP],
+    "tpss_prolongate_add": [_VP, _I, _I, _VP, _VP],
+    "tpss_restrict": [_VP, _I, _I, _VP, _VP],
+    "tpss_assemble_rhs": [_VP, _I, _I, _VP],
+    "tpss_mg_setup": [_VP, ctypes.POINTER(MGParams)],
+    "tpss_vcycle": [_VP, _VP, _VP],
+    "tpss_coarse_solve": [_VP, _VP, _VP],
+    "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                       _VP],
+}
+
+
+def lib():
+    """Load libtpss.so (built by build_lib.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not found: build it with paper_1910_11239_gb300.build_lib.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name == "tpss_last_error" else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, allow=(TPSS_OK,)):
+    if status not in allow:
+        raise TpssError(status, lib().tpss_last_error().decode())
+    return status
+
+
+def _ptr(t, dtype, numel=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """tpss_create / tpss_destroy and the level-wise operations of a context."""
+
+    def __init__(self, dim, degree, widths, nlevels=1, gamma_hat=1.0, penalty_poly=PENALTY_PAPER, stream=None):
+        self._keep = [(ctypes.c_double * len(w))(*[float(v) for v in w]) for w in widths]
+        desc = ProblemDesc()
+        desc.dim, desc.degree, desc.nlevels = dim, degree, nlevels
+        desc.gamma_hat, desc.penalty_poly = gamma_hat, penalty_poly
+        for t in range(3):
+            desc.ncells[t] = len(widths[t]) if t < dim else 1
+            desc.widths[t] = ctypes.cast(self._keep[t], ctypes.POINTER(ctypes.c_double)) if t < dim else None
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        handle = ctypes.c_void_p()
+        _check(lib().tpss_create(ctypes.byref(desc), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)))
+        self.h = handle
+        self.dim, self.degree, self.nlevels = dim, degree, nlevels
+        self._patches = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            for p in self._patches:
+                p.close()
+            lib().tpss_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_info(self, level):
+        n = ctypes.c_int64()
+        nc = (ctypes.c_int * 3)()
+        _check(lib().tpss_level_info(self.h, level, ctypes.byref(n), nc))
+        return n.value, tuple(nc)
+
+    def ndofs(self, level):
+        return self.level_info(level)[0]
+
+    def setup_patches(self, level, kind, precision=FP64):
+        out = ctypes.c_void_p()
+        _check(lib().tpss_setup_patches(self.h, level, kind, precision, ctypes.byref(out)))
+        p = Patches(self, out, level, kind, precision)
+        self._patches.append(p)
+        return p
+
+    def apply_operator(self, level, u, out, nrhs=1):
+        n = self.ndofs(level) * nrhs
+        if u.dtype == torch.float64:
+            _check(lib().tpss_apply_operator(self.h, level, nrhs, _ptr(u, torch.float64, n), _ptr(out, torch.float64, n)))
+        else:
+            _check(lib().tpss_apply_operator_f32(self.h, level, nrhs, _ptr(u, torch.float32, n), _ptr(out, torch.float32, n)))
+        return out
+
+    def residual(self, level, b, x, r, nrhs=1):
+        n = self.ndofs(level) * nrhs
+        _check(lib().tpss_residual(self.h, level, nrhs, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n),
+                                   _ptr(r, torch.float64, n)))
+        return r
+
+    def prolongate_add(self, fine_level, coarse, fine, nrhs=1):
+        _check(lib().tpss_prolongate_add(self.h, fine_level, nrhs,
+                                         _ptr(coarse, torch.float64, self.ndofs(fine_level - 1) * nrhs),
+                                         _ptr(fine, torch.float64, self.ndofs(fine_level) * nrhs)))
+        return fine
+
+    def restrict(self, fine_level, fine, coarse, nrhs=1):
+        _check(lib().tpss_restrict(self.h, fine_level, nrhs, _ptr(fine, torch.float64, self.ndofs(fine_level) * nrhs),
+                                   _ptr(coarse, torch.float64, self.ndofs(fine_level - 1) * nrhs)))
+        return coarse
+
+    def assemble_rhs(self, level, kind, b):
+        _check(lib().tpss_assemble_rhs(self.h, level, kind, _ptr(b, torch.float64, self.ndofs(level))))
+        return b
+
+    def mg_setup(self, smoother, omega, precision=FP64, mult_colors=0, flexible_cg=0):
+        p = MGParams()
+        p.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
+        p.omega, p.precision, p.mult_colors, p.flexible_cg = omega, precision, mult_colors, flexible_cg
+        _check(lib().tpss_mg_setup(self.h, ctypes.byref(p)))
+
+    def vcycle(self, b, x):
+        n = self.ndofs(self.nlevels - 1)
+        _check(lib().tpss_vcycle(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+        return x
+
+    def coarse_solve(self, b, x):
+        n = self.ndofs(0)
+        _check(lib().tpss_coarse_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+        return x
+
+    def pcg_solve(self, b, x, rtol=1e-8, maxit=200, history=False):
+        n = self.ndofs(self.nlevels - 1)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        hist = (ctypes.c_double * (maxit + 1))() if history else None
+        st = lib().tpss_pcg_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n), rtol, maxit,
+                                  ctypes.byref(it), ctypes.byref(rel),
+                                  ctypes.cast(hist, ctypes.c_void_p) if hist is not None else None)
+        _check(st, allow=(TPSS_OK, TPSS_ENOTCONV))
+        out = {"iters": it.value, "rel_res": rel.value, "converged": st == TPSS_OK}
+        if history:
+            out["history"] = [hist[i] for i in range(it.value + 1)]
+        return out
+
+
+class Patches:
+    """A tpss_patches handle: fast-diagonalization data of one level."""
+
+    def __init__(self, problem, handle, level, kind, precision):
+        self.problem, self.h, self.level, self.kind, self.precision = problem, handle, level, kind, precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tpss_patches_destroy(self.h)
+            self.h = None
+
+    def info(self):
+        n, nsub, nc = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        npos = (ctypes.c_int * 3)()
+        _check(lib().tpss_patches_info(self.h, ctypes.byref(n), npos, ctypes.byref(nsub), ctypes.byref(nc)))
+        return {"n": n.value, "npos": tuple(npos), "nsub": nsub.value, "ncolors_mult": nc.value}
+
+    def eigendata(self, t, pos):
+        import numpy as np
+        n = self.info()["n"]
+        A, M, Z = (np.zeros((n, n)) for _ in range(3))
+        lam = np.zeros(n)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().tpss_patches_eigendata(self.h, t, pos, p(A), p(M), p(Z), p(lam)))
+        return A, M, Z, lam
+
+    def set_mult_colors(self, ncolors):
+        _check(lib().tpss_patches_set_mult_colors(self.h, ncolors))
+
+    def smooth_additive(self, omega, b, x, x_is_zero=False, nrhs=1):
+        n = self.problem.ndofs(self.level) * nrhs
+        if self.precision == FP64:
+            _check(lib().tpss_smooth_additive(self.h, omega, nrhs, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n),
+                                              int(bool(x_is_zero))))
+        else:
+            _check(lib().tpss_smooth_additive_f32(self.h, omega, nrhs, _ptr(b, torch.float32, n),
+                                                  _ptr(x, torch.float32, n), int(bool(x_is_zero))))
+        return x
+
+    def smooth_multiplicative(self, omega, b, x, reverse_colors=False, nrhs=1):
+        n = self.problem.ndofs(self.level) * nrhs
+        _check(lib().tpss_smooth_multiplicative(self.h, omega, int(bool(reverse_colors)), nrhs,
+                                                _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+        return x
