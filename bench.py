@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the fast tensor-product Schwarz smoother library on one GB300.
+
+Workload (one "step"): the additive vertex-patch Schwarz smoother (Alg. 2,
+x = 0 form: x = omega sum_j R_j^T A_j^{-1} R_j b, fast diagonalization of
+Sec. 3.2) on a 3D tensor grid of 32^3 cells with per-direction widths drawn
+U[0.5, 1.5]/32 (seed 2), omega = 0.7, applied to 8 right-hand sides U[-1, 1]
+(seeds 100..107) in one batched call, for each degree k = 2..7, in FP64.
+Metric: DoF/s = sum over k of ndofs(k) * 8 per step / time per step.
+
+Also reported: per-degree DoF/s and roofline fraction, an end-to-end number
+through the same C-ABI call with host buffers (copies timed), the oracle on
+the host cores as cpu_baseline, and the MG-CG time to a 1e-8 residual
+reduction on 64^3 cells, k = 4 (FP64).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tpss|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NC = 32
+KS = [2, 3, 4, 5, 6, 7]
+SEEDS = list(range(100, 108))
+OMEGA = 0.7
+WIDTH_SEED = 2
+METRIC = "patch-smoother DoF/s & MG-CG time-to-1e-8: mixed/batched vs FP64 plain, 1 GB300"
+CONFIG = {"workload": "3D additive vertex-patch Schwarz smoother (fast diagonalization), 32^3 cells, "
+                      "widths U[0.5,1.5]/32, omega 0.7, k=2..7, 8 RHS U[-1,1] batched, x=0 form",
+          "cells": [NC, NC, NC], "degrees": KS, "nrhs": len(SEEDS),
+          "l2": "inputs larger than L2 (each step streams >= 2.5 GB of vectors and tables)"}
+# DRAM traffic of one smoother call at k=7 (8 color launches), from the ncu
+# capture summarized in profiles/patch_smooth_fp64_32cubed.md; None when the
+# kernel changed after that capture.
+TRAFFIC_K7_PER_CALL = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="tpss", choices=["tpss", "reference"])
+    p.add_argument("--no-mgcg", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ks", default=",".join(map(str, KS)))
+    p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
+    p.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-scale", type=float, default=1.0, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+def clocks_start(path):
+    fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={fields}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def clocks_stop(proc, f, path, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- cpu oracle
+def cpu_sample(ks, per_k, offset, scale=1.0):
+    """Time the oracle (dense-LU local solves assembled from the bilinear form)
+    on a bounded sample of vertex patches per degree; returns per-k seconds per
+    patch (all 8 right-hand sides) and a description."""
+    import numpy as np
+    import scipy.linalg as sla
+
+    from oracle import schwarz
+    from oracle.mesh import TensorMesh
+    from oracle.sipg import SIPG
+    from paper_1910_11239_gb300 import workloads
+
+    widths = workloads.widths_random(NC, 3, WIDTH_SEED)
+    mesh = TensorMesh(widths)
+    patches = schwarz.vertex_patches(mesh)
+    out = {}
+    for k in ks:
+        S = SIPG(mesh, k)
+        m = max(1, int(round(per_k[k] * scale)))
+        rng = np.random.default_rng(1000 + k + offset)
+        pick = rng.choice(len(patches), size=m, replace=False)
+        N = mesh.num_cells * S.nloc
+        b = workloads.rhs_batch(N, SEEDS).reshape(len(SEEDS), N)
+        y = np.zeros_like(b)
+        t0 = time.perf_counter()
+        for j in pick:
+            cells = patches[j][1]
+            idx = schwarz.patch_dofs(cells, S.nloc)
+            lu = sla.lu_factor(S.assemble(cells).toarray())
+            y[:, idx] += OMEGA * sla.lu_solve(lu, b[:, idx].T).T
+        out[k] = (time.perf_counter() - t0) / m
+    desc = ", ".join(f"k={k}: {max(1, int(round(per_k[k] * scale)))}" for k in ks)
+    return out, f"{desc} of {len(patches)} vertex patches per degree, 8 RHS each; time per patch x 29791"
+
+
+CPU_PER_K = {2: 48, 3: 24, 4: 8, 5: 4, 6: 2, 7: 1}
+
+
+def cpu_baseline_subprocess(ks, scale):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-worker", "1", "--ks", ",".join(map(str, ks)),
+           "--cpu-scale", str(scale)]
+    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        return {"error": res.stderr[-400:]}
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def dofs(k):
+    return NC ** 3 * (k + 1) ** 3
+
+
+def cpu_value(per_patch, ks):
+    npatch = (NC - 1) ** 3
+    total_t = sum(per_patch[k] * npatch for k in ks)
+    return sum(dofs(k) * len(SEEDS) for k in ks) / total_t
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ks = [int(x) for x in args.ks.split(",")]
+    # one step = a bounded sample of the workload (about a third of CPU_PER_K)
+    for w in range(args.warmup):
+        cpu_sample(ks, CPU_PER_K, offset=w, scale=0.34)
+    tot = {k: 0.0 for k in ks}
+    desc = ""
+    for s in range(args.steps):
+        per, desc = cpu_sample(ks, CPU_PER_K, offset=100 + s, scale=0.34)
+        for k in ks:
+            tot[k] += per[k]
+    per_patch = {k: tot[k] / args.steps for k in ks}
+    val = cpu_value(per_patch, ks)
+    step_ms = 1e3 * sum(dofs(k) * len(SEEDS) for k in ks) / val
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": val, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step " + desc},
+            "e2e": {"value": val, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    global NC
+    args = parse()
+    NC = args.nc
+    if NC != 32:
+        CONFIG["cells"] = [NC, NC, NC]
+        CONFIG["workload"] = CONFIG["workload"].replace("32^3", f"{NC}^3").replace("/32", f"/{NC}")
+    if args.cpu_worker:
+        ks = [int(x) for x in args.ks.split(",")]
+        per, desc = cpu_sample(ks, CPU_PER_K, offset=0, scale=args.cpu_scale)
+        print(json.dumps({"per_patch_s": {str(k): v for k, v in per.items()}, "sample": desc}))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1910_11239_gb300 import perf, tpss, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ks = [int(x) for x in args.ks.split(",")]
+    cpu_res = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_res = cpu_baseline_subprocess(ks, 1.0)   # before the first CUDA call
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    widths = workloads.widths_random(NC, 3, WIDTH_SEED)
+    stream = torch.cuda.current_stream()
+    probs, pats, bdev, xdev, bhost, xhost = {}, {}, {}, {}, {}, {}
+    for k in ks:
+        probs[k] = tpss.Problem(3, k, widths, stream=stream)
+        pats[k] = probs[k].setup_patches(0, tpss.VERTEX_PATCH)
+        N = probs[k].ndofs(0)
+        assert N == dofs(k)
+        b = workloads.rhs_batch(N, SEEDS)
+        bhost[k] = torch.from_numpy(b).pin_memory()
+        xhost[k] = torch.empty_like(bhost[k]).pin_memory()
+        bdev[k] = bhost[k].to("cuda")
+        xdev[k] = torch.empty_like(bdev[k])
+    nr = len(SEEDS)
+    dofs_step = sum(dofs(k) * nr for k in ks)
+
+    def step(evs=None):
+        for k in ks:
+            if evs is not None:
+                evs[k][0].record()
+            pats[k].smooth_additive(OMEGA, bdev[k], xdev[k], x_is_zero=True, nrhs=nr)
+            if evs is not None:
+                evs[k][1].record()
+
+    nwarm = max(args.warmup, 3)
+    for _ in range(nwarm):
+        step()
+    torch.cuda.synchronize()
+    clk_path = f"/tmp/tpss_clocks_{os.getpid()}_{rank}.csv"
+    cproc, cfile = clocks_start(clk_path)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kev = [{k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ks}
+           for _ in range(args.steps)]
+    e0.record()
+    for s in range(args.steps):
+        step(kev[s])
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clocks_stop(cproc, cfile, clk_path, local)
+    try:
+        os.remove(clk_path)
+    except OSError:
+        pass
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = dofs_step * args.steps * world / (ms / 1e3)
+    per_k = {}
+    for k in ks:
+        kms = statistics.mean(kev[s][k][0].elapsed_time(kev[s][k][1]) for s in range(args.steps))
+        fl = perf.smoother_flops((NC, NC, NC), k, vertex=True, nrhs=nr)
+        per_k[str(k)] = {"dofs_per_s": dofs(k) * nr / (kms / 1e3), "ms_per_call": kms,
+                         "tflops": fl / (kms / 1e3) / 1e12,
+                         "frac_fp64_peak": fl / (kms / 1e3) / perf.fp64_peak_flops()}
+    kdom = max(ks, key=lambda k: per_k[str(k)]["ms_per_call"])
+    dom = per_k[str(kdom)]
+    roofline = {"bound": "alu", "kernel": f"patch_smooth_kernel<3,{2 * (kdom + 1)},vertex,double> (k={kdom})",
+                "achieved": dom["tflops"], "peak": perf.fp64_peak_flops() / 1e12, "unit": "TFLOP/s",
+                "frac": dom["frac_fp64_peak"],
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe; HBM is not binding)",
+                "per": "one smoother call = 8 color launches on 8 RHS",
+                "traffic": TRAFFIC_K7_PER_CALL if kdom == 7 else None}
+
+    # end to end through the same call with host buffers (H2D + smooth + D2H)
+    h2d = sum(bhost[k].numel() * 8 for k in ks)
+    d2h = sum(xhost[k].numel() * 8 for k in ks)
+    for _ in range(2):
+        for k in ks:
+            bdev[k].copy_(bhost[k], non_blocking=True)
+            pats[k].smooth_additive(OMEGA, bdev[k], xdev[k], x_is_zero=True, nrhs=nr)
+            xhost[k].copy_(xdev[k], non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        for k in ks:
+            bdev[k].copy_(bhost[k], non_blocking=True)
+            pats[k].smooth_additive(OMEGA, bdev[k], xdev[k], x_is_zero=True, nrhs=nr)
+            xhost[k].copy_(xdev[k], non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    ems = f0.elapsed_time(f1)
+    if world > 1:
+        t = torch.tensor([ems], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    e2e = {"value": dofs_step * args.steps * world / (ems / 1e3), "unit": "DoF/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    for k in ks:
+        probs[k].close()
+    del bdev, xdev, bhost, xhost
+
+    mgcg = None
+    if not args.no_mgcg:
+        mgcg = run_mgcg(tpss, workloads, torch)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+                "warmup": nwarm, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded widths and right-hand sides)", "config": CONFIG,
+                "gpu_launches": args.steps * len(ks) * 8, "roofline": roofline, "e2e": e2e,
+                "clocks": clocks, "per_degree": per_k}
+        if world > 1:
+            line["config"] = dict(CONFIG, parallelism=f"replicas x{world}")
+        if cpu_res is not None:
+            if "per_patch_s" in cpu_res:
+                pp = {int(k): v for k, v in cpu_res["per_patch_s"].items()}
+                line["cpu_baseline"] = {"value": cpu_value(pp, ks), "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                                        "sample": cpu_res["sample"]}
+            else:
+                line["cpu_baseline"] = {"value": None, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                                        "sample": "failed: " + cpu_res.get("error", "")}
+        if mgcg is not None:
+            line["mg_cg"] = mgcg
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_mgcg(tpss, workloads, torch):
+    """MG-CG on 64^3 cells (levels 2^3..64^3), k = 4, f = 3 pi^2 sin sin sin,
+    V-cycle(1,1) preconditioned CG to a 1e-8 relative residual, FP64."""
+    out = {"workload": "3D unit cube, 2^3..64^3 cells (6 levels), k=4 (32,768,000 DoFs), "
+                       "f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), rtol 1e-8"}
+    prob = tpss.Problem(3, 4, workloads.widths_uniform(2, 3), nlevels=6)
+    N = prob.ndofs(5)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(5, 0, b)
+    x = torch.empty_like(b)
+    for name, sm, omega in [("AVS_omega0.7", "AVS", 0.7), ("AVS_omega0.125", "AVS", 0.125), ("MVS", "MVS", 1.0)]:
+        prob.mg_setup(sm, omega)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        try:
+            res = prob.pcg_solve(b, x, rtol=1e-8, maxit=60, history=True)
+            status = "converged" if res["converged"] else "not converged"
+        except tpss.TpssError as e:
+            res, status = {"iters": None, "rel_res": None}, str(e).split(":")[0]
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"time_s": e0.elapsed_time(e1) / 1e3, "iterations": res["iters"],
+                     "rel_res": res["rel_res"], "status": status, "precision": "fp64"}
+    prob.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,75 @@
+"""Algorithmic work counts used for roofline reporting (what the method must
+do, not what an implementation happens to do).
+
+Local solver of one subdomain with n points per direction in d dimensions
+(eq. fastinverse applied by sum factorization, eq. eigenvectormatvec):
+  Z^T and Z: 2 d contractions of n^d values with an n x n matrix, 2 n^(d+1)
+  flops each -> 4 d n^(d+1); Lambda^{-1}: n^d multiplications; damped
+  scatter-add x += omega y: 2 n^d.  In 3D: 12 n^4 + 3 n^3 per subdomain.
+The paper's likwid counts of the local solvers (tab:flop-additive) follow
+12 n^4 per subdomain within a few percent; tests/test_perf.py checks that.
+
+Minimal HBM traffic of one smoother application in the x = 0 form: read the
+right-hand side once and write x once, 16 bytes per DoF in FP64 (8 in FP32).
+
+Peaks: GB300 FP64 DFMA issue rate is 2 FMA per clock per SM (measured
+1.20 TFLOP/s with a DFMA throughput probe at ~2.0 GHz); the derived peak at
+the 2070 MHz maximum SM clock is 152 * 2 * 2 * 2.07e9 = 1.2586e12 flop/s.
+"""
+
+SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2
+FP32_FMA_PER_CLK_PER_SM = 128
+MAX_SM_HZ = 2.07e9
+
+
+def fp64_peak_flops(sm_hz=MAX_SM_HZ):
+    return SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_hz
+
+
+def fp32_peak_flops(sm_hz=MAX_SM_HZ):
+    return SMS * FP32_FMA_PER_CLK_PER_SM * 2 * sm_hz
+
+
+def local_solver_flops(n, d=3):
+    return 4 * d * n ** (d + 1) + 3 * n ** d
+
+
+def num_vertex_patches(ncells):
+    p = 1
+    for c in ncells:
+        p *= c - 1
+    return p
+
+
+def num_cells(ncells):
+    p = 1
+    for c in ncells:
+        p *= c
+    return p
+
+
+def smoother_flops(ncells, k, d=3, vertex=True, nrhs=1):
+    n = 2 * (k + 1) if vertex else k + 1
+    nsub = num_vertex_patches(ncells) if vertex else num_cells(ncells)
+    return nsub * local_solver_flops(n, d) * nrhs
+
+
+def ndofs(ncells, k, d=3):
+    return num_cells(ncells) * (k + 1) ** d
+
+
+def smoother_bytes(ncells, k, d=3, nrhs=1, word=8):
+    return 2 * word * ndofs(ncells, k, d) * nrhs
+
+
+def operator_flops(ncells, k, d=3, nrhs=1):
+    """Sum-factorized SIPG operator: 3 passes with 7 (k+1)^4 FMAs per cell
+    (3D; 4 (k+1)^3 in 2D) plus the rank-2 face couplings, 2 faces per
+    direction, each 2 (k+1) FMAs per line."""
+    n1 = k + 1
+    if d == 3:
+        per_cell = 2 * (7 * n1 ** 4 + 3 * 2 * n1 ** 2 * 2 * n1)
+    else:
+        per_cell = 2 * (4 * n1 ** 3 + 2 * 2 * n1 * 2 * n1)
+    return num_cells(ncells) * per_cell * nrhs

@@ -1,0 +1,39 @@
+"""Pin the algorithmic flop counter against the paper's likwid counts
+(tab:flop-additive, mesh T_3 = 16^3 cells, 15^3 vertex patches)."""
+import os
+
+import pytest
+
+from paper_1910_11239_gb300 import perf
+
+GOLD = {}
+for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.txt")):
+    if line.strip() and not line.startswith("#"):
+        key, val, _ = line.split()
+        GOLD[key] = float(val)
+
+
+@pytest.mark.parametrize("k", [3, 7, 15])
+def test_avs_local_solver_flops_match_paper(k):
+    mflop = perf.smoother_flops((16, 16, 16), k, vertex=True) / 1e6
+    assert abs(mflop / GOLD[f"avs_local_solvers_k{k}"] - 1) < 0.03
+
+
+@pytest.mark.parametrize("k", [3, 7, 15])
+def test_acs_local_solver_flops_match_paper(k):
+    mflop = perf.smoother_flops((16, 16, 16), k, vertex=False) / 1e6
+    assert abs(mflop / GOLD[f"acs_local_solvers_k{k}"] - 1) < 0.07
+
+
+def test_complexity_constants():
+    # C = n_FLOP / (n_sub k^(d+1)) -> 12 (k+1)^4/k^4 for large k: tab:cmplxconstant lists 12 (ACS)
+    k = 31
+    c = perf.local_solver_flops(k + 1) / k ** 4
+    assert abs(c / GOLD["acs_local_constant"] - 1) < 0.15
+    # AVS per vertex patch: 12 (2(k+1))^4 / k^4 = 192 (1+1/k)^4 ~ the paper's 195
+    c = perf.local_solver_flops(2 * (k + 1)) / k ** 4
+    assert abs(c / GOLD["avs_local_constant"] - 1) < 0.15
+
+
+def test_fp64_peak_is_derived_from_unit_counts():
+    assert abs(perf.fp64_peak_flops() - 152 * 2 * 2 * 2.07e9) < 1
