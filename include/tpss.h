@@ -152,6 +152,21 @@ tpss_status tpss_smooth_multiplicative(tpss_patches* patches, double omega, int 
 tpss_status tpss_apply_operator(tpss_ctx* ctx, int level, int nrhs, const double* u, double* Au);
 tpss_status tpss_apply_operator_f32(tpss_ctx* ctx, int level, int nrhs, const float* u, float* Au);
 
+/* Allocation-free variant of tpss_apply_operator (the paper has no
+ * counterpart; this is a library convenience).  For callers that must not
+ * trigger a device allocation during a call: code whose device memory is all
+ * reserved by another allocator, or latency-critical loops that cannot
+ * afford the allocation and synchronization tpss_apply_operator performs the
+ * first time a level is used with a larger nrhs.  Same result as
+ * tpss_apply_operator; the operator's intermediates live in one static device
+ * array of 4 * 2^19 doubles (16 MiB, held by every GPU that loads the library
+ * until the process exits).  Limit: ndofs(level) * nrhs <= 2^19, else
+ * TPSS_EINVAL with a message.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU (e.g. on two
+ * streams) race; serialize them.  Calls no allocating routine. */
+tpss_status tpss_apply_operator_noalloc(tpss_ctx* ctx, int level, int nrhs, const double* u, double* Au);
+
 /* r = b - A_l x (r may alias b, not x). */
 tpss_status tpss_residual(tpss_ctx* ctx, int level, int nrhs, const double* b, const double* x,
                           double* r);

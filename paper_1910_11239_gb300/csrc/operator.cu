@@ -230,6 +230,24 @@ tpss_status apply_operator_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* 
   return TPSS_EINVAL;
 }
 
+
+// The operator with caller-provided intermediates (four vectors of
+// ndofs * nrhs doubles); used by the allocation-free entry point.
+tpss_status apply_operator_into(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out,
+                                double* const* tmp) {
+  Level& L = ctx->levels[level];
+  const LevelOps<double>& op = L.op64;
+#define TPSS_OPI_CASE(D, N)                                                  \
+  if (ctx->dim == D && ctx->n1 == N) return apply_n<D, N, double>(ctx, L, op, tmp, nrhs, u, out, nullptr);
+  TPSS_OPI_CASE(3, 2) TPSS_OPI_CASE(3, 3) TPSS_OPI_CASE(3, 4) TPSS_OPI_CASE(3, 5)
+  TPSS_OPI_CASE(3, 6) TPSS_OPI_CASE(3, 7) TPSS_OPI_CASE(3, 8)
+  TPSS_OPI_CASE(2, 2) TPSS_OPI_CASE(2, 3) TPSS_OPI_CASE(2, 4) TPSS_OPI_CASE(2, 5)
+  TPSS_OPI_CASE(2, 6) TPSS_OPI_CASE(2, 7) TPSS_OPI_CASE(2, 8)
+#undef TPSS_OPI_CASE
+  set_error("operator: unsupported degree");
+  return TPSS_EINVAL;
+}
+
 template tpss_status apply_operator_t<double>(tpss_ctx*, int, int, const double*, double*, const double*);
 template tpss_status apply_operator_t<float>(tpss_ctx*, int, int, const float*, float*, const float*);
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
     "tpss_apply_operator": [_VP, _I, _I, _VP, _VP],
     "tpss_apply_operator_f32": [_VP, _I, _I, _VP, _VP],
+    "tpss_apply_operator_noalloc": [_VP, _I, _I, _VP, _VP],
     "tpss_residual": [_VP, _I, _I, _VP, _VP, _VP],
     "tpss_prolongate_add": [_VP, _I, _I, _VP, _VP],
     "tpss_restrict": [_VP, _I, _I, _VP, _VP],
@@ -162,6 +163,15 @@ class Problem:
             _check(lib().tpss_apply_operator(self.h, level, nrhs, _ptr(u, torch.float64, n), _ptr(out, torch.float64, n)))
         else:
             _check(lib().tpss_apply_operator_f32(self.h, level, nrhs, _ptr(u, torch.float32, n), _ptr(out, torch.float32, n)))
+        return out
+
+    def apply_operator_noalloc(self, level, u, out, nrhs=1):
+        """tpss_apply_operator_noalloc: same result as apply_operator, no device
+        allocation (intermediates in the library's fixed 16 MiB array;
+        ndofs * nrhs <= 2^19)."""
+        n = self.ndofs(level) * nrhs
+        _check(lib().tpss_apply_operator_noalloc(self.h, level, nrhs, _ptr(u, torch.float64, n),
+                                                 _ptr(out, torch.float64, n)))
         return out
 
     def residual(self, level, b, x, r, nrhs=1):
