@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
+    p.add_argument("--mixed", default="fp32,tf32,bf16", help="low-precision smoother variants to time")
     p.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--cpu-scale", type=float, default=1.0, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -323,9 +324,13 @@ def main():
         probs[k].close()
     del bdev, xdev, bhost, xhost
 
+    mixed = {}
+    for prec in [p for p in args.mixed.split(",") if p]:
+        mixed[prec] = run_low_precision_smoother(prec, ks, widths, args.steps, tpss, workloads, perf, torch)
+
     mgcg = None
     if not args.no_mgcg:
-        mgcg = run_mgcg(tpss, workloads, torch)
+        mgcg = run_mgcg(tpss, workloads, torch, MGCG_CASES)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -344,6 +349,8 @@ def main():
             else:
                 line["cpu_baseline"] = {"value": None, "unit": "DoF/s", "cores": 1, "kind": "oracle",
                                         "sample": "failed: " + cpu_res.get("error", "")}
+        if mixed:
+            line["mixed_smoother"] = mixed
         if mgcg is not None:
             line["mg_cg"] = mgcg
         print(json.dumps(line))
@@ -351,32 +358,91 @@ def main():
         dist.destroy_process_group()
 
 
-def run_mgcg(tpss, workloads, torch):
-    """MG-CG on 64^3 cells (levels 2^3..64^3), k = 4, f = 3 pi^2 sin sin sin,
-    V-cycle(1,1) preconditioned CG to a 1e-8 relative residual, FP64."""
-    out = {"workload": "3D unit cube, 2^3..64^3 cells (6 levels), k=4 (32,768,000 DoFs), "
-                       "f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), rtol 1e-8"}
-    prob = tpss.Problem(3, 4, workloads.widths_uniform(2, 3), nlevels=6)
-    N = prob.ndofs(5)
-    b = torch.empty(N, dtype=torch.float64, device="cuda")
-    prob.assemble_rhs(5, 0, b)
-    x = torch.empty_like(b)
-    for name, sm, omega in [("AVS_omega0.7", "AVS", 0.7), ("AVS_omega0.125", "AVS", 0.125), ("MVS", "MVS", 1.0)]:
-        prob.mg_setup(sm, omega)
+def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, torch):
+    """The same smoother workload with FP32 vectors and FP32 / TF32 / BF16
+    mode contractions (FP32 accumulation).  Roofline: HBM, 8 bytes per DoF
+    and right-hand side (read b, write x) against the measured copy bandwidth."""
+    import json as _json
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nr = len(SEEDS)
+    out = {"dtype": prec, "accumulate": "fp32", "per_degree": {}}
+    total_ms = 0.0
+    for k in ks:
+        prob = tpss.Problem(3, k, widths)
+        P = prob.setup_patches(0, tpss.VERTEX_PATCH, tpss.PRECISIONS[prec])
+        N = prob.ndofs(0)
+        b = torch.from_numpy(workloads.rhs_batch(N, SEEDS)).to("cuda", torch.float32)
+        x = torch.empty_like(b)
+        for _ in range(3):
+            P.smooth_additive(OMEGA, b, x, x_is_zero=True, nrhs=nr)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        try:
-            res = prob.pcg_solve(b, x, rtol=1e-8, maxit=60, history=True)
-            status = "converged" if res["converged"] else "not converged"
-        except tpss.TpssError as e:
-            res, status = {"iters": None, "rel_res": None}, str(e).split(":")[0]
+        for _ in range(steps):
+            P.smooth_additive(OMEGA, b, x, x_is_zero=True, nrhs=nr)
         e1.record()
         torch.cuda.synchronize()
-        out[name] = {"time_s": e0.elapsed_time(e1) / 1e3, "iterations": res["iters"],
-                     "rel_res": res["rel_res"], "status": status, "precision": "fp64"}
-    prob.close()
+        ms = e0.elapsed_time(e1) / steps
+        total_ms += ms
+        byt = perf.smoother_bytes((NC, NC, NC), k, nrhs=nr, word=4)
+        out["per_degree"][str(k)] = {"dofs_per_s": dofs(k) * nr / (ms / 1e3), "ms_per_call": ms,
+                                     "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
+        prob.close()
+    out["dofs_per_s"] = sum(dofs(k) * nr for k in ks) / (total_ms / 1e3)
+    out["vs_fp64_note"] = "same workload, FP32 vectors; compare with the line's FP64 value"
+    out["hbm_peak_gbs"] = hbm
     return out
+
+
+def run_mgcg(tpss, workloads, torch, cases):
+    """MG-CG on the unit cube, levels 2^3..64^3 cells, f = 3 pi^2 sin sin sin,
+    V-cycle(1,1) preconditioned CG from x = 0 to a 1e-8 relative residual.
+    For every (k, smoother, omega, precisions): time to solution (CUDA events
+    around tpss_pcg_solve, setup excluded), iterations, and for the mixed
+    precisions the relative difference to the FP64 solution.  Mixed runs use
+    flexible CG with the FP32 V-cycle (FP32/TF32/BF16 mode contractions)."""
+    out = {"workload": "3D unit cube, 2^3..64^3 cells (6 levels), f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), "
+                       "g = 0, rtol 1e-8; time excludes setup"}
+    for k, sm, omega, precs in cases:
+        prob = tpss.Problem(3, k, workloads.widths_uniform(2, 3), nlevels=6)
+        N = prob.ndofs(5)
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(5, 0, b)
+        x64 = torch.zeros_like(b)
+        x = torch.empty_like(b)
+        for prec in precs:
+            prob.mg_setup(sm, omega, tpss.PRECISIONS[prec], flexible_cg=0 if prec == "fp64" else 1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            try:
+                res = prob.pcg_solve(b, x, rtol=1e-8, maxit=60)
+                status = "converged" if res["converged"] else "not converged"
+            except tpss.TpssError as e:
+                res, status = {"iters": None, "rel_res": None}, str(e).split(":")[0]
+            e1.record()
+            torch.cuda.synchronize()
+            rec = {"time_s": e0.elapsed_time(e1) / 1e3, "iterations": res["iters"], "rel_res": res["rel_res"],
+                   "status": status, "ndofs": N}
+            if prec == "fp64" and status == "converged":
+                x64.copy_(x)
+            elif status == "converged" and x64.abs().max().item() > 0:
+                rec["rel_diff_to_fp64_solution"] = ((x - x64).norm() / x64.norm()).item()
+            out[f"k{k}_{sm}_omega{omega:g}_{prec}"] = rec
+        prob.close()
+    return out
+
+
+MGCG_CASES = [
+    (4, "AVS", 0.7, ["fp64"]),
+    (4, "AVS", 0.125, ["fp64", "fp32", "tf32", "bf16"]),
+    (4, "MVS", 1.0, ["fp64", "fp32", "tf32", "bf16"]),
+    (3, "MVS", 1.0, ["fp64", "tf32"]),
+    (5, "MVS", 1.0, ["fp64", "tf32"]),
+    (7, "MVS", 1.0, ["fp64", "tf32"]),
+]
 
 
 if __name__ == "__main__":

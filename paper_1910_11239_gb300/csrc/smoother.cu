@@ -212,6 +212,11 @@ static tpss_status launch_smooth(const SmoothArgs<T>& a, int nrhs, cudaStream_t 
 template <typename T>
 tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs, const T* r, T* x,
                        cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (P->precision == TPSS_TF32 || P->precision == TPSS_BF16)
+      return patch_pass_tc(P, list, count, (float)omega, nrhs, reinterpret_cast<const float*>(r),
+                           reinterpret_cast<float*>(x), s);
+  }
   const tpss_ctx* ctx = P->ctx;
   const Level& L = ctx->levels[P->level];
   SmoothArgs<T> a{};

@@ -173,6 +173,10 @@ template <typename T>
 tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs,
                        const T* r, T* x, cudaStream_t s);
 
+// ---- smoother_tc.cu (TF32 / BF16 tensor-core contractions)
+tpss_status patch_pass_tc(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
+                          float* x, cudaStream_t s);
+
 // ---- transfer.cu
 template <typename T>
 tpss_status prolongate_add_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* coarse, T* fine);

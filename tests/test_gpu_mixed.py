@@ -1,0 +1,85 @@
+"""Mixed precision (not in the paper): FP32 smoother / V-cycle inside the FP64
+outer PCG.  Parity against the FP64 oracle with bounds derived from FP32
+rounding, and the FP64 true residual reaching the 1e-8 reduction."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+from gpu_helpers import dev, make, oracle_solvers, oracle_sipg, rel_err
+from oracle import schwarz
+from oracle.multigrid import Hierarchy
+from paper_1910_11239_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+# FP32 bound: the local solve is 2d contractions of length n plus a scale; with
+# unit roundoff 6e-8 and the spread of 1/lambda, relative max-norm errors stay
+# well below 1e-4 (measured ~1e-6); BF16 contractions (unit roundoff 4e-3)
+# are checked at 5e-2.
+TOL32 = 1e-4
+
+
+@pytest.mark.parametrize("dim,k,n", [(3, 2, 4), (3, 4, 3), (3, 7, 2), (2, 3, 6)])
+@pytest.mark.parametrize("kind", ["vertex", "cell"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_low_precision_additive_smoother(dim, k, n, kind, prec):
+    from paper_1910_11239_gb300 import tpss
+    widths = workloads.widths_random(n, dim, seed=30 + n + k)
+    prob = make(dim, k, widths)
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH if kind == "vertex" else tpss.CELL, tpss.PRECISIONS[prec])
+    S = oracle_sipg(widths, k)
+    A = S.assemble().tocsr()
+    _, sol = oracle_solvers(S, A, kind)
+    N = A.shape[0]
+    b = workloads.rhs_uniform(N, seed=9, nrhs=2)
+    x = torch.empty(2 * N, dtype=torch.float32, device="cuda")
+    P.smooth_additive(0.7, dev(b, torch.float32), x, x_is_zero=True, nrhs=2)
+    tol = 5e-2 if prec == "bf16" else (2e-3 if prec == "tf32" else TOL32)
+    for r in range(2):
+        ref = schwarz.additive_local_sum(b[r * N:(r + 1) * N].astype(np.float32).astype(np.float64), sol, 0.7)
+        assert rel_err(x[r * N:(r + 1) * N].double(), ref) < tol
+    prob.close()
+
+
+@pytest.mark.parametrize("smoother,omega", [("AVS", 0.125), ("MVS", 1.0), ("ACS", 0.7)])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_mixed_pcg_reaches_fp64_tolerance(smoother, omega, prec):
+    from paper_1910_11239_gb300 import tpss
+    dim, k, nlevels = 3, 3, 3
+    coarse = workloads.widths_uniform(2, dim)
+    prob = make(dim, k, coarse, nlevels=nlevels)
+    N = prob.ndofs(nlevels - 1)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(nlevels - 1, 0, b)
+    x64 = torch.empty_like(b)
+    prob.mg_setup(smoother, omega, tpss.FP64)
+    r64 = prob.pcg_solve(b, x64, rtol=1e-8, maxit=100)
+    assert r64["converged"]
+    prob.mg_setup(smoother, omega, tpss.PRECISIONS[prec], flexible_cg=1)
+    xm = torch.empty_like(b)
+    rm = prob.pcg_solve(b, xm, rtol=1e-8, maxit=100)
+    assert rm["converged"] and rm["rel_res"] <= 1e-8
+    # the true FP64 residual of the mixed solution meets the tolerance
+    r = torch.empty_like(b)
+    prob.residual(nlevels - 1, b, xm, r)
+    assert (r.norm() / b.norm()).item() < 2e-8
+    # a perturbed preconditioner may need a few more iterations (measured:
+    # AVS k=3, 24 FP64 -> 29 TF32); bound it loosely
+    assert rm["iters"] <= 1.5 * r64["iters"] + 4
+    assert ((xm - x64).norm() / x64.norm()).item() < 1e-6
+    prob.close()
+
+
+def test_mixed_vcycle_close_to_oracle():
+    from paper_1910_11239_gb300 import tpss
+    coarse = workloads.widths_random(2, 3, seed=3)
+    H = Hierarchy(coarse, 2, 2, smoother="MVS", omega=1.0)
+    prob = make(3, 2, coarse, nlevels=2)
+    prob.mg_setup("MVS", 1.0, tpss.FP32)
+    N = H.A[-1].shape[0]
+    b = workloads.rhs_uniform(N, seed=11)
+    x = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.vcycle(dev(b), x)
+    assert rel_err(x, H.precondition(b)) < 1e-4
+    prob.close()
