@@ -222,6 +222,40 @@ tpss_status tpss_coarse_solve(tpss_ctx* ctx, const double* b, double* x);
 tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
                            int* iters, double* rel_res, double* res_hist);
 
+/* --------------------------------------------------------------- batches --
+ * Many independent 3D problems of uneven size and degree (not in the paper):
+ * every problem gets its own hierarchy (descs[p], additive vertex-patch
+ * smoother with params->omega) and nrhs right-hand sides.  The V-cycle runs in
+ * FP32 (FP32 mode contractions, FP32 operators and transfers, FP64 coarse
+ * inverse) with levels aligned from the finest one; at every level ONE
+ * persistent kernel smooths all problems and right-hand sides, pulling work
+ * items (problem, rhs, group of patches) from an atomic counter, largest
+ * degree first, scattering with FP32 atomics (so FP32 summation order is not
+ * fixed).  The number of patches per work item is autotuned per patch size
+ * at creation unless flags & 2; the whole V-cycle is captured as a CUDA graph
+ * unless flags & 1 or the stream is the legacy default stream.
+ * Vector layout of every batched call: problems one after another, each as
+ * nrhs consecutive vectors of its finest level (tpss_batch_info gives offsets).
+ * Synchronizes the stream. */
+typedef struct tpss_batch tpss_batch;
+tpss_status tpss_batch_create(const tpss_problem_desc* descs, int nprob, int nrhs, const tpss_mg_params* params,
+                              int flags, void* cuda_stream, tpss_batch** out);
+tpss_status tpss_batch_destroy(tpss_batch* batch);
+/* Finest-level size and offset of problem p, and its autotuned patches per work item. */
+tpss_status tpss_batch_info(const tpss_batch* batch, int prob, int64_t* ndofs, int64_t* offset, int* ppb);
+/* Concatenated length, number of systems (nprob * nrhs), 1 if the V-cycle is a CUDA graph. */
+tpss_status tpss_batch_summary(const tpss_batch* batch, int64_t* total, int* nsys, int* uses_graph);
+/* Finest level of every problem, x = omega sum_j R_j^T A_j^{-1} R_j b in FP32
+ * (Alg. 2 with x = 0), one persistent launch; b and x are FP32 device vectors. */
+tpss_status tpss_batch_smooth_additive(tpss_batch* batch, const float* b, float* x);
+/* x = MG(0, b) for every system (FP64 in and out, FP32 inside). */
+tpss_status tpss_batch_vcycle(tpss_batch* batch, const double* b, double* x);
+/* Flexible PCG for every system, FP64 outer iteration, from x = 0 to
+ * ||r_k|| <= rtol ||r_0|| per system; iters and rel_res are HOST arrays of
+ * nprob * nrhs entries.  TPSS_ENOTCONV if some system reached maxit. */
+tpss_status tpss_batch_pcg_solve(tpss_batch* batch, const double* b, double* x, double rtol, int maxit,
+                                 int* iters, double* rel_res);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,18 +24,6 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
 template <typename T>
 tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int nrhs, const T* b, T* x);
 
-struct MGState {
-  tpss_mg_params params{};
-  int mixed = 0;                         // 1: V-cycle in FP32
-  std::vector<tpss_patches*> patches;    // per level, [0] unused
-  int64_t n0 = 0;
-  double* coarse_inv = nullptr;          // [n0][n0]
-  std::vector<double*> b64, x64;         // per level right-hand side / solution
-  std::vector<float*> b32, x32;
-  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr;
-  double* gj_tmp = nullptr;              // 2 n0
-};
-
 void destroy_mg(tpss_ctx* ctx) {
   MGState* mg = ctx->mg;
   if (!mg) return;

@@ -105,7 +105,18 @@ struct Level {
   float* t32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
-struct MGState;
+// Multigrid state of one context (solver.cu).
+struct MGState {
+  tpss_mg_params params{};
+  int mixed = 0;                         // 1: V-cycle in FP32
+  std::vector<tpss_patches*> patches;    // per level, [0] unused
+  int64_t n0 = 0;
+  double* coarse_inv = nullptr;          // [n0][n0]
+  std::vector<double*> b64, x64;         // per level right-hand side / solution
+  std::vector<float*> b32, x32;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr;
+  double* gj_tmp = nullptr;              // 2 n0
+};
 
 }  // namespace tpss
 

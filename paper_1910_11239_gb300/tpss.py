@@ -71,6 +71,14 @@ SIGNATURES = {
     "tpss_coarse_solve": [_VP, _VP, _VP],
     "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                        _VP],
+    "tpss_batch_create": [ctypes.POINTER(ProblemDesc), _I, _I, ctypes.POINTER(MGParams), _I, _VP,
+                          ctypes.POINTER(_VP)],
+    "tpss_batch_destroy": [_VP],
+    "tpss_batch_info": [_VP, _I, _I64P, _I64P, ctypes.POINTER(ctypes.c_int)],
+    "tpss_batch_summary": [_VP, _I64P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "tpss_batch_smooth_additive": [_VP, _VP, _VP],
+    "tpss_batch_vcycle": [_VP, _VP, _VP],
+    "tpss_batch_pcg_solve": [_VP, _VP, _VP, _D, _I, _VP, _VP],
 }
 
 
@@ -269,3 +277,68 @@ class Patches:
         _check(lib().tpss_smooth_multiplicative(self.h, omega, int(bool(reverse_colors)), nrhs,
                                                 _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
         return x
+
+
+class Batch:
+    """tpss_batch_*: many independent 3D problems (list of (degree, widths,
+    nlevels)) with nrhs right-hand sides each, mixed-precision V-cycle with one
+    persistent smoother launch per level, optionally graph-captured."""
+
+    def __init__(self, problems, nrhs, omega=0.125, use_graph=True, autotune=True, stream=None,
+                 gamma_hat=1.0, penalty_poly=PENALTY_PAPER):
+        self._keep = []
+        descs = (ProblemDesc * len(problems))()
+        for i, (degree, widths, nlevels) in enumerate(problems):
+            arrs = [(ctypes.c_double * len(w))(*[float(v) for v in w]) for w in widths]
+            self._keep.append(arrs)
+            d = descs[i]
+            d.dim, d.degree, d.nlevels, d.gamma_hat, d.penalty_poly = 3, degree, nlevels, gamma_hat, penalty_poly
+            for t in range(3):
+                d.ncells[t] = len(widths[t])
+                d.widths[t] = ctypes.cast(arrs[t], ctypes.POINTER(ctypes.c_double))
+        p = MGParams()
+        p.smoother, p.omega, p.precision, p.mult_colors, p.flexible_cg = AVS, omega, FP32, 0, 1
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        flags = (0 if use_graph else 1) | (0 if autotune else 2)
+        h = ctypes.c_void_p()
+        _check(lib().tpss_batch_create(descs, len(problems), nrhs, ctypes.byref(p), flags,
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h, self.nprob, self.nrhs = h, len(problems), nrhs
+        t, ns, g = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().tpss_batch_summary(self.h, ctypes.byref(t), ctypes.byref(ns), ctypes.byref(g)))
+        self.total, self.nsys, self.uses_graph = t.value, ns.value, bool(g.value)
+
+    def info(self, p):
+        n, o, g = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().tpss_batch_info(self.h, p, ctypes.byref(n), ctypes.byref(o), ctypes.byref(g)))
+        return {"ndofs": n.value, "offset": o.value, "ppb": g.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tpss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def smooth_additive(self, b, x):
+        _check(lib().tpss_batch_smooth_additive(self.h, _ptr(b, torch.float32, self.total),
+                                                _ptr(x, torch.float32, self.total)))
+        return x
+
+    def vcycle(self, b, x):
+        _check(lib().tpss_batch_vcycle(self.h, _ptr(b, torch.float64, self.total), _ptr(x, torch.float64, self.total)))
+        return x
+
+    def pcg_solve(self, b, x, rtol=1e-8, maxit=100):
+        import numpy as np
+        it = np.zeros(self.nsys, dtype=np.int32)
+        rel = np.zeros(self.nsys)
+        st = lib().tpss_batch_pcg_solve(self.h, _ptr(b, torch.float64, self.total), _ptr(x, torch.float64, self.total),
+                                        rtol, maxit, it.ctypes.data_as(ctypes.c_void_p),
+                                        rel.ctypes.data_as(ctypes.c_void_p))
+        _check(st, allow=(TPSS_OK, TPSS_ENOTCONV))
+        return {"iters": it, "rel_res": rel, "converged": st == TPSS_OK}

@@ -1,0 +1,112 @@
+"""Batched uneven problems (not in the paper): one persistent smoother launch
+per level across problems of different degree and size, FP32 V-cycle,
+CUDA-graph capture, autotuned work items, FP64 outer PCG per system.
+Checked against the per-problem library path and the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import dev, make, rel_err
+from oracle.multigrid import Hierarchy
+from paper_1910_11239_gb300 import tpss, workloads
+
+pytestmark = pytest.mark.gpu
+
+OMEGA = 0.125
+# (degree, coarse cells per direction, nlevels, seed): uneven sizes, degrees and depths
+SPECS = [(2, 2, 2, 11), (3, 3, 2, 12), (1, 2, 3, 13), (4, 2, 2, 14)]
+
+
+def problems():
+    return [(k, workloads.widths_random(c, 3, seed), nl) for k, c, nl, seed in SPECS]
+
+
+def rhs_for(batch, seed):
+    b = np.zeros(batch.total)
+    rng = np.random.default_rng(seed)
+    b[:] = rng.uniform(-1, 1, batch.total)
+    return b
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.Stream()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_smoother_matches_per_problem_fp32(use_graph, stream):
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, use_graph=use_graph, stream=stream)
+        assert B.uses_graph == use_graph
+        b = rhs_for(B, 1)
+        x = torch.empty(B.total, dtype=torch.float32, device="cuda")
+        B.smooth_additive(dev(b, torch.float32), x)
+        torch.cuda.synchronize()
+        for p, (k, widths, nl) in enumerate(problems()):
+            info = B.info(p)
+            prob = make(3, k, widths, nlevels=nl)
+            P = prob.setup_patches(nl - 1, tpss.VERTEX_PATCH, tpss.FP32)
+            n = info["ndofs"]
+            seg = slice(info["offset"], info["offset"] + 2 * n)
+            xr = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+            P.smooth_additive(OMEGA, dev(b[seg], torch.float32), xr, x_is_zero=True, nrhs=2)
+            torch.cuda.synchronize()
+            assert rel_err(x[seg].double(), xr.double().cpu().numpy()) < 1e-5
+            assert info["ppb"] >= 1
+            prob.close()
+        B.close()
+
+
+def test_batch_vcycle_matches_per_problem_and_oracle(stream):
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, stream=stream)
+        b = rhs_for(B, 2)
+        x = torch.empty(B.total, dtype=torch.float64, device="cuda")
+        B.vcycle(dev(b), x)
+        x2 = torch.empty_like(x)
+        B.vcycle(dev(b), x2)   # replay
+        torch.cuda.synchronize()
+        assert rel_err(x2, x.cpu().numpy()) < 1e-5
+        for p, (k, widths, nl) in enumerate(problems()):
+            info = B.info(p)
+            n = info["ndofs"]
+            prob = make(3, k, widths, nlevels=nl)
+            prob.mg_setup("AVS", OMEGA, tpss.FP32)
+            for r in range(2):
+                seg = slice(info["offset"] + r * n, info["offset"] + (r + 1) * n)
+                xr = torch.empty(n, dtype=torch.float64, device="cuda")
+                prob.vcycle(dev(b[seg]), xr)
+                torch.cuda.synchronize()
+                assert rel_err(x[seg], xr.cpu().numpy()) < 1e-4
+            if p == 0:
+                H = Hierarchy(widths, k, nl, smoother="AVS", omega=OMEGA)
+                seg = slice(info["offset"], info["offset"] + n)
+                assert rel_err(x[seg], H.precondition(b[seg])) < 1e-4
+            prob.close()
+        B.close()
+
+
+def test_batch_pcg_converges_every_system(stream):
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, stream=stream)
+        b = rhs_for(B, 3)
+        x = torch.empty(B.total, dtype=torch.float64, device="cuda")
+        res = B.pcg_solve(dev(b), x, rtol=1e-8, maxit=80)
+        torch.cuda.synchronize()
+        assert res["converged"] and (res["rel_res"] <= 1e-8).all()
+        for p, (k, widths, nl) in enumerate(problems()):
+            info = B.info(p)
+            n = info["ndofs"]
+            prob = make(3, k, widths, nlevels=nl)
+            prob.mg_setup("AVS", OMEGA, tpss.FP64)
+            for r in range(2):
+                seg = slice(info["offset"] + r * n, info["offset"] + (r + 1) * n)
+                bs = dev(b[seg])
+                rr = torch.empty_like(bs)
+                prob.residual(nl - 1, bs, x[seg].contiguous(), rr)
+                assert (rr.norm() / bs.norm()).item() < 2e-8
+                x64 = torch.empty_like(bs)
+                prob.pcg_solve(bs, x64, rtol=1e-10, maxit=200)
+                assert ((x[seg] - x64).norm() / x64.norm()).item() < 1e-6
+            prob.close()
+        B.close()
