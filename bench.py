@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--impl", default="tpss", choices=["tpss", "reference"])
     p.add_argument("--no-mgcg", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
     p.add_argument("--mixed", default="fp32,tf32,bf16", help="low-precision smoother variants to time")
@@ -331,6 +332,9 @@ def main():
     mgcg = None
     if not args.no_mgcg:
         mgcg = run_mgcg(tpss, workloads, torch, MGCG_CASES)
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(tpss, workloads, perf, torch, args.steps)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -353,6 +357,8 @@ def main():
             line["mixed_smoother"] = mixed
         if mgcg is not None:
             line["mg_cg"] = mgcg
+        if batch is not None:
+            line["batched"] = batch
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -432,6 +438,94 @@ def run_mgcg(tpss, workloads, torch, cases):
                 rec["rel_diff_to_fp64_solution"] = ((x - x64).norm() / x64.norm()).item()
             out[f"k{k}_{sm}_omega{omega:g}_{prec}"] = rec
         prob.close()
+    return out
+
+
+def batch_specs(workloads):
+    """48 problems = 12 each of (16^3, k=7), (24^3, k=5), (32^3, k=3), (48^3, k=2):
+    coarse widths U[0.5,1.5] h (seed 1000+p), bisected; 4 RHS U[-1,1] (seed 2000+4p+r)."""
+    kinds = [(16, 7, 2), (24, 5, 3), (32, 3, 2), (48, 2, 3)]
+    out = []
+    for p in range(48):
+        n, k, c0 = kinds[p % 4]
+        nl = 1
+        while c0 << (nl - 1) < n:
+            nl += 1
+        out.append((k, workloads.widths_random(c0, 3, 1000 + p), nl))
+    return out
+
+
+def run_batch(tpss, workloads, perf, torch, steps):
+    import numpy as np
+    specs = batch_specs(workloads)
+    nrhs = 4
+    side = torch.cuda.Stream()
+    out = {"workload": "48 independent 3D Poisson problems, 12 each of (16^3,k=7), (24^3,k=5), (32^3,k=3), "
+                       "(48^3,k=2), random widths, 4 RHS each U[-1,1]; AVS omega 1/8; FP32 V-cycle with one "
+                       "persistent smoother launch per level, CUDA graph, autotuned patches per work item, "
+                       "FP64 flexible PCG to 1e-8"}
+    with torch.cuda.stream(side):
+        t0 = time.perf_counter()
+        B = tpss.Batch(specs, nrhs=nrhs, omega=0.125, stream=side)
+        torch.cuda.synchronize()
+        out["setup_s"] = time.perf_counter() - t0
+        out["uses_graph"] = B.uses_graph
+        out["ppb"] = {str(specs[p][0]): B.info(p)["ppb"] for p in range(4)}
+        b = np.empty(B.total)
+        ndofs = []
+        for p in range(48):
+            info = B.info(p)
+            ndofs.append(info["ndofs"])
+            for r in range(nrhs):
+                o = info["offset"] + r * info["ndofs"]
+                b[o:o + info["ndofs"]] = workloads.rhs_uniform(info["ndofs"], 2000 + 4 * p + r)
+        out["total_dofs"] = int(sum(ndofs))
+        b32 = torch.from_numpy(b).to("cuda", torch.float32)
+        x32 = torch.empty_like(b32)
+        for _ in range(3):
+            B.smooth_additive(b32, x32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(steps):
+            B.smooth_additive(b32, x32)
+        e1.record(side)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        byt = 8.0 * B.total
+        peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm = json.load(open(peaks)).get("hbm_gbs", 6800.0) if os.path.exists(peaks) else 6800.0
+        out["smoother"] = {"dofs_per_s": B.total / (ms / 1e3), "ms_per_call": ms, "launches_per_call": 1,
+                           "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
+        bd = torch.from_numpy(b).to("cuda")
+        x = torch.empty_like(bd)
+        e0.record(side)
+        res = B.pcg_solve(bd, x, rtol=1e-8, maxit=100)
+        e1.record(side)
+        torch.cuda.synchronize()
+        out["pcg"] = {"time_s": e0.elapsed_time(e1) / 1e3, "converged": bool(res["converged"]),
+                      "iters_max": int(res["iters"].max()), "iters_mean": float(res["iters"].mean()),
+                      "rel_res_max": float(res["rel_res"].max())}
+        B.close()
+        # one-at-a-time FP64 on the same problems (first right-hand side of each, x 4)
+        t_fp64, its = 0.0, []
+        for p, (k, widths, nl) in enumerate(specs):
+            prob = tpss.Problem(3, k, widths, nlevels=nl, stream=side)
+            prob.mg_setup("AVS", 0.125, tpss.FP64)
+            n = prob.ndofs(nl - 1)
+            bp = torch.from_numpy(workloads.rhs_uniform(n, 2000 + 4 * p)).to("cuda")
+            xp = torch.empty_like(bp)
+            torch.cuda.synchronize()
+            e0.record(side)
+            r = prob.pcg_solve(bp, xp, rtol=1e-8, maxit=100)
+            e1.record(side)
+            torch.cuda.synchronize()
+            t_fp64 += e0.elapsed_time(e1) / 1e3
+            its.append(r["iters"])
+            prob.close()
+        out["one_at_a_time_fp64"] = {"time_s": t_fp64 * nrhs, "measured": "48 problems x 1 RHS, times 4",
+                                     "iters_max": int(max(its)), "iters_mean": float(np.mean(its))}
+        out["speedup_time_to_solution"] = out["one_at_a_time_fp64"]["time_s"] / out["pcg"]["time_s"]
     return out
 
 

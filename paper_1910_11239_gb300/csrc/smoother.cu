@@ -213,6 +213,11 @@ template <typename T>
 tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs, const T* r, T* x,
                        cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (P->precision == TPSS_BF16 && P->ctx->dim == 3) {
+      const tpss_status st = patch_pass_bf16(P, list, count, (float)omega, nrhs, reinterpret_cast<const float*>(r),
+                                             reinterpret_cast<float*>(x), s);
+      if (st != TPSS_EINVAL) return st;   // else: shape not covered, use the generic tensor-core kernel
+    }
     if (P->precision == TPSS_TF32 || P->precision == TPSS_BF16)
       return patch_pass_tc(P, list, count, (float)omega, nrhs, reinterpret_cast<const float*>(r),
                            reinterpret_cast<float*>(x), s);

@@ -188,6 +188,10 @@ tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int
 tpss_status patch_pass_tc(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
                           float* x, cudaStream_t s);
 
+// ---- smoother_bf16.cu (3D BF16 tensor-core path; TPSS_EINVAL for uncovered shapes)
+tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
+                            float* x, cudaStream_t s);
+
 // ---- transfer.cu
 template <typename T>
 tpss_status prolongate_add_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* coarse, T* fine);
