@@ -456,17 +456,53 @@ def batch_specs(workloads):
 
 
 def run_batch(tpss, workloads, perf, torch, steps):
+    """Config 5 for both persistent smoother variants (FP32 SIMT and BF16
+    tensor cores), then the same problems one at a time in FP64."""
     import numpy as np
-    specs = batch_specs(workloads)
-    nrhs = 4
-    side = torch.cuda.Stream()
     out = {"workload": "48 independent 3D Poisson problems, 12 each of (16^3,k=7), (24^3,k=5), (32^3,k=3), "
                        "(48^3,k=2), random widths, 4 RHS each U[-1,1]; AVS omega 1/8; FP32 V-cycle with one "
                        "persistent smoother launch per level, CUDA graph, autotuned patches per work item, "
                        "FP64 flexible PCG to 1e-8"}
+    for prec in ("bf16", "fp32"):
+        out[prec] = run_batch_one(tpss, workloads, torch, steps, prec)
+    specs = batch_specs(workloads)
+    side = torch.cuda.Stream()
+    nrhs = 4
+    with torch.cuda.stream(side):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # one-at-a-time FP64 on the same problems (first right-hand side of each, x 4)
+        t_fp64, its = 0.0, []
+        for p, (k, widths, nl) in enumerate(specs):
+            prob = tpss.Problem(3, k, widths, nlevels=nl, stream=side)
+            prob.mg_setup("AVS", 0.125, tpss.FP64)
+            n = prob.ndofs(nl - 1)
+            bp = torch.from_numpy(workloads.rhs_uniform(n, 2000 + 4 * p)).to("cuda")
+            xp = torch.empty_like(bp)
+            torch.cuda.synchronize()
+            e0.record(side)
+            r = prob.pcg_solve(bp, xp, rtol=1e-8, maxit=100)
+            e1.record(side)
+            torch.cuda.synchronize()
+            t_fp64 += e0.elapsed_time(e1) / 1e3
+            its.append(r["iters"])
+            prob.close()
+        out["one_at_a_time_fp64"] = {"time_s": t_fp64 * nrhs, "measured": "48 problems x 1 RHS, times 4",
+                                     "iters_max": int(max(its)), "iters_mean": float(np.mean(its))}
+    for prec in ("bf16", "fp32"):
+        out[prec]["speedup_time_to_solution_vs_fp64_one_at_a_time"] = (
+            out["one_at_a_time_fp64"]["time_s"] / out[prec]["pcg"]["time_s"])
+    return out
+
+
+def run_batch_one(tpss, workloads, torch, steps, prec):
+    import numpy as np
+    specs = batch_specs(workloads)
+    nrhs = 4
+    side = torch.cuda.Stream()
+    out = {"precision": prec}
     with torch.cuda.stream(side):
         t0 = time.perf_counter()
-        B = tpss.Batch(specs, nrhs=nrhs, omega=0.125, stream=side)
+        B = tpss.Batch(specs, nrhs=nrhs, omega=0.125, stream=side, precision=tpss.PRECISIONS[prec])
         torch.cuda.synchronize()
         out["setup_s"] = time.perf_counter() - t0
         out["uses_graph"] = B.uses_graph
@@ -507,25 +543,6 @@ def run_batch(tpss, workloads, perf, torch, steps):
                       "iters_max": int(res["iters"].max()), "iters_mean": float(res["iters"].mean()),
                       "rel_res_max": float(res["rel_res"].max())}
         B.close()
-        # one-at-a-time FP64 on the same problems (first right-hand side of each, x 4)
-        t_fp64, its = 0.0, []
-        for p, (k, widths, nl) in enumerate(specs):
-            prob = tpss.Problem(3, k, widths, nlevels=nl, stream=side)
-            prob.mg_setup("AVS", 0.125, tpss.FP64)
-            n = prob.ndofs(nl - 1)
-            bp = torch.from_numpy(workloads.rhs_uniform(n, 2000 + 4 * p)).to("cuda")
-            xp = torch.empty_like(bp)
-            torch.cuda.synchronize()
-            e0.record(side)
-            r = prob.pcg_solve(bp, xp, rtol=1e-8, maxit=100)
-            e1.record(side)
-            torch.cuda.synchronize()
-            t_fp64 += e0.elapsed_time(e1) / 1e3
-            its.append(r["iters"])
-            prob.close()
-        out["one_at_a_time_fp64"] = {"time_s": t_fp64 * nrhs, "measured": "48 problems x 1 RHS, times 4",
-                                     "iters_max": int(max(its)), "iters_mean": float(np.mean(its))}
-        out["speedup_time_to_solution"] = out["one_at_a_time_fp64"]["time_s"] / out["pcg"]["time_s"]
     return out
 
 

@@ -226,7 +226,8 @@ tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rto
  * Many independent 3D problems of uneven size and degree (not in the paper):
  * every problem gets its own hierarchy (descs[p], additive vertex-patch
  * smoother with params->omega) and nrhs right-hand sides.  The V-cycle runs in
- * FP32 (FP32 mode contractions, FP32 operators and transfers, FP64 coarse
+ * FP32 (mode contractions in FP32, or on BF16 tensor cores when
+ * params->precision == TPSS_BF16; FP32 operators and transfers; FP64 coarse
  * inverse) with levels aligned from the finest one; at every level ONE
  * persistent kernel smooths all problems and right-hand sides, pulling work
  * items (problem, rhs, group of patches) from an atomic counter, largest

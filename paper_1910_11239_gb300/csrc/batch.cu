@@ -19,6 +19,7 @@
 #include <cmath>
 #include <numeric>
 
+#include "bf16_tc.cuh"
 #include "tpss_internal.cuh"
 
 namespace tpss {
@@ -216,6 +217,92 @@ batch_smooth_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __
   }
 }
 
+// BF16 tensor-core variant of a work item: `count` patches of one problem and
+// right-hand side, one after another, each with the MMA routines of
+// bf16_tc.cuh; the scatter uses FP32 atomics as in the FP32 variant.
+template <int N>
+__device__ void batch_group_bf16(const BatchLevelDesc& D, const BatchItem& it, float omega, __nv_bfloat16* T,
+                                 float* lam) {
+  using S = bf::Shape<N>;
+  constexpr int N1 = N / 2;
+  constexpr int NLOC1 = N1 * N1 * N1;
+  constexpr int NV = 8 * NLOC1;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int64_t vbase = (int64_t)it.rhs * D.ndofs;
+  auto toff = [&](int e) -> int {
+    const int c = e / NLOC1, loc = e % NLOC1;
+    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
+    const int ix = loc % N1, iy = (loc / N1) % N1, iz = loc / (N1 * N1);
+    return (sx * N1 + ix) + bf::LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
+  };
+  __syncthreads();   // the previous item is done with T
+  for (int e = tid; e < S::TOTAL; e += blockDim.x) T[e] = __float2bfloat16(0.f);
+  for (int c = 0; c < it.count; ++c) {
+    const int packed = D.list[it.first + c];
+    const int px = unpack_x(packed), py = unpack_y(packed), pz = unpack_z(packed);
+    __syncthreads();   // zero fill done / previous patch scattered
+    if (tid < 3 * N) {
+      const int d = tid / N, i = tid % N;
+      lam[tid] = D.lam[d][(size_t)(d == 0 ? px : (d == 1 ? py : pz)) * N + i];
+    }
+    for (int e = tid; e < NV; e += blockDim.x) {
+      const int cc = e / NLOC1, loc = e % NLOC1;
+      const int64_t g = (px + (cc & 1)) + (int64_t)D.nc0 * ((py + ((cc >> 1) & 1)) + (int64_t)D.nc1 * (pz + ((cc >> 2) & 1)));
+      T[toff(e)] = __float2bfloat16(__ldg(D.r + vbase + g * NLOC1 + loc));
+    }
+    uint32_t bx[2][2], bxt[2][2], by[2][2], byt[2][2], bzz[2][2], bzt[2][2];
+    bf::load_bfrag<N, false>(bxt, D.Z[0] + (size_t)px * N * N, lane);
+    bf::load_bfrag<N, true>(bx, D.Z[0] + (size_t)px * N * N, lane);
+    bf::load_bfrag<N, false>(byt, D.Z[1] + (size_t)py * N * N, lane);
+    bf::load_bfrag<N, true>(by, D.Z[1] + (size_t)py * N * N, lane);
+    bf::load_bfrag<N, false>(bzt, D.Z[2] + (size_t)pz * N * N, lane);
+    bf::load_bfrag<N, true>(bzz, D.Z[2] + (size_t)pz * N * N, lane);
+    __syncthreads();
+    bf::contract<N, 0>(T, bxt, warp, lane);
+    __syncthreads();
+    bf::contract<N, 1>(T, byt, warp, lane);
+    __syncthreads();
+    bf::zstep<N>(T, bzt, bzz, lam, warp, lane);
+    __syncthreads();
+    bf::contract<N, 1>(T, by, warp, lane);
+    __syncthreads();
+    bf::contract<N, 0>(T, bx, warp, lane);
+    __syncthreads();
+    for (int e = tid; e < NV; e += blockDim.x) {
+      const int cc = e / NLOC1, loc = e % NLOC1;
+      const int64_t g = (px + (cc & 1)) + (int64_t)D.nc0 * ((py + ((cc >> 1) & 1)) + (int64_t)D.nc1 * (pz + ((cc >> 2) & 1)));
+      atomicAdd(D.x + vbase + g * NLOC1 + loc, omega * __bfloat162float(T[toff(e)]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+batch_smooth_bf16_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __restrict__ items, int nitems,
+                         int* __restrict__ counter, float omega) {
+  __shared__ __align__(16) __nv_bfloat16 T[bf::Shape<16>::TOTAL];
+  __shared__ float lam[3 * 16];
+  __shared__ int cur;
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int i = cur;
+    __syncthreads();
+    if (i >= nitems) break;
+    const BatchItem it = items[i];
+    const BatchLevelDesc D = desc[it.prob];
+    switch (D.n) {
+      case 4: batch_group_bf16<4>(D, it, omega, T, lam); break;
+      case 6: batch_group_bf16<6>(D, it, omega, T, lam); break;
+      case 8: batch_group_bf16<8>(D, it, omega, T, lam); break;
+      case 10: batch_group_bf16<10>(D, it, omega, T, lam); break;
+      case 12: batch_group_bf16<12>(D, it, omega, T, lam); break;
+      case 14: batch_group_bf16<14>(D, it, omega, T, lam); break;
+      case 16: batch_group_bf16<16>(D, it, omega, T, lam); break;
+      default: break;
+    }
+  }
+}
+
 // y_r = Ainv b_r for nrhs vectors (FP64 inverse, FP32 vectors), one warp per row
 __global__ void batch_dense_mv_kernel(const double* __restrict__ A, const float* __restrict__ b, float* __restrict__ y,
                                       int64_t n) {
@@ -345,6 +432,7 @@ struct tpss_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int use_graph = 1;
+  int bf16 = 0;                       // 1: BF16 tensor-core persistent smoother
   // CG state (FP64, concatenated)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr;
   int64_t* d_off = nullptr;
@@ -375,7 +463,7 @@ static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>&
     if (only_n && n != only_n) continue;
     const int g = ppb_override ? ppb_override : B->ppb[n];
     const int total = (int)P->nsub;
-    smem_bytes = std::max(smem_bytes, (size_t)g * bshape_slot(n) * sizeof(float));
+    if (!B->bf16) smem_bytes = std::max(smem_bytes, (size_t)g * bshape_slot(n) * sizeof(float));
     for (int r = 0; r < B->nrhs; ++r)
       for (int f = 0; f < total; f += g) {
         const int cnt = std::min(g, total - f);
@@ -389,7 +477,10 @@ static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>&
 
 static tpss_status grid_size(tpss_batch* B, int nitems, size_t smem, int* grid) {
   int per_sm = 0;
-  TPSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_smooth_kernel, kBatchThreads, smem));
+  if (B->bf16)
+    TPSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_smooth_bf16_kernel, kBatchThreads, 0));
+  else
+    TPSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_smooth_kernel, kBatchThreads, smem));
   if (per_sm < 1) {
     set_error("batch smoother: work item does not fit on an SM");
     return TPSS_EINVAL;
@@ -402,7 +493,10 @@ static tpss_status launch_level(tpss_batch* B, const BatchLevelDesc* desc, const
                                 size_t smem, int grid, int* counter, cudaStream_t s) {
   if (nitems == 0) return TPSS_OK;
   TPSS_CHECK_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
-  batch_smooth_kernel<<<grid, kBatchThreads, smem, s>>>(desc, items, nitems, counter, B->omega);
+  if (B->bf16)
+    batch_smooth_bf16_kernel<<<grid, kBatchThreads, 0, s>>>(desc, items, nitems, counter, B->omega);
+  else
+    batch_smooth_kernel<<<grid, kBatchThreads, smem, s>>>(desc, items, nitems, counter, B->omega);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
@@ -491,7 +585,8 @@ static tpss_status batch_vcycle(tpss_batch* B) {
 
 static tpss_status autotune(tpss_batch* B) {
   // time each candidate group size on the finest-level items of each degree
-  const int cands[] = {1, 2, 3, 4, 6, 8};
+  const int cands_simt[] = {1, 2, 3, 4, 6, 8};
+  const int cands_bf16[] = {1, 2, 4, 8, 16, 32};
   cudaEvent_t e0, e1;
   TPSS_CHECK_CUDA(cudaEventCreate(&e0));
   TPSS_CHECK_CUDA(cudaEventCreate(&e1));
@@ -503,9 +598,10 @@ static tpss_status autotune(tpss_batch* B) {
   for (int n : ns) {
     double best = 1e30;
     int bestg = 1;
-    for (int g : cands) {
-      if ((size_t)g * bshape_slot(n) * sizeof(float) > 100 * 1024) continue;
-      if (g * n * n > 4 * kBatchThreads) continue;
+    for (int ci = 0; ci < 6; ++ci) {
+      const int g = B->bf16 ? cands_bf16[ci] : cands_simt[ci];
+      if (!B->bf16 && (size_t)g * bshape_slot(n) * sizeof(float) > 100 * 1024) continue;
+      if (!B->bf16 && g * n * n > 4 * kBatchThreads) continue;
       std::vector<BatchItem> items;
       size_t smem = 0;
       build_items(B, 0, items, smem, n, g);
@@ -586,6 +682,7 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
   B->omega = (float)params->omega;
   B->flexible = 1;
   B->use_graph = (flags & 1) ? 0 : 1;
+  B->bf16 = params->precision == TPSS_BF16 ? 1 : 0;
   B->stream = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -598,7 +695,7 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
     return s;
   };
   tpss_mg_params mp = *params;
-  mp.precision = TPSS_FP32;
+  mp.precision = B->bf16 ? TPSS_BF16 : TPSS_FP32;
   B->probs.resize(nprob);
   for (int p = 0; p < nprob; ++p) {
     BatchProb& bp = B->probs[p];
@@ -643,7 +740,7 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
     if ((st = dalloc_t(&B->d_desc_post[d], nprob)) != TPSS_OK) return fail(st);
     if ((st = set_descs(B, d)) != TPSS_OK) return fail(st);
   }
-  for (int n = 0; n <= 16; ++n) B->ppb[n] = std::max(1, 256 / std::max(1, n * n));
+  for (int n = 0; n <= 16; ++n) B->ppb[n] = B->bf16 ? 4 : std::max(1, 256 / std::max(1, n * n));
   cudaFuncSetAttribute(batch_smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024 + 1024);
   cudaMemsetAsync(B->fb, 0, B->total * sizeof(float), B->stream);
   cudaMemsetAsync(B->fx, 0, B->total * sizeof(float), B->stream);

@@ -28,7 +28,9 @@ struct PatchShape {
   static constexpr int PS = LS * N;
   static constexpr int VOL = DIM == 3 ? PS * N : LS * N;
   static constexpr int VOLC = DIM == 3 ? N * N * N : N * N;
-  static constexpr int PPB = (256 + LINES / 2) / LINES > 0 ? (256 + LINES / 2) / LINES : 1;
+  // subdomains per CTA: about 256 threads, except n = 14 (196 lines: one
+  // subdomain would leave 12.5% of the lanes of its last warp idle)
+  static constexpr int PPB = LINES == 196 ? 2 : ((256 + LINES / 2) / LINES > 0 ? (256 + LINES / 2) / LINES : 1);
   static constexpr int THREADS = PPB * LINES;
 };
 

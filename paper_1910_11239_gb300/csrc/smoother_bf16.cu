@@ -15,166 +15,56 @@
 // padded) is held in registers as B fragments for the whole subdomain.  The
 // z-step Z^T -> Lambda^{-1} -> Z is chained in registers: the FP32
 // accumulator of the first MMA, scaled, is the A fragment of the second.  The
-// gather of the next right-hand side is issued into registers before the
-// contractions of the current one.
-#include <cuda_bf16.h>
-
-#include "tpss_internal.cuh"
+// right-hand side and x of the next system are staged into shared memory with
+// cp.async while the current one is contracted (double-buffered x), so the
+// final x = x_old + omega y is written without a dependent global load.
+#include "bf16_tc.cuh"
 
 namespace tpss {
 
 namespace bf {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int LS = 24;
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int N>
-struct Shape {
-  static constexpr int PS = LS * N + 8;          // (LS N)/8 = 3N is even for even N: +8 makes it odd
-  static constexpr int VOL = PS * N;             // bf16 elements of the tensor
-  static constexpr int ZROW = VOL;               // 8 zero elements (16 B)
-  static constexpr int DROW = VOL + 8;           // 8 dummy elements (discarded stores)
-  static constexpr int TOTAL = VOL + 16;
+// Stage the 2^d cells of one right-hand side (cell-major, NV floats) into
+// shared memory with asynchronous copies (16 bytes when cells are 16-byte
+// multiples, else 4 bytes).
+struct CellBase {
+  int px, py, pz, nc0, nc1;
+  // first DoF of the patch's cell c (c = sx + 2 sy + 4 sz)
+  template <int NLOC1>
+  __device__ __forceinline__ int64_t operator()(int c) const {
+    return ((px + (c & 1)) + (int64_t)nc0 * ((py + ((c >> 1) & 1)) + (int64_t)nc1 * (pz + ((c >> 2) & 1)))) * NLOC1;
+  }
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
-}
-__device__ __forceinline__ void stsm_x4(uint32_t addr, const uint32_t (&r)[4]) {
-  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};"
-               :: "r"(addr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
-}
-__device__ __forceinline__ void stsm_x4_t(uint32_t addr, const uint32_t (&r)[4]) {
-  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};"
-               :: "r"(addr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
-}
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// B fragments of W (k x i, 16 x 16, zero padded) for the two 8-column tiles:
-// b[nt][0] = (W[2t][8nt+g], W[2t+1][8nt+g]), b[nt][1] = (W[2t+8][..], W[2t+9][..]).
-// TRANSPOSE = false: W[k][i] = Z[k][i] (applies Z^T); true: W[k][i] = Z[i][k] (applies Z).
-template <int N, bool TRANSPOSE>
-__device__ __forceinline__ void load_bfrag(uint32_t (&b)[2][2], const float* __restrict__ Z, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  auto w = [&](int k, int i) -> float {
-    if (k >= N || i >= N) return 0.f;
-    return TRANSPOSE ? __ldg(Z + i * N + k) : __ldg(Z + k * N + i);
-  };
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    const int i = 8 * nt + g;
-    b[nt][0] = pack2(w(2 * t, i), w(2 * t + 1, i));
-    b[nt][1] = pack2(w(2 * t + 8, i), w(2 * t + 9, i));
-  }
-}
-
-// One contraction along DIR for all tiles of the subdomain (warps stride over tiles).
-template <int N, int DIR>
-__device__ __forceinline__ void contract(__nv_bfloat16* T, const uint32_t (&b)[2][2], int warp, int lane) {
-  using S = Shape<N>;
-  const uint32_t base = smem_u32(T);
-  const int j = lane >> 3, q = lane & 7;          // ldmatrix / stmatrix: matrix j, row q
-  constexpr int TILES = DIR == 0 ? (N * N + 15) / 16 : N;
-  for (int tile = warp; tile < TILES; tile += kWarps) {
-    uint32_t a[4];
-    if (DIR == 0) {
-      const int line = tile * 16 + (j & 1) * 8 + q;
-      const int off = line < N * N ? (LS * (line % N) + S::PS * (line / N) + 8 * (j >> 1)) : S::ZROW;
-      ldsm_x4(a, base + 2u * off);
-    } else {
-      const int k = 8 * (j >> 1) + q;               // contraction index (memory row)
-      const int x0 = 8 * (j & 1);
-      int off;
-      if (k >= N) off = S::ZROW;
-      else off = DIR == 1 ? (x0 + LS * k + S::PS * tile) : (x0 + LS * tile + S::PS * k);
-      ldsm_x4_t(a, base + 2u * off);
+template <int NLOC1, int NCELL>
+__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, const CellBase& cb, int tid) {
+  const uint32_t d = smem_u32(dst);
+  if constexpr (NLOC1 % 4 == 0) {
+    constexpr int CH = NLOC1 / 4;
+    for (int e = tid; e < NCELL * CH; e += kThreads) {
+      const int c = e / CH, o = (e % CH) * 4;
+      cp_async16(d + 4u * (c * NLOC1 + o), src + cb.template operator()<NLOC1>(c) + o);
     }
-    float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    mma16816(c[0], a, b[0][0], b[0][1]);
-    mma16816(c[1], a, b[1][0], b[1][1]);
-    uint32_t r[4];
-    // matrix jj = (row half jj&1, column half jj>>1) of the 16 x 16 result
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) r[jj] = pack2(c[jj >> 1][(jj & 1) * 2], c[jj >> 1][(jj & 1) * 2 + 1]);
-    if (DIR == 0) {
-      const int line = tile * 16 + (j & 1) * 8 + q;
-      const int off = line < N * N ? (LS * (line % N) + S::PS * (line / N) + 8 * (j >> 1)) : S::DROW;
-      stsm_x4(base + 2u * off, r);
-    } else {
-      const int i = 8 * (j >> 1) + q;                // output index (memory row)
-      const int x0 = 8 * (j & 1);
-      int off;
-      if (i >= N) off = S::DROW;
-      else off = DIR == 1 ? (x0 + LS * i + S::PS * tile) : (x0 + LS * tile + S::PS * i);
-      stsm_x4_t(base + 2u * off, r);
+  } else {
+    for (int e = tid; e < NCELL * NLOC1; e += kThreads) {
+      const int c = e / NLOC1, o = e % NLOC1;
+      cp_async4(d + 4u * (c * NLOC1 + o), src + cb.template operator()<NLOC1>(c) + o);
     }
   }
 }
 
-// z-step: Z^T along z, scale by 1/(lx + ly + lz), Z along z, chained in registers.
-template <int N>
-__device__ __forceinline__ void zstep(__nv_bfloat16* T, const uint32_t (&bt)[2][2], const uint32_t (&bz)[2][2],
-                                      const float* __restrict__ lam, int warp, int lane) {
-  using S = Shape<N>;
-  const uint32_t base = smem_u32(T);
-  const int j = lane >> 3, q = lane & 7;
-  const int g = lane >> 2, t = lane & 3;
-  for (int tile = warp; tile < N; tile += kWarps) {   // tile = y
-    uint32_t a[4];
-    {
-      const int k = 8 * (j >> 1) + q, x0 = 8 * (j & 1);
-      const int off = k >= N ? S::ZROW : (x0 + LS * tile + S::PS * k);
-      ldsm_x4_t(a, base + 2u * off);
-    }
-    float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    mma16816(c[0], a, bt[0][0], bt[0][1]);
-    mma16816(c[1], a, bt[1][0], bt[1][1]);
-    // rows x = g, g+8; columns i = 8 nt + 2t, +1
-    const float ly = lam[N + tile];
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int x = g + (e >> 1) * 8, i = 8 * nt + 2 * t + (e & 1);
-        c[nt][e] = (x < N && i < N) ? c[nt][e] / (lam[x] + ly + lam[2 * N + i]) : 0.f;
-      }
-    // accumulator layout of m16n8k16 == A-fragment layout for K = 16
-    uint32_t a2[4] = {pack2(c[0][0], c[0][1]), pack2(c[0][2], c[0][3]), pack2(c[1][0], c[1][1]),
-                      pack2(c[1][2], c[1][3])};
-    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    mma16816(d[0], a2, bz[0][0], bz[0][1]);
-    mma16816(d[1], a2, bz[1][0], bz[1][1]);
-    uint32_t r[4];
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) r[jj] = pack2(d[jj >> 1][(jj & 1) * 2], d[jj >> 1][(jj & 1) * 2 + 1]);
-    const int i = 8 * (j >> 1) + q, x0 = 8 * (j & 1);
-    const int off = i >= N ? S::DROW : (x0 + LS * tile + S::PS * i);
-    stsm_x4_t(base + 2u * off, r);
-  }
-}
-
+// Dynamic shared memory: [T: Shape<N>::TOTAL bf16][SB: NV f32][SX: 2 x NV f32]
 template <int N, bool VERTEX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__ Z0, const float* __restrict__ Z1,
                          const float* __restrict__ Z2, const float* __restrict__ L0, const float* __restrict__ L1,
                          const float* __restrict__ L2, const float* __restrict__ r, float* __restrict__ x, float omega,
@@ -183,13 +73,20 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
   constexpr int N1 = VERTEX ? N / 2 : N;
   constexpr int NLOC1 = N1 * N1 * N1;
   constexpr int NCELL = VERTEX ? 8 : 1;
-  constexpr int NV = NCELL * NLOC1;                       // values gathered per rhs
-  constexpr int PER = (NV + kThreads - 1) / kThreads;     // per thread
-  __shared__ __align__(16) __nv_bfloat16 T[S::TOTAL];
+  constexpr int NV = NCELL * NLOC1;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __nv_bfloat16* T = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float* SB = reinterpret_cast<float*>(dsm + ((S::TOTAL * 2 + 15) / 16) * 16);
+  float* SX = SB + NV;   // two buffers of NV
   __shared__ float lam[3 * N];
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int packed = list[blockIdx.x];
   const int px = unpack_x(packed), py = unpack_y(packed), pz = unpack_z(packed);
+  const CellBase cbase{px, py, pz, nc0, nc1};
+  // first right-hand side: b -> SB, x -> SX[0]
+  stage<NLOC1, NCELL>(SB, r, cbase, tid);
+  stage<NLOC1, NCELL>(SX, x, cbase, tid);
+  cp_async_commit();
   for (int e = tid; e < S::TOTAL; e += kThreads) T[e] = __float2bfloat16(0.f);
   if (tid < 3 * N) {
     const int d = tid / N, i = tid % N;
@@ -204,40 +101,22 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
   load_bfrag<N, true>(by, Z1 + (size_t)py * N * N, lane);
   load_bfrag<N, false>(bzt, Z2 + (size_t)pz * N * N, lane);
   load_bfrag<N, true>(bzz, Z2 + (size_t)pz * N * N, lane);
-  // element e of the gather: global offset (relative to the rhs base) and tensor offset
-  auto goff = [&](int e) -> int64_t {
-    const int c = e / NLOC1, loc = e % NLOC1;
-    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
-    const int64_t gcell = (px + sx) + (int64_t)nc0 * ((py + sy) + (int64_t)nc1 * (pz + sz));
-    return gcell * NLOC1 + loc;
-  };
   auto toff = [&](int e) -> int {
     const int c = e / NLOC1, loc = e % NLOC1;
     const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
     const int ix = loc % N1, iy = (loc / N1) % N1, iz = loc / (N1 * N1);
     return (sx * N1 + ix) + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
   };
-  float pre[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int e = tid + u * kThreads;
-    pre[u] = e < NV ? __ldg(r + goff(e)) : 0.f;
-  }
   for (int rhs = 0; rhs < nrhs; ++rhs) {
-    __syncthreads();   // previous scatter finished reading T; zero fill done
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + u * kThreads;
-      if (e < NV) T[toff(e)] = __float2bfloat16(pre[u]);
-    }
-    __syncthreads();
-    if (rhs + 1 < nrhs) {
-      const float* rn = r + (int64_t)(rhs + 1) * ndofs;
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int e = tid + u * kThreads;
-        pre[u] = e < NV ? __ldg(rn + goff(e)) : 0.f;
-      }
+    float* sx_cur = SX + (rhs & 1) * NV;
+    cp_async_wait_all();
+    __syncthreads();   // staged data visible; previous scatter done with T and the other SX buffer
+    for (int e = tid; e < NV; e += kThreads) T[toff(e)] = __float2bfloat16(SB[e]);
+    __syncthreads();   // SB consumed
+    if (rhs + 1 < nrhs) {   // prefetch the next right-hand side and its x while computing this one
+      stage<NLOC1, NCELL>(SB, r + (int64_t)(rhs + 1) * ndofs, cbase, tid);
+      stage<NLOC1, NCELL>(SX + ((rhs + 1) & 1) * NV, x + (int64_t)(rhs + 1) * ndofs, cbase, tid);
+      cp_async_commit();
     }
     contract<N, 0>(T, bxt, warp, lane);
     __syncthreads();
@@ -250,23 +129,33 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
     contract<N, 0>(T, bx, warp, lane);
     __syncthreads();
     float* xr = x + (int64_t)rhs * ndofs;
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + u * kThreads;
-      if (e < NV) {
-        float* p = xr + goff(e);
-        *p = fmaf(omega, __bfloat162float(T[toff(e)]), *p);
-      }
+    for (int e = tid; e < NV; e += kThreads) {
+      const int c = e / NLOC1, loc = e % NLOC1;
+      xr[cbase.template operator()<NLOC1>(c) + loc] = fmaf(omega, __bfloat162float(T[toff(e)]), sx_cur[e]);
     }
   }
 }
 
 template <int N, bool VERTEX>
+constexpr size_t smem_bytes() {
+  constexpr int N1 = VERTEX ? N / 2 : N;
+  constexpr int NV = (VERTEX ? 8 : 1) * N1 * N1 * N1;
+  return ((Shape<N>::TOTAL * 2 + 15) / 16) * 16 + 3 * (size_t)NV * 4;
+}
+
+template <int N, bool VERTEX>
 static tpss_status launch(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
                           float* x, cudaStream_t s) {
+  constexpr size_t smem = smem_bytes<N, VERTEX>();
+  static bool attr = false;
+  if (!attr) {
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(patch_smooth_bf16_kernel<N, VERTEX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
   if (count <= 0) return TPSS_OK;
   const Level& L = P->ctx->levels[P->level];
-  patch_smooth_bf16_kernel<N, VERTEX><<<count, kThreads, 0, s>>>(
+  patch_smooth_bf16_kernel<N, VERTEX><<<count, kThreads, smem, s>>>(
       list, P->d_Z32[0], P->d_Z32[1], P->d_Z32[2], P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r, x, omega,
       L.nc[0], L.nc[1], L.ndofs, nrhs);
   TPSS_CHECK_LAUNCH();

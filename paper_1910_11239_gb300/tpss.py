@@ -285,7 +285,7 @@ class Batch:
     persistent smoother launch per level, optionally graph-captured."""
 
     def __init__(self, problems, nrhs, omega=0.125, use_graph=True, autotune=True, stream=None,
-                 gamma_hat=1.0, penalty_poly=PENALTY_PAPER):
+                 gamma_hat=1.0, penalty_poly=PENALTY_PAPER, precision=FP32):
         self._keep = []
         descs = (ProblemDesc * len(problems))()
         for i, (degree, widths, nlevels) in enumerate(problems):
@@ -297,7 +297,7 @@ class Batch:
                 d.ncells[t] = len(widths[t])
                 d.widths[t] = ctypes.cast(arrs[t], ctypes.POINTER(ctypes.c_double))
         p = MGParams()
-        p.smoother, p.omega, p.precision, p.mult_colors, p.flexible_cg = AVS, omega, FP32, 0, 1
+        p.smoother, p.omega, p.precision, p.mult_colors, p.flexible_cg = AVS, omega, precision, 0, 1
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = (0 if use_graph else 1) | (0 if autotune else 2)
         h = ctypes.c_void_p()

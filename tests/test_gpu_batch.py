@@ -33,10 +33,12 @@ def stream():
     return torch.cuda.Stream()
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_smoother_matches_per_problem_fp32(use_graph, stream):
+@pytest.mark.parametrize("use_graph,prec", [(True, "fp32"), (False, "fp32"), (True, "bf16")])
+def test_batch_smoother_matches_per_problem(use_graph, prec, stream):
+    tol = 1e-5 if prec == "fp32" else 2e-2
     with torch.cuda.stream(stream):
-        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, use_graph=use_graph, stream=stream)
+        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, use_graph=use_graph, stream=stream,
+                       precision=tpss.PRECISIONS[prec])
         assert B.uses_graph == use_graph
         b = rhs_for(B, 1)
         x = torch.empty(B.total, dtype=torch.float32, device="cuda")
@@ -45,13 +47,13 @@ def test_batch_smoother_matches_per_problem_fp32(use_graph, stream):
         for p, (k, widths, nl) in enumerate(problems()):
             info = B.info(p)
             prob = make(3, k, widths, nlevels=nl)
-            P = prob.setup_patches(nl - 1, tpss.VERTEX_PATCH, tpss.FP32)
+            P = prob.setup_patches(nl - 1, tpss.VERTEX_PATCH, tpss.PRECISIONS[prec])
             n = info["ndofs"]
             seg = slice(info["offset"], info["offset"] + 2 * n)
             xr = torch.empty(2 * n, dtype=torch.float32, device="cuda")
             P.smooth_additive(OMEGA, dev(b[seg], torch.float32), xr, x_is_zero=True, nrhs=2)
             torch.cuda.synchronize()
-            assert rel_err(x[seg].double(), xr.double().cpu().numpy()) < 1e-5
+            assert rel_err(x[seg].double(), xr.double().cpu().numpy()) < tol
             assert info["ppb"] >= 1
             prob.close()
         B.close()
@@ -86,9 +88,10 @@ def test_batch_vcycle_matches_per_problem_and_oracle(stream):
         B.close()
 
 
-def test_batch_pcg_converges_every_system(stream):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_pcg_converges_every_system(prec, stream):
     with torch.cuda.stream(stream):
-        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, stream=stream)
+        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec])
         b = rhs_for(B, 3)
         x = torch.empty(B.total, dtype=torch.float64, device="cuda")
         res = B.pcg_solve(dev(b), x, rtol=1e-8, maxit=80)
