@@ -36,10 +36,11 @@ CONFIG = {"workload": "3D additive vertex-patch Schwarz smoother (fast diagonali
                       "widths U[0.5,1.5]/32, omega 0.7, k=2..7, 8 RHS U[-1,1] batched, x=0 form",
           "cells": [NC, NC, NC], "degrees": KS, "nrhs": len(SEEDS),
           "l2": "inputs larger than L2 (each step streams >= 2.5 GB of vectors and tables)"}
-# DRAM traffic of one smoother call at k=7 (8 color launches), from the ncu
-# capture summarized in profiles/patch_smooth_fp64_32cubed.md; None when the
-# kernel changed after that capture.
-TRAFFIC_K7_PER_CALL = None
+# DRAM bytes (read + write) of one FP64 smoother call at k=7 (8 color
+# launches, 8 RHS) at the full 32^3 size, from the single-pass ncu capture
+# summarized in profiles/patch_smooth_fp64_32cubed.md; set to None when the
+# kernel changes after that capture.
+TRAFFIC_K7_PER_CALL = 30.98e9
 
 
 def parse():
@@ -51,6 +52,7 @@ def parse():
     p.add_argument("--no-mgcg", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-problems", type=int, default=48, help="use the first N problems of the batch (profiling)")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
     p.add_argument("--mixed", default="fp32,tf32,bf16", help="low-precision smoother variants to time")
@@ -190,9 +192,10 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- GPU arm
 def main():
-    global NC
+    global NC, BATCH_PROBLEMS
     args = parse()
     NC = args.nc
+    BATCH_PROBLEMS = args.batch_problems
     if NC != 32:
         CONFIG["cells"] = [NC, NC, NC]
         CONFIG["workload"] = CONFIG["workload"].replace("32^3", f"{NC}^3").replace("/32", f"/{NC}")
@@ -293,7 +296,9 @@ def main():
                 "frac": dom["frac_fp64_peak"],
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe; HBM is not binding)",
                 "per": "one smoother call = 8 color launches on 8 RHS",
-                "traffic": TRAFFIC_K7_PER_CALL if kdom == 7 else None}
+                "traffic": TRAFFIC_K7_PER_CALL if kdom == 7 else None,
+                "traffic_unit": "bytes per call (dram read + write, ncu)",
+                "algorithmic_bytes": perf.smoother_bytes((NC, NC, NC), kdom, nrhs=nr)}
 
     # end to end through the same call with host buffers (H2D + smooth + D2H)
     h2d = sum(bhost[k].numel() * 8 for k in ks)
@@ -441,6 +446,9 @@ def run_mgcg(tpss, workloads, torch, cases):
     return out
 
 
+BATCH_PROBLEMS = 48
+
+
 def batch_specs(workloads):
     """48 problems = 12 each of (16^3, k=7), (24^3, k=5), (32^3, k=3), (48^3, k=2):
     coarse widths U[0.5,1.5] h (seed 1000+p), bisected; 4 RHS U[-1,1] (seed 2000+4p+r)."""
@@ -452,7 +460,7 @@ def batch_specs(workloads):
         while c0 << (nl - 1) < n:
             nl += 1
         out.append((k, workloads.widths_random(c0, 3, 1000 + p), nl))
-    return out
+    return out[:BATCH_PROBLEMS]
 
 
 def run_batch(tpss, workloads, perf, torch, steps):
@@ -486,7 +494,8 @@ def run_batch(tpss, workloads, perf, torch, steps):
             t_fp64 += e0.elapsed_time(e1) / 1e3
             its.append(r["iters"])
             prob.close()
-        out["one_at_a_time_fp64"] = {"time_s": t_fp64 * nrhs, "measured": "48 problems x 1 RHS, times 4",
+        out["one_at_a_time_fp64"] = {"time_s": t_fp64 * nrhs,
+                                     "measured": f"{len(specs)} problems x 1 RHS, times 4",
                                      "iters_max": int(max(its)), "iters_mean": float(np.mean(its))}
     for prec in ("bf16", "fp32"):
         out[prec]["speedup_time_to_solution_vs_fp64_one_at_a_time"] = (
@@ -509,7 +518,7 @@ def run_batch_one(tpss, workloads, torch, steps, prec):
         out["ppb"] = {str(specs[p][0]): B.info(p)["ppb"] for p in range(4)}
         b = np.empty(B.total)
         ndofs = []
-        for p in range(48):
+        for p in range(len(specs)):
             info = B.info(p)
             ndofs.append(info["ndofs"])
             for r in range(nrhs):
