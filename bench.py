@@ -61,6 +61,24 @@ def parse():
     return p.parse_args()
 
 
+# --------------------------------------------------------------- ranks
+def reduce_max(value, world, device):
+    """Max over ranks of a host float (the timed region of the slowest rank);
+    identity on one rank.  Works with NCCL (device cuda) and gloo (cpu)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank_step, steps, world, max_ms):
+    """Whole-job throughput: units processed by all ranks / slowest rank's time."""
+    return units_per_rank_step * steps * world / (max_ms / 1e3)
+
+
 # ------------------------------------------------------------------ clocks
 def clocks_start(path):
     fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -276,12 +294,8 @@ def main():
         os.remove(clk_path)
     except OSError:
         pass
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = dofs_step * args.steps * world / (ms / 1e3)
+    ms = reduce_max(e0.elapsed_time(e1), world, "cuda")
+    value = aggregate_rate(dofs_step, args.steps, world, ms)
     per_k = {}
     for k in ks:
         kms = statistics.mean(kev[s][k][0].elapsed_time(kev[s][k][1]) for s in range(args.steps))
@@ -319,12 +333,8 @@ def main():
             xhost[k].copy_(xdev[k], non_blocking=True)
     f1.record()
     torch.cuda.synchronize()
-    ems = f0.elapsed_time(f1)
-    if world > 1:
-        t = torch.tensor([ems], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
-    e2e = {"value": dofs_step * args.steps * world / (ems / 1e3), "unit": "DoF/s",
+    ems = reduce_max(f0.elapsed_time(f1), world, "cuda")
+    e2e = {"value": aggregate_rate(dofs_step, args.steps, world, ems), "unit": "DoF/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     for k in ks:
         probs[k].close()
@@ -337,6 +347,9 @@ def main():
     mgcg = None
     if not args.no_mgcg:
         mgcg = run_mgcg(tpss, workloads, torch, MGCG_CASES)
+    paper_its = None
+    if not args.no_mgcg:
+        paper_its = run_paper_iterations(tpss, workloads, perf, torch)
     batch = None
     if not args.no_batch:
         batch = run_batch(tpss, workloads, perf, torch, args.steps)
@@ -364,6 +377,8 @@ def main():
             line["mg_cg"] = mgcg
         if batch is not None:
             line["batched"] = batch
+        if paper_its is not None:
+            line["paper_iterations"] = paper_its
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -447,6 +462,34 @@ def run_mgcg(tpss, workloads, torch, cases):
 
 
 BATCH_PROBLEMS = 48
+
+# Fractional iteration counts printed in the paper (tab:cubecp, tab:cubemvp),
+# 3D, level L = 3 (16^3 cells), Gaussian-bell solution; ACS with CG, MCS and
+# MVS with GMRES (here: CG with the symmetric color order).
+PAPER_NU = {("ACS", 3): 17.1, ("ACS", 7): 21.9, ("MCS", 3): 8.6, ("MCS", 7): 11.8, ("MVS", 3): 2.4, ("MVS", 7): 2.1}
+
+
+def run_paper_iterations(tpss, workloads, perf, torch):
+    """Residual-based fractional iterations on the paper's setup (unit cube,
+    T_0 = 2^3 cells, L = 3, Gaussian bells with boundary data, V-cycle(1,1),
+    rtol 1e-8), next to the paper's values.  Differences of setup: exact
+    coarse solve (paper: Chebyshev + ACS to 1e-8), CG with symmetric color
+    order for MCS/MVS (paper: GMRES), residual norm (paper: energy norm for CG)."""
+    out = {}
+    for k in (3, 7):
+        prob = tpss.Problem(3, k, workloads.widths_uniform(2, 3), nlevels=4)
+        N = prob.ndofs(3)
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(3, 1, b)
+        x = torch.empty_like(b)
+        for sm, omega in (("ACS", 0.7), ("MCS", 1.0), ("MVS", 1.0)):
+            prob.mg_setup(sm, omega, tpss.FP64)
+            res = prob.pcg_solve(b, x, rtol=1e-8, maxit=100, history=True)
+            out[f"{sm}_k{k}"] = {"iterations": res["iters"],
+                                 "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
+                                 "paper_nu_frac": PAPER_NU[(sm, k)]}
+        prob.close()
+    return out
 
 
 def batch_specs(workloads):

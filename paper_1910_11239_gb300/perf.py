@@ -73,3 +73,16 @@ def operator_flops(ncells, k, d=3, nrhs=1):
     else:
         per_cell = 2 * (4 * n1 ** 3 + 2 * 2 * n1 * 2 * n1)
     return num_cells(ncells) * per_cell * nrhs
+
+
+def fractional_iterations(hist, rtol):
+    """Fractional iteration count of Sec. 2.4:
+    nu_frac = nu - 1 + log(e_{nu-1} / tol) / log(e_{nu-1} / e_nu), tol = rtol e_0,
+    nu the first step with e_nu <= tol, here with e = residual norm (the
+    paper uses the energy norm of the error for CG)."""
+    import math
+    tol = rtol * hist[0]
+    for nu in range(1, len(hist)):
+        if hist[nu] <= tol:
+            return nu - 1 + math.log(hist[nu - 1] / tol) / math.log(hist[nu - 1] / hist[nu])
+    return float("nan")

@@ -37,3 +37,16 @@ def test_complexity_constants():
 
 def test_fp64_peak_is_derived_from_unit_counts():
     assert abs(perf.fp64_peak_flops() - 152 * 2 * 2 * 2.07e9) < 1
+
+
+def test_fractional_iterations_hand_values():
+    hist = [1.0, 0.1, 0.01, 1e-3, 1e-4]
+    assert abs(perf.fractional_iterations(hist, 10 ** -2.5) - 2.5) < 1e-12
+    assert abs(perf.fractional_iterations(hist, 1e-3) - 3.0) < 1e-12
+
+
+def test_fractional_iterations_agrees_with_oracle():
+    from oracle.multigrid import fractional_iterations as oracle_frac
+    hist = [3.0, 1.1, 0.2, 0.031, 0.004, 2e-4, 1.5e-5]
+    for rtol in [1e-2, 1e-3, 3e-5, 1e-5]:
+        assert abs(perf.fractional_iterations(hist, rtol) - oracle_frac(hist, rtol)) < 1e-12
