@@ -142,7 +142,7 @@ __device__ __forceinline__ void zstep(__nv_bfloat16* T, const uint32_t (&bt)[2][
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int x = g + (e >> 1) * 8, i = 8 * nt + 2 * t + (e & 1);
-        c[nt][e] = (x < N && i < N) ? c[nt][e] / (lam[x] + ly + lam[2 * N + i]) : 0.f;
+        c[nt][e] = (x < N && i < N) ? __fdividef(c[nt][e], lam[x] + ly + lam[2 * N + i]) : 0.f;
       }
     // accumulator layout of m16n8k16 == A-fragment layout for K = 16
     uint32_t a2[4] = {pack2(c[0][0], c[0][1]), pack2(c[0][2], c[0][3]), pack2(c[1][0], c[1][1]),

@@ -62,6 +62,86 @@ __device__ __forceinline__ void stage(float* dst, const float* __restrict__ src,
   }
 }
 
+// Row-wise copies: a "row" is the N1 values of one cell along x, contiguous
+// both in the staged cell-major buffers and in the patch tensor.  V = 4, 2 or
+// 1 values per vector access (N1 divisible by 4, by 2, or odd).
+template <int N1>
+struct RowVec {
+  static constexpr int V = (N1 % 4 == 0) ? 4 : ((N1 % 2 == 0) ? 2 : 1);
+};
+
+// SB (f32, cell-major) -> T (bf16 patch tensor), one cell row per iteration.
+template <int N, int N1, int NCELL>
+__device__ __forceinline__ void rows_to_tensor(__nv_bfloat16* __restrict__ T, const float* __restrict__ SB, int tid) {
+  using S = Shape<N>;
+  constexpr int V = RowVec<N1>::V;
+  constexpr int NROW = NCELL * N1 * N1;
+  for (int rw = tid; rw < NROW; rw += kThreads) {
+    const int c = rw / (N1 * N1), rr = rw % (N1 * N1);
+    const int iy = rr % N1, iz = rr / N1;
+    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
+    const float* src = SB + c * N1 * N1 * N1 + rr * N1;
+    __nv_bfloat16* dst = T + sx * N1 + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
+#pragma unroll
+    for (int v = 0; v < N1; v += V) {
+      if constexpr (V == 4) {
+        const float4 f = *reinterpret_cast<const float4*>(src + v);
+        uint2 o;
+        o.x = pack2(f.x, f.y);
+        o.y = pack2(f.z, f.w);
+        *reinterpret_cast<uint2*>(dst + v) = o;
+      } else if constexpr (V == 2) {
+        const float2 f = *reinterpret_cast<const float2*>(src + v);
+        *reinterpret_cast<uint32_t*>(dst + v) = pack2(f.x, f.y);
+      } else {
+        dst[v] = __float2bfloat16(src[v]);
+      }
+    }
+  }
+}
+
+// x[cell rows] = SX + omega T, one cell row per iteration.
+template <int N, int N1, int NCELL>
+__device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, const __nv_bfloat16* __restrict__ T,
+                                            const float* __restrict__ SX, float omega, const CellBase& cb, int tid) {
+  using S = Shape<N>;
+  constexpr int V = RowVec<N1>::V;
+  constexpr int NLOC1 = N1 * N1 * N1;
+  constexpr int NROW = NCELL * N1 * N1;
+  for (int rw = tid; rw < NROW; rw += kThreads) {
+    const int c = rw / (N1 * N1), rr = rw % (N1 * N1);
+    const int iy = rr % N1, iz = rr / N1;
+    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
+    const float* xo = SX + c * NLOC1 + rr * N1;
+    const __nv_bfloat16* t = T + sx * N1 + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
+    float* dst = xr + cb.template operator()<NLOC1>(c) + rr * N1;
+#pragma unroll
+    for (int v = 0; v < N1; v += V) {
+      if constexpr (V == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(xo + v);
+        const uint2 tb = *reinterpret_cast<const uint2*>(t + v);
+        const float2 t01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&tb.x));
+        const float2 t23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&tb.y));
+        float4 o;
+        o.x = fmaf(omega, t01.x, a.x);
+        o.y = fmaf(omega, t01.y, a.y);
+        o.z = fmaf(omega, t23.x, a.z);
+        o.w = fmaf(omega, t23.y, a.w);
+        *reinterpret_cast<float4*>(dst + v) = o;
+      } else if constexpr (V == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(xo + v);
+        const float2 tt = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(t + v));
+        float2 o;
+        o.x = fmaf(omega, tt.x, a.x);
+        o.y = fmaf(omega, tt.y, a.y);
+        *reinterpret_cast<float2*>(dst + v) = o;
+      } else {
+        dst[v] = fmaf(omega, __bfloat162float(t[v]), xo[v]);
+      }
+    }
+  }
+}
+
 // Dynamic shared memory: [T: Shape<N>::TOTAL bf16][SB: NV f32][SX: 2 x NV f32]
 template <int N, bool VERTEX>
 __global__ void __launch_bounds__(kThreads, 3)
@@ -101,17 +181,11 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
   load_bfrag<N, true>(by, Z1 + (size_t)py * N * N, lane);
   load_bfrag<N, false>(bzt, Z2 + (size_t)pz * N * N, lane);
   load_bfrag<N, true>(bzz, Z2 + (size_t)pz * N * N, lane);
-  auto toff = [&](int e) -> int {
-    const int c = e / NLOC1, loc = e % NLOC1;
-    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
-    const int ix = loc % N1, iy = (loc / N1) % N1, iz = loc / (N1 * N1);
-    return (sx * N1 + ix) + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
-  };
   for (int rhs = 0; rhs < nrhs; ++rhs) {
     float* sx_cur = SX + (rhs & 1) * NV;
     cp_async_wait_all();
     __syncthreads();   // staged data visible; previous scatter done with T and the other SX buffer
-    for (int e = tid; e < NV; e += kThreads) T[toff(e)] = __float2bfloat16(SB[e]);
+    rows_to_tensor<N, N1, NCELL>(T, SB, tid);
     __syncthreads();   // SB consumed
     if (rhs + 1 < nrhs) {   // prefetch the next right-hand side and its x while computing this one
       stage<NLOC1, NCELL>(SB, r + (int64_t)(rhs + 1) * ndofs, cbase, tid);
@@ -128,11 +202,7 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
     __syncthreads();
     contract<N, 0>(T, bx, warp, lane);
     __syncthreads();
-    float* xr = x + (int64_t)rhs * ndofs;
-    for (int e = tid; e < NV; e += kThreads) {
-      const int c = e / NLOC1, loc = e % NLOC1;
-      xr[cbase.template operator()<NLOC1>(c) + loc] = fmaf(omega, __bfloat162float(T[toff(e)]), sx_cur[e]);
-    }
+    tensor_to_x<N, N1, NCELL>(x + (int64_t)rhs * ndofs, T, sx_cur, omega, cbase, tid);
   }
 }
 
@@ -168,6 +238,9 @@ static tpss_status launch(tpss_patches* P, const int* list, int count, float ome
 tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
                             float* x, cudaStream_t s) {
   if (P->ctx->dim != 3) return TPSS_EINVAL;
+  // 16-byte cp.async and vector accesses need 16-byte aligned vectors; other
+  // pointers take the generic tensor-core kernel
+  if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x)) & 15) return TPSS_EINVAL;
   const bool v = P->kind == TPSS_VERTEX_PATCH;
   switch (P->n) {
     case 4: return v ? bf::launch<4, true>(P, list, count, omega, nrhs, r, x, s)

@@ -83,3 +83,23 @@ def test_mixed_vcycle_close_to_oracle():
     prob.vcycle(dev(b), x)
     assert rel_err(x, H.precondition(b)) < 1e-4
     prob.close()
+
+
+def test_bf16_smoother_with_unaligned_vectors_matches_aligned():
+    # vectors offset by one float are not 16-byte aligned: the library takes the
+    # generic kernel, and the result agrees with the aligned call
+    from paper_1910_11239_gb300 import tpss
+    widths = workloads.widths_random(4, 3, seed=5)
+    prob = make(3, 3, widths)
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH, tpss.BF16)
+    N = prob.ndofs(0)
+    b = dev(workloads.rhs_uniform(N, seed=3), torch.float32)
+    xa = torch.empty(N, dtype=torch.float32, device="cuda")
+    P.smooth_additive(0.7, b, xa, x_is_zero=True)
+    bb = torch.empty(N + 1, dtype=torch.float32, device="cuda")
+    bb[1:] = b
+    xx = torch.empty(N + 1, dtype=torch.float32, device="cuda")
+    P.smooth_additive(0.7, bb[1:], xx[1:], x_is_zero=True)
+    torch.cuda.synchronize()
+    assert rel_err(xx[1:].double(), xa.double().cpu().numpy()) < 2e-2
+    prob.close()
