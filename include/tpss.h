@@ -197,6 +197,8 @@ typedef struct {
                           whole V-cycle then runs in FP32 with these contractions) */
   int mult_colors;     /* 0 = default (2^(d+1) for MVS), else as tpss_patches_set_mult_colors */
   int flexible_cg;     /* 1: Polak-Ribiere beta in tpss_pcg_solve (use with inexact V-cycles) */
+  int nonsymmetric;    /* 1: the post-smoother keeps the pre-smoother's color order (the
+                          non-symmetric V-cycle used with GMRES); 0: reversed (symmetric) */
 } tpss_mg_params;
 
 /* Build smoothers on levels 1..L and the coarse solver on level 0 (the level 0
@@ -256,6 +258,18 @@ tpss_status tpss_batch_vcycle(tpss_batch* batch, const double* b, double* x);
  * nprob * nrhs entries.  TPSS_ENOTCONV if some system reached maxit. */
 tpss_status tpss_batch_pcg_solve(tpss_batch* batch, const double* b, double* x, double rtol, int maxit,
                                  int* iters, double* rel_res);
+
+/* Flexible right-preconditioned GMRES(restart) (Sec. 2.4: the Krylov method
+ * used with the multiplicative smoothers) on the finest level with one
+ * V-cycle per step as preconditioner, from x = 0, stopped when the
+ * least-squares residual ||b - A x_k||_2 <= rtol ||b||_2 or after maxit steps.
+ * Arnoldi by classical Gram-Schmidt with one reorthogonalization on the
+ * device; the Hessenberg least-squares problem (Givens rotations) on the
+ * host.  *iters, *rel_res and res_hist (maxit+1 host doubles, may be NULL)
+ * as in tpss_pcg_solve.  Allocates (restart+1) + restart finest-level vectors
+ * on its first call.  TPSS_ENOTCONV at maxit. */
+tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit, int restart,
+                             int* iters, double* rel_res, double* res_hist);
 
 #ifdef __cplusplus
 }

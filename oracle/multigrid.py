@@ -7,8 +7,9 @@ solved exactly (dense Cholesky); the paper uses a Chebyshev iteration to a
 relative accuracy of 1e-8 there (Sec. 2.4), which it does not specify further,
 so the exact solve is the reading taken.  Pre-smoothing visits the colors in
 order and post-smoothing in reverse order, so that with multiplicative
-smoothers the V-cycle is symmetric and CG applies (the paper uses GMRES for
-multiplicative smoothers; that is a different outer method, not implemented).
+smoothers the V-cycle is symmetric and CG applies; with symmetric=False the
+post-smoother keeps the pre-smoother's order (the non-symmetric V-cycle the
+paper combines with GMRES for multiplicative smoothers).
 
 PCG: standard preconditioned conjugate gradients from x_0 = 0, stopped when
 ||r_k||_2 <= rtol ||r_0||_2 (Sec. 2.4: relative residual reduction 1e-8).
@@ -18,8 +19,13 @@ log(e_{nu-1}/e_nu) with tol = rtol e_0, here with e the residual norm (the
 paper uses the energy norm of the error for CG; the residual-based value is
 labelled as such where reported).
 
-Pins (tests/test_oracle_multigrid.py): the PCG solution matches a direct
-sparse solve to the residual tolerance; the V-cycle operator is symmetric for
+Flexible GMRES (right preconditioned, restarted) for the non-symmetric
+V-cycle of the multiplicative smoothers (the paper's choice for MCS and MVS).
+
+Pins (tests/test_oracle_multigrid.py): the PCG and FGMRES solutions match a
+direct sparse solve to the residual tolerance; unpreconditioned GMRES
+terminates in at most n steps on an n x n system and its least-squares
+residual history equals the true residual norms; the V-cycle operator is symmetric for
 the additive and the symmetrically ordered multiplicative smoothers; on T_0
 the V-cycle is the exact coarse solve; the fractional count reproduces
 hand-computed values.
@@ -42,8 +48,11 @@ class Hierarchy:
               'MVS' (multiplicative vertex patches, 2^(d+1) colors)."""
 
     def __init__(self, coarse_widths, k, nlevels, smoother="AVS", omega=None,
-                 gamma_hat=1.0, penalty_poly="paper"):
+                 gamma_hat=1.0, penalty_poly="paper", symmetric=True):
         self.k = k
+        # symmetric=False: the post-smoother visits the colors in the same
+        # order as the pre-smoother (the non-symmetric V-cycle used with GMRES)
+        self.symmetric = symmetric
         self.smoother = smoother
         self.omega = omega if omega is not None else default_omega(smoother, len(coarse_widths))
         self.meshes = [TensorMesh(coarse_widths)]
@@ -81,7 +90,7 @@ class Hierarchy:
         if self.smoother in ("ACS", "AVS"):
             return schwarz.additive_smoother(self.A[l], b, x, self.solvers[l], self.omega)
         return schwarz.multiplicative_smoother(self.A[l], b, x, self.solvers[l], self.colors[l],
-                                               self.omega, reverse=post)
+                                               self.omega, reverse=post and self.symmetric)
 
     def vcycle(self, l, x, b):
         """Alg. 1, MG_l(x, b)."""
@@ -129,6 +138,62 @@ def pcg(A, b, precondition, rtol=1e-8, maxit=500):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, maxit, hist, False
+
+
+def fgmres(A, b, precondition, rtol=1e-8, maxit=500, restart=30):
+    """Flexible right-preconditioned GMRES(restart) from x_0 = 0 (the Krylov
+    method of Sec. 2.4 for the multiplicative smoothers): Arnoldi with modified
+    Gram-Schmidt on A z_j, z_j = M v_j, Givens rotations, x = x_0 + Z y.
+    Returns (x, iterations, residual norm history, converged); the history
+    holds the Euclidean norms of b - A x_k (the least-squares residuals)."""
+    n = b.shape[0]
+    x = np.zeros(n)
+    beta0 = np.linalg.norm(b)
+    hist = [beta0]
+    if beta0 == 0.0:
+        return x, 0, hist, True
+    it = 0
+    r = b.copy()
+    while it < maxit:
+        beta = np.linalg.norm(r)
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        j_done = 0
+        for j in range(restart):
+            it += 1
+            z = precondition(V[j])
+            Z.append(z)
+            w = A @ z
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j] = d
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            hist.append(abs(g[j + 1]))
+            j_done = j + 1
+            if abs(g[j + 1]) <= rtol * beta0 or it >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
+        for i in range(j_done):
+            x = x + y[i] * Z[i]
+        r = b - A @ x
+        if np.linalg.norm(r) <= rtol * beta0 * (1 + 1e-6) or hist[-1] <= rtol * beta0:
+            return x, it, hist, True
+    return x, it, hist, False
 
 
 def fractional_iterations(hist, rtol):

@@ -36,6 +36,7 @@ void destroy_mg(tpss_ctx* ctx) {
   for (auto* v : mg->b32) dfree(v);
   for (auto* v : mg->x32) dfree(v);
   dfree(mg->r); dfree(mg->z); dfree(mg->p); dfree(mg->q); dfree(mg->zold);
+  dfree(mg->gm_V); dfree(mg->gm_Z); dfree(mg->gm_h);
   delete mg;
   ctx->mg = nullptr;
 }
@@ -231,7 +232,8 @@ static tpss_status smooth(tpss_ctx* ctx, MGState* mg, int l, const T* b, T* x, b
   const T omega = (T)mg->params.omega;
   if (kind == TPSS_ACS || kind == TPSS_AVS) return smooth_additive_t<T>(P, omega, 1, b, x, x_zero ? 1 : 0);
   if (x_zero) TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)ctx->levels[l].ndofs * sizeof(T), ctx->stream));
-  return smooth_multiplicative_t<T>(P, omega, post ? 1 : 0, 1, b, x);
+  const bool reverse = post && !mg->params.nonsymmetric;
+  return smooth_multiplicative_t<T>(P, omega, reverse ? 1 : 0, 1, b, x);
 }
 
 // x_l = MG_l(0, b_l) (Alg. 1); b, x are level-l vectors.
@@ -263,6 +265,42 @@ static tpss_status precondition(tpss_ctx* ctx, MGState* mg, const double* r, dou
   copy_convert_kernel<float, double><<<grid_for(ctx, n), 256, 0, ctx->stream>>>(xf, z, n);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
+}
+
+// ------------------------------------------------------------------ GMRES
+// partial sums of <V_i, w> for i < j: grid (chunks, j)
+__global__ void multi_dot_kernel(const double* __restrict__ V, const double* __restrict__ w, int64_t n,
+                                 double* __restrict__ partials, int chunks) {
+  const int i = blockIdx.y;
+  const double* v = V + (int64_t)i * n;
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s = fma(v[e], w[e], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[(int64_t)i * chunks + blockIdx.x] = s;
+}
+
+__global__ void multi_final_kernel(const double* __restrict__ partials, int chunks, double* __restrict__ out) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) s += partials[(int64_t)i * chunks + c];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[i] = s;
+}
+
+// w += sign * sum_{i < j} c_i V_i
+__global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ c,
+                                  int j, int64_t n, double sign) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < j; ++i) acc = fma(sign * c[i], V[(int64_t)i * n + e], acc);
+    w[e] = acc;
+  }
+}
+
+__global__ void scale_copy_kernel(double* __restrict__ dst, const double* __restrict__ src, double s, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = s * src[e];
 }
 
 // ------------------------------------------------------------ right-hand side
@@ -574,5 +612,139 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
     TPSS_CHECK_LAUNCH();
   }
   set_error("tpss_pcg_solve: not converged within maxit");
+  return TPSS_ENOTCONV;
+}
+
+
+extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
+                                        int restart, int* iters, double* rel_res, double* res_hist) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && x && iters && rel_res, "tpss_gmres_solve: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_gmres_solve: call tpss_mg_setup first");
+  TPSS_REQUIRE(rtol > 0.0 && maxit >= 1 && restart >= 1 && restart <= 200,
+               "tpss_gmres_solve: rtol > 0, maxit >= 1, 1 <= restart <= 200 required");
+  MGState* mg = ctx->mg;
+  const int L = ctx->nlevels - 1;
+  const int64_t n = ctx->levels[L].ndofs;
+  cudaStream_t s = ctx->stream;
+  if (mg->gm_restart < restart) {
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    dfree(mg->gm_V); dfree(mg->gm_Z); dfree(mg->gm_h);
+    mg->gm_V = mg->gm_Z = mg->gm_h = nullptr;
+    mg->gm_restart = 0;
+    TPSS_TRY(dalloc_t(&mg->gm_V, (size_t)(restart + 1) * n));
+    TPSS_TRY(dalloc_t(&mg->gm_Z, (size_t)restart * n));
+    TPSS_TRY(dalloc_t(&mg->gm_h, (size_t)2 * (restart + 1)));
+    mg->gm_restart = restart;
+  }
+  // partial sums of the multi-dot live in ctx->d_partials (4096 doubles)
+  const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(n / (kRedThreads * 8), 4096 / (restart + 1)));
+  const int g = grid_for(ctx, n);
+  double* V = mg->gm_V;
+  double* Z = mg->gm_Z;
+  double* dh = mg->gm_h;
+  double* w = mg->q;   // finest-level scratch vector
+  auto vec = [&](double* base, int i) { return base + (int64_t)i * n; };
+  // <V_i, w> for i < j into dh[0..j), copied to the host
+  auto project = [&](int j, std::vector<double>& h) -> tpss_status {
+    dim3 grid(chunks, j);
+    multi_dot_kernel<<<grid, kRedThreads, 0, s>>>(V, w, n, ctx->d_partials, chunks);
+    multi_final_kernel<<<j, kRedThreads, 0, s>>>(ctx->d_partials, chunks, dh);
+    TPSS_CHECK_LAUNCH();
+    h.resize(j);
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(h.data(), dh, j * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    multi_axpy_kernel<<<g, 256, 0, s>>>(w, V, dh, j, n, -1.0);
+    TPSS_CHECK_LAUNCH();
+    return TPSS_OK;
+  };
+  auto norm = [&](const double* v, double* out) -> tpss_status {
+    TPSS_TRY(dot(ctx, v, v, n, ctx->d_scalars + 6));
+    double hv = 0.0;
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(&hv, ctx->d_scalars + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    *out = std::sqrt(std::max(hv, 0.0));
+    return TPSS_OK;
+  };
+  TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double beta0 = 0.0;
+  TPSS_TRY(norm(mg->r, &beta0));
+  *iters = 0;
+  *rel_res = beta0 > 0.0 ? 1.0 : 0.0;
+  if (res_hist) res_hist[0] = beta0;
+  if (!std::isfinite(beta0)) {
+    set_error("tpss_gmres_solve: right-hand side is not finite");
+    return TPSS_EBREAKDOWN;
+  }
+  if (beta0 == 0.0) return TPSS_OK;
+  int it = 0;
+  std::vector<double> H((size_t)(restart + 1) * restart), gv(restart + 1), cs(restart), sn(restart), h1, h2;
+  double beta = beta0;
+  while (it < maxit) {
+    scale_copy_kernel<<<g, 256, 0, s>>>(vec(V, 0), mg->r, 1.0 / beta, n);
+    TPSS_CHECK_LAUNCH();
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    bool done = false;
+    for (int j = 0; j < restart && it < maxit; ++j) {
+      ++it;
+      TPSS_TRY(precondition(ctx, mg, vec(V, j), vec(Z, j)));
+      TPSS_TRY(apply_operator_t<double>(ctx, L, 1, vec(Z, j), w, nullptr));
+      TPSS_TRY(project(j + 1, h1));   // classical Gram-Schmidt ...
+      TPSS_TRY(project(j + 1, h2));   // ... with one reorthogonalization
+      auto Hij = [&](int i, int jj) -> double& { return H[(size_t)i * restart + jj]; };
+      for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
+      double hn = 0.0;
+      TPSS_TRY(norm(w, &hn));
+      Hij(j + 1, j) = hn;
+      if (!std::isfinite(hn)) {
+        set_error("tpss_gmres_solve: breakdown (non-finite Arnoldi vector)");
+        return TPSS_EBREAKDOWN;
+      }
+      if (hn > 0.0) {
+        scale_copy_kernel<<<g, 256, 0, s>>>(vec(V, j + 1), w, 1.0 / hn, n);
+        TPSS_CHECK_LAUNCH();
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double d = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cs[j] = Hij(j, j) / d;
+      sn[j] = Hij(j + 1, j) / d;
+      Hij(j, j) = d;
+      Hij(j + 1, j) = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      if (res_hist) res_hist[it] = std::fabs(gv[j + 1]);
+      *iters = it;
+      *rel_res = std::fabs(gv[j + 1]) / beta0;
+      jdone = j + 1;
+      if (std::fabs(gv[j + 1]) <= rtol * beta0 || hn == 0.0) {
+        done = true;
+        break;
+      }
+    }
+    // x += Z y with H(1:j,1:j) y = g(1:j)
+    std::vector<double> y(jdone);
+    for (int i = jdone - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * restart + k] * y[k];
+      y[i] = acc / H[(size_t)i * restart + i];
+    }
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(dh, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s));
+    multi_axpy_kernel<<<g, 256, 0, s>>>(x, Z, dh, jdone, n, 1.0);
+    TPSS_CHECK_LAUNCH();
+    if (done) return TPSS_OK;
+    // restart from the true residual
+    TPSS_TRY(apply_operator_t<double>(ctx, L, 1, x, mg->r, b));
+    TPSS_TRY(norm(mg->r, &beta));
+    if (!(beta > 0.0)) return TPSS_OK;
+  }
+  set_error("tpss_gmres_solve: not converged within maxit");
   return TPSS_ENOTCONV;
 }

@@ -116,6 +116,10 @@ struct MGState {
   std::vector<float*> b32, x32;
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr;
   double* gj_tmp = nullptr;              // 2 n0
+  int gm_restart = 0;                    // GMRES basis: (restart+1) V vectors, restart Z vectors
+  double* gm_V = nullptr;
+  double* gm_Z = nullptr;
+  double* gm_h = nullptr;                // device scalars (2 (restart+1))
 };
 
 }  // namespace tpss

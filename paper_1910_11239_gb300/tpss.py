@@ -38,7 +38,7 @@ class ProblemDesc(ctypes.Structure):
 
 class MGParams(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
-                ("mult_colors", ctypes.c_int), ("flexible_cg", ctypes.c_int)]
+                ("mult_colors", ctypes.c_int), ("flexible_cg", ctypes.c_int), ("nonsymmetric", ctypes.c_int)]
 
 
 _lib = None
@@ -71,6 +71,8 @@ SIGNATURES = {
     "tpss_coarse_solve": [_VP, _VP, _VP],
     "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                        _VP],
+    "tpss_gmres_solve": [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                         _VP],
     "tpss_batch_create": [ctypes.POINTER(ProblemDesc), _I, _I, ctypes.POINTER(MGParams), _I, _VP,
                           ctypes.POINTER(_VP)],
     "tpss_batch_destroy": [_VP],
@@ -203,10 +205,11 @@ class Problem:
         _check(lib().tpss_assemble_rhs(self.h, level, kind, _ptr(b, torch.float64, self.ndofs(level))))
         return b
 
-    def mg_setup(self, smoother, omega, precision=FP64, mult_colors=0, flexible_cg=0):
+    def mg_setup(self, smoother, omega, precision=FP64, mult_colors=0, flexible_cg=0, nonsymmetric=0):
         p = MGParams()
         p.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
         p.omega, p.precision, p.mult_colors, p.flexible_cg = omega, precision, mult_colors, flexible_cg
+        p.nonsymmetric = int(bool(nonsymmetric))
         _check(lib().tpss_mg_setup(self.h, ctypes.byref(p)))
 
     def vcycle(self, b, x):
@@ -231,6 +234,23 @@ class Problem:
         if history:
             out["history"] = [hist[i] for i in range(it.value + 1)]
         return out
+
+
+def _gmres(self, b, x, rtol=1e-8, maxit=200, restart=30, history=False):
+    n = self.ndofs(self.nlevels - 1)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    hist = (ctypes.c_double * (maxit + 1))() if history else None
+    st = lib().tpss_gmres_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n), rtol, maxit, restart,
+                                ctypes.byref(it), ctypes.byref(rel),
+                                ctypes.cast(hist, ctypes.c_void_p) if hist is not None else None)
+    _check(st, allow=(TPSS_OK, TPSS_ENOTCONV))
+    out = {"iters": it.value, "rel_res": rel.value, "converged": st == TPSS_OK}
+    if history:
+        out["history"] = [hist[i] for i in range(it.value + 1)]
+    return out
+
+
+Problem.gmres_solve = _gmres
 
 
 class Patches:

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle.multigrid import Hierarchy, fractional_iterations, pcg
+from oracle.multigrid import Hierarchy, fgmres, fractional_iterations, pcg
 
 
 def coarse(d, n=2):
@@ -44,3 +44,38 @@ def test_fractional_iterations_hand_values():
     hist = [1.0, 0.1, 0.01, 1e-3, 1e-4]
     assert np.isclose(fractional_iterations(hist, 10 ** -2.5), 2.5)
     assert np.isclose(fractional_iterations(hist, 1e-3), 3.0)
+
+
+def test_gmres_unpreconditioned_finite_termination_and_true_residuals():
+    rng = np.random.default_rng(4)
+    n = 12
+    A = rng.standard_normal((n, n)) + 4 * np.eye(n)      # non-symmetric
+    b = rng.standard_normal(n)
+    # record the iterates through a restart length of 1 (hist = true residuals)
+    x, it, hist, ok = fgmres(A, b, lambda v: v, rtol=1e-12, maxit=n, restart=n)
+    assert ok and it <= n
+    assert np.linalg.norm(A @ x - b) <= 1e-10 * np.linalg.norm(b)
+    # the least-squares residuals are non-increasing
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
+    # GMRES(1) residual after one step equals the true residual of x_1 = alpha b
+    x1, _, h1, _ = fgmres(A, b, lambda v: v, rtol=1e-300, maxit=1, restart=1)
+    assert np.isclose(h1[1], np.linalg.norm(b - A @ x1), rtol=1e-10)
+
+
+@pytest.mark.parametrize("smoother", ["MCS", "MVS"])
+def test_fgmres_with_nonsymmetric_vcycle_matches_direct_solve(smoother):
+    H = Hierarchy(coarse(2), k=2, nlevels=3, smoother=smoother, symmetric=False)
+    A = H.A[-1]
+    b = np.random.default_rng(5).uniform(-1, 1, A.shape[0])
+    x, it, hist, ok = fgmres(A, b, H.precondition, rtol=1e-10, maxit=60)
+    assert ok
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    assert it < 20
+
+
+def test_nonsymmetric_vcycle_is_not_symmetric():
+    H = Hierarchy(coarse(2), k=1, nlevels=3, smoother="MVS", symmetric=False)
+    N = H.A[-1].shape[0]
+    B = np.column_stack([H.precondition(e) for e in np.eye(N)])
+    assert np.abs(B - B.T).max() > 1e-6 * np.abs(B).max()
