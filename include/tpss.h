@@ -238,7 +238,9 @@ tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rto
  * at creation unless flags & 2; the whole V-cycle is captured as a CUDA graph
  * unless flags & 1 or the stream is the legacy default stream.
  * Vector layout of every batched call: problems one after another, each as
- * nrhs consecutive vectors of its finest level (tpss_batch_info gives offsets).
+ * nrhs consecutive vectors of its finest level, each problem's block starting
+ * on a 16-byte boundary (tpss_batch_info gives offsets; entries between blocks
+ * are padding and are ignored).  Vectors must be 16-byte aligned.
  * Synchronizes the stream. */
 typedef struct tpss_batch tpss_batch;
 tpss_status tpss_batch_create(const tpss_problem_desc* descs, int nprob, int nrhs, const tpss_mg_params* params,

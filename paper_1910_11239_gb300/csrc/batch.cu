@@ -36,6 +36,7 @@ struct BatchLevelDesc {
   int nc0, nc1;
   int64_t ndofs;
   int n;
+  int variant;         // local solver routine: 0 FP32 SIMT, 1 BF16 tensor cores
 };
 
 struct BatchItem {
@@ -191,73 +192,55 @@ __device__ void batch_group(const BatchLevelDesc& D, const BatchItem& it, float 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchThreads)
-batch_smooth_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __restrict__ items, int nitems,
-                    int* __restrict__ counter, float omega) {
-  extern __shared__ float bsm[];
-  __shared__ int cur;
-  for (;;) {
-    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
-    __syncthreads();
-    const int i = cur;
-    __syncthreads();
-    if (i >= nitems) break;
-    const BatchItem it = items[i];
-    const BatchLevelDesc D = desc[it.prob];
-    switch (D.n) {
-      case 4: batch_group<4>(D, it, omega, bsm); break;
-      case 6: batch_group<6>(D, it, omega, bsm); break;
-      case 8: batch_group<8>(D, it, omega, bsm); break;
-      case 10: batch_group<10>(D, it, omega, bsm); break;
-      case 12: batch_group<12>(D, it, omega, bsm); break;
-      case 14: batch_group<14>(D, it, omega, bsm); break;
-      case 16: batch_group<16>(D, it, omega, bsm); break;
-      default: break;
-    }
-  }
-}
-
 // BF16 tensor-core variant of a work item: `count` patches of one problem and
-// right-hand side, one after another, each with the MMA routines of
-// bf16_tc.cuh; the scatter uses FP32 atomics as in the FP32 variant.
+// right-hand side, one after another, with the routines of bf16_tc.cuh.  The
+// right-hand side of the next patch is staged by cp.async (double buffer)
+// while the current one is contracted; the scatter uses FP32 atomics.
+// Dynamic shared memory: [T: Shape<16> bf16][SB: 2 x 8 NLOC1(16) f32].
+constexpr int kBf16SbOffset = ((bf::Shape<16>::TOTAL * 2 + 15) / 16) * 16;
+constexpr size_t kBf16Smem = kBf16SbOffset + 2 * 8 * 512 * sizeof(float);
+
 template <int N>
-__device__ void batch_group_bf16(const BatchLevelDesc& D, const BatchItem& it, float omega, __nv_bfloat16* T,
+__device__ void batch_group_bf16(const BatchLevelDesc& D, const BatchItem& it, float omega, unsigned char* dsm,
                                  float* lam) {
   using S = bf::Shape<N>;
   constexpr int N1 = N / 2;
   constexpr int NLOC1 = N1 * N1 * N1;
   constexpr int NV = 8 * NLOC1;
+  __nv_bfloat16* T = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float* SB = reinterpret_cast<float*>(dsm + kBf16SbOffset);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int64_t vbase = (int64_t)it.rhs * D.ndofs;
-  auto toff = [&](int e) -> int {
-    const int c = e / NLOC1, loc = e % NLOC1;
-    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
-    const int ix = loc % N1, iy = (loc / N1) % N1, iz = loc / (N1 * N1);
-    return (sx * N1 + ix) + bf::LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
-  };
-  __syncthreads();   // the previous item is done with T
-  for (int e = tid; e < S::TOTAL; e += blockDim.x) T[e] = __float2bfloat16(0.f);
-  for (int c = 0; c < it.count; ++c) {
+  const float* rb = D.r + (int64_t)it.rhs * D.ndofs;
+  float* xb = D.x + (int64_t)it.rhs * D.ndofs;
+  auto cellbase = [&](int c) -> bf::CellBase {
     const int packed = D.list[it.first + c];
-    const int px = unpack_x(packed), py = unpack_y(packed), pz = unpack_z(packed);
-    __syncthreads();   // zero fill done / previous patch scattered
+    return bf::CellBase{unpack_x(packed), unpack_y(packed), unpack_z(packed), D.nc0, D.nc1};
+  };
+  __syncthreads();   // the previous item is done with T and SB
+  for (int e = tid; e < S::TOTAL; e += blockDim.x) T[e] = __float2bfloat16(0.f);
+  bf::stage<NLOC1, 8>(SB, rb, cellbase(0), tid);
+  bf::cp_async_commit();
+  for (int c = 0; c < it.count; ++c) {
+    const bf::CellBase cb = cellbase(c);
+    bf::cp_async_wait_all();
+    __syncthreads();   // staged data visible; zero fill / previous patch done with T
     if (tid < 3 * N) {
       const int d = tid / N, i = tid % N;
-      lam[tid] = D.lam[d][(size_t)(d == 0 ? px : (d == 1 ? py : pz)) * N + i];
+      lam[tid] = D.lam[d][(size_t)(d == 0 ? cb.px : (d == 1 ? cb.py : cb.pz)) * N + i];
     }
-    for (int e = tid; e < NV; e += blockDim.x) {
-      const int cc = e / NLOC1, loc = e % NLOC1;
-      const int64_t g = (px + (cc & 1)) + (int64_t)D.nc0 * ((py + ((cc >> 1) & 1)) + (int64_t)D.nc1 * (pz + ((cc >> 2) & 1)));
-      T[toff(e)] = __float2bfloat16(__ldg(D.r + vbase + g * NLOC1 + loc));
-    }
+    bf::rows_to_tensor<N, N1, 8>(T, SB + (c & 1) * NV, tid);
     uint32_t bx[2][2], bxt[2][2], by[2][2], byt[2][2], bzz[2][2], bzt[2][2];
-    bf::load_bfrag<N, false>(bxt, D.Z[0] + (size_t)px * N * N, lane);
-    bf::load_bfrag<N, true>(bx, D.Z[0] + (size_t)px * N * N, lane);
-    bf::load_bfrag<N, false>(byt, D.Z[1] + (size_t)py * N * N, lane);
-    bf::load_bfrag<N, true>(by, D.Z[1] + (size_t)py * N * N, lane);
-    bf::load_bfrag<N, false>(bzt, D.Z[2] + (size_t)pz * N * N, lane);
-    bf::load_bfrag<N, true>(bzz, D.Z[2] + (size_t)pz * N * N, lane);
-    __syncthreads();
+    bf::load_bfrag<N, false>(bxt, D.Z[0] + (size_t)cb.px * N * N, lane);
+    bf::load_bfrag<N, true>(bx, D.Z[0] + (size_t)cb.px * N * N, lane);
+    bf::load_bfrag<N, false>(byt, D.Z[1] + (size_t)cb.py * N * N, lane);
+    bf::load_bfrag<N, true>(by, D.Z[1] + (size_t)cb.py * N * N, lane);
+    bf::load_bfrag<N, false>(bzt, D.Z[2] + (size_t)cb.pz * N * N, lane);
+    bf::load_bfrag<N, true>(bzz, D.Z[2] + (size_t)cb.pz * N * N, lane);
+    __syncthreads();   // T and lam ready; the other SB buffer is free
+    if (c + 1 < it.count) {
+      bf::stage<NLOC1, 8>(SB + ((c + 1) & 1) * NV, rb, cellbase(c + 1), tid);
+      bf::cp_async_commit();
+    }
     bf::contract<N, 0>(T, bxt, warp, lane);
     __syncthreads();
     bf::contract<N, 1>(T, byt, warp, lane);
@@ -268,20 +251,18 @@ __device__ void batch_group_bf16(const BatchLevelDesc& D, const BatchItem& it, f
     __syncthreads();
     bf::contract<N, 0>(T, bx, warp, lane);
     __syncthreads();
-    for (int e = tid; e < NV; e += blockDim.x) {
-      const int cc = e / NLOC1, loc = e % NLOC1;
-      const int64_t g = (px + (cc & 1)) + (int64_t)D.nc0 * ((py + ((cc >> 1) & 1)) + (int64_t)D.nc1 * (pz + ((cc >> 2) & 1)));
-      atomicAdd(D.x + vbase + g * NLOC1 + loc, omega * __bfloat162float(T[toff(e)]));
-    }
+    bf::tensor_atomic_add<N, N1, 8>(xb, T, omega, cb, tid);
   }
 }
 
+// FP32-only persistent smoother (batches without BF16): a separate kernel so
+// that its register allocation is not set by the tensor-core routines.
 __global__ void __launch_bounds__(kBatchThreads)
-batch_smooth_bf16_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __restrict__ items, int nitems,
+batch_smooth_simt_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __restrict__ items, int nitems,
                          int* __restrict__ counter, float omega) {
-  __shared__ __align__(16) __nv_bfloat16 T[bf::Shape<16>::TOTAL];
-  __shared__ float lam[3 * 16];
+  extern __shared__ __align__(16) unsigned char bdsm[];
   __shared__ int cur;
+  float* fsm = reinterpret_cast<float*>(bdsm);
   for (;;) {
     if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
     __syncthreads();
@@ -291,14 +272,58 @@ batch_smooth_bf16_kernel(const BatchLevelDesc* __restrict__ desc, const BatchIte
     const BatchItem it = items[i];
     const BatchLevelDesc D = desc[it.prob];
     switch (D.n) {
-      case 4: batch_group_bf16<4>(D, it, omega, T, lam); break;
-      case 6: batch_group_bf16<6>(D, it, omega, T, lam); break;
-      case 8: batch_group_bf16<8>(D, it, omega, T, lam); break;
-      case 10: batch_group_bf16<10>(D, it, omega, T, lam); break;
-      case 12: batch_group_bf16<12>(D, it, omega, T, lam); break;
-      case 14: batch_group_bf16<14>(D, it, omega, T, lam); break;
-      case 16: batch_group_bf16<16>(D, it, omega, T, lam); break;
+      case 4: batch_group<4>(D, it, omega, fsm); break;
+      case 6: batch_group<6>(D, it, omega, fsm); break;
+      case 8: batch_group<8>(D, it, omega, fsm); break;
+      case 10: batch_group<10>(D, it, omega, fsm); break;
+      case 12: batch_group<12>(D, it, omega, fsm); break;
+      case 14: batch_group<14>(D, it, omega, fsm); break;
+      case 16: batch_group<16>(D, it, omega, fsm); break;
       default: break;
+    }
+  }
+}
+
+// The persistent smoother with both routines: every CTA pulls work items
+// until the list is exhausted and runs the routine chosen for the item's
+// patch size.
+__global__ void __launch_bounds__(kBatchThreads)
+batch_smooth_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __restrict__ items, int nitems,
+                    int* __restrict__ counter, float omega) {
+  extern __shared__ __align__(16) unsigned char bdsm[];
+  __shared__ float lam[3 * 16];
+  __shared__ int cur;
+  float* fsm = reinterpret_cast<float*>(bdsm);
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int i = cur;
+    __syncthreads();
+    if (i >= nitems) break;
+    const BatchItem it = items[i];
+    const BatchLevelDesc D = desc[it.prob];
+    if (D.variant == 1) {
+      switch (D.n) {
+        case 4: batch_group_bf16<4>(D, it, omega, bdsm, lam); break;
+        case 6: batch_group_bf16<6>(D, it, omega, bdsm, lam); break;
+        case 8: batch_group_bf16<8>(D, it, omega, bdsm, lam); break;
+        case 10: batch_group_bf16<10>(D, it, omega, bdsm, lam); break;
+        case 12: batch_group_bf16<12>(D, it, omega, bdsm, lam); break;
+        case 14: batch_group_bf16<14>(D, it, omega, bdsm, lam); break;
+        case 16: batch_group_bf16<16>(D, it, omega, bdsm, lam); break;
+        default: break;
+      }
+    } else {
+      switch (D.n) {
+        case 4: batch_group<4>(D, it, omega, fsm); break;
+        case 6: batch_group<6>(D, it, omega, fsm); break;
+        case 8: batch_group<8>(D, it, omega, fsm); break;
+        case 10: batch_group<10>(D, it, omega, fsm); break;
+        case 12: batch_group<12>(D, it, omega, fsm); break;
+        case 14: batch_group<14>(D, it, omega, fsm); break;
+        case 16: batch_group<16>(D, it, omega, fsm); break;
+        default: break;
+      }
     }
   }
 }
@@ -428,6 +453,7 @@ struct tpss_batch {
   std::vector<int> grid;                      // persistent grid size per depth
   int* d_counter = nullptr;           // one counter per depth and phase (2 * maxdepth + 1)
   int ppb[17] = {0};                  // patches per work item, by n (autotuned)
+  int variant[17] = {0};              // local solver routine by n: 0 FP32 SIMT, 1 BF16 (autotuned)
   // graph of the FP32 V-cycle (input fb, output fx)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -446,7 +472,7 @@ struct tpss_batch {
 namespace tpss {
 
 static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>& items, size_t& smem_bytes,
-                               int only_n = 0, int ppb_override = 0) {
+                               int only_n = 0, int ppb_override = 0, int variant_override = -1) {
   items.clear();
   smem_bytes = 0;
   struct Cost {
@@ -463,7 +489,8 @@ static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>&
     if (only_n && n != only_n) continue;
     const int g = ppb_override ? ppb_override : B->ppb[n];
     const int total = (int)P->nsub;
-    if (!B->bf16) smem_bytes = std::max(smem_bytes, (size_t)g * bshape_slot(n) * sizeof(float));
+    const int var = variant_override >= 0 ? variant_override : B->variant[n];
+    smem_bytes = std::max(smem_bytes, var == 1 ? kBf16Smem : (size_t)g * bshape_slot(n) * sizeof(float));
     for (int r = 0; r < B->nrhs; ++r)
       for (int f = 0; f < total; f += g) {
         const int cnt = std::min(g, total - f);
@@ -478,9 +505,10 @@ static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>&
 static tpss_status grid_size(tpss_batch* B, int nitems, size_t smem, int* grid) {
   int per_sm = 0;
   if (B->bf16)
-    TPSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_smooth_bf16_kernel, kBatchThreads, 0));
-  else
     TPSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_smooth_kernel, kBatchThreads, smem));
+  else
+    TPSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_smooth_simt_kernel, kBatchThreads,
+                                                                  smem));
   if (per_sm < 1) {
     set_error("batch smoother: work item does not fit on an SM");
     return TPSS_EINVAL;
@@ -494,9 +522,9 @@ static tpss_status launch_level(tpss_batch* B, const BatchLevelDesc* desc, const
   if (nitems == 0) return TPSS_OK;
   TPSS_CHECK_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
   if (B->bf16)
-    batch_smooth_bf16_kernel<<<grid, kBatchThreads, 0, s>>>(desc, items, nitems, counter, B->omega);
-  else
     batch_smooth_kernel<<<grid, kBatchThreads, smem, s>>>(desc, items, nitems, counter, B->omega);
+  else
+    batch_smooth_simt_kernel<<<grid, kBatchThreads, smem, s>>>(desc, items, nitems, counter, B->omega);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
@@ -519,6 +547,7 @@ static tpss_status set_descs(tpss_batch* B, int depth) {
       d.nc1 = L.nc[1];
       d.ndofs = L.ndofs;
       d.n = P->n;
+      d.variant = B->variant[P->n];
       d.x = bp.x[l];
       d.r = bp.b[l];
     }
@@ -584,7 +613,8 @@ static tpss_status batch_vcycle(tpss_batch* B) {
 }
 
 static tpss_status autotune(tpss_batch* B) {
-  // time each candidate group size on the finest-level items of each degree
+  // time every (routine, patches per work item) candidate on the finest-level
+  // items of each patch size and keep the fastest
   const int cands_simt[] = {1, 2, 3, 4, 6, 8};
   const int cands_bf16[] = {1, 2, 4, 8, 16, 32};
   cudaEvent_t e0, e1;
@@ -597,38 +627,44 @@ static tpss_status autotune(tpss_batch* B) {
   BatchItem* d_tmp = nullptr;
   for (int n : ns) {
     double best = 1e30;
-    int bestg = 1;
-    for (int ci = 0; ci < 6; ++ci) {
-      const int g = B->bf16 ? cands_bf16[ci] : cands_simt[ci];
-      if (!B->bf16 && (size_t)g * bshape_slot(n) * sizeof(float) > 100 * 1024) continue;
-      if (!B->bf16 && g * n * n > 4 * kBatchThreads) continue;
-      std::vector<BatchItem> items;
-      size_t smem = 0;
-      build_items(B, 0, items, smem, n, g);
-      if (items.empty()) continue;
-      dfree(d_tmp);
-      d_tmp = nullptr;
-      TPSS_TRY(dalloc_t(&d_tmp, items.size()));
-      TPSS_CHECK_CUDA(cudaMemcpyAsync(d_tmp, items.data(), items.size() * sizeof(BatchItem),
-                                      cudaMemcpyHostToDevice, B->stream));
-      double t_best = 1e30;
-      int grid = 1;
-      TPSS_TRY(grid_size(B, (int)items.size(), smem, &grid));
-      for (int rep = 0; rep < 3; ++rep) {
-        TPSS_CHECK_CUDA(cudaEventRecord(e0, B->stream));
-        TPSS_TRY(launch_level(B, B->d_desc[0], d_tmp, (int)items.size(), smem, grid, B->d_counter, B->stream));
-        TPSS_CHECK_CUDA(cudaEventRecord(e1, B->stream));
-        TPSS_CHECK_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        t_best = std::min(t_best, (double)ms);
-      }
-      if (t_best < best) {
-        best = t_best;
-        bestg = g;
+    int bestg = 1, bestv = 0;
+    for (int var = 0; var <= (B->bf16 ? 1 : 0); ++var) {
+      for (int ci = 0; ci < 6; ++ci) {
+        const int g = var ? cands_bf16[ci] : cands_simt[ci];
+        if (!var && (size_t)g * bshape_slot(n) * sizeof(float) > 100 * 1024) continue;
+        if (!var && g * n * n > 4 * kBatchThreads) continue;
+        std::vector<BatchItem> items;
+        size_t smem = 0;
+        build_items(B, 0, items, smem, n, g, var);
+        if (items.empty()) continue;
+        B->variant[n] = var;
+        TPSS_TRY(set_descs(B, 0));
+        dfree(d_tmp);
+        d_tmp = nullptr;
+        TPSS_TRY(dalloc_t(&d_tmp, items.size()));
+        TPSS_CHECK_CUDA(cudaMemcpyAsync(d_tmp, items.data(), items.size() * sizeof(BatchItem),
+                                        cudaMemcpyHostToDevice, B->stream));
+        double t_best = 1e30;
+        int grid = 1;
+        TPSS_TRY(grid_size(B, (int)items.size(), smem, &grid));
+        for (int rep = 0; rep < 3; ++rep) {
+          TPSS_CHECK_CUDA(cudaEventRecord(e0, B->stream));
+          TPSS_TRY(launch_level(B, B->d_desc[0], d_tmp, (int)items.size(), smem, grid, B->d_counter, B->stream));
+          TPSS_CHECK_CUDA(cudaEventRecord(e1, B->stream));
+          TPSS_CHECK_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          t_best = std::min(t_best, (double)ms);
+        }
+        if (t_best < best) {
+          best = t_best;
+          bestg = g;
+          bestv = var;
+        }
       }
     }
     B->ppb[n] = bestg;
+    B->variant[n] = bestv;
   }
   dfree(d_tmp);
   cudaEventDestroy(e0);
@@ -703,8 +739,8 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
     if ((st = tpss_mg_setup(bp.ctx, &mp)) != TPSS_OK) return fail(st);
     bp.L = bp.ctx->nlevels - 1;
     B->maxdepth = std::max(B->maxdepth, bp.L);
-    bp.off = B->total;
-    B->total += bp.ctx->levels[bp.L].ndofs * nrhs;
+    bp.off = (B->total + 3) / 4 * 4;   // 16-byte aligned problem blocks (vector and cp.async accesses)
+    B->total = bp.off + bp.ctx->levels[bp.L].ndofs * nrhs;
     for (int l = 0; l <= bp.L; ++l)
       if ((st = ensure_level_scratch(bp.ctx, l, nrhs)) != TPSS_OK) return fail(st);
   }
@@ -740,12 +776,18 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
     if ((st = dalloc_t(&B->d_desc_post[d], nprob)) != TPSS_OK) return fail(st);
     if ((st = set_descs(B, d)) != TPSS_OK) return fail(st);
   }
-  for (int n = 0; n <= 16; ++n) B->ppb[n] = B->bf16 ? 4 : std::max(1, 256 / std::max(1, n * n));
+  for (int n = 0; n <= 16; ++n) {
+    B->variant[n] = 0;
+    B->ppb[n] = std::max(1, 256 / std::max(1, n * n));
+  }
   cudaFuncSetAttribute(batch_smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024 + 1024);
+  cudaFuncSetAttribute(batch_smooth_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024 + 1024);
   cudaMemsetAsync(B->fb, 0, B->total * sizeof(float), B->stream);
   cudaMemsetAsync(B->fx, 0, B->total * sizeof(float), B->stream);
   if (!(flags & 2))
     if ((st = autotune(B)) != TPSS_OK) return fail(st);
+  for (int d = 0; d < D; ++d)
+    if ((st = set_descs(B, d)) != TPSS_OK) return fail(st);
   for (int d = 0; d < D; ++d) {
     std::vector<BatchItem> items;
     size_t smem = 0;
@@ -854,6 +896,8 @@ extern "C" tpss_status tpss_batch_smooth_additive(tpss_batch* B, const float* b,
   clear_error();
   TPSS_REQUIRE(B && b && x, "tpss_batch_smooth_additive: null argument");
   TPSS_REQUIRE(b != x, "tpss_batch_smooth_additive: b and x must not alias");
+  TPSS_REQUIRE(((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0,
+               "tpss_batch_smooth_additive: b and x must be 16-byte aligned");
   // finest level of every problem, x = omega sum_j R_j^T A_j^{-1} R_j b, one persistent launch
   std::vector<BatchLevelDesc> desc(B->probs.size());
   for (int p = 0; p < (int)B->probs.size(); ++p) {
@@ -870,6 +914,7 @@ extern "C" tpss_status tpss_batch_smooth_additive(tpss_batch* B, const float* b,
     d.nc1 = L.nc[1];
     d.ndofs = L.ndofs;
     d.n = P->n;
+    d.variant = B->variant[P->n];
     d.r = b + bp.off;
     d.x = x + bp.off;
     desc[p] = d;

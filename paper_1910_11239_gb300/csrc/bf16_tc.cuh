@@ -159,5 +159,114 @@ __device__ __forceinline__ void zstep(__nv_bfloat16* T, const uint32_t (&bt)[2][
   }
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Stage the 2^d cells of one right-hand side (cell-major, NV floats) into
+// shared memory with asynchronous copies (16 bytes when cells are 16-byte
+// multiples, else 4 bytes).
+struct CellBase {
+  int px, py, pz, nc0, nc1;
+  // first DoF of the patch's cell c (c = sx + 2 sy + 4 sz)
+  template <int NLOC1>
+  __device__ __forceinline__ int64_t operator()(int c) const {
+    return ((px + (c & 1)) + (int64_t)nc0 * ((py + ((c >> 1) & 1)) + (int64_t)nc1 * (pz + ((c >> 2) & 1)))) * NLOC1;
+  }
+};
+
+template <int NLOC1, int NCELL>
+__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, const CellBase& cb, int tid) {
+  const uint32_t d = smem_u32(dst);
+  if constexpr (NLOC1 % 4 == 0) {
+    constexpr int CH = NLOC1 / 4;
+    for (int e = tid; e < NCELL * CH; e += kThreads) {
+      const int c = e / CH, o = (e % CH) * 4;
+      cp_async16(d + 4u * (c * NLOC1 + o), src + cb.template operator()<NLOC1>(c) + o);
+    }
+  } else {
+    for (int e = tid; e < NCELL * NLOC1; e += kThreads) {
+      const int c = e / NLOC1, o = e % NLOC1;
+      cp_async4(d + 4u * (c * NLOC1 + o), src + cb.template operator()<NLOC1>(c) + o);
+    }
+  }
+}
+
+// Row-wise copies: a "row" is the N1 values of one cell along x, contiguous
+// both in the staged cell-major buffers and in the patch tensor.  V = 4, 2 or
+// 1 values per vector access (N1 divisible by 4, by 2, or odd).
+template <int N1>
+struct RowVec {
+  static constexpr int V = (N1 % 4 == 0) ? 4 : ((N1 % 2 == 0) ? 2 : 1);
+};
+
+// SB (f32, cell-major) -> T (bf16 patch tensor), one cell row per iteration.
+template <int N, int N1, int NCELL>
+__device__ __forceinline__ void rows_to_tensor(__nv_bfloat16* __restrict__ T, const float* __restrict__ SB, int tid) {
+  using S = Shape<N>;
+  constexpr int V = RowVec<N1>::V;
+  constexpr int NROW = NCELL * N1 * N1;
+  for (int rw = tid; rw < NROW; rw += kThreads) {
+    const int c = rw / (N1 * N1), rr = rw % (N1 * N1);
+    const int iy = rr % N1, iz = rr / N1;
+    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
+    const float* src = SB + c * N1 * N1 * N1 + rr * N1;
+    __nv_bfloat16* dst = T + sx * N1 + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
+#pragma unroll
+    for (int v = 0; v < N1; v += V) {
+      if constexpr (V == 4) {
+        const float4 f = *reinterpret_cast<const float4*>(src + v);
+        uint2 o;
+        o.x = pack2(f.x, f.y);
+        o.y = pack2(f.z, f.w);
+        *reinterpret_cast<uint2*>(dst + v) = o;
+      } else if constexpr (V == 2) {
+        const float2 f = *reinterpret_cast<const float2*>(src + v);
+        *reinterpret_cast<uint32_t*>(dst + v) = pack2(f.x, f.y);
+      } else {
+        dst[v] = __float2bfloat16(src[v]);
+      }
+    }
+  }
+}
+
+// x[cell rows] += omega T with atomic adds (several CTAs may update the same
+// cells), vectorized to 16 / 8 bytes when the rows allow it.
+template <int N, int N1, int NCELL>
+__device__ __forceinline__ void tensor_atomic_add(float* __restrict__ xr, const __nv_bfloat16* __restrict__ T,
+                                                  float omega, const CellBase& cb, int tid) {
+  using S = Shape<N>;
+  constexpr int V = RowVec<N1>::V;
+  constexpr int NLOC1 = N1 * N1 * N1;
+  constexpr int NROW = NCELL * N1 * N1;
+  for (int rw = tid; rw < NROW; rw += kThreads) {
+    const int c = rw / (N1 * N1), rr = rw % (N1 * N1);
+    const int iy = rr % N1, iz = rr / N1;
+    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
+    const __nv_bfloat16* t = T + sx * N1 + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
+    float* dst = xr + cb.template operator()<NLOC1>(c) + rr * N1;
+#pragma unroll
+    for (int v = 0; v < N1; v += V) {
+      if constexpr (V == 4) {
+        const uint2 tb = *reinterpret_cast<const uint2*>(t + v);
+        const float2 t01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&tb.x));
+        const float2 t23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&tb.y));
+        atomicAdd(reinterpret_cast<float4*>(dst + v),
+                  make_float4(omega * t01.x, omega * t01.y, omega * t23.x, omega * t23.y));
+      } else if constexpr (V == 2) {
+        const float2 tt = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(t + v));
+        atomicAdd(reinterpret_cast<float2*>(dst + v), make_float2(omega * tt.x, omega * tt.y));
+      } else {
+        atomicAdd(dst + v, omega * __bfloat162float(t[v]));
+      }
+    }
+  }
+}
+
 }  // namespace bf
 }  // namespace tpss
