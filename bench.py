@@ -10,8 +10,10 @@ Metric: DoF/s = sum over k of ndofs(k) * 8 per step / time per step.
 
 Also reported: per-degree DoF/s and roofline fraction, an end-to-end number
 through the same C-ABI call with host buffers (copies timed), the oracle on
-the host cores as cpu_baseline, and the MG-CG time to a 1e-8 residual
-reduction on 64^3 cells, k = 4 (FP64).
+the host cores as cpu_baseline, the MG-CG time to a 1e-8 residual
+reduction on 64^3 cells (FP64 and mixed precision), batched solves, the
+paper's fractional iteration counts, and the k = 15 smoothers on the paper's
+16^3-cell FLOP-table mesh.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tpss|reference]
 """
@@ -52,6 +54,7 @@ def parse():
     p.add_argument("--no-mgcg", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-high-degree", action="store_true")
     p.add_argument("--batch-problems", type=int, default=48, help="use the first N problems of the batch (profiling)")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
@@ -353,6 +356,9 @@ def main():
     batch = None
     if not args.no_batch:
         batch = run_batch(tpss, workloads, perf, torch, args.steps)
+    high = None
+    if not args.no_high_degree:
+        high = run_high_degree(tpss, workloads, perf, torch, max(2, min(args.steps, 5)))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -379,6 +385,8 @@ def main():
             line["batched"] = batch
         if paper_its is not None:
             line["paper_iterations"] = paper_its
+        if high is not None:
+            line["high_degree_k15"] = high
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -438,8 +446,12 @@ def run_mgcg(tpss, workloads, torch, cases):
         prob.assemble_rhs(5, 0, b)
         x64 = torch.zeros_like(b)
         x = torch.empty_like(b)
-        for prec in precs:
-            prob.mg_setup(sm, omega, tpss.PRECISIONS[prec], flexible_cg=0 if prec == "fp64" else 1)
+        for prec_mode in precs:
+            # "+full": Alg. 3 as printed (residual recomputed before every
+            # color) instead of the default per-color residual update
+            prec, full = prec_mode.replace("+full", ""), prec_mode.endswith("+full")
+            prob.mg_setup(sm, omega, tpss.PRECISIONS[prec], flexible_cg=0 if prec == "fp64" else 1,
+                          mult_residual=tpss.MULT_RESIDUAL_FULL if full else tpss.MULT_RESIDUAL_UPDATE)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -452,11 +464,11 @@ def run_mgcg(tpss, workloads, torch, cases):
             torch.cuda.synchronize()
             rec = {"time_s": e0.elapsed_time(e1) / 1e3, "iterations": res["iters"], "rel_res": res["rel_res"],
                    "status": status, "ndofs": N}
-            if prec == "fp64" and status == "converged":
+            if prec_mode == "fp64" and status == "converged":
                 x64.copy_(x)
             elif status == "converged" and x64.abs().max().item() > 0:
                 rec["rel_diff_to_fp64_solution"] = ((x - x64).norm() / x64.norm()).item()
-            out[f"k{k}_{sm}_omega{omega:g}_{prec}"] = rec
+            out[f"k{k}_{sm}_omega{omega:g}_{prec}" + ("_full_residual_per_color" if full else "")] = rec
         prob.close()
     return out
 
@@ -496,6 +508,73 @@ def run_paper_iterations(tpss, workloads, perf, torch):
                                            "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
                                            "paper_nu_frac": PAPER_NU[(sm, k)]}
         prob.close()
+    return out
+
+
+# tab:flop-additive: MFLOP of all local solvers of one additive smoother
+# application on T_3 = 16^3 cells (3375 vertex patches), d = 3, k = 15
+PAPER_MFLOP_K15 = {"AVS": 42709, "ACS": 3256}
+# tab:cubecp / tab:cubemvpminimal, 3D, L = 1, k = 15
+PAPER_NU_K15_L1 = {"ACS": 28.5, "MCS": 15.7, "MVS": 1.5}
+
+
+def run_high_degree(tpss, workloads, perf, torch, steps):
+    """k = 15 in FP64 (subdomains of n = 32 points per direction): the
+    additive vertex-patch and cell smoothers on the 16^3-cell mesh of the
+    paper's local-solver FLOP table, timed per call (CUDA events), with the
+    FLOP count of that table and the fraction of the FP64 pipe peak; and the
+    residual-based fractional iterations of the k = 15 columns on 3D L = 1."""
+    nc = 16
+    widths = workloads.widths_random(nc, 3, WIDTH_SEED)
+    out = {"workload": f"3D, {nc}^3 cells, widths U[0.5,1.5]/{nc} (seed {WIDTH_SEED}), k = 15, FP64, "
+                       "1 RHS U[-1,1], x = 0 form"}
+    prob = tpss.Problem(3, 15, widths)
+    N = prob.ndofs(0)
+    b = torch.from_numpy(workloads.rhs_batch(N, SEEDS[:1])).to("cuda")
+    x = torch.empty_like(b)
+    for name, kind, omega, kern in (("AVS", tpss.VERTEX_PATCH, 0.125, "patch_smooth_large_kernel<32>"),
+                                    ("ACS", tpss.CELL, 0.7, "patch_smooth_kernel<3,16,cell,double>")):
+        P = prob.setup_patches(0, kind)
+        for _ in range(2):
+            P.smooth_additive(omega, b, x, x_is_zero=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            P.smooth_additive(omega, b, x, x_is_zero=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        fl = perf.smoother_flops((nc, nc, nc), 15, vertex=kind == tpss.VERTEX_PATCH)
+        out[name] = {"kernel": kern, "ms_per_call": ms, "mflop_per_call": fl / 1e6,
+                     "paper_mflop_per_call": PAPER_MFLOP_K15[name], "tflops": fl / (ms / 1e3) / 1e12,
+                     "frac_fp64_peak": fl / (ms / 1e3) / perf.fp64_peak_flops(),
+                     "dofs_per_s": N / (ms / 1e3)}
+        P.close()
+    prob.close()
+    its = {}
+    prob = tpss.Problem(3, 15, workloads.widths_uniform(2, 3), nlevels=2)
+    N = prob.ndofs(1)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(1, 1, b)
+    x = torch.empty_like(b)
+    for sm in ("ACS", "MCS", "MVS"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sm == "ACS":
+            prob.mg_setup("ACS", 0.7, tpss.FP64)
+            e0.record()
+            res = prob.pcg_solve(b, x, rtol=1e-8, maxit=100, history=True)
+        else:
+            prob.mg_setup(sm, 1.0, tpss.FP64, nonsymmetric=1)
+            e0.record()
+            res = prob.gmres_solve(b, x, rtol=1e-8, maxit=100, restart=30, history=True)
+        e1.record()
+        torch.cuda.synchronize()
+        its[f"{sm}_L1"] = {"krylov": "cg" if sm == "ACS" else "gmres", "iterations": res["iters"],
+                           "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
+                           "paper_nu_frac": PAPER_NU_K15_L1[sm], "time_s": e0.elapsed_time(e1) / 1e3}
+    prob.close()
+    out["paper_iterations_k15"] = its
     return out
 
 
@@ -608,10 +687,10 @@ def run_batch_one(tpss, workloads, torch, steps, prec):
 MGCG_CASES = [
     (4, "AVS", 0.7, ["fp64"]),
     (4, "AVS", 0.125, ["fp64", "fp32", "tf32", "bf16"]),
-    (4, "MVS", 1.0, ["fp64", "fp32", "tf32", "bf16"]),
+    (4, "MVS", 1.0, ["fp64", "fp64+full", "fp32", "tf32", "bf16"]),
     (3, "MVS", 1.0, ["fp64", "tf32"]),
     (5, "MVS", 1.0, ["fp64", "tf32"]),
-    (7, "MVS", 1.0, ["fp64", "tf32"]),
+    (7, "MVS", 1.0, ["fp64", "fp64+full", "tf32"]),
 ]
 
 

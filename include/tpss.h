@@ -67,7 +67,7 @@ typedef enum { TPSS_PENALTY_PAPER = 0, TPSS_PENALTY_KP1SQ = 1 } tpss_penalty_pol
  * (lower corner at the origin); level l bisects T_0 l times. */
 typedef struct {
   int dim;                  /* 2 or 3 */
-  int degree;               /* k, 1 <= k <= 7 */
+  int degree;               /* k, 1 <= k <= 15 (FP32/TF32/BF16 smoothers and batches: k <= 7) */
   int ncells[3];            /* cells per direction on level 0 (ncells[2] ignored for dim 2) */
   const double* widths[3];  /* HOST arrays, copied during tpss_create */
   int nlevels;              /* >= 1; level nlevels-1 is the finest */
@@ -101,8 +101,12 @@ const char* tpss_last_error(void);
  * cyclic Jacobi on L^{-1} A L^{-T}).  Also builds the colorings (additive:
  * none for cells, 2^d parity colors for vertex patches; multiplicative:
  * red-black for cells, 2^(d+1) colors for vertex patches, Sec. 2.3) and the
- * per-subdomain table 1/(lambda_i + lambda_j + lambda_l) of eq. fastinverse.
- * Level must be >= 0; vertex patches need >= 2 cells per direction.
+ * per-subdomain table 1/(lambda_i + lambda_j + lambda_l) of eq. fastinverse
+ * (FP64, except 3D vertex patches with k >= 8, whose n = 2(k+1) >= 18 local
+ * solves form these sums on the fly and keep their n^3 tensors in a device
+ * scratch of one slab per resident CTA, allocated here).
+ * Level must be >= 0; vertex patches need >= 2 cells per direction;
+ * precisions other than FP64 need k <= 7.
  * Returns TPSS_ENUMERIC if some 1D problem is not positive definite.
  * Synchronizes the stream. */
 tpss_status tpss_setup_patches(tpss_ctx* ctx, int level, int kind, int precision,
@@ -125,6 +129,21 @@ tpss_status tpss_patches_eigendata(const tpss_patches* patches, int t, int pos,
  * the parity coloring only (same-color patches then share faces, so the sweep
  * is not eq. multschwarz1 in any order). */
 tpss_status tpss_patches_set_mult_colors(tpss_patches* patches, int ncolors);
+
+/* Residual handling of the multiplicative sweep (tpss_smooth_multiplicative).
+ *   UPDATE (default): r = b - A x is formed once per sweep and updated after
+ *     each color instead of being recomputed (Alg. 3 recomputes it; the paper
+ *     names avoiding this as the main cost reduction for MVS).  Exact up to
+ *     rounding: the coloring keeps face-adjacent cells of one color in one
+ *     subdomain and the local solves are exact, so r becomes (1 - omega) r on
+ *     the color's cells and changes by the face couplings of the update on
+ *     the cells next to them.  Used with the 2^(d+1)-color vertex coloring
+ *     or red-black cells (the 2^d-color coloring recomputes the residual).
+ *     With FP32 / TF32 / BF16 contractions (mixed V-cycles) the carried
+ *     residual omits the rounding error of the local solves.
+ *   FULL: recompute r = b - A x before every color (Alg. 3 as printed). */
+typedef enum { TPSS_MULT_RESIDUAL_UPDATE = 0, TPSS_MULT_RESIDUAL_FULL = 1 } tpss_mult_residual;
+tpss_status tpss_patches_set_mult_residual(tpss_patches* patches, int mode);
 
 /* ------------------------------------------------------------- smoothers --
  * Additive Schwarz smoother, Alg. 2 with the damping of eq. additiveschwarz:
@@ -199,12 +218,25 @@ typedef struct {
   int flexible_cg;     /* 1: Polak-Ribiere beta in tpss_pcg_solve (use with inexact V-cycles) */
   int nonsymmetric;    /* 1: the post-smoother keeps the pre-smoother's color order (the
                           non-symmetric V-cycle used with GMRES); 0: reversed (symmetric) */
+  int coarse_solver;   /* tpss_coarse_solver (0 = automatic) */
+  int mult_residual;   /* tpss_mult_residual for MCS / MVS (0 = update per color) */
 } tpss_mg_params;
 
-/* Build smoothers on levels 1..L and the coarse solver on level 0 (the level 0
- * matrix assembled by applying the operator to unit vectors and inverted by
- * Gauss-Jordan elimination on the device; this replaces the paper's
- * Chebyshev coarse iteration by an exact solve).  Synchronizes the stream. */
+/* Exact coarse solvers on level 0.
+ *   DENSE: A_0 assembled by applying the operator to unit vectors and inverted
+ *          by Gauss-Jordan elimination on the device (level 0 up to 16384
+ *          unknowns); one dense matrix-vector product per solve.
+ *   FD:    when level 0 has 1 cell per direction (one cell subdomain) or 2
+ *          cells per direction (one vertex patch), the subdomain is the whole
+ *          mesh and its fast-diagonalization inverse (Sec. 3.2) is A_0^{-1}
+ *          exactly (FP64 V-cycles only).
+ *   AUTO:  FD where it applies and level 0 has more than 4096 unknowns, else
+ *          DENSE. */
+typedef enum { TPSS_COARSE_AUTO = 0, TPSS_COARSE_DENSE = 1, TPSS_COARSE_FD = 2 } tpss_coarse_solver;
+
+/* Build smoothers on levels 1..L and the exact coarse solver on level 0 (this
+ * replaces the paper's Chebyshev coarse iteration).  TPSS_EINVAL if the
+ * requested coarse solver does not apply.  Synchronizes the stream. */
 tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params);
 
 /* One V-cycle of Alg. 1 on the finest level with x_L = 0 on entry:

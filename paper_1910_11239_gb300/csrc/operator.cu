@@ -225,8 +225,15 @@ tpss_status apply_operator_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* 
   TPSS_OP_CASE(3, 6) TPSS_OP_CASE(3, 7) TPSS_OP_CASE(3, 8)
   TPSS_OP_CASE(2, 2) TPSS_OP_CASE(2, 3) TPSS_OP_CASE(2, 4) TPSS_OP_CASE(2, 5)
   TPSS_OP_CASE(2, 6) TPSS_OP_CASE(2, 7) TPSS_OP_CASE(2, 8)
+  if constexpr (sizeof(T) == sizeof(double)) {   // degrees 8..15: FP64 only
+    TPSS_OP_CASE(3, 9) TPSS_OP_CASE(3, 10) TPSS_OP_CASE(3, 11) TPSS_OP_CASE(3, 12)
+    TPSS_OP_CASE(3, 13) TPSS_OP_CASE(3, 14) TPSS_OP_CASE(3, 15) TPSS_OP_CASE(3, 16)
+    TPSS_OP_CASE(2, 9) TPSS_OP_CASE(2, 10) TPSS_OP_CASE(2, 11) TPSS_OP_CASE(2, 12)
+    TPSS_OP_CASE(2, 13) TPSS_OP_CASE(2, 14) TPSS_OP_CASE(2, 15) TPSS_OP_CASE(2, 16)
+  }
 #undef TPSS_OP_CASE
-  set_error("operator: unsupported degree");
+  set_error(sizeof(T) == sizeof(double) ? "operator: unsupported degree"
+                                        : "operator: FP32 operators support degrees up to 7");
   return TPSS_EINVAL;
 }
 
@@ -243,6 +250,10 @@ tpss_status apply_operator_into(tpss_ctx* ctx, int level, int nrhs, const double
   TPSS_OPI_CASE(3, 6) TPSS_OPI_CASE(3, 7) TPSS_OPI_CASE(3, 8)
   TPSS_OPI_CASE(2, 2) TPSS_OPI_CASE(2, 3) TPSS_OPI_CASE(2, 4) TPSS_OPI_CASE(2, 5)
   TPSS_OPI_CASE(2, 6) TPSS_OPI_CASE(2, 7) TPSS_OPI_CASE(2, 8)
+  TPSS_OPI_CASE(3, 9) TPSS_OPI_CASE(3, 10) TPSS_OPI_CASE(3, 11) TPSS_OPI_CASE(3, 12)
+  TPSS_OPI_CASE(3, 13) TPSS_OPI_CASE(3, 14) TPSS_OPI_CASE(3, 15) TPSS_OPI_CASE(3, 16)
+  TPSS_OPI_CASE(2, 9) TPSS_OPI_CASE(2, 10) TPSS_OPI_CASE(2, 11) TPSS_OPI_CASE(2, 12)
+  TPSS_OPI_CASE(2, 13) TPSS_OPI_CASE(2, 14) TPSS_OPI_CASE(2, 15) TPSS_OPI_CASE(2, 16)
 #undef TPSS_OPI_CASE
   set_error("operator: unsupported degree");
   return TPSS_EINVAL;

@@ -97,54 +97,68 @@ __device__ bool gauss_rule(int nq, double* x, double* w) {
   return ok;
 }
 
-__global__ void setup_basis_kernel(Basis1D* B, int k) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block: thread 0 finds the nodes and Gauss rules (Newton), then the
+// tables are filled in parallel; the reference mass and stiffness matrices
+// come from tabulated basis values and derivatives at the Gauss points.
+constexpr int kBasisThreads = 256;
+
+__global__ void __launch_bounds__(kBasisThreads) setup_basis_kernel(Basis1D* B, int k) {
+  __shared__ double Vq[kMaxN1 * kMaxN1], Dq[kMaxN1 * kMaxN1];   // phi_i(xq_q), phi_i'(xq_q) at [q*n1+i]
   const double pi = 3.14159265358979323846;
-  const int n1 = k + 1;
-  B->k = k;
-  B->n1 = n1;
-  B->nq_rhs = k + 2;
-  B->status = 0;
-  // Gauss-Lobatto nodes: end points and roots of P_k' (Newton, P_k'' from the
-  // Legendre equation (1-t^2) P'' = 2 t P' - k(k+1) P).
-  double t_nodes[kMaxN1];
-  t_nodes[0] = -1.0;
-  t_nodes[k] = 1.0;
-  for (int j = 1; j < k; ++j) {
-    double t = -cos(pi * j / k);
-    int it = 0;
-    for (; it < 100; ++it) {
-      double P, dP;
-      legendre_eval(k, t, &P, &dP);
-      double d2P = (2.0 * t * dP - k * (k + 1.0) * P) / (1.0 - t * t);
-      double dt = dP / d2P;
-      t -= dt;
-      if (fabs(dt) < 1e-16) break;
+  const int n1 = k + 1, tid = threadIdx.x;
+  if (tid == 0) {
+    B->k = k;
+    B->n1 = n1;
+    B->nq_rhs = k + 2;
+    B->status = 0;
+    // Gauss-Lobatto nodes: end points and roots of P_k' (Newton, P_k'' from the
+    // Legendre equation (1-t^2) P'' = 2 t P' - k(k+1) P).
+    double t_nodes[kMaxN1];
+    t_nodes[0] = -1.0;
+    t_nodes[k] = 1.0;
+    for (int j = 1; j < k; ++j) {
+      double t = -cos(pi * j / k);
+      int it = 0;
+      for (; it < 100; ++it) {
+        double P, dP;
+        legendre_eval(k, t, &P, &dP);
+        double d2P = (2.0 * t * dP - k * (k + 1.0) * P) / (1.0 - t * t);
+        double dt = dP / d2P;
+        t -= dt;
+        if (fabs(dt) < 1e-16) break;
+      }
+      if (it == 100) B->status = 1;
+      t_nodes[j] = t;
     }
-    if (it == 100) B->status = 1;
-    t_nodes[j] = t;
+    for (int j = 0; j <= k; ++j) B->nodes[j] = 0.5 * (t_nodes[j] + 1.0);
+    if (!gauss_rule(n1, B->xq, B->wq)) B->status = 2;
+    if (!gauss_rule(n1 + 1, B->xr, B->wr)) B->status = 3;
   }
-  for (int j = 0; j <= k; ++j) B->nodes[j] = 0.5 * (t_nodes[j] + 1.0);
-  if (!gauss_rule(n1, B->xq, B->wq)) B->status = 2;
-  if (!gauss_rule(n1 + 1, B->xr, B->wr)) B->status = 3;
+  __syncthreads();
   const double* nd = B->nodes;
-  for (int q = 0; q < n1 + 1; ++q)
-    for (int i = 0; i < n1; ++i) B->Vr[q * n1 + i] = lagrange_val(nd, n1, i, B->xr[q]);
-  for (int i = 0; i < n1; ++i) {
+  for (int e = tid; e < n1 * n1; e += kBasisThreads) {
+    const int q = e / n1, i = e % n1;
+    Vq[e] = lagrange_val(nd, n1, i, B->xq[q]);
+    Dq[e] = lagrange_der(nd, n1, i, B->xq[q]);
+    for (int s2 = 0; s2 < 2; ++s2) B->Pc[s2][e] = lagrange_val(nd, n1, i, 0.5 * (nd[q] + s2));   // e = q*n1+i: row q, col i
+  }
+  for (int e = tid; e < (n1 + 1) * n1; e += kBasisThreads)
+    B->Vr[e] = lagrange_val(nd, n1, e % n1, B->xr[e / n1]);
+  for (int i = tid; i < n1; i += kBasisThreads) {
     B->d0[i] = lagrange_der(nd, n1, i, 0.0);
     B->d1[i] = lagrange_der(nd, n1, i, 1.0);
   }
-  for (int i = 0; i < n1; ++i)
-    for (int j = 0; j < n1; ++j) {
-      double m = 0.0, l = 0.0;
-      for (int q = 0; q < n1; ++q) {
-        m += B->wq[q] * lagrange_val(nd, n1, i, B->xq[q]) * lagrange_val(nd, n1, j, B->xq[q]);
-        l += B->wq[q] * lagrange_der(nd, n1, i, B->xq[q]) * lagrange_der(nd, n1, j, B->xq[q]);
-      }
-      B->Mhat[i * n1 + j] = m;
-      B->Lhat[i * n1 + j] = l;
-      for (int s = 0; s < 2; ++s) B->Pc[s][i * n1 + j] = lagrange_val(nd, n1, j, 0.5 * (nd[i] + s));
+  __syncthreads();
+  for (int e = tid; e < n1 * n1; e += kBasisThreads) {
+    const int i = e / n1, j = e % n1;
+    double m = 0.0, l = 0.0;
+    for (int q = 0; q < n1; ++q) {
+      m += B->wq[q] * Vq[q * n1 + i] * Vq[q * n1 + j];
+      l += B->wq[q] * Dq[q * n1 + i] * Dq[q * n1 + j];
     }
+    B->Mhat[e] = m;
+    B->Lhat[e] = l;
+  }
 }
 
 // Per-level 1D data.  For cell c of direction t with width h = w[c]:
@@ -489,6 +503,7 @@ static void free_patches(tpss_patches* P) {
     dfree(P->d_Z32[t]); dfree(P->d_lam32[t]);
   }
   dfree(P->d_inv);
+  dfree(P->d_scratch);
   dfree(P->d_add_list);
   dfree(P->d_mul_list);
   dfree(P->d_mul8_list);
@@ -507,7 +522,7 @@ extern "C" tpss_status tpss_create(const tpss_problem_desc* desc, void* cuda_str
   TPSS_REQUIRE(desc && out, "tpss_create: null argument");
   *out = nullptr;
   TPSS_REQUIRE(desc->dim == 2 || desc->dim == 3, "tpss_create: dim must be 2 or 3");
-  TPSS_REQUIRE(desc->degree >= 1 && desc->degree <= kMaxDegree, "tpss_create: degree must be in 1..7");
+  TPSS_REQUIRE(desc->degree >= 1 && desc->degree <= kMaxDegree, "tpss_create: degree must be in 1..15");
   TPSS_REQUIRE(desc->nlevels >= 1 && desc->nlevels <= 12, "tpss_create: nlevels must be in 1..12");
   TPSS_REQUIRE(desc->gamma_hat > 0.0, "tpss_create: gamma_hat must be positive");
   TPSS_REQUIRE(desc->penalty_poly == TPSS_PENALTY_PAPER || desc->penalty_poly == TPSS_PENALTY_KP1SQ,
@@ -555,7 +570,7 @@ extern "C" tpss_status tpss_create(const tpss_problem_desc* desc, void* cuda_str
   if ((st = dalloc_t(&ctx->d_basis, 1)) != TPSS_OK) return fail(st);
   if ((st = dalloc_t(&ctx->d_scalars, 64)) != TPSS_OK) return fail(st);
   if ((st = dalloc_t(&ctx->d_partials, 4096)) != TPSS_OK) return fail(st);
-  setup_basis_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_basis, ctx->k);
+  setup_basis_kernel<<<1, kBasisThreads, 0, ctx->stream>>>(ctx->d_basis, ctx->k);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("setup_basis_kernel launch failed");
     return fail(TPSS_ECUDA);
@@ -634,7 +649,7 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
     if ((st = dalloc_t(&P->d_lam[t], (size_t)np * n)) != TPSS_OK) return fail(st);
     patch_matrices_kernel<<<np, 128, 0, ctx->stream>>>(ctx->d_basis, L.op64.M[t], L.op64.A[t], L.op64.F[t],
                                                        np, kind == TPSS_VERTEX_PATCH, P->d_A[t], P->d_M[t]);
-    const int warps = 4;
+    const int warps = n > 16 ? 1 : 4;
     const size_t smem = (size_t)warps * 3 * n * n * sizeof(double);
     gen_eig_kernel<<<(np + warps - 1) / warps, warps * 32, smem, ctx->stream>>>(
         P->d_A[t], P->d_M[t], np, n, P->d_Z[t], P->d_lam[t], d_err);
@@ -650,7 +665,11 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
       convert(P->d_lam[t], P->d_lam32[t], (size_t)np * n, ctx->stream);
     }
   }
-  if (precision == TPSS_FP64) {
+  const bool large = d == 3 && n > kMaxSharedPatchN;
+  if (large) {   // per-CTA tensor slabs of the large-patch kernel (no inverse table)
+    if ((st = patch_large_ctas(n, ctx->num_sms, &P->scratch_ctas)) != TPSS_OK) return fail(st);
+    if ((st = dalloc_t(&P->d_scratch, (size_t)P->scratch_ctas * n * n * n)) != TPSS_OK) return fail(st);
+  } else if (precision == TPSS_FP64) {
     const size_t vol = d == 3 ? (size_t)n * n * n : (size_t)n * n;
     if ((st = dalloc_t(&P->d_inv, vol * P->nsub)) != TPSS_OK) return fail(st);
     inv_table_kernel<<<2048, 256, 0, ctx->stream>>>(P->d_lam[0], P->d_lam[1], d == 3 ? P->d_lam[2] : nullptr,
@@ -724,6 +743,8 @@ extern "C" tpss_status tpss_setup_patches(tpss_ctx* ctx, int level, int kind, in
   TPSS_REQUIRE(level >= 0 && level < ctx->nlevels, "tpss_setup_patches: level out of range");
   TPSS_REQUIRE(kind == TPSS_CELL || kind == TPSS_VERTEX_PATCH, "tpss_setup_patches: unknown kind");
   TPSS_REQUIRE(precision >= TPSS_FP64 && precision <= TPSS_BF16, "tpss_setup_patches: unknown precision");
+  TPSS_REQUIRE(precision == TPSS_FP64 || ctx->k <= kMaxMixedDegree,
+               "tpss_setup_patches: FP32/TF32/BF16 smoothers support degrees up to 7");
   if (kind == TPSS_VERTEX_PATCH)
     for (int t = 0; t < ctx->dim; ++t)
       TPSS_REQUIRE(ctx->levels[level].nc[t] >= 2, "tpss_setup_patches: vertex patches need >= 2 cells per direction");
@@ -781,5 +802,14 @@ extern "C" tpss_status tpss_patches_set_mult_colors(tpss_patches* P, int ncolors
     TPSS_REQUIRE(ncolors == 2, "tpss_patches_set_mult_colors: cells take 2 colors");
   }
   P->mul_colors_active = ncolors;
+  return TPSS_OK;
+}
+
+extern "C" tpss_status tpss_patches_set_mult_residual(tpss_patches* P, int mode) {
+  clear_error();
+  TPSS_REQUIRE(P, "tpss_patches_set_mult_residual: null patches");
+  TPSS_REQUIRE(mode == TPSS_MULT_RESIDUAL_UPDATE || mode == TPSS_MULT_RESIDUAL_FULL,
+               "tpss_patches_set_mult_residual: mode must be 0 (update) or 1 (full)");
+  P->mult_update = mode == TPSS_MULT_RESIDUAL_UPDATE ? 1 : 0;
   return TPSS_OK;
 }

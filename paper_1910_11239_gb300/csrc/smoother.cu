@@ -29,8 +29,14 @@ struct PatchShape {
   static constexpr int VOL = DIM == 3 ? PS * N : LS * N;
   static constexpr int VOLC = DIM == 3 ? N * N * N : N * N;
   // subdomains per CTA: about 256 threads, except n = 14 (196 lines: one
-  // subdomain would leave 12.5% of the lanes of its last warp idle)
-  static constexpr int PPB = LINES == 196 ? 2 : ((256 + LINES / 2) / LINES > 0 ? (256 + LINES / 2) / LINES : 1);
+  // subdomain would leave 12.5% of the lanes of its last warp idle), and at
+  // most what fits in 200 KB of shared memory (FP64 slot size; binds only
+  // for the 2D subdomains with n > 16)
+  static constexpr int PPB_LINES =
+      LINES == 196 ? 2 : ((256 + LINES / 2) / LINES > 0 ? (256 + LINES / 2) / LINES : 1);
+  static constexpr int SLOT_BYTES = (VOL + 2 * DIM * N * N + DIM * N) * 8;
+  static constexpr int PPB_SMEM = (200 * 1024) / SLOT_BYTES > 0 ? (200 * 1024) / SLOT_BYTES : 1;
+  static constexpr int PPB = PPB_LINES < PPB_SMEM ? PPB_LINES : PPB_SMEM;
   static constexpr int THREADS = PPB * LINES;
 };
 
@@ -43,6 +49,7 @@ struct SmoothArgs {
   int count;
   const T* r;
   T* x;
+  T* d;                // optional: d = omega u on the subdomain's DoFs (the update of x)
   T omega;
   int nc0, nc1;        // cells per direction (x, y)
   int np0, np1;        // subdomain positions per direction (x, y)
@@ -187,8 +194,9 @@ patch_smooth_kernel(SmoothArgs<T> a) {
       const int ix = loc % N1, iy = (loc / N1) % N1, iz = DIM == 3 ? loc / (N1 * N1) : 0;
       const int64_t gcell = (pos[0] + sx) + (int64_t)a.nc0 * ((pos[1] + sy) + (int64_t)a.nc1 * (DIM == 3 ? pos[2] + sz : 0));
       const int pidx = (sx * N1 + ix) + S::LS * (sy * N1 + iy) + (DIM == 3 ? S::PS * (sz * N1 + iz) : 0);
-      T* px = a.x + vbase + gcell * NLOC1 + loc;
-      *px = fma(a.omega, buf[pidx], *px);
+      const int64_t gi = vbase + gcell * NLOC1 + loc;
+      a.x[gi] = fma(a.omega, buf[pidx], a.x[gi]);
+      if (a.d != nullptr) a.d[gi] = a.omega * buf[pidx];
     }
   }
 }
@@ -213,16 +221,17 @@ static tpss_status launch_smooth(const SmoothArgs<T>& a, int nrhs, cudaStream_t 
 
 template <typename T>
 tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs, const T* r, T* x,
-                       cudaStream_t s) {
+                       cudaStream_t s, T* d) {
   if constexpr (sizeof(T) == 4) {
+    float* df = reinterpret_cast<float*>(d);
     if (P->precision == TPSS_BF16 && P->ctx->dim == 3) {
       const tpss_status st = patch_pass_bf16(P, list, count, (float)omega, nrhs, reinterpret_cast<const float*>(r),
-                                             reinterpret_cast<float*>(x), s);
+                                             reinterpret_cast<float*>(x), s, df);
       if (st != TPSS_EINVAL) return st;   // else: shape not covered, use the generic tensor-core kernel
     }
     if (P->precision == TPSS_TF32 || P->precision == TPSS_BF16)
       return patch_pass_tc(P, list, count, (float)omega, nrhs, reinterpret_cast<const float*>(r),
-                           reinterpret_cast<float*>(x), s);
+                           reinterpret_cast<float*>(x), s, df);
   }
   const tpss_ctx* ctx = P->ctx;
   const Level& L = ctx->levels[P->level];
@@ -241,6 +250,7 @@ tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int
   a.count = count;
   a.r = r;
   a.x = x;
+  a.d = d;
   a.omega = omega;
   a.nc0 = L.nc[0];
   a.nc1 = L.nc[1];
@@ -251,6 +261,15 @@ tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int
   const int n = P->n;
 #define TPSS_SM_CASE(D, NN, V)                                                     \
   if (ctx->dim == D && n == NN && v == V) return launch_smooth<D, NN, V, T>(a, nrhs, s);
+  if constexpr (sizeof(T) == sizeof(double)) {   // degrees 8..15: FP64 only
+    if (ctx->dim == 3 && v && n > kMaxSharedPatchN) return patch_pass_large(P, list, count, omega, nrhs, r, x, s, d);
+    TPSS_SM_CASE(3, 9, false) TPSS_SM_CASE(3, 10, false) TPSS_SM_CASE(3, 11, false) TPSS_SM_CASE(3, 12, false)
+    TPSS_SM_CASE(3, 13, false) TPSS_SM_CASE(3, 14, false) TPSS_SM_CASE(3, 15, false) TPSS_SM_CASE(3, 16, false)
+    TPSS_SM_CASE(2, 9, false) TPSS_SM_CASE(2, 10, false) TPSS_SM_CASE(2, 11, false) TPSS_SM_CASE(2, 12, false)
+    TPSS_SM_CASE(2, 13, false) TPSS_SM_CASE(2, 14, false) TPSS_SM_CASE(2, 15, false) TPSS_SM_CASE(2, 16, false)
+    TPSS_SM_CASE(2, 18, true) TPSS_SM_CASE(2, 20, true) TPSS_SM_CASE(2, 22, true) TPSS_SM_CASE(2, 24, true)
+    TPSS_SM_CASE(2, 26, true) TPSS_SM_CASE(2, 28, true) TPSS_SM_CASE(2, 30, true) TPSS_SM_CASE(2, 32, true)
+  }
   TPSS_SM_CASE(3, 4, true) TPSS_SM_CASE(3, 6, true) TPSS_SM_CASE(3, 8, true) TPSS_SM_CASE(3, 10, true)
   TPSS_SM_CASE(3, 12, true) TPSS_SM_CASE(3, 14, true) TPSS_SM_CASE(3, 16, true)
   TPSS_SM_CASE(3, 2, false) TPSS_SM_CASE(3, 3, false) TPSS_SM_CASE(3, 4, false) TPSS_SM_CASE(3, 5, false)
@@ -264,8 +283,10 @@ tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int
   return TPSS_EINVAL;
 }
 
-template tpss_status patch_pass<double>(tpss_patches*, const int*, int, double, int, const double*, double*, cudaStream_t);
-template tpss_status patch_pass<float>(tpss_patches*, const int*, int, float, int, const float*, float*, cudaStream_t);
+template tpss_status patch_pass<double>(tpss_patches*, const int*, int, double, int, const double*, double*, cudaStream_t,
+                                        double*);
+template tpss_status patch_pass<float>(tpss_patches*, const int*, int, float, int, const float*, float*, cudaStream_t,
+                                       float*);
 
 template <typename T>
 static T* residual_buffer(Level& L);
@@ -273,6 +294,12 @@ template <>
 double* residual_buffer<double>(Level& L) { return L.t64[4]; }
 template <>
 float* residual_buffer<float>(Level& L) { return L.t32[4]; }
+template <typename T>
+static T* update_buffer(Level& L);
+template <>
+double* update_buffer<double>(Level& L) { return L.t64[0]; }
+template <>
+float* update_buffer<float>(Level& L) { return L.t32[0]; }
 
 template <typename T>
 tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T* x, int x_is_zero) {
@@ -296,6 +323,15 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
   return TPSS_OK;
 }
 
+// Multiplicative sweep over the colors (Alg. 3).  With P->mult_update set
+// (default; used where it is exact: red-black cells and the 2^(d+1)-color
+// vertex coloring) the residual is formed once and then updated after each
+// color from the color's update d (smoother_mult.cu); otherwise
+// r = b - A x is recomputed before every color.  The update takes the local
+// solves as exact; with FP32 / TF32 / BF16 contractions it therefore omits
+// their rounding error from the residual it carries (a change of the
+// preconditioner at that level, which the flexible PCG of the mixed path
+// absorbs; tests compare iteration counts with the recomputed residual).
 template <typename T>
 tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int nrhs, const T* b, T* x) {
   tpss_ctx* ctx = P->ctx;
@@ -307,6 +343,24 @@ tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int n
   const std::vector<int>& offs = alt ? P->mul8_offsets : P->mul_offsets;
   const int* list = alt ? P->d_mul8_list : P->d_mul_list;
   const int nc = (int)offs.size() - 1;
+  const bool update = P->mult_update && !alt;
+  if (update) {
+    T* dx = update_buffer<T>(L);   // an operator temporary, free after the first residual
+    TPSS_TRY(apply_operator_t<T>(ctx, P->level, nrhs, x, rb, b));
+    int last = -1;
+    for (int i = 0; i < nc; ++i) {
+      const int c = reverse ? nc - 1 - i : i;
+      if (offs[c + 1] > offs[c]) last = i;
+    }
+    for (int i = 0; i <= last; ++i) {
+      const int c = reverse ? nc - 1 - i : i;
+      const int o = offs[c], cnt = offs[c + 1] - o;
+      if (cnt == 0) continue;
+      TPSS_TRY(patch_pass<T>(P, list + o, cnt, omega, nrhs, rb, x, s, dx));
+      if (i < last) TPSS_TRY(mult_residual_update<T>(P, c, omega, nrhs, dx, rb, s));
+    }
+    return TPSS_OK;
+  }
   for (int i = 0; i < nc; ++i) {
     const int c = reverse ? nc - 1 - i : i;
     const int o = offs[c], cnt = offs[c + 1] - o;

@@ -26,8 +26,9 @@ namespace bf {
 
 // x[cell rows] = SX + omega T, one cell row per iteration.
 template <int N, int N1, int NCELL>
-__device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, const __nv_bfloat16* __restrict__ T,
-                                            const float* __restrict__ SX, float omega, const CellBase& cb, int tid) {
+__device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, float* __restrict__ dr,
+                                            const __nv_bfloat16* __restrict__ T, const float* __restrict__ SX,
+                                            float omega, const CellBase& cb, int tid) {
   using S = Shape<N>;
   constexpr int V = RowVec<N1>::V;
   constexpr int NLOC1 = N1 * N1 * N1;
@@ -38,7 +39,8 @@ __device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, const __nv_b
     const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
     const float* xo = SX + c * NLOC1 + rr * N1;
     const __nv_bfloat16* t = T + sx * N1 + LS * (sy * N1 + iy) + S::PS * (sz * N1 + iz);
-    float* dst = xr + cb.template operator()<NLOC1>(c) + rr * N1;
+    const int64_t off = cb.template operator()<NLOC1>(c) + rr * N1;
+    float* dst = xr + off;
 #pragma unroll
     for (int v = 0; v < N1; v += V) {
       if constexpr (V == 4) {
@@ -52,6 +54,9 @@ __device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, const __nv_b
         o.z = fmaf(omega, t23.x, a.z);
         o.w = fmaf(omega, t23.y, a.w);
         *reinterpret_cast<float4*>(dst + v) = o;
+        if (dr != nullptr)
+          *reinterpret_cast<float4*>(dr + off + v) = make_float4(omega * t01.x, omega * t01.y, omega * t23.x,
+                                                                 omega * t23.y);
       } else if constexpr (V == 2) {
         const float2 a = *reinterpret_cast<const float2*>(xo + v);
         const float2 tt = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(t + v));
@@ -59,8 +64,10 @@ __device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, const __nv_b
         o.x = fmaf(omega, tt.x, a.x);
         o.y = fmaf(omega, tt.y, a.y);
         *reinterpret_cast<float2*>(dst + v) = o;
+        if (dr != nullptr) *reinterpret_cast<float2*>(dr + off + v) = make_float2(omega * tt.x, omega * tt.y);
       } else {
         dst[v] = fmaf(omega, __bfloat162float(t[v]), xo[v]);
+        if (dr != nullptr) dr[off + v] = omega * __bfloat162float(t[v]);
       }
     }
   }
@@ -71,8 +78,8 @@ template <int N, bool VERTEX>
 __global__ void __launch_bounds__(kThreads, 3)
 patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__ Z0, const float* __restrict__ Z1,
                          const float* __restrict__ Z2, const float* __restrict__ L0, const float* __restrict__ L1,
-                         const float* __restrict__ L2, const float* __restrict__ r, float* __restrict__ x, float omega,
-                         int nc0, int nc1, int64_t ndofs, int nrhs) {
+                         const float* __restrict__ L2, const float* __restrict__ r, float* __restrict__ x,
+                         float* __restrict__ d, float omega, int nc0, int nc1, int64_t ndofs, int nrhs) {
   using S = Shape<N>;
   constexpr int N1 = VERTEX ? N / 2 : N;
   constexpr int NLOC1 = N1 * N1 * N1;
@@ -126,7 +133,8 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
     __syncthreads();
     contract<N, 0>(T, bx, warp, lane);
     __syncthreads();
-    tensor_to_x<N, N1, NCELL>(x + (int64_t)rhs * ndofs, T, sx_cur, omega, cbase, tid);
+    tensor_to_x<N, N1, NCELL>(x + (int64_t)rhs * ndofs, d ? d + (int64_t)rhs * ndofs : nullptr, T, sx_cur, omega,
+                              cbase, tid);
   }
 }
 
@@ -139,7 +147,7 @@ constexpr size_t smem_bytes() {
 
 template <int N, bool VERTEX>
 static tpss_status launch(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                          float* x, cudaStream_t s) {
+                          float* x, float* d, cudaStream_t s) {
   constexpr size_t smem = smem_bytes<N, VERTEX>();
   static bool attr = false;
   if (!attr) {
@@ -150,7 +158,7 @@ static tpss_status launch(tpss_patches* P, const int* list, int count, float ome
   if (count <= 0) return TPSS_OK;
   const Level& L = P->ctx->levels[P->level];
   patch_smooth_bf16_kernel<N, VERTEX><<<count, kThreads, smem, s>>>(
-      list, P->d_Z32[0], P->d_Z32[1], P->d_Z32[2], P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r, x, omega,
+      list, P->d_Z32[0], P->d_Z32[1], P->d_Z32[2], P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r, x, d, omega,
       L.nc[0], L.nc[1], L.ndofs, nrhs);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
@@ -160,23 +168,24 @@ static tpss_status launch(tpss_patches* P, const int* list, int count, float ome
 
 // 3D BF16 path; returns TPSS_EINVAL (without launching) for shapes it does not cover.
 tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                            float* x, cudaStream_t s) {
+                            float* x, cudaStream_t s, float* d) {
   if (P->ctx->dim != 3) return TPSS_EINVAL;
   // 16-byte cp.async and vector accesses need 16-byte aligned vectors; other
   // pointers take the generic tensor-core kernel
-  if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x)) & 15) return TPSS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(d)) & 15)
+    return TPSS_EINVAL;
   const bool v = P->kind == TPSS_VERTEX_PATCH;
   switch (P->n) {
-    case 4: return v ? bf::launch<4, true>(P, list, count, omega, nrhs, r, x, s)
-                     : bf::launch<4, false>(P, list, count, omega, nrhs, r, x, s);
-    case 6: return v ? bf::launch<6, true>(P, list, count, omega, nrhs, r, x, s)
-                     : bf::launch<6, false>(P, list, count, omega, nrhs, r, x, s);
-    case 8: return v ? bf::launch<8, true>(P, list, count, omega, nrhs, r, x, s)
-                     : bf::launch<8, false>(P, list, count, omega, nrhs, r, x, s);
-    case 10: return v ? bf::launch<10, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
-    case 12: return v ? bf::launch<12, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
-    case 14: return v ? bf::launch<14, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
-    case 16: return v ? bf::launch<16, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
+    case 4: return v ? bf::launch<4, true>(P, list, count, omega, nrhs, r, x, d, s)
+                     : bf::launch<4, false>(P, list, count, omega, nrhs, r, x, d, s);
+    case 6: return v ? bf::launch<6, true>(P, list, count, omega, nrhs, r, x, d, s)
+                     : bf::launch<6, false>(P, list, count, omega, nrhs, r, x, d, s);
+    case 8: return v ? bf::launch<8, true>(P, list, count, omega, nrhs, r, x, d, s)
+                     : bf::launch<8, false>(P, list, count, omega, nrhs, r, x, d, s);
+    case 10: return v ? bf::launch<10, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
+    case 12: return v ? bf::launch<12, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
+    case 14: return v ? bf::launch<14, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
+    case 16: return v ? bf::launch<16, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
     default: return TPSS_EINVAL;
   }
 }

@@ -159,8 +159,8 @@ __device__ __forceinline__ void tc_contract(float* __restrict__ buf, const float
 template <int DIM, int N, bool VERTEX, bool BF16>
 __global__ void __launch_bounds__(TcShape<DIM, N, BF16>::THREADS)
 patch_smooth_tc_kernel(const int* __restrict__ list, int count, const float* __restrict__ r, float* __restrict__ x,
-                       float omega, int nc0, int nc1, int64_t ndofs, const float* Z0, const float* Z1,
-                       const float* Z2, const float* L0, const float* L1, const float* L2) {
+                       float* __restrict__ d, float omega, int nc0, int nc1, int64_t ndofs, const float* Z0,
+                       const float* Z1, const float* Z2, const float* L0, const float* L1, const float* L2) {
   using S = TcShape<DIM, N, BF16>;
   constexpr int N1 = VERTEX ? N / 2 : N;
   constexpr int NLOC1 = DIM == 3 ? N1 * N1 * N1 : N1 * N1;
@@ -227,15 +227,16 @@ patch_smooth_tc_kernel(const int* __restrict__ list, int count, const float* __r
       const int ix = loc % N1, iy = (loc / N1) % N1, iz = DIM == 3 ? loc / (N1 * N1) : 0;
       const int64_t gcell = (pos[0] + sx) + (int64_t)nc0 * ((pos[1] + sy) + (int64_t)nc1 * (DIM == 3 ? pos[2] + sz : 0));
       const int pidx = (sx * N1 + ix) + S::LS * (sy * N1 + iy) + (DIM == 3 ? S::PS * (sz * N1 + iz) : 0);
-      float* px = x + vbase + gcell * NLOC1 + loc;
-      *px = fmaf(omega, buf[pidx], *px);
+      const int64_t gi = vbase + gcell * NLOC1 + loc;
+      x[gi] = fmaf(omega, buf[pidx], x[gi]);
+      if (d != nullptr) d[gi] = omega * buf[pidx];   // the update, for the multiplicative residual update
     }
   }
 }
 
 template <int DIM, int N, bool VERTEX, bool BF16>
 static tpss_status launch_tc(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                             float* x, cudaStream_t s) {
+                             float* x, float* d, cudaStream_t s) {
   using S = TcShape<DIM, N, BF16>;
   const size_t smem = (size_t)S::PPB * S::SLOT * sizeof(float);
   if (smem > 48 * 1024)
@@ -245,7 +246,7 @@ static tpss_status launch_tc(tpss_patches* P, const int* list, int count, float 
   const Level& L = P->ctx->levels[P->level];
   dim3 grid((count + S::PPB - 1) / S::PPB, nrhs);
   patch_smooth_tc_kernel<DIM, N, VERTEX, BF16><<<grid, S::THREADS, smem, s>>>(
-      list, count, r, x, omega, L.nc[0], L.nc[1], L.ndofs, P->d_Z32[0], P->d_Z32[1],
+      list, count, r, x, d, omega, L.nc[0], L.nc[1], L.ndofs, P->d_Z32[0], P->d_Z32[1],
       DIM == 3 ? P->d_Z32[2] : P->d_Z32[0], P->d_lam32[0], P->d_lam32[1],
       DIM == 3 ? P->d_lam32[2] : P->d_lam32[0]);
   TPSS_CHECK_LAUNCH();
@@ -253,14 +254,14 @@ static tpss_status launch_tc(tpss_patches* P, const int* list, int count, float 
 }
 
 tpss_status patch_pass_tc(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                          float* x, cudaStream_t s) {
-  const int d = P->ctx->dim, n = P->n;
+                          float* x, cudaStream_t s, float* d) {
+  const int dim = P->ctx->dim, n = P->n;
   const bool v = P->kind == TPSS_VERTEX_PATCH;
   const bool bf = P->precision == TPSS_BF16;
 #define TPSS_TC_CASE(D, NN, V)                                                                  \
-  if (d == D && n == NN && v == V)                                                             \
-    return bf ? launch_tc<D, NN, V, true>(P, list, count, omega, nrhs, r, x, s)                \
-              : launch_tc<D, NN, V, false>(P, list, count, omega, nrhs, r, x, s);
+  if (dim == D && n == NN && v == V)                                                           \
+    return bf ? launch_tc<D, NN, V, true>(P, list, count, omega, nrhs, r, x, d, s)             \
+              : launch_tc<D, NN, V, false>(P, list, count, omega, nrhs, r, x, d, s);
   TPSS_TC_CASE(3, 4, true) TPSS_TC_CASE(3, 6, true) TPSS_TC_CASE(3, 8, true) TPSS_TC_CASE(3, 10, true)
   TPSS_TC_CASE(3, 12, true) TPSS_TC_CASE(3, 14, true) TPSS_TC_CASE(3, 16, true)
   TPSS_TC_CASE(3, 2, false) TPSS_TC_CASE(3, 3, false) TPSS_TC_CASE(3, 4, false) TPSS_TC_CASE(3, 5, false)

@@ -29,6 +29,7 @@ void destroy_mg(tpss_ctx* ctx) {
   if (!mg) return;
   for (auto* P : mg->patches)
     if (P) tpss_patches_destroy(P);
+  if (mg->coarse_fd) tpss_patches_destroy(mg->coarse_fd);
   dfree(mg->coarse_inv);
   dfree(mg->gj_tmp);
   for (auto* v : mg->b64) dfree(v);
@@ -163,10 +164,33 @@ __global__ void dense_mv_kernel(const double* __restrict__ A, const S* __restric
   if (lane == 0) y[row] = (D)s;
 }
 
+// Level 0 is a single subdomain (1 cell, or 2 cells = one vertex patch, per
+// direction): its fast-diagonalization inverse is A_0^{-1}.
+static bool coarse_is_one_subdomain(const tpss_ctx* ctx, int* kind) {
+  const Level& L0 = ctx->levels[0];
+  bool ones = true, twos = true;
+  for (int t = 0; t < ctx->dim; ++t) {
+    ones = ones && L0.nc[t] == 1;
+    twos = twos && L0.nc[t] == 2;
+  }
+  *kind = ones ? TPSS_CELL : TPSS_VERTEX_PATCH;
+  return ones || twos;
+}
+
+constexpr int64_t kDenseCoarseAuto = 4096;   // AUTO: dense inverse up to this size
+
 static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
   const Level& L0 = ctx->levels[0];
   const int64_t n = L0.ndofs;
   mg->n0 = n;
+  int kind = TPSS_CELL;
+  const bool fd_ok = !mg->mixed && coarse_is_one_subdomain(ctx, &kind);
+  const int choice = mg->params.coarse_solver;
+  if (choice == TPSS_COARSE_FD || (choice == TPSS_COARSE_AUTO && fd_ok && n > kDenseCoarseAuto)) {
+    TPSS_REQUIRE(fd_ok, "tpss_mg_setup: the fast-diagonalization coarse solve needs an FP64 V-cycle and "
+                        "1 or 2 cells per direction on level 0");
+    return create_patches(ctx, 0, kind, TPSS_FP64, &mg->coarse_fd);
+  }
   TPSS_REQUIRE(n <= 16384, "tpss_mg_setup: coarse level too large for the dense coarse solver");
   TPSS_TRY(dalloc_t(&mg->coarse_inv, (size_t)n * n));
   TPSS_TRY(dalloc_t(&mg->gj_tmp, (size_t)2 * n));
@@ -197,6 +221,12 @@ static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
 
 template <typename S, typename D>
 static tpss_status coarse_apply(tpss_ctx* ctx, MGState* mg, const S* b, D* x) {
+  if (mg->coarse_fd) {   // FP64 only (set up for FP64 V-cycles)
+    if constexpr (sizeof(S) == sizeof(double) && sizeof(D) == sizeof(double))
+      return smooth_additive_t<double>(mg->coarse_fd, 1.0, 1, b, x, 1);
+    set_error("coarse solve: the fast-diagonalization coarse solver is FP64 only");
+    return TPSS_EINVAL;
+  }
   const int64_t n = mg->n0;
   const int threads = 256;
   const int64_t blocks = (n * 32 + threads - 1) / threads;
@@ -478,6 +508,11 @@ extern "C" tpss_status tpss_assemble_rhs(tpss_ctx* ctx, int level, int kind, dou
   a.b = b;
   const int nq = ctx->n1 + 1;
   const size_t smem = 3 * (size_t)(ctx->dim == 3 ? nq * nq * nq : nq * nq) * sizeof(double);
+  static bool attr = false;   // up to 118 KB at k = 15 in 3D
+  if (!attr) {
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+    attr = true;
+  }
   rhs_kernel<<<(unsigned)L.ncells, 128, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
@@ -489,6 +524,12 @@ extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params
   TPSS_REQUIRE(params->smoother >= TPSS_ACS && params->smoother <= TPSS_MVS, "tpss_mg_setup: unknown smoother");
   TPSS_REQUIRE(params->precision >= TPSS_FP64 && params->precision <= TPSS_BF16, "tpss_mg_setup: unknown precision");
   TPSS_REQUIRE(params->omega > 0.0 && std::isfinite(params->omega), "tpss_mg_setup: omega must be positive");
+  TPSS_REQUIRE(params->precision == TPSS_FP64 || ctx->k <= kMaxMixedDegree,
+               "tpss_mg_setup: mixed-precision V-cycles support degrees up to 7");
+  TPSS_REQUIRE(params->coarse_solver >= TPSS_COARSE_AUTO && params->coarse_solver <= TPSS_COARSE_FD,
+               "tpss_mg_setup: unknown coarse solver");
+  TPSS_REQUIRE(params->mult_residual == TPSS_MULT_RESIDUAL_UPDATE || params->mult_residual == TPSS_MULT_RESIDUAL_FULL,
+               "tpss_mg_setup: mult_residual must be 0 (update) or 1 (full)");
   const bool vertex = params->smoother == TPSS_AVS || params->smoother == TPSS_MVS;
   if (vertex)
     for (int l = 1; l < ctx->nlevels; ++l)
@@ -516,6 +557,7 @@ extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params
       return fail(st);
     if (params->mult_colors != 0 && (params->smoother == TPSS_MVS || params->smoother == TPSS_MCS))
       if ((st = tpss_patches_set_mult_colors(mg->patches[l], params->mult_colors)) != TPSS_OK) return fail(st);
+    mg->patches[l]->mult_update = params->mult_residual == TPSS_MULT_RESIDUAL_FULL ? 0 : 1;
     if ((st = ensure_level_scratch(ctx, l, 1)) != TPSS_OK) return fail(st);
   }
   if ((st = ensure_level_scratch(ctx, 0, 1)) != TPSS_OK) return fail(st);

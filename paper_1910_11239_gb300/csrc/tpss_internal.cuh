@@ -20,7 +20,8 @@
 
 namespace tpss {
 
-constexpr int kMaxDegree = 7;
+constexpr int kMaxDegree = 15;
+constexpr int kMaxMixedDegree = 7;        // FP32 / TF32 / BF16 smoothers and batches
 constexpr int kMaxN1 = kMaxDegree + 1;    // (k+1)
 constexpr int kMaxNP = 2 * kMaxN1;        // 2(k+1): vertex patch 1D size
 constexpr int kMaxNQ = kMaxN1 + 1;        // Gauss points of the right-hand side rule
@@ -120,6 +121,7 @@ struct MGState {
   double* gm_V = nullptr;
   double* gm_Z = nullptr;
   double* gm_h = nullptr;                // device scalars (2 (restart+1))
+  tpss_patches* coarse_fd = nullptr;     // exact coarse solve by fast diagonalization (else coarse_inv)
 };
 
 }  // namespace tpss
@@ -150,7 +152,9 @@ struct tpss_patches {
   double* d_lam[3] = {nullptr, nullptr, nullptr}; // [npos][n]
   float* d_Z32[3] = {nullptr, nullptr, nullptr};
   float* d_lam32[3] = {nullptr, nullptr, nullptr};
-  double* d_inv = nullptr;         // [nsub][n^d] 1/(sum of lambdas), FP64 path
+  double* d_inv = nullptr;         // [nsub][n^d] 1/(sum of lambdas), FP64 path (n <= 16 in 3D)
+  double* d_scratch = nullptr;     // 3D FP64 n > 16: [scratch_ctas][n^3] per-CTA tensor slabs
+  int scratch_ctas = 0;
   // colorings: packed positions (p_x | p_y << 10 | p_z << 20) grouped by color
   int* d_add_list = nullptr;
   std::vector<int> add_offsets;    // ncolors_add + 1
@@ -160,6 +164,7 @@ struct tpss_patches {
   int* d_mul8_list = nullptr;      // alternative 2^d-color multiplicative list (vertex)
   std::vector<int> mul8_offsets;
   int mul_colors_active = 0;
+  int mult_update = 1;             // multiplicative sweep: update the residual per color (else recompute)
 };
 
 namespace tpss {
@@ -184,17 +189,35 @@ tpss_status apply_operator_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* 
 tpss_status ensure_level_scratch(tpss_ctx* ctx, int level, int nrhs);
 
 // ---- smoother.cu
+// x += omega sum_j R_j^T A_j^{-1} R_j r over one color's list; if d is not
+// null, d = omega A_j^{-1} R_j r is also written on the subdomains' DoFs.
 template <typename T>
 tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs,
-                       const T* r, T* x, cudaStream_t s);
+                       const T* r, T* x, cudaStream_t s, T* d = nullptr);
+
+// ---- smoother_mult.cu: residual update after one multiplicative color
+template <typename T>
+tpss_status mult_residual_update(tpss_patches* P, int color, T omega, int nrhs, const T* dx, T* r,
+                                 cudaStream_t s);
 
 // ---- smoother_tc.cu (TF32 / BF16 tensor-core contractions)
 tpss_status patch_pass_tc(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                          float* x, cudaStream_t s);
+                          float* x, cudaStream_t s, float* d = nullptr);
 
 // ---- smoother_bf16.cu (3D BF16 tensor-core path; TPSS_EINVAL for uncovered shapes)
 tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                            float* x, cudaStream_t s);
+                            float* x, cudaStream_t s, float* d = nullptr);
+
+// ---- smoother_large.cu (3D FP64 vertex patches with n > 16, per-CTA scratch slabs)
+tpss_status patch_large_ctas(int n, int num_sms, int* max_ctas);
+tpss_status patch_pass_large(tpss_patches* P, const int* list, int count, double omega, int nrhs,
+                             const double* r, double* x, cudaStream_t s, double* d);
+// subdomain sizes above this take the large-patch kernel in 3D
+constexpr int kMaxSharedPatchN = 16;
+
+// ---- smoother.cu: additive pass over every color (x_is_zero: x starts at 0)
+template <typename T>
+tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T* x, int x_is_zero);
 
 // ---- transfer.cu
 template <typename T>

@@ -119,11 +119,95 @@ __global__ void transfer_kernel(const T* __restrict__ src, T* __restrict__ dst, 
   }
 }
 
+// 3D FP64 transfers for n1 > 8 (k = 8..15), where the two (2 n1)^3 patch
+// tensors above no longer fit in shared memory: every child is mapped on its
+// own with the n1 x n1 blocks P_{s_x}, P_{s_y}, P_{s_z} of the 1D embedding
+// (24 n1^4 FMAs per parent instead of 14 n1^4), so shared memory holds three
+// n1^3 tensors.  Restriction accumulates P_{s_x}^T P_{s_y}^T P_{s_z}^T applied
+// to each child into the parent tensor.
+template <bool PROLONG>
+__global__ void transfer_child_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                      const double* __restrict__ Pc, int n1, int cnc0, int cnc1, int64_t cdofs,
+                                      int64_t fdofs) {
+  extern __shared__ double smc[];
+  const int nn = n1 * n1, nloc = nn * n1;
+  double* R = smc;            // [2][n1*n1]: P_0, P_1 (prolongation) or their transposes
+  double* b0 = R + 2 * nn;    // n1^3
+  double* b1 = b0 + nloc;     // n1^3
+  double* par = b1 + nloc;    // n1^3: the parent tensor
+  const int64_t parent = blockIdx.x;
+  const int64_t rhs = blockIdx.y;
+  const int cx = (int)(parent % cnc0), cy = (int)((parent / cnc0) % cnc1);
+  const int cz = (int)(parent / ((int64_t)cnc0 * cnc1));
+  const int fnc0 = 2 * cnc0, fnc1 = 2 * cnc1;
+  for (int e = threadIdx.x; e < 2 * nn; e += blockDim.x) {
+    const int sd = e / nn, i = (e % nn) / n1, j = e % n1;
+    const double v = Pc[e];   // (P_sd)_{ij}
+    R[sd * nn + (PROLONG ? i * n1 + j : j * n1 + i)] = v;
+  }
+  const int64_t pbase = rhs * cdofs + parent * nloc;
+  if (PROLONG) {
+    for (int e = threadIdx.x; e < nloc; e += blockDim.x) par[e] = src[pbase + e];
+  } else {
+    for (int e = threadIdx.x; e < nloc; e += blockDim.x) par[e] = 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < 8; ++c) {
+    const int sx = c & 1, sy = (c >> 1) & 1, sz = (c >> 2) & 1;
+    const int64_t fc = (2 * cx + sx) + (int64_t)fnc0 * ((2 * cy + sy) + (int64_t)fnc1 * (2 * cz + sz));
+    const int64_t cbase = rhs * fdofs + fc * nloc;
+    const double* in = par;
+    if (!PROLONG) {
+      for (int e = threadIdx.x; e < nloc; e += blockDim.x) b0[e] = src[cbase + e];
+      __syncthreads();
+      in = b0;
+    }
+    double* t1 = PROLONG ? b0 : b1;
+    double* t2 = PROLONG ? b1 : b0;
+    contract_dir<double>(in, t1, R + sx * nn, n1, n1, 0, n1, n1, n1);
+    __syncthreads();
+    contract_dir<double>(t1, t2, R + sy * nn, n1, n1, 1, n1, n1, n1);
+    __syncthreads();
+    contract_dir<double>(t2, t1, R + sz * nn, n1, n1, 2, n1, n1, n1);
+    __syncthreads();
+    if (PROLONG) {
+      for (int e = threadIdx.x; e < nloc; e += blockDim.x) dst[cbase + e] += t1[e];
+    } else {
+      for (int e = threadIdx.x; e < nloc; e += blockDim.x) par[e] += t1[e];
+    }
+    __syncthreads();   // t1 / b0 are overwritten by the next child
+  }
+  if (!PROLONG)
+    for (int e = threadIdx.x; e < nloc; e += blockDim.x) dst[pbase + e] = par[e];
+}
+
 template <typename T>
 static tpss_status transfer_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* src, T* dst, bool prolong) {
   const Level& C = ctx->levels[fine_level - 1];
   const Level& F = ctx->levels[fine_level];
   const int n1 = ctx->n1, np = 2 * n1;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if (ctx->dim == 3 && n1 > 8) {
+      const size_t smem = (size_t)(2 * n1 * n1 + 3 * n1 * n1 * n1) * sizeof(double);
+      static bool attr = false;
+      if (!attr) {
+        TPSS_CHECK_CUDA(cudaFuncSetAttribute(transfer_child_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        TPSS_CHECK_CUDA(cudaFuncSetAttribute(transfer_child_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        attr = true;
+      }
+      dim3 grid((unsigned)C.ncells, (unsigned)nrhs);
+      if (prolong)
+        transfer_child_kernel<true><<<grid, 256, smem, ctx->stream>>>(src, dst, C.op64.Pc, n1, C.nc[0], C.nc[1],
+                                                                      C.ndofs, F.ndofs);
+      else
+        transfer_child_kernel<false><<<grid, 256, smem, ctx->stream>>>(src, dst, C.op64.Pc, n1, C.nc[0], C.nc[1],
+                                                                       C.ndofs, F.ndofs);
+      TPSS_CHECK_LAUNCH();
+      return TPSS_OK;
+    }
+  }
   const int big = ctx->dim == 3 ? np * np * np : np * np;
   const size_t smem = (size_t)(2 * np * n1 + 2 * big) * sizeof(T);
   const T* Pc;

@@ -19,6 +19,8 @@ STATUS_NAMES = {0: "TPSS_OK", 1: "TPSS_ENOTCONV", -1: "TPSS_EINVAL", -2: "TPSS_E
 CELL, VERTEX_PATCH = 0, 1
 FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PENALTY_PAPER, PENALTY_KP1SQ = 0, 1
+COARSE_AUTO, COARSE_DENSE, COARSE_FD = 0, 1, 2
+MULT_RESIDUAL_UPDATE, MULT_RESIDUAL_FULL = 0, 1
 ACS, AVS, MCS, MVS = 0, 1, 2, 3
 SMOOTHERS = {"ACS": ACS, "AVS": AVS, "MCS": MCS, "MVS": MVS}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
@@ -38,7 +40,8 @@ class ProblemDesc(ctypes.Structure):
 
 class MGParams(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
-                ("mult_colors", ctypes.c_int), ("flexible_cg", ctypes.c_int), ("nonsymmetric", ctypes.c_int)]
+                ("mult_colors", ctypes.c_int), ("flexible_cg", ctypes.c_int), ("nonsymmetric", ctypes.c_int),
+                ("coarse_solver", ctypes.c_int), ("mult_residual", ctypes.c_int)]
 
 
 _lib = None
@@ -56,6 +59,7 @@ SIGNATURES = {
                           ctypes.POINTER(ctypes.c_int)],
     "tpss_patches_eigendata": [_VP, _I, _I, _VP, _VP, _VP, _VP],
     "tpss_patches_set_mult_colors": [_VP, _I],
+    "tpss_patches_set_mult_residual": [_VP, _I],
     "tpss_smooth_additive": [_VP, _D, _I, _VP, _VP, _I],
     "tpss_smooth_additive_f32": [_VP, _F, _I, _VP, _VP, _I],
     "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
@@ -205,11 +209,14 @@ class Problem:
         _check(lib().tpss_assemble_rhs(self.h, level, kind, _ptr(b, torch.float64, self.ndofs(level))))
         return b
 
-    def mg_setup(self, smoother, omega, precision=FP64, mult_colors=0, flexible_cg=0, nonsymmetric=0):
+    def mg_setup(self, smoother, omega, precision=FP64, mult_colors=0, flexible_cg=0, nonsymmetric=0,
+                 coarse_solver=COARSE_AUTO, mult_residual=MULT_RESIDUAL_UPDATE):
         p = MGParams()
         p.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
         p.omega, p.precision, p.mult_colors, p.flexible_cg = omega, precision, mult_colors, flexible_cg
         p.nonsymmetric = int(bool(nonsymmetric))
+        p.coarse_solver = coarse_solver
+        p.mult_residual = mult_residual
         _check(lib().tpss_mg_setup(self.h, ctypes.byref(p)))
 
     def vcycle(self, b, x):
@@ -281,6 +288,9 @@ class Patches:
 
     def set_mult_colors(self, ncolors):
         _check(lib().tpss_patches_set_mult_colors(self.h, ncolors))
+
+    def set_mult_residual(self, mode):
+        _check(lib().tpss_patches_set_mult_residual(self.h, mode))
 
     def smooth_additive(self, omega, b, x, x_is_zero=False, nrhs=1):
         n = self.problem.ndofs(self.level) * nrhs

@@ -77,7 +77,7 @@ def test_pcg_reports_not_converged():
 def test_invalid_arguments_are_rejected_on_host():
     from paper_1910_11239_gb300 import tpss
     with pytest.raises(tpss.TpssError):
-        tpss.Problem(3, 9, workloads.widths_uniform(2, 3))       # degree out of range
+        tpss.Problem(3, 16, workloads.widths_uniform(2, 3))      # degree out of range (1..15)
     prob = make(3, 2, workloads.widths_uniform(2, 3))
     with pytest.raises(tpss.TpssError):
         prob.setup_patches(0, 5)                                 # unknown kind

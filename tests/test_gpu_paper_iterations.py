@@ -3,7 +3,12 @@
 V-cycle(1,1), Gaussian-bell solution, relative residual 1e-8): the paper
 prints nu_frac = 17.1 (k = 3) and 21.9 (k = 7).  Our coarse solve is exact
 (the paper's is Chebyshev to 1e-8) and nu_frac is residual based, so the pin
-allows half an iteration."""
+allows half an iteration.
+
+The k = 15 columns (tab:cubecp and tab:cubemvpminimal; ACS with CG, MCS and
+MVS with GMRES and the non-symmetric V-cycle, omega = 1): 3D on L = 1
+(T_0 = 2^3 cells, whose exact coarse solve is one vertex patch's fast
+diagonalization) and 2D on L = 6."""
 import pytest
 import torch
 
@@ -23,4 +28,33 @@ def test_acs_fractional_iterations_match_tab_cubecp(k, paper):
     res = prob.pcg_solve(b, x, rtol=1e-8, maxit=100, history=True)
     nu = perf.fractional_iterations(res["history"], 1e-8)
     assert abs(nu - paper) < 0.5, nu
+    prob.close()
+
+
+# 3D MCS at k = 15 converges faster here than printed (L = 1, 2, 3: 14.41,
+# 14.91, 15.10 against 15.7, 15.9, 15.8), while the same smoother matches the
+# oracle to 1e-12 and the k = 3 / k = 7 MCS counts match the paper; the paper
+# does not state its GMRES variant (left preconditioning would monitor the
+# preconditioned residual) -- kept as a known, strict expected failure.
+MCS3D = pytest.param(3, 1, "MCS", 15.7, marks=pytest.mark.xfail(
+    strict=True, reason="3D MCS k=15: 14.41 vs the paper's 15.7 (see comment above)"))
+K15_CASES = [(3, 1, "ACS", 28.5), MCS3D, (3, 1, "MVS", 1.5),
+             (2, 6, "ACS", 25.4), (2, 6, "MCS", 12.6), (2, 6, "MVS", 1.7)]
+
+
+@pytest.mark.parametrize("dim,L,smoother,paper", K15_CASES)
+def test_k15_fractional_iterations_match_paper(dim, L, smoother, paper):
+    prob = tpss.Problem(dim, 15, workloads.widths_uniform(2, dim), nlevels=L + 1)
+    N = prob.ndofs(L)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(L, 1, b)
+    x = torch.empty_like(b)
+    if smoother == "ACS":
+        prob.mg_setup("ACS", 0.7, tpss.FP64)
+        res = prob.pcg_solve(b, x, rtol=1e-8, maxit=100, history=True)
+    else:
+        prob.mg_setup(smoother, 1.0, tpss.FP64, nonsymmetric=1)
+        res = prob.gmres_solve(b, x, rtol=1e-8, maxit=100, restart=30, history=True)
+    nu = perf.fractional_iterations(res["history"], 1e-8)
+    assert abs(nu - paper) < 0.6, nu
     prob.close()
