@@ -293,17 +293,24 @@ tpss_status tpss_batch_vcycle(tpss_batch* batch, const double* b, double* x);
 tpss_status tpss_batch_pcg_solve(tpss_batch* batch, const double* b, double* x, double rtol, int maxit,
                                  int* iters, double* rel_res);
 
-/* Flexible right-preconditioned GMRES(restart) (Sec. 2.4: the Krylov method
- * used with the multiplicative smoothers) on the finest level with one
- * V-cycle per step as preconditioner, from x = 0, stopped when the
- * least-squares residual ||b - A x_k||_2 <= rtol ||b||_2 or after maxit steps.
+/* GMRES(restart) (Sec. 2.4: the Krylov method used with the multiplicative
+ * smoothers) on the finest level with one V-cycle M per step as
+ * preconditioner, from x = 0.
+ *   left = 0: flexible right preconditioning, x = Z y with z_j = M v_j;
+ *             stopped when the least-squares residual ||b - A x_k||_2 <=
+ *             rtol ||b||_2.
+ *   left = 1: left preconditioning (Arnoldi on M A, x = V y); the monitored
+ *             and minimized residual is ||M (b - A x_k)||_2, stopped when it
+ *             is <= rtol ||M b||_2 (M must then be a fixed linear operator:
+ *             an FP64 V-cycle).
  * Arnoldi by classical Gram-Schmidt with one reorthogonalization on the
  * device; the Hessenberg least-squares problem (Givens rotations) on the
- * host.  *iters, *rel_res and res_hist (maxit+1 host doubles, may be NULL)
- * as in tpss_pcg_solve.  Allocates (restart+1) + restart finest-level vectors
- * on its first call.  TPSS_ENOTCONV at maxit. */
+ * host.  *iters, *rel_res and res_hist (maxit+1 host doubles, may be NULL;
+ * the monitored residual norms) as in tpss_pcg_solve.  Allocates
+ * (restart+1) + restart finest-level vectors on its first call.
+ * TPSS_ENOTCONV at maxit. */
 tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit, int restart,
-                             int* iters, double* rel_res, double* res_hist);
+                             int left, int* iters, double* rel_res, double* res_hist);
 
 #ifdef __cplusplus
 }

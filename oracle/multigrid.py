@@ -20,12 +20,17 @@ paper uses the energy norm of the error for CG; the residual-based value is
 labelled as such where reported).
 
 Flexible GMRES (right preconditioned, restarted) for the non-symmetric
-V-cycle of the multiplicative smoothers (the paper's choice for MCS and MVS).
+V-cycle of the multiplicative smoothers (the paper's choice for MCS and MVS),
+and GMRES with the preconditioner on the left, which monitors the
+preconditioned residual (the paper does not say which side it uses).
 
 Pins (tests/test_oracle_multigrid.py): the PCG and FGMRES solutions match a
 direct sparse solve to the residual tolerance; unpreconditioned GMRES
 terminates in at most n steps on an n x n system and its least-squares
-residual history equals the true residual norms; the V-cycle operator is symmetric for
+residual history equals the true residual norms; left-preconditioned GMRES
+terminates in at most n steps, its history equals the explicitly recomputed
+||M (b - A x_k)||, and with M = I it is the unpreconditioned method; the
+V-cycle operator is symmetric for
 the additive and the symmetrically ordered multiplicative smoothers; on T_0
 the V-cycle is the exact coarse solve; the fractional count reproduces
 hand-computed values.
@@ -192,6 +197,62 @@ def fgmres(A, b, precondition, rtol=1e-8, maxit=500, restart=30):
             x = x + y[i] * Z[i]
         r = b - A @ x
         if np.linalg.norm(r) <= rtol * beta0 * (1 + 1e-6) or hist[-1] <= rtol * beta0:
+            return x, it, hist, True
+    return x, it, hist, False
+
+
+def gmres_left(A, b, precondition, rtol=1e-8, maxit=500, restart=30):
+    """Left-preconditioned GMRES(restart) from x_0 = 0: GMRES applied to
+    M A x = M b (M = precondition), Arnoldi with modified Gram-Schmidt on
+    M A v_j, Givens rotations, x = x_0 + V y.  The residual it minimizes and
+    monitors is the preconditioned one, ||M (b - A x_k)||; stopped when that
+    falls to rtol ||M b||.  Returns (x, iterations, history of the
+    preconditioned residual norms, converged).  (The Krylov method of Sec. 2.4
+    for multiplicative smoothers, with the preconditioner applied from the
+    left; `fgmres` applies it from the right.)"""
+    n = b.shape[0]
+    x = np.zeros(n)
+    r = precondition(b)
+    beta0 = np.linalg.norm(r)
+    hist = [beta0]
+    if beta0 == 0.0:
+        return x, 0, hist, True
+    it = 0
+    while it < maxit:
+        beta = np.linalg.norm(r)
+        V = [r / beta]
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        j_done = 0
+        for j in range(restart):
+            it += 1
+            w = precondition(A @ V[j])
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j] = d
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            hist.append(abs(g[j + 1]))
+            j_done = j + 1
+            if abs(g[j + 1]) <= rtol * beta0 or it >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
+        for i in range(j_done):
+            x = x + y[i] * V[i]
+        r = precondition(b - A @ x)
+        if hist[-1] <= rtol * beta0:
             return x, it, hist, True
     return x, it, hist, False
 

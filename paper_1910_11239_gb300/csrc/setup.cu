@@ -507,6 +507,26 @@ static void free_patches(tpss_patches* P) {
   dfree(P->d_add_list);
   dfree(P->d_mul_list);
   dfree(P->d_mul8_list);
+  dfree(P->d_flux_list);
+}
+
+// Is cell m in a subdomain of multiplicative color `color`?  (The same rule
+// as the colorings below: vertex v with parity bits and the extra bit
+// (sum floor(v_t/2)) mod 2, interior vertices only; cells red-black.)
+static bool host_in_color(const int* m, const int* nc, int dim, bool vertex, int color) {
+  if (!vertex) {
+    int s = 0;
+    for (int t = 0; t < dim; ++t) s += m[t];
+    return (s & 1) == color;
+  }
+  int extra = 0;
+  for (int t = 0; t < dim; ++t) {
+    const int bit = (color >> t) & 1;
+    const int v = ((m[t] & 1) == bit) ? m[t] : m[t] + 1;
+    if (v < 1 || v > nc[t] - 1) return false;
+    extra += v / 2;
+  }
+  return (extra & 1) == ((color >> dim) & 1);
 }
 
 tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tpss_patches** out);
@@ -617,6 +637,38 @@ extern "C" tpss_status tpss_level_info(const tpss_ctx* ctx, int level, int64_t* 
 
 namespace tpss {
 
+// Per multiplicative color, the cells outside the color that share a face
+// with a cell of the color, with the mask of those faces.
+static tpss_status build_flux_lists(tpss_patches* P, int dim, bool vertex) {
+  const Level& L = P->ctx->levels[P->level];
+  int nc[3] = {1, 1, 1};
+  for (int t = 0; t < dim; ++t) nc[t] = L.nc[t];
+  const int ncolors = vertex ? 1 << (dim + 1) : 2;
+  std::vector<int2> flat;
+  P->flux_offsets.assign(1, 0);
+  for (int c = 0; c < ncolors; ++c) {
+    for (int64_t cell = 0; cell < L.ncells; ++cell) {
+      int m[3] = {(int)(cell % nc[0]), (int)((cell / nc[0]) % nc[1]), (int)(cell / ((int64_t)nc[0] * nc[1]))};
+      if (host_in_color(m, nc, dim, vertex, c)) continue;
+      int mask = 0;
+      for (int t = 0; t < dim; ++t)
+        for (int side = 0; side < 2; ++side) {
+          int mn[3] = {m[0], m[1], m[2]};
+          mn[t] += side ? 1 : -1;
+          if (mn[t] < 0 || mn[t] >= nc[t]) continue;
+          if (host_in_color(mn, nc, dim, vertex, c)) mask |= 1 << (2 * t + side);
+        }
+      if (mask) flat.push_back(make_int2((int)cell, mask));
+    }
+    P->flux_offsets.push_back((int)flat.size());
+  }
+  TPSS_TRY(dalloc_t(&P->d_flux_list, flat.size()));
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(P->d_flux_list, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                  P->ctx->stream));
+  TPSS_CHECK_CUDA(cudaStreamSynchronize(P->ctx->stream));   // flat goes out of scope
+  return TPSS_OK;
+}
+
 tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tpss_patches** out) {
   const Level& L = ctx->levels[level];
   const int d = ctx->dim, n1 = ctx->n1;
@@ -708,12 +760,14 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
     if ((st = build(mul, 1 << (d + 1), &P->d_mul_list, P->mul_offsets)) != TPSS_OK) return fail(st);
     if ((st = build(add, 1 << d, &P->d_mul8_list, P->mul8_offsets)) != TPSS_OK) return fail(st);
     P->mul_colors_default = 1 << (d + 1);
+    if ((st = build_flux_lists(P, d, true)) != TPSS_OK) return fail(st);
   } else {
     auto one = [&](int, int, int) { return 0; };
     auto rb = [&](int px, int py, int pz) { return (px + py + pz) & 1; };
     if ((st = build(one, 1, &P->d_add_list, P->add_offsets)) != TPSS_OK) return fail(st);
     if ((st = build(rb, 2, &P->d_mul_list, P->mul_offsets)) != TPSS_OK) return fail(st);
     P->mul_colors_default = 2;
+    if ((st = build_flux_lists(P, d, false)) != TPSS_OK) return fail(st);
   }
   P->mul_colors_active = P->mul_colors_default;
   int h_err = 0;

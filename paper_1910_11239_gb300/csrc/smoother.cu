@@ -49,7 +49,8 @@ struct SmoothArgs {
   int count;
   const T* r;
   T* x;
-  T* d;                // optional: d = omega u on the subdomain's DoFs (the update of x)
+  T* d;                // optional: d = omega u on the subdomain's DoFs (the update of x) ...
+  T* rw;               // ... and then r *= 1 - omega there (r writable)
   T omega;
   int nc0, nc1;        // cells per direction (x, y)
   int np0, np1;        // subdomain positions per direction (x, y)
@@ -196,7 +197,10 @@ patch_smooth_kernel(SmoothArgs<T> a) {
       const int pidx = (sx * N1 + ix) + S::LS * (sy * N1 + iy) + (DIM == 3 ? S::PS * (sz * N1 + iz) : 0);
       const int64_t gi = vbase + gcell * NLOC1 + loc;
       a.x[gi] = fma(a.omega, buf[pidx], a.x[gi]);
-      if (a.d != nullptr) a.d[gi] = a.omega * buf[pidx];
+      if (a.d != nullptr) {
+        a.d[gi] = a.omega * buf[pidx];
+        a.rw[gi] *= T(1) - a.omega;
+      }
     }
   }
 }
@@ -251,6 +255,7 @@ tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int
   a.r = r;
   a.x = x;
   a.d = d;
+  a.rw = const_cast<T*>(r);
   a.omega = omega;
   a.nc0 = L.nc[0];
   a.nc1 = L.nc[1];
@@ -357,7 +362,7 @@ tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int n
       const int o = offs[c], cnt = offs[c + 1] - o;
       if (cnt == 0) continue;
       TPSS_TRY(patch_pass<T>(P, list + o, cnt, omega, nrhs, rb, x, s, dx));
-      if (i < last) TPSS_TRY(mult_residual_update<T>(P, c, omega, nrhs, dx, rb, s));
+      if (i < last) TPSS_TRY(mult_residual_update<T>(P, c, nrhs, dx, rb, s));
     }
     return TPSS_OK;
   }

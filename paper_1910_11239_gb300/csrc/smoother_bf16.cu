@@ -24,9 +24,11 @@ namespace tpss {
 
 namespace bf {
 
-// x[cell rows] = SX + omega T, one cell row per iteration.
+// x[cell rows] = SX + omega T, one cell row per iteration.  With dr: also
+// dr = omega T (the update) and rres *= 1 - omega (the residual after the
+// color on the patch), for the multiplicative residual update.
 template <int N, int N1, int NCELL>
-__device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, float* __restrict__ dr,
+__device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, float* __restrict__ dr, float* rres,
                                             const __nv_bfloat16* __restrict__ T, const float* __restrict__ SX,
                                             float omega, const CellBase& cb, int tid) {
   using S = Shape<N>;
@@ -54,9 +56,14 @@ __device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, float* __res
         o.z = fmaf(omega, t23.x, a.z);
         o.w = fmaf(omega, t23.y, a.w);
         *reinterpret_cast<float4*>(dst + v) = o;
-        if (dr != nullptr)
+        if (dr != nullptr) {
           *reinterpret_cast<float4*>(dr + off + v) = make_float4(omega * t01.x, omega * t01.y, omega * t23.x,
                                                                  omega * t23.y);
+          float4 rv = *reinterpret_cast<float4*>(rres + off + v);
+          const float s = 1.f - omega;
+          rv.x *= s; rv.y *= s; rv.z *= s; rv.w *= s;
+          *reinterpret_cast<float4*>(rres + off + v) = rv;
+        }
       } else if constexpr (V == 2) {
         const float2 a = *reinterpret_cast<const float2*>(xo + v);
         const float2 tt = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(t + v));
@@ -64,10 +71,19 @@ __device__ __forceinline__ void tensor_to_x(float* __restrict__ xr, float* __res
         o.x = fmaf(omega, tt.x, a.x);
         o.y = fmaf(omega, tt.y, a.y);
         *reinterpret_cast<float2*>(dst + v) = o;
-        if (dr != nullptr) *reinterpret_cast<float2*>(dr + off + v) = make_float2(omega * tt.x, omega * tt.y);
+        if (dr != nullptr) {
+          *reinterpret_cast<float2*>(dr + off + v) = make_float2(omega * tt.x, omega * tt.y);
+          float2 rv = *reinterpret_cast<float2*>(rres + off + v);
+          rv.x *= 1.f - omega;
+          rv.y *= 1.f - omega;
+          *reinterpret_cast<float2*>(rres + off + v) = rv;
+        }
       } else {
         dst[v] = fmaf(omega, __bfloat162float(t[v]), xo[v]);
-        if (dr != nullptr) dr[off + v] = omega * __bfloat162float(t[v]);
+        if (dr != nullptr) {
+          dr[off + v] = omega * __bfloat162float(t[v]);
+          rres[off + v] *= 1.f - omega;
+        }
       }
     }
   }
@@ -133,8 +149,8 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
     __syncthreads();
     contract<N, 0>(T, bx, warp, lane);
     __syncthreads();
-    tensor_to_x<N, N1, NCELL>(x + (int64_t)rhs * ndofs, d ? d + (int64_t)rhs * ndofs : nullptr, T, sx_cur, omega,
-                              cbase, tid);
+    tensor_to_x<N, N1, NCELL>(x + (int64_t)rhs * ndofs, d ? d + (int64_t)rhs * ndofs : nullptr,
+                              const_cast<float*>(r) + (int64_t)rhs * ndofs, T, sx_cur, omega, cbase, tid);
   }
 }
 

@@ -43,7 +43,8 @@ struct LargeArgs {
   int nrhs;
   const double* r;
   double* x;
-  double* d;              // optional: d = omega u (the update of x)
+  double* d;              // optional: d = omega u (the update of x), and then
+  double* rw;             // r *= 1 - omega on the patch's DoFs
   double omega;
   int nc0, nc1;
   int64_t ndofs;
@@ -176,7 +177,10 @@ __global__ void __launch_bounds__(kLargeThreads, 2) patch_smooth_large_kernel(La
         const int64_t gi = vbase + gcell * NLOC1 + (x % N1) + N1 * ((y % N1) + N1 * (z % N1));
         const double u = pl[p * S::PS + y * S::LS + x];
         a.x[gi] = fma(a.omega, u, a.x[gi]);
-        if (a.d != nullptr) a.d[gi] = a.omega * u;
+        if (a.d != nullptr) {
+          a.d[gi] = a.omega * u;
+          a.rw[gi] *= 1.0 - a.omega;
+        }
       }
     }
   }
@@ -217,6 +221,7 @@ static tpss_status large_launch(tpss_patches* P, const int* list, int count, dou
   a.r = r;
   a.x = x;
   a.d = d;
+  a.rw = const_cast<double*>(r);
   a.omega = omega;
   a.nc0 = L.nc[0];
   a.nc1 = L.nc[1];

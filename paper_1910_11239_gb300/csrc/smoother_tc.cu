@@ -229,7 +229,10 @@ patch_smooth_tc_kernel(const int* __restrict__ list, int count, const float* __r
       const int pidx = (sx * N1 + ix) + S::LS * (sy * N1 + iy) + (DIM == 3 ? S::PS * (sz * N1 + iz) : 0);
       const int64_t gi = vbase + gcell * NLOC1 + loc;
       x[gi] = fmaf(omega, buf[pidx], x[gi]);
-      if (d != nullptr) d[gi] = omega * buf[pidx];   // the update, for the multiplicative residual update
+      if (d != nullptr) {   // the update and the color's residual, for the multiplicative residual update
+        d[gi] = omega * buf[pidx];
+        const_cast<float*>(r)[gi] *= 1.f - omega;
+      }
     }
   }
 }

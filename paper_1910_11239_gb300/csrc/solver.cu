@@ -659,7 +659,7 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
 
 
 extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
-                                        int restart, int* iters, double* rel_res, double* res_hist) {
+                                        int restart, int left, int* iters, double* rel_res, double* res_hist) {
   clear_error();
   TPSS_REQUIRE(ctx && b && x && iters && rel_res, "tpss_gmres_solve: null argument");
   TPSS_REQUIRE(ctx->mg, "tpss_gmres_solve: call tpss_mg_setup first");
@@ -685,7 +685,9 @@ extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* 
   double* V = mg->gm_V;
   double* Z = mg->gm_Z;
   double* dh = mg->gm_h;
-  double* w = mg->q;   // finest-level scratch vector
+  double* w = mg->q;   // finest-level scratch vectors
+  double* av = mg->p;
+  const bool left_pc = left != 0;
   auto vec = [&](double* base, int i) { return base + (int64_t)i * n; };
   // <V_i, w> for i < j into dh[0..j), copied to the host
   auto project = [&](int j, std::vector<double>& h) -> tpss_status {
@@ -709,7 +711,11 @@ extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* 
     return TPSS_OK;
   };
   TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
-  TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (left_pc) {
+    TPSS_TRY(precondition(ctx, mg, b, mg->r));   // r_0 = M b
+  } else {
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   double beta0 = 0.0;
   TPSS_TRY(norm(mg->r, &beta0));
   *iters = 0;
@@ -733,8 +739,13 @@ extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* 
     bool done = false;
     for (int j = 0; j < restart && it < maxit; ++j) {
       ++it;
-      TPSS_TRY(precondition(ctx, mg, vec(V, j), vec(Z, j)));
-      TPSS_TRY(apply_operator_t<double>(ctx, L, 1, vec(Z, j), w, nullptr));
+      if (left_pc) {   // w = M A v_j
+        TPSS_TRY(apply_operator_t<double>(ctx, L, 1, vec(V, j), av, nullptr));
+        TPSS_TRY(precondition(ctx, mg, av, w));
+      } else {         // z_j = M v_j, w = A z_j
+        TPSS_TRY(precondition(ctx, mg, vec(V, j), vec(Z, j)));
+        TPSS_TRY(apply_operator_t<double>(ctx, L, 1, vec(Z, j), w, nullptr));
+      }
       TPSS_TRY(project(j + 1, h1));   // classical Gram-Schmidt ...
       TPSS_TRY(project(j + 1, h2));   // ... with one reorthogonalization
       auto Hij = [&](int i, int jj) -> double& { return H[(size_t)i * restart + jj]; };
@@ -779,11 +790,16 @@ extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* 
       y[i] = acc / H[(size_t)i * restart + i];
     }
     TPSS_CHECK_CUDA(cudaMemcpyAsync(dh, y.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s));
-    multi_axpy_kernel<<<g, 256, 0, s>>>(x, Z, dh, jdone, n, 1.0);
+    multi_axpy_kernel<<<g, 256, 0, s>>>(x, left_pc ? V : Z, dh, jdone, n, 1.0);
     TPSS_CHECK_LAUNCH();
     if (done) return TPSS_OK;
-    // restart from the true residual
-    TPSS_TRY(apply_operator_t<double>(ctx, L, 1, x, mg->r, b));
+    // restart from the true (left: preconditioned) residual
+    if (left_pc) {
+      TPSS_TRY(apply_operator_t<double>(ctx, L, 1, x, av, b));
+      TPSS_TRY(precondition(ctx, mg, av, mg->r));
+    } else {
+      TPSS_TRY(apply_operator_t<double>(ctx, L, 1, x, mg->r, b));
+    }
     TPSS_TRY(norm(mg->r, &beta));
     if (!(beta > 0.0)) return TPSS_OK;
   }

@@ -165,6 +165,10 @@ struct tpss_patches {
   std::vector<int> mul8_offsets;
   int mul_colors_active = 0;
   int mult_update = 1;             // multiplicative sweep: update the residual per color (else recompute)
+  // per multiplicative color: cells outside the color with a face to it,
+  // {cell index, face mask (bit 2t+side: neighbour at -1 / +1 along t)}
+  int2* d_flux_list = nullptr;
+  std::vector<int> flux_offsets;
 };
 
 namespace tpss {
@@ -190,15 +194,16 @@ tpss_status ensure_level_scratch(tpss_ctx* ctx, int level, int nrhs);
 
 // ---- smoother.cu
 // x += omega sum_j R_j^T A_j^{-1} R_j r over one color's list; if d is not
-// null, d = omega A_j^{-1} R_j r is also written on the subdomains' DoFs.
+// null, d = omega A_j^{-1} R_j r is also written on the subdomains' DoFs and
+// r (then writable) is scaled by 1 - omega there (the residual after the
+// color on its own cells, for the multiplicative residual update).
 template <typename T>
 tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int nrhs,
                        const T* r, T* x, cudaStream_t s, T* d = nullptr);
 
 // ---- smoother_mult.cu: residual update after one multiplicative color
 template <typename T>
-tpss_status mult_residual_update(tpss_patches* P, int color, T omega, int nrhs, const T* dx, T* r,
-                                 cudaStream_t s);
+tpss_status mult_residual_update(tpss_patches* P, int color, int nrhs, const T* dx, T* r, cudaStream_t s);
 
 // ---- smoother_tc.cu (TF32 / BF16 tensor-core contractions)
 tpss_status patch_pass_tc(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,

@@ -75,8 +75,8 @@ SIGNATURES = {
     "tpss_coarse_solve": [_VP, _VP, _VP],
     "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                        _VP],
-    "tpss_gmres_solve": [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
-                         _VP],
+    "tpss_gmres_solve": [_VP, _VP, _VP, _D, _I, _I, _I, ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_double), _VP],
     "tpss_batch_create": [ctypes.POINTER(ProblemDesc), _I, _I, ctypes.POINTER(MGParams), _I, _VP,
                           ctypes.POINTER(_VP)],
     "tpss_batch_destroy": [_VP],
@@ -243,12 +243,12 @@ class Problem:
         return out
 
 
-def _gmres(self, b, x, rtol=1e-8, maxit=200, restart=30, history=False):
+def _gmres(self, b, x, rtol=1e-8, maxit=200, restart=30, history=False, left=False):
     n = self.ndofs(self.nlevels - 1)
     it, rel = ctypes.c_int(), ctypes.c_double()
     hist = (ctypes.c_double * (maxit + 1))() if history else None
     st = lib().tpss_gmres_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n), rtol, maxit, restart,
-                                ctypes.byref(it), ctypes.byref(rel),
+                                int(bool(left)), ctypes.byref(it), ctypes.byref(rel),
                                 ctypes.cast(hist, ctypes.c_void_p) if hist is not None else None)
     _check(st, allow=(TPSS_OK, TPSS_ENOTCONV))
     out = {"iters": it.value, "rel_res": rel.value, "converged": st == TPSS_OK}

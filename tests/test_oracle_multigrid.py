@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle.multigrid import Hierarchy, fgmres, fractional_iterations, pcg
+from oracle.multigrid import Hierarchy, fgmres, fractional_iterations, gmres_left, pcg
 
 
 def coarse(d, n=2):
@@ -79,3 +79,45 @@ def test_nonsymmetric_vcycle_is_not_symmetric():
     N = H.A[-1].shape[0]
     B = np.column_stack([H.precondition(e) for e in np.eye(N)])
     assert np.abs(B - B.T).max() > 1e-6 * np.abs(B).max()
+
+
+def test_left_gmres_history_is_the_preconditioned_residual():
+    rng = np.random.default_rng(11)
+    n = 14
+    A = rng.standard_normal((n, n)) + 5 * np.eye(n)
+    Mmat = np.diag(rng.uniform(0.5, 2.0, n)) + 0.1 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    M = lambda v: Mmat @ v
+    x, it, hist, ok = gmres_left(A, b, M, rtol=1e-12, maxit=n, restart=n)
+    assert ok and it <= n
+    assert np.linalg.norm(A @ x - b) <= 1e-9 * np.linalg.norm(b)
+    # GMRES(1) steps one at a time: each history entry is ||M (b - A x_k)|| of
+    # the iterate the restart recomputes
+    xs, hs = np.zeros(n), [np.linalg.norm(M(b))]
+    for _ in range(4):
+        xk, _, hk, _ = gmres_left(A, b - A @ xs, M, rtol=1e-300, maxit=1, restart=1)
+        xs = xs + xk
+        hs.append(hk[1])
+        assert np.isclose(hk[1], np.linalg.norm(M(b - A @ xs)), rtol=1e-10)
+    # a dropped preconditioner on the restart residual would break this
+    assert all(hs[i + 1] <= hs[i] * (1 + 1e-12) for i in range(len(hs) - 1))
+
+
+def test_left_gmres_with_identity_is_unpreconditioned_gmres():
+    rng = np.random.default_rng(12)
+    n = 10
+    A = rng.standard_normal((n, n)) + 4 * np.eye(n)
+    b = rng.standard_normal(n)
+    _, it1, h1, _ = gmres_left(A, b, lambda v: v, rtol=1e-10, maxit=n, restart=n)
+    _, it2, h2, _ = fgmres(A, b, lambda v: v, rtol=1e-10, maxit=n, restart=n)
+    assert it1 == it2 and np.allclose(h1, h2, rtol=1e-8)
+
+
+def test_left_gmres_with_nonsymmetric_vcycle_matches_direct_solve():
+    H = Hierarchy(coarse(2), k=2, nlevels=3, smoother="MVS", symmetric=False)
+    A = H.A[-1]
+    b = np.random.default_rng(13).uniform(-1, 1, A.shape[0])
+    x, it, hist, ok = gmres_left(A, b, H.precondition, rtol=1e-10, maxit=60)
+    assert ok and it < 20
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
