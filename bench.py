@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-high-degree", action="store_true")
+    p.add_argument("--no-kernels", action="store_true")
     p.add_argument("--batch-problems", type=int, default=48, help="use the first N problems of the batch (profiling)")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
@@ -356,6 +357,9 @@ def main():
     batch = None
     if not args.no_batch:
         batch = run_batch(tpss, workloads, perf, torch, args.steps)
+    kernels = None
+    if not args.no_kernels:
+        kernels = run_kernels(tpss, workloads, perf, torch, max(3, min(args.steps, 10)))
     high = None
     if not args.no_high_degree:
         high = run_high_degree(tpss, workloads, perf, torch, max(2, min(args.steps, 5)))
@@ -385,6 +389,8 @@ def main():
             line["batched"] = batch
         if paper_its is not None:
             line["paper_iterations"] = paper_its
+        if kernels is not None:
+            line["kernels"] = kernels
         if high is not None:
             line["high_degree_k15"] = high
         print(json.dumps(line))
@@ -510,6 +516,78 @@ def run_paper_iterations(tpss, workloads, perf, torch):
                         "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
                         "paper_nu_frac": PAPER_NU[(sm, k)]}
         prob.close()
+    return out
+
+
+def _time_calls(torch, fn, steps):
+    """Mean milliseconds of fn() over `steps` calls after 2 warm-up calls,
+    CUDA events on the current stream."""
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_kernels(tpss, workloads, perf, torch, steps):
+    """The other kernels of the path on 32^3 cells (fine level of a 16^3 ->
+    32^3 pair, widths U[0.5,1.5] per cell): the matrix-free operator (FP64
+    and FP32), the transfers, and one multiplicative vertex-patch sweep with
+    the residual updated per color and recomputed per color; each with its
+    algorithmic flops and bytes against the FP64 pipe, FP32 pipe or HBM peak."""
+    import json as _json
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"workload": "3D, 32^3 cells (fine level of 16^3 -> 32^3), widths U[0.5,1.5]/16 (seed 2), 1 RHS",
+           "peaks": {"fp64_tflops": perf.fp64_peak_flops() / 1e12, "fp32_tflops": perf.fp32_peak_flops() / 1e12,
+                     "hbm_gbs": hbm}}
+    cw = workloads.widths_random(16, 3, WIDTH_SEED)
+    fine, coarse = (32, 32, 32), (16, 16, 16)
+    for k in (4, 7):
+        prob = tpss.Problem(3, k, cw, nlevels=2)
+        nf, nc = prob.ndofs(1), prob.ndofs(0)
+        u = torch.from_numpy(workloads.rhs_uniform(nf, seed=3)).to("cuda")
+        au = torch.empty_like(u)
+        rec = {}
+        ms = _time_calls(torch, lambda: prob.apply_operator(1, u, au), steps)
+        fl, by = perf.operator_flops(fine, k), perf.operator_bytes(fine, k)
+        rec["operator_fp64"] = {"ms": ms, "tflops": fl / ms / 1e9, "frac_fp64_peak": fl / ms / 1e9 / (
+            perf.fp64_peak_flops() / 1e12), "algorithmic_gbs": by / ms / 1e6}
+        u32, au32 = u.float(), torch.empty(nf, dtype=torch.float32, device="cuda")
+        ms = _time_calls(torch, lambda: prob.apply_operator(1, u32, au32), steps)
+        by32 = perf.operator_bytes(fine, k, word=4)
+        rec["operator_fp32"] = {"ms": ms, "tflops": fl / ms / 1e9,
+                                "frac_fp32_peak": fl / ms / 1e9 / (perf.fp32_peak_flops() / 1e12),
+                                "algorithmic_gbs": by32 / ms / 1e6, "frac_hbm": by32 / ms / 1e6 / hbm,
+                                "note": "three sum-factorization passes stream 4 intermediate vectors through HBM"}
+        c = torch.from_numpy(workloads.rhs_uniform(nc, seed=4)).to("cuda")
+        ms = _time_calls(torch, lambda: prob.prolongate_add(1, c, au), steps)
+        fl = perf.transfer_flops(coarse, k)
+        by = perf.transfer_bytes(coarse, k, prolong=True)
+        rec["prolongate_add_fp64"] = {"ms": ms, "tflops": fl / ms / 1e9,
+                                      "frac_fp64_peak": fl / ms / 1e9 / (perf.fp64_peak_flops() / 1e12),
+                                      "algorithmic_gbs": by / ms / 1e6}
+        ms = _time_calls(torch, lambda: prob.restrict(1, u, c), steps)
+        by = perf.transfer_bytes(coarse, k, prolong=False)
+        rec["restrict_fp64"] = {"ms": ms, "tflops": fl / ms / 1e9,
+                                "frac_fp64_peak": fl / ms / 1e9 / (perf.fp64_peak_flops() / 1e12),
+                                "algorithmic_gbs": by / ms / 1e6}
+        P = prob.setup_patches(1, tpss.VERTEX_PATCH)
+        x = torch.zeros_like(u)
+        for mode, name in ((tpss.MULT_RESIDUAL_UPDATE, "mvs_sweep_fp64_residual_updated"),
+                           (tpss.MULT_RESIDUAL_FULL, "mvs_sweep_fp64_residual_recomputed")):
+            P.set_mult_residual(mode)
+            ms = _time_calls(torch, lambda: P.smooth_multiplicative(1.0, u, x), max(2, steps // 2))
+            rec[name] = {"ms": ms, "colors": 16}
+        P.close()
+        prob.close()
+        out[f"k{k}"] = rec
     return out
 
 

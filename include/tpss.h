@@ -145,6 +145,15 @@ tpss_status tpss_patches_set_mult_colors(tpss_patches* patches, int ncolors);
 typedef enum { TPSS_MULT_RESIDUAL_UPDATE = 0, TPSS_MULT_RESIDUAL_FULL = 1 } tpss_mult_residual;
 tpss_status tpss_patches_set_mult_residual(tpss_patches* patches, int mode);
 
+/* 3D vertex patches with k >= 8 (n >= 18 points per direction): number of
+ * CTAs that share one subdomain solve, as a thread-block cluster (1, 2, 4 or
+ * 8; 0 = chosen per launch from the number of subdomains, the default).  The
+ * result does not depend on it (every line is contracted by the same
+ * arithmetic); it is a tuning knob.  TPSS_EINVAL at launch if the GPU cannot
+ * co-schedule a cluster of that size for the kernel; no effect on other
+ * patch sets. */
+tpss_status tpss_patches_set_large_cluster(tpss_patches* patches, int ctas);
+
 /* ------------------------------------------------------------- smoothers --
  * Additive Schwarz smoother, Alg. 2 with the damping of eq. additiveschwarz:
  *   r = b - A x;   x <- x + omega * sum_j R_j^T A_j^{-1} R_j r

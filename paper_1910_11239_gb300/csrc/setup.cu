@@ -859,6 +859,15 @@ extern "C" tpss_status tpss_patches_set_mult_colors(tpss_patches* P, int ncolors
   return TPSS_OK;
 }
 
+extern "C" tpss_status tpss_patches_set_large_cluster(tpss_patches* P, int ctas) {
+  clear_error();
+  TPSS_REQUIRE(P, "tpss_patches_set_large_cluster: null patches");
+  TPSS_REQUIRE(ctas == 0 || ctas == 1 || ctas == 2 || ctas == 4 || ctas == 8,
+               "tpss_patches_set_large_cluster: ctas must be 0 (automatic), 1, 2, 4 or 8");
+  P->large_cluster = ctas;
+  return TPSS_OK;
+}
+
 extern "C" tpss_status tpss_patches_set_mult_residual(tpss_patches* P, int mode) {
   clear_error();
   TPSS_REQUIRE(P, "tpss_patches_set_mult_residual: null patches");

@@ -153,8 +153,9 @@ struct tpss_patches {
   float* d_Z32[3] = {nullptr, nullptr, nullptr};
   float* d_lam32[3] = {nullptr, nullptr, nullptr};
   double* d_inv = nullptr;         // [nsub][n^d] 1/(sum of lambdas), FP64 path (n <= 16 in 3D)
-  double* d_scratch = nullptr;     // 3D FP64 n > 16: [scratch_ctas][n^3] per-CTA tensor slabs
+  double* d_scratch = nullptr;     // 3D FP64 n > 16: [scratch_ctas][n^3] tensor slabs (one per cluster)
   int scratch_ctas = 0;
+  int large_cluster = 0;           // CTAs per subdomain in that kernel: 0 = chosen per launch
   // colorings: packed positions (p_x | p_y << 10 | p_z << 20) grouped by color
   int* d_add_list = nullptr;
   std::vector<int> add_offsets;    // ncolors_add + 1

@@ -75,6 +75,30 @@ def operator_flops(ncells, k, d=3, nrhs=1):
     return num_cells(ncells) * per_cell * nrhs
 
 
+def operator_bytes(ncells, k, d=3, nrhs=1, word=8):
+    """Minimal HBM traffic of one operator application: read u, write A u."""
+    return 2 * word * ndofs(ncells, k, d) * nrhs
+
+
+def transfer_flops(coarse_ncells, k, d=3, nrhs=1):
+    """Embedding of a parent's (k+1)^d values into its 2^d children by sum
+    factorization, one direction after another: 2 n1^4 + 4 n1^4 + 8 n1^4
+    FMAs in 3D (2 n1^3 + 4 n1^3 in 2D), n1 = k+1; restriction is the
+    transpose with the same count."""
+    n1 = k + 1
+    fmas = 14 * n1 ** 4 if d == 3 else 6 * n1 ** 3
+    return num_cells(coarse_ncells) * 2 * fmas * nrhs
+
+
+def transfer_bytes(coarse_ncells, k, d=3, nrhs=1, word=8, prolong=True):
+    """Minimal HBM traffic: prolongate-add reads the coarse vector and reads
+    and writes the fine one; restriction reads the fine vector and writes the
+    coarse one."""
+    nc = ndofs(coarse_ncells, k, d)
+    nf = nc * 2 ** d
+    return word * (nc + 2 * nf if prolong else nf + nc) * nrhs
+
+
 def fractional_iterations(hist, rtol):
     """Fractional iteration count of Sec. 2.4:
     nu_frac = nu - 1 + log(e_{nu-1} / tol) / log(e_{nu-1} / e_nu), tol = rtol e_0,

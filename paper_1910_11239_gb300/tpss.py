@@ -60,6 +60,7 @@ SIGNATURES = {
     "tpss_patches_eigendata": [_VP, _I, _I, _VP, _VP, _VP, _VP],
     "tpss_patches_set_mult_colors": [_VP, _I],
     "tpss_patches_set_mult_residual": [_VP, _I],
+    "tpss_patches_set_large_cluster": [_VP, _I],
     "tpss_smooth_additive": [_VP, _D, _I, _VP, _VP, _I],
     "tpss_smooth_additive_f32": [_VP, _F, _I, _VP, _VP, _I],
     "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
@@ -291,6 +292,9 @@ class Patches:
 
     def set_mult_residual(self, mode):
         _check(lib().tpss_patches_set_mult_residual(self.h, mode))
+
+    def set_large_cluster(self, ctas):
+        _check(lib().tpss_patches_set_large_cluster(self.h, ctas))
 
     def smooth_additive(self, omega, b, x, x_is_zero=False, nrhs=1):
         n = self.problem.ndofs(self.level) * nrhs

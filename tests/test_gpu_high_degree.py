@@ -224,3 +224,31 @@ def test_mixed_precision_limited_to_degree_7():
     with pytest.raises(RuntimeError, match="up to 7"):
         prob.mg_setup("AVS", 0.125, tpss.BF16)
     prob.close()
+
+
+@pytest.mark.parametrize("k,n", [(8, 4), (15, 3), (11, 5)])
+def test_large_patch_cluster_sizes_agree(k, n):
+    """The 3D large-patch kernel splits a subdomain over a thread-block
+    cluster of 1, 2, 4 or 8 CTAs; every line is contracted by the same
+    arithmetic, so all cluster sizes (and the automatic choice) give the
+    same bits, for the additive and the multiplicative sweep."""
+    from paper_1910_11239_gb300 import tpss
+    widths = widths_case(3, (n, n, n), seed=200 + k)
+    prob = make(3, k, widths)
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH)
+    N = prob.ndofs(0)
+    b = dev(workloads.rhs_uniform(N, seed=k, nrhs=2))
+    x0 = workloads.rhs_uniform(N, seed=k + 1, nrhs=2)
+    outs = []
+    for cs in (0, 1, 2, 4, 8):
+        P.set_large_cluster(cs)
+        xa = torch.empty_like(b)
+        P.smooth_additive(0.125, b, xa, x_is_zero=True, nrhs=2)
+        xm = dev(x0)
+        P.smooth_multiplicative(1.0, b, xm, nrhs=2)
+        outs.append((xa, xm))
+    for xa, xm in outs[1:]:
+        assert torch.equal(xa, outs[0][0]) and torch.equal(xm, outs[0][1])
+    with pytest.raises(RuntimeError):
+        P.set_large_cluster(3)
+    prob.close()
