@@ -408,6 +408,8 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
     hbm = peaks.get("hbm_gbs", 6800.0)
     nr = len(SEEDS)
     out = {"dtype": prec, "accumulate": "fp32", "per_degree": {}}
+    out["schedule"] = ("colored launches (default); plane-by-plane" +
+                       (" and single-launch atomic" if prec == "bf16" else "") + " schedules timed beside it")
     total_ms = 0.0
     for k in ks:
         prob = tpss.Problem(3, k, widths)
@@ -429,6 +431,20 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
         byt = perf.smoother_bytes((NC, NC, NC), k, nrhs=nr, word=4)
         out["per_degree"][str(k)] = {"dofs_per_s": dofs(k) * nr / (ms / 1e3), "ms_per_call": ms,
                                      "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
+        # the other schedules of the same smoother (default: colored launches)
+        for name, sch in (("planes", tpss.ADDITIVE_PLANES), ("atomic", tpss.ADDITIVE_ATOMIC)):
+            if sch == tpss.ADDITIVE_ATOMIC and prec != "bf16":
+                continue
+            P.set_additive_schedule(sch)
+            P.smooth_additive(OMEGA, b, x, x_is_zero=True, nrhs=nr)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                P.smooth_additive(OMEGA, b, x, x_is_zero=True, nrhs=nr)
+            e1.record()
+            torch.cuda.synchronize()
+            out["per_degree"][str(k)][f"{name}_ms_per_call"] = e0.elapsed_time(e1) / steps
+        P.set_additive_schedule(tpss.ADDITIVE_COLORS)
         prob.close()
     out["dofs_per_s"] = sum(dofs(k) * nr for k in ks) / (total_ms / 1e3)
     out["vs_fp64_note"] = "same workload, FP32 vectors; compare with the line's FP64 value"

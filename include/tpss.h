@@ -154,6 +154,21 @@ tpss_status tpss_patches_set_mult_residual(tpss_patches* patches, int mode);
  * patch sets. */
 tpss_status tpss_patches_set_large_cluster(tpss_patches* patches, int ctas);
 
+/* Order of the subdomain solves of the additive smoother (the result is the
+ * same sum; the schedules differ in memory traffic).
+ *   COLORS (default): one launch per color (2^d for vertex patches), each over
+ *     the whole mesh; deterministic.
+ *   PLANES (3D vertex patches): plane of patches by plane of patches, the 4
+ *     colors of a plane in turn, so that the two cell planes a patch plane
+ *     touches stay in L2 across its colors (r and x are read from HBM about
+ *     twice instead of once per color); deterministic; 4 launches per plane.
+ *   ATOMIC (3D, BF16 contractions): one launch over all subdomains in
+ *     lexicographic order, x accumulated with FP32 atomic adds; the order of
+ *     the contributions to a DoF, and so the FP32 rounding, varies between runs.
+ * Schedules that do not apply to a patch set fall back to COLORS. */
+typedef enum { TPSS_ADDITIVE_COLORS = 0, TPSS_ADDITIVE_PLANES = 1, TPSS_ADDITIVE_ATOMIC = 2 } tpss_additive_schedule;
+tpss_status tpss_patches_set_additive_schedule(tpss_patches* patches, int schedule);
+
 /* ------------------------------------------------------------- smoothers --
  * Additive Schwarz smoother, Alg. 2 with the damping of eq. additiveschwarz:
  *   r = b - A x;   x <- x + omega * sum_j R_j^T A_j^{-1} R_j r

@@ -508,6 +508,8 @@ static void free_patches(tpss_patches* P) {
   dfree(P->d_mul_list);
   dfree(P->d_mul8_list);
   dfree(P->d_flux_list);
+  dfree(P->d_lex_list);
+  dfree(P->d_plane_list);
 }
 
 // Is cell m in a subdomain of multiplicative color `color`?  (The same rule
@@ -770,6 +772,16 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
     if ((st = build_flux_lists(P, d, false)) != TPSS_OK) return fail(st);
   }
   P->mul_colors_active = P->mul_colors_default;
+  {
+    std::vector<int> lex_offsets;
+    auto one = [&](int, int, int) { return 0; };
+    if ((st = build(one, 1, &P->d_lex_list, lex_offsets)) != TPSS_OK) return fail(st);
+  }
+  if (kind == TPSS_VERTEX_PATCH && d == 3) {
+    // plane by plane: the 4 additive colors of plane p_z, ((p_x+1)&1) | ((p_y+1)&1) << 1
+    auto plane_color = [&](int px, int py, int pz) { return 4 * pz + (((px + 1) & 1) | (((py + 1) & 1) << 1)); };
+    if ((st = build(plane_color, 4 * P->npos[2], &P->d_plane_list, P->plane_offsets)) != TPSS_OK) return fail(st);
+  }
   int h_err = 0;
   cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -865,6 +877,16 @@ extern "C" tpss_status tpss_patches_set_large_cluster(tpss_patches* P, int ctas)
   TPSS_REQUIRE(ctas == 0 || ctas == 1 || ctas == 2 || ctas == 4 || ctas == 8,
                "tpss_patches_set_large_cluster: ctas must be 0 (automatic), 1, 2, 4 or 8");
   P->large_cluster = ctas;
+  return TPSS_OK;
+}
+
+extern "C" tpss_status tpss_patches_set_additive_schedule(tpss_patches* P, int schedule) {
+  clear_error();
+  TPSS_REQUIRE(P, "tpss_patches_set_additive_schedule: null patches");
+  TPSS_REQUIRE(schedule == TPSS_ADDITIVE_COLORS || schedule == TPSS_ADDITIVE_PLANES ||
+                   schedule == TPSS_ADDITIVE_ATOMIC,
+               "tpss_patches_set_additive_schedule: unknown schedule");
+  P->additive_schedule = schedule;
   return TPSS_OK;
 }
 

@@ -320,6 +320,36 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
     TPSS_TRY(apply_operator_t<T>(ctx, P->level, nrhs, x, rb, b));
     r = rb;
   }
+  if constexpr (sizeof(T) == 4) {
+    // BF16 3D: one launch over all subdomains, atomic accumulation into x
+    if (P->precision == TPSS_BF16 && P->additive_schedule == TPSS_ADDITIVE_ATOMIC) {
+      const tpss_status st = patch_pass_bf16_atomic(P, P->d_lex_list, (int)P->nsub, (float)omega, nrhs,
+                                                    reinterpret_cast<const float*>(r), reinterpret_cast<float*>(x), s);
+      if (st != TPSS_EINVAL) return st;   // else: shape or alignment not covered, colored launches
+    }
+  }
+  if (P->additive_schedule == TPSS_ADDITIVE_PLANES && P->d_plane_list != nullptr) {
+    // 3D vertex patches plane by plane: the cells of two neighbouring cell
+    // planes stay in L2 across the plane's 4 color launches
+    const int ncell_slots = ctx->num_sms * 3;
+    for (size_t g = 0; g + 1 < P->plane_offsets.size(); ++g) {
+      const int o = P->plane_offsets[g], cnt = P->plane_offsets[g + 1] - o;
+      if (cnt == 0) continue;
+      if constexpr (sizeof(T) == 4) {
+        if (P->precision == TPSS_BF16) {
+          // enough CTAs for ~4 waves: split the right-hand sides over CTAs
+          const int rpc = std::max(1, std::min(nrhs, (int)((int64_t)cnt * nrhs / (4 * ncell_slots))));
+          const tpss_status st = patch_pass_bf16(P, P->d_plane_list + o, cnt, (float)omega, nrhs,
+                                                 reinterpret_cast<const float*>(r), reinterpret_cast<float*>(x), s,
+                                                 nullptr, rpc);
+          if (st == TPSS_OK) continue;
+          if (st != TPSS_EINVAL) return st;
+        }
+      }
+      TPSS_TRY(patch_pass<T>(P, P->d_plane_list + o, cnt, omega, nrhs, r, x, s));
+    }
+    return TPSS_OK;
+  }
   const int nc = (int)P->add_offsets.size() - 1;
   for (int c = 0; c < nc; ++c) {
     const int o = P->add_offsets[c], cnt = P->add_offsets[c + 1] - o;

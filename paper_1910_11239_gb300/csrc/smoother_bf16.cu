@@ -95,12 +95,21 @@ __global__ void __launch_bounds__(kThreads, 3)
 patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__ Z0, const float* __restrict__ Z1,
                          const float* __restrict__ Z2, const float* __restrict__ L0, const float* __restrict__ L1,
                          const float* __restrict__ L2, const float* __restrict__ r, float* __restrict__ x,
-                         float* __restrict__ d, float omega, int nc0, int nc1, int64_t ndofs, int nrhs) {
+                         float* __restrict__ d, float omega, int nc0, int nc1, int64_t ndofs, int nrhs,
+                         int rpc) {
   using S = Shape<N>;
   constexpr int N1 = VERTEX ? N / 2 : N;
   constexpr int NLOC1 = N1 * N1 * N1;
   constexpr int NCELL = VERTEX ? 8 : 1;
   constexpr int NV = NCELL * NLOC1;
+  // right-hand sides [blockIdx.y * rpc, +rpc) of this CTA
+  {
+    const int64_t off = (int64_t)blockIdx.y * rpc * ndofs;
+    r += off;
+    x += off;
+    if (d != nullptr) d += off;
+    nrhs = min(rpc, nrhs - (int)blockIdx.y * rpc);
+  }
   extern __shared__ __align__(16) unsigned char dsm[];
   __nv_bfloat16* T = reinterpret_cast<__nv_bfloat16*>(dsm);
   float* SB = reinterpret_cast<float*>(dsm + ((S::TOTAL * 2 + 15) / 16) * 16);
@@ -154,6 +163,93 @@ patch_smooth_bf16_kernel(const int* __restrict__ list, const float* __restrict__
   }
 }
 
+// One (subdomain, right-hand side) per CTA over ALL subdomains in one launch,
+// x accumulated with FP32 vector atomics instead of colored read-modify-write
+// launches.  With the subdomains in lexicographic order the 2^d patches that
+// share a cell run close together in time, so the cell's r and x stay in L2
+// across them and HBM sees each vector about once per call instead of once
+// per color; the summation order of the 2^d contributions then varies from
+// run to run (FP32 rounding).
+template <int N, bool VERTEX>
+__global__ void __launch_bounds__(kThreads, 4)
+patch_smooth_bf16_atomic_kernel(const int* __restrict__ list, const float* __restrict__ Z0,
+                                const float* __restrict__ Z1, const float* __restrict__ Z2,
+                                const float* __restrict__ L0, const float* __restrict__ L1,
+                                const float* __restrict__ L2, const float* __restrict__ r, float* __restrict__ x,
+                                float omega, int nc0, int nc1, int64_t ndofs) {
+  using S = Shape<N>;
+  constexpr int N1 = VERTEX ? N / 2 : N;
+  constexpr int NLOC1 = N1 * N1 * N1;
+  constexpr int NCELL = VERTEX ? 8 : 1;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __nv_bfloat16* T = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float* SB = reinterpret_cast<float*>(dsm + ((S::TOTAL * 2 + 15) / 16) * 16);
+  __shared__ float lam[3 * N];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int packed = list[blockIdx.x];
+  const int px = unpack_x(packed), py = unpack_y(packed), pz = unpack_z(packed);
+  const CellBase cbase{px, py, pz, nc0, nc1};
+  const int64_t vbase = (int64_t)blockIdx.y * ndofs;
+  stage<NLOC1, NCELL>(SB, r + vbase, cbase, tid);
+  cp_async_commit();
+  for (int e = tid; e < S::TOTAL; e += kThreads) T[e] = __float2bfloat16(0.f);
+  if (tid < 3 * N) {
+    const int d = tid / N, i = tid % N;
+    const float* Ld = d == 0 ? L0 : (d == 1 ? L1 : L2);
+    const int p = d == 0 ? px : (d == 1 ? py : pz);
+    lam[tid] = Ld[(size_t)p * N + i];
+  }
+  uint32_t bx[2][2], bxt[2][2], by[2][2], byt[2][2], bzz[2][2], bzt[2][2];
+  load_bfrag<N, false>(bxt, Z0 + (size_t)px * N * N, lane);
+  load_bfrag<N, true>(bx, Z0 + (size_t)px * N * N, lane);
+  load_bfrag<N, false>(byt, Z1 + (size_t)py * N * N, lane);
+  load_bfrag<N, true>(by, Z1 + (size_t)py * N * N, lane);
+  load_bfrag<N, false>(bzt, Z2 + (size_t)pz * N * N, lane);
+  load_bfrag<N, true>(bzz, Z2 + (size_t)pz * N * N, lane);
+  cp_async_wait_all();
+  __syncthreads();   // staged r, zeroed tensor and lam visible
+  rows_to_tensor<N, N1, NCELL>(T, SB, tid);
+  __syncthreads();
+  contract<N, 0>(T, bxt, warp, lane);
+  __syncthreads();
+  contract<N, 1>(T, byt, warp, lane);
+  __syncthreads();
+  zstep<N>(T, bzt, bzz, lam, warp, lane);
+  __syncthreads();
+  contract<N, 1>(T, by, warp, lane);
+  __syncthreads();
+  contract<N, 0>(T, bx, warp, lane);
+  __syncthreads();
+  tensor_atomic_add<N, N1, NCELL>(x + vbase, T, omega, cbase, tid);
+}
+
+template <int N, bool VERTEX>
+constexpr size_t smem_bytes_atomic() {
+  constexpr int N1 = VERTEX ? N / 2 : N;
+  constexpr int NV = (VERTEX ? 8 : 1) * N1 * N1 * N1;
+  return ((Shape<N>::TOTAL * 2 + 15) / 16) * 16 + (size_t)NV * 4;
+}
+
+template <int N, bool VERTEX>
+static tpss_status launch_atomic(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
+                                 float* x, cudaStream_t s) {
+  constexpr size_t smem = smem_bytes_atomic<N, VERTEX>();
+  static bool attr = false;
+  if (!attr) {
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(patch_smooth_bf16_atomic_kernel<N, VERTEX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  if (count <= 0) return TPSS_OK;
+  const Level& L = P->ctx->levels[P->level];
+  dim3 grid((unsigned)count, (unsigned)nrhs);
+  patch_smooth_bf16_atomic_kernel<N, VERTEX><<<grid, kThreads, smem, s>>>(
+      list, P->d_Z32[0], P->d_Z32[1], P->d_Z32[2], P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r, x, omega,
+      L.nc[0], L.nc[1], L.ndofs);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
 template <int N, bool VERTEX>
 constexpr size_t smem_bytes() {
   constexpr int N1 = VERTEX ? N / 2 : N;
@@ -163,7 +259,7 @@ constexpr size_t smem_bytes() {
 
 template <int N, bool VERTEX>
 static tpss_status launch(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                          float* x, float* d, cudaStream_t s) {
+                          float* x, float* d, cudaStream_t s, int rpc) {
   constexpr size_t smem = smem_bytes<N, VERTEX>();
   static bool attr = false;
   if (!attr) {
@@ -173,18 +269,43 @@ static tpss_status launch(tpss_patches* P, const int* list, int count, float ome
   }
   if (count <= 0) return TPSS_OK;
   const Level& L = P->ctx->levels[P->level];
-  patch_smooth_bf16_kernel<N, VERTEX><<<count, kThreads, smem, s>>>(
+  if (rpc < 1 || rpc > nrhs) rpc = nrhs;
+  dim3 grid((unsigned)count, (unsigned)((nrhs + rpc - 1) / rpc));
+  patch_smooth_bf16_kernel<N, VERTEX><<<grid, kThreads, smem, s>>>(
       list, P->d_Z32[0], P->d_Z32[1], P->d_Z32[2], P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r, x, d, omega,
-      L.nc[0], L.nc[1], L.ndofs, nrhs);
+      L.nc[0], L.nc[1], L.ndofs, nrhs, rpc);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
 
 }  // namespace bf
 
+// One launch over every subdomain of the list with atomic accumulation into x
+// (additive smoother); TPSS_EINVAL (without launching) for shapes it does not
+// cover or vectors that are not 16-byte aligned.
+tpss_status patch_pass_bf16_atomic(tpss_patches* P, const int* list, int count, float omega, int nrhs,
+                                   const float* r, float* x, cudaStream_t s) {
+  if (P->ctx->dim != 3) return TPSS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x)) & 15) return TPSS_EINVAL;
+  const bool v = P->kind == TPSS_VERTEX_PATCH;
+  switch (P->n) {
+    case 4: return v ? bf::launch_atomic<4, true>(P, list, count, omega, nrhs, r, x, s)
+                     : bf::launch_atomic<4, false>(P, list, count, omega, nrhs, r, x, s);
+    case 6: return v ? bf::launch_atomic<6, true>(P, list, count, omega, nrhs, r, x, s)
+                     : bf::launch_atomic<6, false>(P, list, count, omega, nrhs, r, x, s);
+    case 8: return v ? bf::launch_atomic<8, true>(P, list, count, omega, nrhs, r, x, s)
+                     : bf::launch_atomic<8, false>(P, list, count, omega, nrhs, r, x, s);
+    case 10: return v ? bf::launch_atomic<10, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
+    case 12: return v ? bf::launch_atomic<12, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
+    case 14: return v ? bf::launch_atomic<14, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
+    case 16: return v ? bf::launch_atomic<16, true>(P, list, count, omega, nrhs, r, x, s) : TPSS_EINVAL;
+    default: return TPSS_EINVAL;
+  }
+}
+
 // 3D BF16 path; returns TPSS_EINVAL (without launching) for shapes it does not cover.
 tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                            float* x, cudaStream_t s, float* d) {
+                            float* x, cudaStream_t s, float* d, int rpc) {
   if (P->ctx->dim != 3) return TPSS_EINVAL;
   // 16-byte cp.async and vector accesses need 16-byte aligned vectors; other
   // pointers take the generic tensor-core kernel
@@ -192,16 +313,16 @@ tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float o
     return TPSS_EINVAL;
   const bool v = P->kind == TPSS_VERTEX_PATCH;
   switch (P->n) {
-    case 4: return v ? bf::launch<4, true>(P, list, count, omega, nrhs, r, x, d, s)
-                     : bf::launch<4, false>(P, list, count, omega, nrhs, r, x, d, s);
-    case 6: return v ? bf::launch<6, true>(P, list, count, omega, nrhs, r, x, d, s)
-                     : bf::launch<6, false>(P, list, count, omega, nrhs, r, x, d, s);
-    case 8: return v ? bf::launch<8, true>(P, list, count, omega, nrhs, r, x, d, s)
-                     : bf::launch<8, false>(P, list, count, omega, nrhs, r, x, d, s);
-    case 10: return v ? bf::launch<10, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
-    case 12: return v ? bf::launch<12, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
-    case 14: return v ? bf::launch<14, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
-    case 16: return v ? bf::launch<16, true>(P, list, count, omega, nrhs, r, x, d, s) : TPSS_EINVAL;
+    case 4: return v ? bf::launch<4, true>(P, list, count, omega, nrhs, r, x, d, s, rpc)
+                     : bf::launch<4, false>(P, list, count, omega, nrhs, r, x, d, s, rpc);
+    case 6: return v ? bf::launch<6, true>(P, list, count, omega, nrhs, r, x, d, s, rpc)
+                     : bf::launch<6, false>(P, list, count, omega, nrhs, r, x, d, s, rpc);
+    case 8: return v ? bf::launch<8, true>(P, list, count, omega, nrhs, r, x, d, s, rpc)
+                     : bf::launch<8, false>(P, list, count, omega, nrhs, r, x, d, s, rpc);
+    case 10: return v ? bf::launch<10, true>(P, list, count, omega, nrhs, r, x, d, s, rpc) : TPSS_EINVAL;
+    case 12: return v ? bf::launch<12, true>(P, list, count, omega, nrhs, r, x, d, s, rpc) : TPSS_EINVAL;
+    case 14: return v ? bf::launch<14, true>(P, list, count, omega, nrhs, r, x, d, s, rpc) : TPSS_EINVAL;
+    case 16: return v ? bf::launch<16, true>(P, list, count, omega, nrhs, r, x, d, s, rpc) : TPSS_EINVAL;
     default: return TPSS_EINVAL;
   }
 }

@@ -166,6 +166,13 @@ struct tpss_patches {
   std::vector<int> mul8_offsets;
   int mul_colors_active = 0;
   int mult_update = 1;             // multiplicative sweep: update the residual per color (else recompute)
+  int* d_lex_list = nullptr;       // every subdomain, lexicographic (x fastest)
+  // 3D vertex patches: additive colors plane by plane, sorted (p_z, color,
+  // p_y, p_x); plane_offsets[4 p_z + c] starts the c-th of the 4 colors
+  // present in plane p_z
+  int* d_plane_list = nullptr;
+  std::vector<int> plane_offsets;
+  int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule
   // per multiplicative color: cells outside the color with a face to it,
   // {cell index, face mask (bit 2t+side: neighbour at -1 / +1 along t)}
   int2* d_flux_list = nullptr;
@@ -211,8 +218,11 @@ tpss_status patch_pass_tc(tpss_patches* P, const int* list, int count, float ome
                           float* x, cudaStream_t s, float* d = nullptr);
 
 // ---- smoother_bf16.cu (3D BF16 tensor-core path; TPSS_EINVAL for uncovered shapes)
+// rpc: right-hand sides per CTA (0 = all of them in every CTA)
 tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float omega, int nrhs, const float* r,
-                            float* x, cudaStream_t s, float* d = nullptr);
+                            float* x, cudaStream_t s, float* d = nullptr, int rpc = 0);
+tpss_status patch_pass_bf16_atomic(tpss_patches* P, const int* list, int count, float omega, int nrhs,
+                                   const float* r, float* x, cudaStream_t s);
 
 // ---- smoother_large.cu (3D FP64 vertex patches with n > 16, per-CTA scratch slabs)
 tpss_status patch_large_ctas(int n, int num_sms, int* max_ctas);

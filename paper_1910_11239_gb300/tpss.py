@@ -21,6 +21,7 @@ FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PENALTY_PAPER, PENALTY_KP1SQ = 0, 1
 COARSE_AUTO, COARSE_DENSE, COARSE_FD = 0, 1, 2
 MULT_RESIDUAL_UPDATE, MULT_RESIDUAL_FULL = 0, 1
+ADDITIVE_COLORS, ADDITIVE_PLANES, ADDITIVE_ATOMIC = 0, 1, 2
 ACS, AVS, MCS, MVS = 0, 1, 2, 3
 SMOOTHERS = {"ACS": ACS, "AVS": AVS, "MCS": MCS, "MVS": MVS}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
@@ -61,6 +62,7 @@ SIGNATURES = {
     "tpss_patches_set_mult_colors": [_VP, _I],
     "tpss_patches_set_mult_residual": [_VP, _I],
     "tpss_patches_set_large_cluster": [_VP, _I],
+    "tpss_patches_set_additive_schedule": [_VP, _I],
     "tpss_smooth_additive": [_VP, _D, _I, _VP, _VP, _I],
     "tpss_smooth_additive_f32": [_VP, _F, _I, _VP, _VP, _I],
     "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
@@ -295,6 +297,9 @@ class Patches:
 
     def set_large_cluster(self, ctas):
         _check(lib().tpss_patches_set_large_cluster(self.h, ctas))
+
+    def set_additive_schedule(self, schedule):
+        _check(lib().tpss_patches_set_additive_schedule(self.h, schedule))
 
     def smooth_additive(self, omega, b, x, x_is_zero=False, nrhs=1):
         n = self.problem.ndofs(self.level) * nrhs

@@ -103,3 +103,30 @@ def test_bf16_smoother_with_unaligned_vectors_matches_aligned():
     torch.cuda.synchronize()
     assert rel_err(xx[1:].double(), xa.double().cpu().numpy()) < 2e-2
     prob.close()
+
+
+@pytest.mark.parametrize("k,n", [(2, 7), (3, 6), (7, 4)])
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp64"])
+def test_additive_schedules_agree(k, n, prec):
+    """The additive smoother's schedules (colored launches, plane by plane,
+    one atomic launch for BF16) compute the same local solves; only the
+    summation order of the up to 8 contributions per DoF differs."""
+    from paper_1910_11239_gb300 import tpss
+    widths = workloads.widths_random(n, 3, seed=60 + k)
+    prob = tpss.Problem(3, k, widths)
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH, tpss.PRECISIONS[prec])
+    N = prob.ndofs(0)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    b = torch.from_numpy(workloads.rhs_uniform(N, seed=3, nrhs=2)).to("cuda", dt)
+    outs = []
+    scheds = [tpss.ADDITIVE_COLORS, tpss.ADDITIVE_PLANES] + ([tpss.ADDITIVE_ATOMIC] if prec == "bf16" else [])
+    for sch in scheds:
+        P.set_additive_schedule(sch)
+        x = torch.empty_like(b)
+        P.smooth_additive(0.7, b, x, x_is_zero=True, nrhs=2)
+        outs.append(x)
+    tol = 1e-14 if prec == "fp64" else 1e-5
+    for o in outs[1:]:
+        d = (o - outs[0]).abs().max().item() / outs[0].abs().max().item()
+        assert d < tol, d
+    prob.close()

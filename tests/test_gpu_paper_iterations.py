@@ -56,3 +56,27 @@ def test_k15_fractional_iterations_match_paper(dim, L, smoother, paper, left):
     nu = perf.fractional_iterations(res["history"], 1e-8)
     assert abs(nu - paper) < (0.2 if left else 0.6), nu
     prob.close()
+
+
+# The 2D columns of tab:cubecp / tab:cubemvpminimal at k = 3 (L = 8) and
+# k = 7 (L = 7), 4.2 M DoFs each; 8 colors for MVS in 2D.
+TWO_D_CASES = [(3, 8, "ACS", 14.5, False), (7, 7, "ACS", 18.7, False), (3, 8, "MCS", 7.3, True),
+               (7, 7, "MCS", 9.7, True), (3, 8, "MVS", 2.5, False), (7, 7, "MVS", 2.1, False)]
+
+
+@pytest.mark.parametrize("k,L,smoother,paper,left", TWO_D_CASES)
+def test_2d_fractional_iterations_match_paper(k, L, smoother, paper, left):
+    prob = tpss.Problem(2, k, workloads.widths_uniform(2, 2), nlevels=L + 1)
+    N = prob.ndofs(L)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(L, 1, b)
+    x = torch.empty_like(b)
+    if smoother == "ACS":
+        prob.mg_setup("ACS", 0.7, tpss.FP64)
+        res = prob.pcg_solve(b, x, rtol=1e-8, maxit=100, history=True)
+    else:
+        prob.mg_setup(smoother, 1.0, tpss.FP64, nonsymmetric=1)
+        res = prob.gmres_solve(b, x, rtol=1e-8, maxit=100, restart=30, history=True, left=left)
+    nu = perf.fractional_iterations(res["history"], 1e-8)
+    assert abs(nu - paper) < (0.2 if left else 0.6), nu
+    prob.close()
