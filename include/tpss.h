@@ -254,9 +254,21 @@ typedef struct {
  *          cells per direction (one vertex patch), the subdomain is the whole
  *          mesh and its fast-diagonalization inverse (Sec. 3.2) is A_0^{-1}
  *          exactly (FP64 V-cycles only).
+ *   CHEBYSHEV: the paper's coarse solver (Sec. 2.4), inexact: a Chebyshev
+ *          iteration preconditioned by the additive cell smoother (omega = 1)
+ *          with a fixed number of steps for a 1e-8 reduction of the A-norm
+ *          error over the interval [0.8 theta_min, 1.1 theta_max], theta the
+ *          extreme Ritz values of 50 preconditioned CG steps from a
+ *          SplitMix64 start vector (FP64 V-cycles only; see
+ *          tpss_coarse_chebyshev_info).
  *   AUTO:  FD where it applies and level 0 has more than 4096 unknowns, else
  *          DENSE. */
-typedef enum { TPSS_COARSE_AUTO = 0, TPSS_COARSE_DENSE = 1, TPSS_COARSE_FD = 2 } tpss_coarse_solver;
+typedef enum {
+  TPSS_COARSE_AUTO = 0,
+  TPSS_COARSE_DENSE = 1,
+  TPSS_COARSE_FD = 2,
+  TPSS_COARSE_CHEBYSHEV = 3
+} tpss_coarse_solver;
 
 /* Build smoothers on levels 1..L and the exact coarse solver on level 0 (this
  * replaces the paper's Chebyshev coarse iteration).  TPSS_EINVAL if the
@@ -267,8 +279,13 @@ tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params);
  * x = MG_L(0, b).  b and x are finest-level FP64 vectors (one right-hand side). */
 tpss_status tpss_vcycle(tpss_ctx* ctx, const double* b, double* x);
 
-/* Exact coarse solve x = A_0^{-1} b on level 0 (after tpss_mg_setup). */
+/* Coarse solve x = A_0^{-1} b on level 0 (after tpss_mg_setup; exact except
+ * with TPSS_COARSE_CHEBYSHEV). */
 tpss_status tpss_coarse_solve(tpss_ctx* ctx, const double* b, double* x);
+
+/* The Chebyshev coarse solver's interval [a, b] for P A_0 and its number of
+ * steps (host values); TPSS_EINVAL if that solver is not set up. */
+tpss_status tpss_coarse_chebyshev_info(const tpss_ctx* ctx, double* a, double* b, int* steps);
 
 /* Preconditioned CG (Sec. 2.4) on the finest level with one V-cycle as
  * preconditioner, from x = 0, stopped at ||r_k||_2 <= rtol ||r_0||_2 or after

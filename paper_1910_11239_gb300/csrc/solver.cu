@@ -30,6 +30,8 @@ void destroy_mg(tpss_ctx* ctx) {
   for (auto* P : mg->patches)
     if (P) tpss_patches_destroy(P);
   if (mg->coarse_fd) tpss_patches_destroy(mg->coarse_fd);
+  if (mg->coarse_acs) tpss_patches_destroy(mg->coarse_acs);
+  dfree(mg->cheb_vec);
   dfree(mg->coarse_inv);
   dfree(mg->gj_tmp);
   for (auto* v : mg->b64) dfree(v);
@@ -179,6 +181,170 @@ static bool coarse_is_one_subdomain(const tpss_ctx* ctx, int* kind) {
 
 constexpr int64_t kDenseCoarseAuto = 4096;   // AUTO: dense inverse up to this size
 
+// ------------------------------------------- Chebyshev coarse solver (Sec. 2.4)
+// The paper solves the coarse problem to a relative accuracy of 1e-8 with a
+// Chebyshev iteration preconditioned by the additive cell smoother (P, omega
+// = 1).  Spectral interval of P A_0: Lanczos matrix of 50 PCG steps from a
+// SplitMix64 start vector, its extreme Ritz values widened to [0.8, 1.1] x;
+// steps: the smallest m with 2 q^m / (1 + q^2m) <= 1e-8,
+// q = (sqrt(kappa) - 1)/(sqrt(kappa) + 1), kappa = b/a.  Three-term recurrence
+//   theta = (b+a)/2, delta = (b-a)/2, sigma = theta/delta, rho_0 = 1/sigma,
+//   d_0 = P f / theta, x_1 = d_0, and for k >= 1: r_k = f - A x_k,
+//   rho_k = 1/(2 sigma - rho_(k-1)), d_k = rho_k rho_(k-1) d_(k-1) + (2 rho_k/delta) P r_k,
+//   x_(k+1) = x_k + d_k.
+constexpr int kChebLanczosSteps = 50;
+constexpr double kChebLow = 0.8, kChebHigh = 1.1, kChebTol = 1e-8;
+
+static uint64_t splitmix64(uint64_t i) {   // output i of SplitMix64 from state 0
+  uint64_t z = (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (diag, off) below x
+// (Sturm sequence of the LDL^T pivots).
+static int sturm_count(const std::vector<double>& diag, const std::vector<double>& off, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t j = 0; j < diag.size(); ++j) {
+    const double o2 = j > 0 ? off[j - 1] * off[j - 1] : 0.0;
+    q = diag[j] - x - (j > 0 ? o2 / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// i-th smallest eigenvalue (0-based) by bisection inside the Gershgorin interval
+static double tridiag_eig(const std::vector<double>& diag, const std::vector<double>& off, int i) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t j = 0; j < diag.size(); ++j) {
+    const double rad = (j > 0 ? std::fabs(off[j - 1]) : 0.0) + (j + 1 < diag.size() ? std::fabs(off[j]) : 0.0);
+    lo = std::min(lo, diag[j] - rad);
+    hi = std::max(hi, diag[j] + rad);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(diag, off, mid) > i) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = fma(a, x[e], y[e]);
+}
+__global__ void xpay_kernel(double* __restrict__ p, const double* __restrict__ z, double b, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = fma(b, p[e], z[e]);
+}
+// d = c1 d + c2 z; x += d
+__global__ void cheb_step_kernel(double* __restrict__ x, double* __restrict__ d, const double* __restrict__ z,
+                                 double c1, double c2, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double dn = fma(c1, d[e], c2 * z[e]);
+    d[e] = dn;
+    x[e] += dn;
+  }
+}
+
+static tpss_status chebyshev_setup(tpss_ctx* ctx, MGState* mg) {
+  const int64_t n = mg->n0;
+  cudaStream_t s = ctx->stream;
+  TPSS_TRY(create_patches(ctx, 0, TPSS_CELL, TPSS_FP64, &mg->coarse_acs));
+  TPSS_TRY(dalloc_t(&mg->cheb_vec, (size_t)4 * n));
+  double* r = mg->cheb_vec;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  {
+    std::vector<double> sv((size_t)n);
+    for (int64_t i = 0; i < n; ++i) sv[i] = 2.0 * ((double)(splitmix64((uint64_t)i) >> 11) * 0x1.0p-53) - 1.0;
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(r, sv.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+  }
+  double* sc = ctx->d_scalars;
+  auto host_dot = [&](const double* a, const double* b, double* out) -> tpss_status {
+    TPSS_TRY(dot(ctx, a, b, n, sc + 7));
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(out, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    return TPSS_OK;
+  };
+  const int g = grid_for(ctx, n);
+  TPSS_TRY(smooth_additive_t<double>(mg->coarse_acs, 1.0, 1, r, z, 1));   // z = P r
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double rz = 0.0;
+  TPSS_TRY(host_dot(r, z, &rz));
+  std::vector<double> alphas, betas;
+  const int steps = (int)std::min<int64_t>(n, kChebLanczosSteps);
+  for (int j = 0; j < steps && rz > 0.0; ++j) {
+    TPSS_TRY(apply_operator_t<double>(ctx, 0, 1, p, q, nullptr));
+    double pq = 0.0;
+    TPSS_TRY(host_dot(p, q, &pq));
+    if (!(pq > 0.0)) break;
+    const double alpha = rz / pq;
+    axpy_kernel<<<g, 256, 0, s>>>(r, q, -alpha, n);
+    TPSS_CHECK_LAUNCH();
+    TPSS_TRY(smooth_additive_t<double>(mg->coarse_acs, 1.0, 1, r, z, 1));
+    double rz_new = 0.0;
+    TPSS_TRY(host_dot(r, z, &rz_new));
+    alphas.push_back(alpha);
+    betas.push_back(rz_new / rz);
+    if (!(rz_new > 0.0)) break;
+    xpay_kernel<<<g, 256, 0, s>>>(p, z, rz_new / rz, n);
+    TPSS_CHECK_LAUNCH();
+    rz = rz_new;
+  }
+  const int m = (int)alphas.size();
+  TPSS_REQUIRE(m >= 1, "tpss_mg_setup: Chebyshev coarse solver: no Lanczos step");
+  std::vector<double> diag(m), off(m > 1 ? m - 1 : 0);
+  for (int j = 0; j < m; ++j) {
+    diag[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
+    if (j + 1 < m) off[j] = std::sqrt(betas[j]) / alphas[j];
+  }
+  const double tmin = tridiag_eig(diag, off, 0), tmax = tridiag_eig(diag, off, m - 1);
+  TPSS_REQUIRE(tmin > 0.0 && std::isfinite(tmax), "tpss_mg_setup: Chebyshev coarse solver: bad spectral estimate");
+  mg->cheb_a = kChebLow * tmin;
+  mg->cheb_b = kChebHigh * tmax;
+  const double kappa = mg->cheb_b / mg->cheb_a, qq = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
+  int steps_needed = 0;
+  double qm = 1.0;
+  while (2.0 * qm / (1.0 + qm * qm) > kChebTol && steps_needed < 100000) {
+    qm *= qq;
+    ++steps_needed;
+  }
+  mg->cheb_m = steps_needed;
+  return TPSS_OK;
+}
+
+static tpss_status chebyshev_apply(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
+  const int64_t n = mg->n0;
+  cudaStream_t s = ctx->stream;
+  double* r = mg->cheb_vec;
+  double* z = r + n;
+  double* d = z + n;
+  const double a = mg->cheb_a, b = mg->cheb_b;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const int g = grid_for(ctx, n);
+  if (mg->cheb_m < 1) {
+    TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    return TPSS_OK;
+  }
+  TPSS_TRY(smooth_additive_t<double>(mg->coarse_acs, 1.0 / theta, 1, f, d, 1));   // d_0 = P f / theta
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(x, d, n * sizeof(double), cudaMemcpyDeviceToDevice, s));   // x_1
+  for (int k = 1; k < mg->cheb_m; ++k) {
+    TPSS_TRY(apply_operator_t<double>(ctx, 0, 1, x, r, f));                // r_k = f - A x_k
+    TPSS_TRY(smooth_additive_t<double>(mg->coarse_acs, 1.0, 1, r, z, 1));  // z = P r_k
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    cheb_step_kernel<<<g, 256, 0, s>>>(x, d, z, rho_new * rho, 2.0 * rho_new / delta, n);
+    TPSS_CHECK_LAUNCH();
+    rho = rho_new;
+  }
+  return TPSS_OK;
+}
+
 static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
   const Level& L0 = ctx->levels[0];
   const int64_t n = L0.ndofs;
@@ -186,6 +352,10 @@ static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
   int kind = TPSS_CELL;
   const bool fd_ok = !mg->mixed && coarse_is_one_subdomain(ctx, &kind);
   const int choice = mg->params.coarse_solver;
+  if (choice == TPSS_COARSE_CHEBYSHEV) {
+    TPSS_REQUIRE(!mg->mixed, "tpss_mg_setup: the Chebyshev coarse solver needs an FP64 V-cycle");
+    return chebyshev_setup(ctx, mg);
+  }
   if (choice == TPSS_COARSE_FD || (choice == TPSS_COARSE_AUTO && fd_ok && n > kDenseCoarseAuto)) {
     TPSS_REQUIRE(fd_ok, "tpss_mg_setup: the fast-diagonalization coarse solve needs an FP64 V-cycle and "
                         "1 or 2 cells per direction on level 0");
@@ -221,10 +391,12 @@ static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
 
 template <typename S, typename D>
 static tpss_status coarse_apply(tpss_ctx* ctx, MGState* mg, const S* b, D* x) {
-  if (mg->coarse_fd) {   // FP64 only (set up for FP64 V-cycles)
-    if constexpr (sizeof(S) == sizeof(double) && sizeof(D) == sizeof(double))
-      return smooth_additive_t<double>(mg->coarse_fd, 1.0, 1, b, x, 1);
-    set_error("coarse solve: the fast-diagonalization coarse solver is FP64 only");
+  if (mg->coarse_fd || mg->coarse_acs) {   // FP64 only (set up for FP64 V-cycles)
+    if constexpr (sizeof(S) == sizeof(double) && sizeof(D) == sizeof(double)) {
+      if (mg->coarse_fd) return smooth_additive_t<double>(mg->coarse_fd, 1.0, 1, b, x, 1);
+      return chebyshev_apply(ctx, mg, b, x);
+    }
+    set_error("coarse solve: the fast-diagonalization and Chebyshev coarse solvers are FP64 only");
     return TPSS_EINVAL;
   }
   const int64_t n = mg->n0;
@@ -526,7 +698,7 @@ extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params
   TPSS_REQUIRE(params->omega > 0.0 && std::isfinite(params->omega), "tpss_mg_setup: omega must be positive");
   TPSS_REQUIRE(params->precision == TPSS_FP64 || ctx->k <= kMaxMixedDegree,
                "tpss_mg_setup: mixed-precision V-cycles support degrees up to 7");
-  TPSS_REQUIRE(params->coarse_solver >= TPSS_COARSE_AUTO && params->coarse_solver <= TPSS_COARSE_FD,
+  TPSS_REQUIRE(params->coarse_solver >= TPSS_COARSE_AUTO && params->coarse_solver <= TPSS_COARSE_CHEBYSHEV,
                "tpss_mg_setup: unknown coarse solver");
   TPSS_REQUIRE(params->mult_residual == TPSS_MULT_RESIDUAL_UPDATE || params->mult_residual == TPSS_MULT_RESIDUAL_FULL,
                "tpss_mg_setup: mult_residual must be 0 (update) or 1 (full)");
@@ -593,6 +765,16 @@ extern "C" tpss_status tpss_coarse_solve(tpss_ctx* ctx, const double* b, double*
   TPSS_REQUIRE(ctx->mg, "tpss_coarse_solve: call tpss_mg_setup first");
   TPSS_REQUIRE(b != x, "tpss_coarse_solve: b and x must not alias");
   return coarse_apply<double, double>(ctx, ctx->mg, b, x);
+}
+
+extern "C" tpss_status tpss_coarse_chebyshev_info(const tpss_ctx* ctx, double* a, double* b, int* steps) {
+  clear_error();
+  TPSS_REQUIRE(ctx && a && b && steps, "tpss_coarse_chebyshev_info: null argument");
+  TPSS_REQUIRE(ctx->mg && ctx->mg->coarse_acs, "tpss_coarse_chebyshev_info: no Chebyshev coarse solver set up");
+  *a = ctx->mg->cheb_a;
+  *b = ctx->mg->cheb_b;
+  *steps = ctx->mg->cheb_m;
+  return TPSS_OK;
 }
 
 extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,

@@ -122,6 +122,10 @@ struct MGState {
   double* gm_Z = nullptr;
   double* gm_h = nullptr;                // device scalars (2 (restart+1))
   tpss_patches* coarse_fd = nullptr;     // exact coarse solve by fast diagonalization (else coarse_inv)
+  tpss_patches* coarse_acs = nullptr;    // Chebyshev coarse solve: additive cell smoother on level 0
+  double cheb_a = 0.0, cheb_b = 0.0;     // spectral interval of P A_0 used by the iteration
+  int cheb_m = 0;                        // Chebyshev steps per coarse solve
+  double* cheb_vec = nullptr;            // 4 level-0 vectors
 };
 
 }  // namespace tpss

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "TPSS_OK", 1: "TPSS_ENOTCONV", -1: "TPSS_EINVAL", -2: "TPSS_E
 CELL, VERTEX_PATCH = 0, 1
 FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PENALTY_PAPER, PENALTY_KP1SQ = 0, 1
-COARSE_AUTO, COARSE_DENSE, COARSE_FD = 0, 1, 2
+COARSE_AUTO, COARSE_DENSE, COARSE_FD, COARSE_CHEBYSHEV = 0, 1, 2, 3
 MULT_RESIDUAL_UPDATE, MULT_RESIDUAL_FULL = 0, 1
 ADDITIVE_COLORS, ADDITIVE_PLANES, ADDITIVE_ATOMIC = 0, 1, 2
 ACS, AVS, MCS, MVS = 0, 1, 2, 3
@@ -76,6 +76,8 @@ SIGNATURES = {
     "tpss_mg_setup": [_VP, ctypes.POINTER(MGParams)],
     "tpss_vcycle": [_VP, _VP, _VP],
     "tpss_coarse_solve": [_VP, _VP, _VP],
+    "tpss_coarse_chebyshev_info": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int)],
     "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                        _VP],
     "tpss_gmres_solve": [_VP, _VP, _VP, _D, _I, _I, _I, ctypes.POINTER(ctypes.c_int),
@@ -232,6 +234,11 @@ class Problem:
         _check(lib().tpss_coarse_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
         return x
 
+
+    def coarse_chebyshev_info(self):
+        a, b, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().tpss_coarse_chebyshev_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m)))
+        return {"a": a.value, "b": b.value, "steps": m.value}
     def pcg_solve(self, b, x, rtol=1e-8, maxit=200, history=False):
         n = self.ndofs(self.nlevels - 1)
         it, rel = ctypes.c_int(), ctypes.c_double()
