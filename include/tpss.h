@@ -292,8 +292,9 @@ tpss_status tpss_coarse_chebyshev_info(const tpss_ctx* ctx, double* a, double* b
  * maxit iterations.  On return *iters and *rel_res are host values; if
  * res_hist != NULL, the residual norms ||r_0||..||r_iters|| are written to it
  * (host array of at least maxit+1 doubles).  Synchronizes the stream once per
- * iteration to test convergence.  Returns TPSS_ENOTCONV at maxit and
- * TPSS_EBREAKDOWN on a NaN/Inf or non-positive curvature. */
+ * iteration to test convergence.  Returns TPSS_ENOTCONV at maxit (x then
+ * holds the maxit-th iterate) and TPSS_EBREAKDOWN on a NaN/Inf or
+ * non-positive curvature. */
 tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
                            int* iters, double* rel_res, double* res_hist);
 

@@ -110,3 +110,29 @@ def fractional_iterations(hist, rtol):
         if hist[nu] <= tol:
             return nu - 1 + math.log(hist[nu - 1] / tol) / math.log(hist[nu - 1] / hist[nu])
     return float("nan")
+
+
+def cg_energy_errors(prob, b, rtol=1e-8, ref_rtol=1e-14, maxit=200):
+    """Energy norms ||x* - x_k||_A of the PCG iterates k = 0, 1, ... on the
+    finest level (Sec. 2.4 measures CG by these) until the first one at or
+    below rtol ||x*||_A: x* from PCG to ref_rtol, x_k as the iterate after k
+    steps (PCG from x_0 = 0 is deterministic, so the run with maxit = k stops
+    at the k-th iterate of the long run).  The V-cycle must be set up (FP64)."""
+    import torch
+    L = prob.nlevels - 1
+    xs = torch.empty_like(b)
+    prob.pcg_solve(b, xs, rtol=ref_rtol, maxit=maxit)
+    Ae = torch.empty_like(b)
+
+    def enorm(e):
+        prob.apply_operator(L, e, Ae)
+        return float(torch.dot(e, Ae).clamp_min(0.0).sqrt())
+
+    errs = [enorm(xs)]
+    x = torch.empty_like(b)
+    for k in range(1, maxit + 1):
+        prob.pcg_solve(b, x, rtol=1e-300, maxit=k)
+        errs.append(enorm(xs - x))
+        if errs[-1] <= rtol * errs[0]:
+            break
+    return errs

@@ -18,6 +18,28 @@ from paper_1910_11239_gb300 import perf, tpss, workloads
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("k,L", [(3, 3), (7, 2)])
+def test_acs_energy_norm_fractional_iterations(k, L):
+    """Sec. 2.4 states that CG is measured by the energy norm of the error.
+    The A-norm errors ||x* - x_k||_A (x* by PCG to 1e-14) decrease
+    monotonically, as CG guarantees; their nu_frac (17.70 at k = 3) lies
+    above the residual-based one (17.13), which is the one that matches the
+    printed 17.1 / 21.9 -- so the pins above use the residual reading."""
+    prob = tpss.Problem(3, k, workloads.widths_uniform(2, 3), nlevels=L + 1)
+    N = prob.ndofs(L)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(L, 1, b)
+    prob.mg_setup("ACS", 0.7, tpss.FP64)
+    errs = perf.cg_energy_errors(prob, b)
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))   # CG decreases the A-norm error
+    x = torch.empty_like(b)
+    res = prob.pcg_solve(b, x, rtol=1e-8, maxit=100, history=True)
+    nu_r = perf.fractional_iterations(res["history"], 1e-8)
+    nu_e = perf.fractional_iterations(errs, 1e-8)
+    assert nu_r - 0.2 < nu_e < nu_r + 2.0, (nu_e, nu_r)
+    prob.close()
+
+
 @pytest.mark.parametrize("k,paper", [(3, 17.1), (7, 21.9)])
 def test_acs_fractional_iterations_match_tab_cubecp(k, paper):
     prob = tpss.Problem(3, k, workloads.widths_uniform(2, 3), nlevels=4)
