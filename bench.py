@@ -470,10 +470,13 @@ def run_mgcg(tpss, workloads, torch, cases):
         x = torch.empty_like(b)
         for prec_mode in precs:
             # "+full": Alg. 3 as printed (residual recomputed before every
-            # color) instead of the default per-color residual update
-            prec, full = prec_mode.replace("+full", ""), prec_mode.endswith("+full")
+            # color) instead of the default per-color residual update;
+            # "+8colors": the 2^d-color vertex coloring (face-conflicting)
+            prec = prec_mode.split("+")[0]
+            full, colors8 = "+full" in prec_mode, "+8colors" in prec_mode
             prob.mg_setup(sm, omega, tpss.PRECISIONS[prec], flexible_cg=0 if prec == "fp64" else 1,
-                          mult_residual=tpss.MULT_RESIDUAL_FULL if full else tpss.MULT_RESIDUAL_UPDATE)
+                          mult_residual=tpss.MULT_RESIDUAL_FULL if full else tpss.MULT_RESIDUAL_UPDATE,
+                          mult_colors=8 if colors8 else 0)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -490,7 +493,8 @@ def run_mgcg(tpss, workloads, torch, cases):
                 x64.copy_(x)
             elif status == "converged" and x64.abs().max().item() > 0:
                 rec["rel_diff_to_fp64_solution"] = ((x - x64).norm() / x64.norm()).item()
-            out[f"k{k}_{sm}_omega{omega:g}_{prec}" + ("_full_residual_per_color" if full else "")] = rec
+            out[f"k{k}_{sm}_omega{omega:g}_{prec}" + ("_full_residual_per_color" if full else "")
+                + ("_8colors_face_conflicting" if colors8 else "")] = rec
         prob.close()
     return out
 
@@ -788,7 +792,7 @@ def run_batch_one(tpss, workloads, torch, steps, prec):
 MGCG_CASES = [
     (4, "AVS", 0.7, ["fp64"]),
     (4, "AVS", 0.125, ["fp64", "fp32", "tf32", "bf16"]),
-    (4, "MVS", 1.0, ["fp64", "fp64+full", "fp32", "tf32", "bf16"]),
+    (4, "MVS", 1.0, ["fp64", "fp64+full", "fp64+8colors", "fp32", "tf32", "bf16"]),
     (3, "MVS", 1.0, ["fp64", "tf32"]),
     (5, "MVS", 1.0, ["fp64", "tf32"]),
     (7, "MVS", 1.0, ["fp64", "fp64+full", "tf32"]),
