@@ -493,6 +493,16 @@ def run_mgcg(tpss, workloads, torch, cases):
                 x64.copy_(x)
             elif status == "converged" and x64.abs().max().item() > 0:
                 rec["rel_diff_to_fp64_solution"] = ((x - x64).norm() / x64.norm()).item()
+            if prec != "fp64" and not full and not colors8:
+                # the same V-cycle inside mixed-precision iterative refinement
+                torch.cuda.synchronize()
+                e0.record()
+                ir = prob.ir_solve(b, x, rtol=1e-8, inner_rtol=1e-3)
+                e1.record()
+                torch.cuda.synchronize()
+                rec["iterative_refinement"] = {"time_s": e0.elapsed_time(e1) / 1e3, "outer": ir["outer"],
+                                               "inner_iterations": ir["inner"], "rel_res": ir["rel_res"],
+                                               "converged": ir["converged"]}
             out[f"k{k}_{sm}_omega{omega:g}_{prec}" + ("_full_residual_per_color" if full else "")
                 + ("_8colors_face_conflicting" if colors8 else "")] = rec
         prob.close()

@@ -298,6 +298,18 @@ tpss_status tpss_coarse_chebyshev_info(const tpss_ctx* ctx, double* a, double* b
 tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
                            int* iters, double* rel_res, double* res_hist);
 
+/* Mixed-precision iterative refinement (not in the paper): from x = 0, repeat
+ *   r = b - A x (FP64);  solve A e = r / ||r|| approximately by PCG in FP32
+ *   (the FP32 operator, the FP32 / TF32 / BF16 V-cycle of tpss_mg_setup,
+ *   flexible beta) to a relative residual inner_rtol or max_inner steps;
+ *   x += ||r|| e (FP64),
+ * until ||b - A x|| <= rtol ||b|| or max_outer refinement steps.  Needs a
+ * mixed-precision V-cycle.  *outer_iters, *inner_iters (total) and *rel_res
+ * are host values; allocates 5 finest-level FP32 vectors on its first call.
+ * TPSS_ENOTCONV at max_outer. */
+tpss_status tpss_ir_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int max_outer, double inner_rtol,
+                          int max_inner, int* outer_iters, int* inner_iters, double* rel_res);
+
 /* --------------------------------------------------------------- batches --
  * Many independent 3D problems of uneven size and degree (not in the paper):
  * every problem gets its own hierarchy (descs[p], additive vertex-patch

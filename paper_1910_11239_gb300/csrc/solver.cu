@@ -32,6 +32,7 @@ void destroy_mg(tpss_ctx* ctx) {
   if (mg->coarse_fd) tpss_patches_destroy(mg->coarse_fd);
   if (mg->coarse_acs) tpss_patches_destroy(mg->coarse_acs);
   dfree(mg->cheb_vec);
+  dfree(mg->ir_vec);
   dfree(mg->coarse_inv);
   dfree(mg->gj_tmp);
   for (auto* v : mg->b64) dfree(v);
@@ -67,11 +68,12 @@ __device__ double block_sum(double v) {
   return v;
 }
 
-__global__ void dot_partial_kernel(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+template <typename T>
+__global__ void dot_partial_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
                                    double* __restrict__ partials) {
-  double s = 0.0;
+  double s = 0.0;   // FP64 accumulation for FP32 vectors too
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s = fma(x[i], y[i], s);
+    s = fma((double)x[i], (double)y[i], s);
   s = block_sum(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -83,30 +85,45 @@ __global__ void dot_final_kernel(const double* __restrict__ partials, int nb, do
   if (threadIdx.x == 0) *out = s;
 }
 
-static tpss_status dot(tpss_ctx* ctx, const double* x, const double* y, int64_t n, double* out) {
+template <typename T>
+static tpss_status dot(tpss_ctx* ctx, const T* x, const T* y, int64_t n, double* out) {
   int nb = (int)std::min<int64_t>((n + kRedThreads * 4 - 1) / (kRedThreads * 4), kRedBlocksMax);
   if (nb < 1) nb = 1;
-  dot_partial_kernel<<<nb, kRedThreads, 0, ctx->stream>>>(x, y, n, ctx->d_partials);
+  dot_partial_kernel<T><<<nb, kRedThreads, 0, ctx->stream>>>(x, y, n, ctx->d_partials);
   dot_final_kernel<<<1, kRedThreads, 0, ctx->stream>>>(ctx->d_partials, nb, out);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
 
 // scalars: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 r.zold, 5 rr0
-__global__ void cg_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                             const double* __restrict__ q, int64_t n, const double* __restrict__ s) {
-  const double alpha = s[0] / s[1];
+template <typename T>
+__global__ void cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                             const T* __restrict__ q, int64_t n, const double* __restrict__ s) {
+  const T alpha = (T)(s[0] / s[1]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     r[i] = fma(-alpha, q[i], r[i]);
   }
 }
 
-__global__ void cg_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+template <typename T>
+__global__ void cg_p_kernel(T* __restrict__ p, const T* __restrict__ z, int64_t n,
                             const double* __restrict__ s, int flexible) {
-  const double beta = (s[3] - (flexible ? s[4] : 0.0)) / s[0];
+  const T beta = (T)((s[3] - (flexible ? s[4] : 0.0)) / s[0]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(beta, p[i], z[i]);
+}
+
+// dst = s * src (types may differ)
+template <typename S, typename D>
+__global__ void scaled_convert_kernel(const S* __restrict__ src, D* __restrict__ dst, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = static_cast<D>(s * (double)src[i]);
+}
+// x += s * e (e in FP32)
+__global__ void add_scaled_f32_kernel(double* __restrict__ x, const float* __restrict__ e, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(s, (double)e[i], x[i]);
 }
 
 __global__ void cg_shift_kernel(double* s) { s[0] = s[3]; }
@@ -814,7 +831,7 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
   for (int it = 1; it <= maxit; ++it) {
     TPSS_TRY(apply_operator_t<double>(ctx, L, 1, mg->p, mg->q, nullptr));
     TPSS_TRY(dot(ctx, mg->p, mg->q, n, sc + 1));
-    cg_xr_kernel<<<g, 256, 0, s>>>(x, mg->r, mg->p, mg->q, n, sc);
+    cg_xr_kernel<double><<<g, 256, 0, s>>>(x, mg->r, mg->p, mg->q, n, sc);
     TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 2));
     TPSS_CHECK_CUDA(cudaMemcpyAsync(h, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -831,7 +848,7 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
     TPSS_TRY(precondition(ctx, mg, mg->r, mg->z));
     TPSS_TRY(dot(ctx, mg->r, mg->z, n, sc + 3));
     if (flex) TPSS_TRY(dot(ctx, mg->r, mg->zold, n, sc + 4));
-    cg_p_kernel<<<g, 256, 0, s>>>(mg->p, mg->z, n, sc, flex ? 1 : 0);
+    cg_p_kernel<double><<<g, 256, 0, s>>>(mg->p, mg->z, n, sc, flex ? 1 : 0);
     cg_shift_kernel<<<1, 1, 0, s>>>(sc);
     TPSS_CHECK_LAUNCH();
   }
@@ -839,6 +856,104 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
   return TPSS_ENOTCONV;
 }
 
+
+// Mixed-precision iterative refinement: FP64 residual outside, an FP32 PCG
+// with the FP32 V-cycle and the FP32 operator inside on the normalized
+// residual, FP64 correction.  Flexible beta in the inner CG (the FP32
+// V-cycle is not exactly symmetric).
+extern "C" tpss_status tpss_ir_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int max_outer,
+                                     double inner_rtol, int max_inner, int* outer_iters, int* inner_iters,
+                                     double* rel_res) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && x && outer_iters && inner_iters && rel_res, "tpss_ir_solve: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_ir_solve: call tpss_mg_setup first");
+  TPSS_REQUIRE(ctx->mg->mixed, "tpss_ir_solve: needs a mixed-precision (FP32 / TF32 / BF16) V-cycle");
+  TPSS_REQUIRE(rtol > 0.0 && inner_rtol > 0.0 && inner_rtol < 1.0 && max_outer >= 1 && max_inner >= 1,
+               "tpss_ir_solve: rtol > 0, 0 < inner_rtol < 1, max_outer >= 1 and max_inner >= 1 required");
+  MGState* mg = ctx->mg;
+  const int L = ctx->nlevels - 1;
+  const int64_t n = ctx->levels[L].ndofs;
+  cudaStream_t s = ctx->stream;
+  if (mg->ir_vec == nullptr) TPSS_TRY(dalloc_t(&mg->ir_vec, (size_t)5 * n));
+  float* r32 = mg->ir_vec;
+  float* z32 = r32 + n;
+  float* p32 = z32 + n;
+  float* q32 = p32 + n;
+  float* e32 = q32 + n;
+  double* sc = ctx->d_scalars;
+  const int g = grid_for(ctx, n);
+  double h[8];
+  auto fetch = [&]() -> tpss_status {
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(h, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    return TPSS_OK;
+  };
+  *outer_iters = 0;
+  *inner_iters = 0;
+  *rel_res = 1.0;
+  TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 5));
+  TPSS_TRY(fetch());
+  const double rr0 = h[5];
+  if (!std::isfinite(rr0)) {
+    set_error("tpss_ir_solve: right-hand side is not finite");
+    return TPSS_EBREAKDOWN;
+  }
+  if (rr0 == 0.0) {
+    *rel_res = 0.0;
+    return TPSS_OK;
+  }
+  double rnorm = std::sqrt(rr0);
+  for (int outer = 1; outer <= max_outer; ++outer) {
+    // inner: A e = r / ||r|| in FP32 from e = 0
+    scaled_convert_kernel<double, float><<<g, 256, 0, s>>>(mg->r, r32, 1.0 / rnorm, n);
+    TPSS_CHECK_CUDA(cudaMemsetAsync(e32, 0, n * sizeof(float), s));
+    TPSS_CHECK_LAUNCH();
+    TPSS_TRY(dot(ctx, r32, r32, n, sc + 5));
+    TPSS_TRY(vcycle_t<float>(ctx, mg, L, r32, z32));
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(p32, z32, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    TPSS_TRY(dot(ctx, r32, z32, n, sc + 0));
+    TPSS_TRY(fetch());
+    const double irr0 = h[5];
+    for (int it = 1; it <= max_inner; ++it) {
+      TPSS_TRY(apply_operator_t<float>(ctx, L, 1, p32, q32, nullptr));
+      TPSS_TRY(dot(ctx, p32, q32, n, sc + 1));
+      cg_xr_kernel<float><<<g, 256, 0, s>>>(e32, r32, p32, q32, n, sc);
+      TPSS_TRY(dot(ctx, r32, r32, n, sc + 2));
+      TPSS_TRY(fetch());
+      ++*inner_iters;
+      if (!std::isfinite(h[1]) || !(h[1] > 0.0) || !std::isfinite(h[2])) {
+        set_error("tpss_ir_solve: inner breakdown (p^T A p <= 0 or non-finite residual)");
+        return TPSS_EBREAKDOWN;
+      }
+      if (std::sqrt(std::max(h[2], 0.0) / irr0) <= inner_rtol) break;
+      std::swap(z32, q32);   // q32 is free until the next operator application: keeps z_old
+      TPSS_TRY(vcycle_t<float>(ctx, mg, L, r32, z32));
+      TPSS_TRY(dot(ctx, r32, z32, n, sc + 3));
+      TPSS_TRY(dot(ctx, r32, q32, n, sc + 4));
+      cg_p_kernel<float><<<g, 256, 0, s>>>(p32, z32, n, sc, 1);
+      cg_shift_kernel<<<1, 1, 0, s>>>(sc);
+      TPSS_CHECK_LAUNCH();
+    }
+    // x += ||r|| e; r = b - A x in FP64
+    add_scaled_f32_kernel<<<g, 256, 0, s>>>(x, e32, rnorm, n);
+    TPSS_CHECK_LAUNCH();
+    TPSS_TRY(apply_operator_t<double>(ctx, L, 1, x, mg->r, b));
+    TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 6));
+    TPSS_TRY(fetch());
+    rnorm = std::sqrt(std::max(h[6], 0.0));
+    *outer_iters = outer;
+    *rel_res = rnorm / std::sqrt(rr0);
+    if (!std::isfinite(rnorm)) {
+      set_error("tpss_ir_solve: non-finite residual");
+      return TPSS_EBREAKDOWN;
+    }
+    if (*rel_res <= rtol) return TPSS_OK;
+  }
+  set_error("tpss_ir_solve: not converged within max_outer");
+  return TPSS_ENOTCONV;
+}
 
 extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
                                         int restart, int left, int* iters, double* rel_res, double* res_hist) {

@@ -126,6 +126,7 @@ struct MGState {
   double cheb_a = 0.0, cheb_b = 0.0;     // spectral interval of P A_0 used by the iteration
   int cheb_m = 0;                        // Chebyshev steps per coarse solve
   double* cheb_vec = nullptr;            // 4 level-0 vectors
+  float* ir_vec = nullptr;               // iterative refinement: 5 finest-level FP32 vectors
 };
 
 }  // namespace tpss

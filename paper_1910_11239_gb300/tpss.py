@@ -76,6 +76,8 @@ SIGNATURES = {
     "tpss_mg_setup": [_VP, ctypes.POINTER(MGParams)],
     "tpss_vcycle": [_VP, _VP, _VP],
     "tpss_coarse_solve": [_VP, _VP, _VP],
+    "tpss_ir_solve": [_VP, _VP, _VP, _D, _I, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                      ctypes.POINTER(ctypes.c_double)],
     "tpss_coarse_chebyshev_info": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int)],
     "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
@@ -234,6 +236,15 @@ class Problem:
         _check(lib().tpss_coarse_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
         return x
 
+
+    def ir_solve(self, b, x, rtol=1e-8, max_outer=20, inner_rtol=1e-3, max_inner=100):
+        """Mixed-precision iterative refinement (FP64 residual, FP32 inner PCG)."""
+        n = self.ndofs(self.nlevels - 1)
+        o, i, rel = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        st = lib().tpss_ir_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n), rtol, max_outer,
+                                 inner_rtol, max_inner, ctypes.byref(o), ctypes.byref(i), ctypes.byref(rel))
+        _check(st, allow=(TPSS_OK, TPSS_ENOTCONV))
+        return {"outer": o.value, "inner": i.value, "rel_res": rel.value, "converged": st == TPSS_OK}
 
     def coarse_chebyshev_info(self):
         a, b, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()

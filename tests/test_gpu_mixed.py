@@ -130,3 +130,37 @@ def test_additive_schedules_agree(k, n, prec):
         d = (o - outs[0]).abs().max().item() / outs[0].abs().max().item()
         assert d < tol, d
     prob.close()
+
+
+@pytest.mark.parametrize("smoother,omega,prec", [("MVS", 1.0, "bf16"), ("AVS", 0.125, "fp32"), ("ACS", 0.7, "tf32")])
+def test_iterative_refinement_reaches_fp64_tolerance(smoother, omega, prec):
+    """FP64 outer residual, FP32 inner PCG with the low-precision V-cycle:
+    converges to the FP64 1e-8 residual reduction and to the FP64 PCG's
+    solution (both within 1e-8 of the discrete solution)."""
+    from paper_1910_11239_gb300 import tpss
+    prob = tpss.Problem(3, 3, workloads.widths_uniform(2, 3), nlevels=4)
+    N = prob.ndofs(3)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(3, 0, b)
+    prob.mg_setup(smoother, omega, tpss.FP64)
+    x64 = torch.empty_like(b)
+    assert prob.pcg_solve(b, x64, rtol=1e-10, maxit=200)["converged"]
+    prob.mg_setup(smoother, omega, tpss.PRECISIONS[prec])
+    x = torch.empty_like(b)
+    res = prob.ir_solve(b, x, rtol=1e-8, inner_rtol=1e-3)
+    assert res["converged"] and res["rel_res"] <= 1e-8 and res["outer"] >= 2
+    r = torch.empty_like(b)
+    prob.residual(3, b, x, r)
+    assert (r.norm() / b.norm()).item() <= 1.0001e-8
+    assert ((x - x64).norm() / x64.norm()).item() < 1e-6
+    prob.close()
+
+
+def test_iterative_refinement_needs_mixed_vcycle():
+    from paper_1910_11239_gb300 import tpss
+    prob = tpss.Problem(3, 2, workloads.widths_uniform(2, 3), nlevels=2)
+    prob.mg_setup("ACS", 0.7, tpss.FP64)
+    b = torch.ones(prob.ndofs(1), dtype=torch.float64, device="cuda")
+    with pytest.raises(tpss.TpssError, match="mixed"):
+        prob.ir_solve(b, torch.empty_like(b))
+    prob.close()
