@@ -40,3 +40,14 @@ def oracle_solvers(S, A, kind):
         return A[idx][:, idx]
 
     return patches, schwarz.LocalSolvers(patches, S.nloc, local)
+
+
+def paper_value(key):
+    """A value printed in the paper, from tests/golden/paper_tables.txt."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.txt")
+    for line in open(path):
+        parts = line.split()
+        if parts and not line.startswith("#") and parts[0] == key:
+            return float(parts[1])
+    raise KeyError(key)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import dev, make, oracle_sipg, rel_err
+from gpu_helpers import dev, make, oracle_sipg, paper_value, rel_err
 from oracle import schwarz
 from oracle.chebyshev import chebyshev, iteration_count, spectral_bounds
 from paper_1910_11239_gb300 import perf, tpss, workloads
@@ -41,7 +41,8 @@ def test_chebyshev_coarse_solve_matches_oracle(dim, k):
     prob.close()
 
 
-@pytest.mark.parametrize("smoother,k,paper,left", [("ACS", 3, 17.1, False), ("MCS", 3, 8.6, True)])
+@pytest.mark.parametrize("smoother,k,paper,left", [("ACS", 3, paper_value("acs3d_k3_L3"), False),
+                                                   ("MCS", 3, paper_value("mcs3d_k3_L3"), True)])
 def test_paper_counts_with_chebyshev_coarse_solver(smoother, k, paper, left):
     """tab:cubecp, 3D, L = 3 with the paper's coarse solver: the fractional
     counts equal those with the exact coarse solve (a 1e-8 coarse accuracy is
