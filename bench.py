@@ -40,8 +40,9 @@ CONFIG = {"workload": "3D additive vertex-patch Schwarz smoother (fast diagonali
           "l2": "inputs larger than L2 (each step streams >= 2.5 GB of vectors and tables)"}
 # DRAM bytes (read + write) of one FP64 smoother call at k=7 (8 color
 # launches, 8 RHS) at the full 32^3 size, from the single-pass ncu capture
-# summarized in profiles/patch_smooth_fp64_32cubed.md; set to None when the
-# kernel changes after that capture.
+# summarized in profiles/patch_smooth_fp64_32cubed.md (captured again after
+# the kernel's last change, same value); set to None when the kernel changes
+# after that capture.
 TRAFFIC_K7_PER_CALL = 30.98e9
 
 
