@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-high-degree", action="store_true")
     p.add_argument("--no-kernels", action="store_true")
+    p.add_argument("--no-distorted", action="store_true")
     p.add_argument("--batch-problems", type=int, default=48, help="use the first N problems of the batch (profiling)")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
@@ -388,6 +389,9 @@ def main():
     high = None
     if not args.no_high_degree:
         high = run_high_degree(tpss, workloads, perf, torch, max(2, min(args.steps, 5)))
+    distorted = None
+    if not args.no_distorted:
+        distorted = run_distorted(tpss, workloads, perf, torch, max(3, min(args.steps, 10)))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -418,6 +422,8 @@ def main():
             line["kernels"] = kernels
         if high is not None:
             line["high_degree_k15"] = high
+        if distorted is not None:
+            line["distorted_2d"] = distorted
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -715,6 +721,73 @@ def run_high_degree(tpss, workloads, perf, torch, steps):
                            "paper_nu_frac": PAPER_NU_K15_L1[sm], "time_s": e0.elapsed_time(e1) / 1e3}
     prob.close()
     out["paper_iterations_k15"] = its
+    return out
+
+
+# tab:cubedist25acp / tab:cubedist25mcp, 2D, L = 3 (32 x 32 coarse cells, 25% distortion)
+PAPER_NU_DIST2D_L3 = {("ACS", 1, 3): 38.7, ("ACS", 2, 3): 24.3, ("MCS", 1, 3): 24.7, ("MCS", 2, 3): 15.3,
+                      ("ACS", 1, 7): 47.7, ("MCS", 1, 7): 43.5}
+DIST_SEED = 1
+
+
+def run_distorted(tpss, workloads, perf, torch, steps):
+    """Sec. 4: the 32 x 32 mesh of the unit square with 25% vertex distortion
+    (seed DIST_SEED), gamma_hat = 4, refined to about 16.7 M DoFs (k = 3: L = 5,
+    1024^2 cells; k = 7: L = 4, 512^2 cells): the matrix-free operator, one
+    ACS and one MCS sweep with Cartesian-surrogate cell solvers, the V-cycle and
+    a PCG solve to 1e-8 (f = 2 pi^2 sin(pi x) sin(pi y), Chebyshev coarse
+    solve), timed with CUDA events; and the energy-norm fractional counts of
+    the paper's L = 3 columns."""
+    V0 = workloads.vertices_distorted(32, DIST_SEED)
+    out = {"workload": f"2D, 32^2 coarse cells of [0,1]^2, 25% distortion (seed {DIST_SEED}), gamma_hat 4, FP64"}
+    fp64 = perf.fp64_peak_flops()
+    for k, L, om_a, om_m in ((3, 5, 0.5, 0.75), (7, 4, 0.5, 0.5)):
+        prob = tpss.Problem.mapped(k, V0, nlevels=L + 1, gamma_hat=4.0)
+        N, nc = prob.level_info(L)
+        u = torch.from_numpy(workloads.rhs_uniform(N, seed=3)).to("cuda")
+        au = torch.empty_like(u)
+        ms = _time_calls(torch, lambda: prob.apply_operator(L, u, au), steps)
+        fl = perf.mapped_operator_flops(nc[:2], k)
+        rec = {"L": L, "cells": nc[0] * nc[1], "dofs": N,
+               "operator": {"kernel": f"mapped_op_kernel<{k + 1}>", "ms": ms, "dofs_per_s": N / (ms / 1e3),
+                            "tflops": fl / ms / 1e9, "frac_fp64_peak": fl / (ms / 1e3) / fp64,
+                            "algorithmic_gbs": perf.mapped_operator_bytes(nc[:2], k) / ms / 1e6}}
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(L, 0, b)
+        x = torch.zeros_like(b)
+        P = prob.setup_patches(L, tpss.CELL)
+        ms = _time_calls(torch, lambda: P.smooth_additive(om_a, b, x, x_is_zero=True), steps)
+        rec["acs_sweep"] = {"ms": ms, "dofs_per_s": N / (ms / 1e3), "note": "residual (operator) + local solves"}
+        ms = _time_calls(torch, lambda: P.smooth_multiplicative(om_m, b, x), max(2, steps // 2))
+        rec["mcs_sweep"] = {"ms": ms, "dofs_per_s": N / (ms / 1e3), "note": "2 colors, full residual per color"}
+        P.close()
+        for sm, om in (("ACS", om_a), ("MCS", om_m)):
+            prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV)
+            z = torch.empty_like(b)
+            ms = _time_calls(torch, lambda: prob.vcycle(b, z), max(2, steps // 2))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = prob.pcg_solve(b, x, rtol=1e-8, maxit=200, history=True)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            rec[f"{sm}1_pcg"] = {"omega": om, "vcycle_ms": ms, "iterations": res["iters"],
+                                 "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
+                                 "solve_s": t, "dofs_per_s": N / t}
+        prob.close()
+        out[f"k{k}"] = rec
+    its = {}
+    for (sm, m, k), paper in PAPER_NU_DIST2D_L3.items():
+        om = 0.5 if sm == "ACS" or k == 7 else 0.75
+        prob = tpss.Problem.mapped(k, V0, nlevels=4, gamma_hat=4.0)
+        prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV, smoothing_steps=m)
+        b = torch.empty(prob.ndofs(3), dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(3, 0, b)
+        errs = perf.cg_energy_errors(prob, b, rtol=1e-8, maxit=150)
+        prob.close()
+        its[f"{sm}{m}_k{k}_L3"] = {"omega": om, "nu_frac_energy": perf.fractional_iterations(errs, 1e-8),
+                                   "paper_nu_frac": paper}
+    out["paper_iterations_L3"] = its
     return out
 
 

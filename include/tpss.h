@@ -78,6 +78,38 @@ typedef struct {
 typedef struct tpss_ctx tpss_ctx;
 typedef struct tpss_patches tpss_patches;
 
+/* ------------------------------------------- meshes of quadrilaterals --
+ * Sec. 4: a 2D mesh of bilinear quadrilaterals given by a structured
+ * (nx+1) x (ny+1) vertex array, `vertices` a HOST array of (x, y) pairs with
+ * the x index fastest: vertex (i, j) at vertices[2 (j (nx+1) + i)].  Cell
+ * (i, j), numbered i + nx j, has the corners (i, j), (i+1, j), (i, j+1),
+ * (i+1, j+1) at the reference corners (0,0), (1,0), (0,1), (1,1); every cell
+ * must be convex and counter-clockwise (TPSS_EINVAL otherwise).  Level l+1
+ * splits every cell of level l at its reference midpoints (edge midpoints
+ * and the mean of the four corners as new vertices), so the spaces are
+ * nested and the transfers are those of Cartesian meshes.
+ * Operator: eq. bfsipg on the mapped cells (gradients through J^{-T}, the
+ * edges' unit normals, the paper's 1/sqrt(2) averages), penalty of
+ * eq. penalty with h^+- = |K^+-| / |e|; the paper takes gamma_hat = 4 on its
+ * 25%-distorted meshes (Sec. 4).  FP64, degree 1..7.
+ * Cell patches (tpss_setup_patches with TPSS_CELL, FP64) use the inexact
+ * local solvers of eq. schwarzproj on the Cartesian surrogate of each cell
+ * (eq. avglength: mean lengths of opposite edges, the neighbours' surrogate
+ * widths across its faces), by fast diagonalization per cell.
+ * Not available on these contexts (TPSS_EINVAL): vertex patches, FP32 / TF32
+ * / BF16 operators and smoothers, tpss_ir_solve, kind 1 of
+ * tpss_assemble_rhs, the per-color residual update of MCS (the full
+ * residual is recomputed) and the fast-diagonalization coarse solver.
+ * Every other call of this header works as on Cartesian contexts;
+ * tpss_mg_setup's AUTO coarse solver takes the Chebyshev iteration above
+ * 4096 coarse DoFs.  Release with tpss_destroy. */
+tpss_status tpss_create_mapped(int degree, int nx, int ny, const double* vertices, int nlevels, double gamma_hat,
+                               int penalty_poly, void* cuda_stream, tpss_ctx** out);
+
+/* Copy level `level`'s vertex array ((nc0+1)(nc1+1) (x, y) pairs) to the HOST
+ * array `vertices`.  TPSS_EINVAL on a Cartesian context. */
+tpss_status tpss_mapped_vertices(const tpss_ctx* ctx, int level, double* vertices);
+
 /* Create a context: copies the description, runs the 1D setup kernels (Gauss-
  * Lobatto basis, Gauss rules, per-direction 1D mass/stiffness/face matrices of
  * eq. 1Dstiffnessmass - eq. 1Dsipg for every level) on `cuda_stream`
@@ -120,7 +152,8 @@ tpss_status tpss_patches_info(const tpss_patches* patches, int* n, int npos[3],
 
 /* Copy the FP64 1D data of direction t at position pos to HOST arrays (each
  * may be NULL): A and M (n*n, row-major, test index first), Z (n*n row-major,
- * column j = eigenvector j) and lambda (n).  Synchronizes the stream. */
+ * column j = eigenvector j) and lambda (n).  Synchronizes the stream.  On a
+ * mesh of quadrilaterals the data are per cell: pos = the cell index. */
 tpss_status tpss_patches_eigendata(const tpss_patches* patches, int t, int pos,
                                    double* A, double* M, double* Z, double* lambda);
 
@@ -226,7 +259,8 @@ tpss_status tpss_restrict(tpss_ctx* ctx, int fine_level, int nrhs, const double*
  * direction.  kind 0: f = d pi^2 prod_t sin(pi x_t), g = 0 (exact solution
  * prod_t sin(pi x_t) on the unit cube); kind 1: the three-Gaussian solution of
  * Sec. 2.4 read as u = sum_i exp(-|x - x_i|^2 / sigma^2) / (sqrt(2 pi) sigma),
- * sigma = 1/3, with f = -Laplace(u) and g = u. */
+ * sigma = 1/3, with f = -Laplace(u) and g = u.  On a mesh of quadrilaterals
+ * (kind 0 only) the integrals are taken over the mapped cells, in 2D. */
 tpss_status tpss_assemble_rhs(tpss_ctx* ctx, int level, int kind, double* b);
 
 /* ------------------------------------------------------------- multigrid --
@@ -244,6 +278,8 @@ typedef struct {
                           non-symmetric V-cycle used with GMRES); 0: reversed (symmetric) */
   int coarse_solver;   /* tpss_coarse_solver (0 = automatic) */
   int mult_residual;   /* tpss_mult_residual for MCS / MVS (0 = update per color) */
+  int smoothing_steps; /* m pre- and post-smoothing steps per level (ACS_m, MCS_m of Sec. 4);
+                          0 = 1, at most 16 */
 } tpss_mg_params;
 
 /* Exact coarse solvers on level 0.

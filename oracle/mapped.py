@@ -9,10 +9,9 @@ v2 = V[j+1, i], v3 = V[j+1, i+1] at the reference corners (0,0), (1,0),
 (0,1), (1,1) and the bilinear map x(xi) = v0 (1-xi0)(1-xi1) + v1 xi0 (1-xi1)
 + v2 (1-xi0) xi1 + v3 xi0 xi1.  Cells are numbered with i fastest, the DoFs
 of a cell are the GL nodal values ordered with the first reference index
-fastest (the layout of the Cartesian case).  `distorted_vertices` follows
-Sec. 4: a uniform n x n grid of the unit square whose interior vertices are
-moved by alpha h_v in a random direction, h_v the smallest length of the
-edges at v (alpha = 0.25 in the paper).  `refine` splits every cell at its
+fastest (the layout of the Cartesian case).  The distorted meshes of Sec. 4
+come from the shared input generators (workloads.vertices_distorted).
+`refine` splits every cell at its
 reference midpoints: the new vertices are the images of the edge midpoints
 and of the cell centre under the cell's bilinear map, so every child map is
 the parent map composed with the affine child map; the fine space contains
@@ -58,31 +57,6 @@ SQRT2 = np.sqrt(2.0)
 
 
 # ------------------------------------------------------------------ meshes
-def cartesian_vertices(wx, wy):
-    """Vertex array of the Cartesian mesh with column widths wx, row widths wy."""
-    xs = np.concatenate(([0.0], np.cumsum(wx)))
-    ys = np.concatenate(([0.0], np.cumsum(wy)))
-    V = np.zeros((len(ys), len(xs), 2))
-    V[:, :, 0] = xs[None, :]
-    V[:, :, 1] = ys[:, None]
-    return V
-
-
-def distorted_vertices(n, seed, alpha=0.25):
-    """Sec. 4: uniform n x n grid of [0,1]^2, interior vertices moved by
-    alpha h_v in a random direction (numpy default_rng(seed))."""
-    V = cartesian_vertices(np.full(n, 1.0 / n), np.full(n, 1.0 / n))
-    rng = np.random.default_rng(seed)
-    theta = rng.uniform(0.0, 2.0 * np.pi, (n + 1, n + 1))
-    out = V.copy()
-    for j in range(1, n):
-        for i in range(1, n):
-            nb = [V[j, i - 1], V[j, i + 1], V[j - 1, i], V[j + 1, i]]
-            hv = min(np.linalg.norm(V[j, i] - w) for w in nb)
-            out[j, i] = V[j, i] + alpha * hv * np.array([np.cos(theta[j, i]), np.sin(theta[j, i])])
-    return out
-
-
 def refine(V):
     """Split every cell at its reference midpoints (bilinear images)."""
     ny, nx = V.shape[0] - 1, V.shape[1] - 1

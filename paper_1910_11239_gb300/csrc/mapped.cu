@@ -1,0 +1,639 @@
+// SIPG on 2D meshes of bilinear quadrilaterals and the inexact cell solvers
+// on Cartesian surrogate cells of Sec. 4 (eq. schwarzproj, eq. avglength).
+//
+// Mesh: a structured (nx+1) x (ny+1) vertex array per level (x index
+// fastest); cell (i, j) has the corners v0 = V[j][i], v1 = V[j][i+1],
+// v2 = V[j+1][i], v3 = V[j+1][i+1] at the reference corners (0,0), (1,0),
+// (0,1), (1,1) and the bilinear map
+//   x(a, b) = v0 (1-a)(1-b) + v1 a (1-b) + v2 (1-a) b + v3 a b.
+// Finer levels split every cell at its reference midpoints, so the child
+// maps are the parent map on quarters of the reference square, the spaces
+// are nested and the transfers are the Cartesian ones (transfer.cu).
+//
+// Operator (eq. bfsipg on mapped cells, matrix-free): one CTA handles CPB
+// cells, (k+1)^2 threads per cell.  The geometry is recomputed on the fly
+// from the 4 x 4 vertex block around the cell, so the kernel reads only
+// the DoF vectors and 32 doubles of vertices per cell.
+//   cell term   sum_q w_q |det J| (J^{-1} J^{-T} g_u) . g_v with reference
+//               gradients g from sum factorization (Gauss points xq, k+1 per
+//               direction; Vq, Dq the basis values and derivatives there)
+//   face terms  per edge point: jump [u] = u^K - u^N, normal derivatives
+//               d_n u = (J^{-1} n) . g_ref u on both sides (each with its own
+//               Jacobian), and, with the paper's 1/sqrt(2) averages,
+//                 v^K:          W (gamma/2 [u] - (d_n u^K + d_n u^N)/2)
+//                 d_n v^K:      -W [u] / 2
+//               boundary edges: W (gamma u - d_n u) and -W u; W = w_q |e|.
+// The penalty is gamma_hat P(k) (1/h^+ + 1/h^-) (eq. penalty) with h^+- =
+// |K^+-| / |e|, the mean extent of the cell normal to the edge; h^+ = h^- on
+// boundary edges.
+//
+// Surrogate cell solvers (eq. avglength): cell K is replaced by the
+// rectangle with hbar_0 = (l_01 + l_23)/2, hbar_1 = (l_02 + l_13)/2 (vertex
+// distances); its local matrix is the Cartesian cell block of that
+// rectangle, M_1 x A_0 + A_1 x M_0, whose 1D matrices take the neighbours'
+// surrogate widths normal to the shared faces for the penalty.  The 1D
+// generalized eigenproblems are solved per cell and direction by the same
+// kernel as on Cartesian meshes; the smoother reads them per cell.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tpss_internal.cuh"
+
+namespace tpss {
+
+namespace {
+
+struct Quad {
+  double2 v0, v1, v2, v3;
+};
+
+// J = [dx/da dx/db; dy/da dy/db] at (a, b); returns det J, writes J^{-1}
+// (row-major: Ji[0] Ji[1] / Ji[2] Ji[3]).
+__device__ __forceinline__ double inverse_jacobian(const Quad& Q, double a, double b, double Ji[4]) {
+  const double j00 = (Q.v1.x - Q.v0.x) * (1.0 - b) + (Q.v3.x - Q.v2.x) * b;
+  const double j10 = (Q.v1.y - Q.v0.y) * (1.0 - b) + (Q.v3.y - Q.v2.y) * b;
+  const double j01 = (Q.v2.x - Q.v0.x) * (1.0 - a) + (Q.v3.x - Q.v1.x) * a;
+  const double j11 = (Q.v2.y - Q.v0.y) * (1.0 - a) + (Q.v3.y - Q.v1.y) * a;
+  const double det = j00 * j11 - j01 * j10;
+  const double inv = 1.0 / det;
+  Ji[0] = j11 * inv;
+  Ji[1] = -j01 * inv;
+  Ji[2] = -j10 * inv;
+  Ji[3] = j00 * inv;
+  return det;
+}
+
+__device__ __forceinline__ double quad_area(const Quad& Q) {
+  // shoelace over v0, v1, v3, v2 (counter-clockwise for a positively oriented map)
+  const double s = (Q.v0.x * Q.v1.y - Q.v1.x * Q.v0.y) + (Q.v1.x * Q.v3.y - Q.v3.x * Q.v1.y) +
+                   (Q.v3.x * Q.v2.y - Q.v2.x * Q.v3.y) + (Q.v2.x * Q.v0.y - Q.v0.x * Q.v2.y);
+  return 0.5 * fabs(s);
+}
+
+__device__ __forceinline__ double dist(double2 a, double2 b) {
+  const double dx = b.x - a.x, dy = b.y - a.y;
+  return sqrt(dx * dx + dy * dy);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- meshes
+// F = refinement of V (nx x ny cells): edge midpoints 0.5 (a + b), cell
+// centres 0.25 (((a + b) + c) + d) -- the images of the reference midpoints.
+__global__ void refine_vertices_kernel(const double2* __restrict__ V, int nx, int ny, double2* __restrict__ F) {
+  const int fx = 2 * nx + 1, fy = 2 * ny + 1, sx = nx + 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < fx * fy; e += gridDim.x * blockDim.x) {
+    const int i = e % fx, j = e / fx;
+    const int i0 = i / 2, j0 = j / 2;
+    const double2 a = V[j0 * sx + i0];
+    double2 p;
+    if (!(i & 1) && !(j & 1)) {
+      p = a;
+    } else if (!(j & 1)) {
+      const double2 b = V[j0 * sx + i0 + 1];
+      p = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+    } else if (!(i & 1)) {
+      const double2 c = V[(j0 + 1) * sx + i0];
+      p = make_double2(0.5 * (a.x + c.x), 0.5 * (a.y + c.y));
+    } else {
+      const double2 b = V[j0 * sx + i0 + 1], c = V[(j0 + 1) * sx + i0], d = V[(j0 + 1) * sx + i0 + 1];
+      p = make_double2(0.25 * (((a.x + b.x) + c.x) + d.x), 0.25 * (((a.y + b.y) + c.y) + d.y));
+    }
+    F[e] = p;
+  }
+}
+
+// -------------------------------------------------------------- operator
+template <int N1>
+struct MappedShape {
+  static constexpr int NL = N1 * N1;
+  static constexpr int CPB_RAW = 256 / NL;
+  static constexpr int CPB = CPB_RAW > 32 ? 32 : (CPB_RAW < 1 ? 1 : CPB_RAW);
+  static constexpr int THREADS = CPB * NL;
+  // per-cell slot (doubles): 16 vertices (double2, 16-byte aligned: the slot
+  // and the tables have even lengths), 5 areas, U (own + 4 neighbours), tA,
+  // tB, F0, F1, 9 face arrays [4][N1]
+  static constexpr int VB = 0, AREA = 32, U = 38, TA = U + 5 * NL, TB = TA + NL, F0 = TB + NL, F1 = F0 + NL;
+  static constexpr int FACE = F1 + NL;
+  static constexpr int SLOT = FACE + 9 * 4 * N1 + ((FACE + 9 * 4 * N1) & 1);
+  static constexpr int TABLES = 2 * NL + 4 * N1;   // even
+  static constexpr size_t SMEM = (size_t)(TABLES + CPB * SLOT) * sizeof(double);
+};
+
+struct MappedOpArgs {
+  const double* u;
+  double* out;
+  const double* rhs;   // not null: out = rhs - A u
+  const double2* V;
+  const Basis1D* B;
+  int nx, ny;
+  int64_t ncells, ndofs;
+  double gpk;          // gamma_hat P(k)
+};
+
+template <int N1>
+__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(MappedOpArgs a) {
+  using S = MappedShape<N1>;
+  constexpr int NL = N1 * N1, K = N1 - 1;
+  extern __shared__ __align__(16) double sm[];
+  double* Vq = sm;
+  double* Dq = Vq + NL;
+  double* dd = Dq + NL;        // d0 then d1: phi_i'(0), phi_i'(1)
+  double* xq = dd + 2 * N1;
+  double* wq = xq + N1;
+  for (int e = threadIdx.x; e < NL; e += S::THREADS) {
+    Vq[e] = a.B->Vq[e];
+    Dq[e] = a.B->Dq[e];
+  }
+  for (int e = threadIdx.x; e < N1; e += S::THREADS) {
+    dd[e] = a.B->d0[e];
+    dd[N1 + e] = a.B->d1[e];
+    xq[e] = a.B->xq[e];
+    wq[e] = a.B->wq[e];
+  }
+  const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
+  double* W = sm + S::TABLES + slot * S::SLOT;
+  double* U = W + S::U;
+  double* tA = W + S::TA;
+  double* tB = W + S::TB;
+  double* F0 = W + S::F0;
+  double* F1 = W + S::F1;
+  double* trK = W + S::FACE;
+  double* dlK = trK + 4 * N1;
+  double* trN = dlK + 4 * N1;
+  double* dlN = trN + 4 * N1;
+  double* al = dlN + 4 * N1;
+  double* be = al + 4 * N1;
+  double* de = be + 4 * N1;
+  double* As = de + 4 * N1;
+  double* Bs = As + 4 * N1;
+  double2* vb = reinterpret_cast<double2*>(W + S::VB);   // 4 x 4 vertex block around the cell
+  double* area = W + S::AREA;                            // own, then faces 0..3
+  const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
+  const bool active = cell < a.ncells;
+  const int cx = active ? (int)(cell % a.nx) : 0, cy = active ? (int)(cell / a.nx) : 0;
+  const int64_t vbase = (int64_t)blockIdx.y * a.ndofs;
+  // face f = 2 t + side: neighbour along t at -1 (side 0) / +1 (side 1)
+  const int hasm = (cx > 0 ? 1 : 0) | (cx + 1 < a.nx ? 2 : 0) | (cy > 0 ? 4 : 0) | (cy + 1 < a.ny ? 8 : 0);
+  auto has = [&](int f) { return ((hasm >> f) & 1) != 0; };
+  auto nbr = [&](int f) -> int64_t {
+    return cell + (f == 0 ? -1 : f == 1 ? 1 : f == 2 ? -a.nx : a.nx);
+  };
+  auto quad = [&](int dx, int dy) -> Quad {
+    Quad Q;
+    Q.v0 = vb[(1 + dy) * 4 + 1 + dx];
+    Q.v1 = vb[(1 + dy) * 4 + 2 + dx];
+    Q.v2 = vb[(2 + dy) * 4 + 1 + dx];
+    Q.v3 = vb[(2 + dy) * 4 + 2 + dx];
+    return Q;
+  };
+  auto face_quad = [&](int f) -> Quad {
+    return f == 0 ? quad(-1, 0) : f == 1 ? quad(1, 0) : f == 2 ? quad(0, -1) : quad(0, 1);
+  };
+  // local index of (i_t = it, the other index = j) for direction t
+  auto lidx = [](int t, int it, int j) { return t == 0 ? it + N1 * j : j + N1 * it; };
+
+  // ---- P0: DoF values of the cell and its neighbours, vertex block
+  if (active) {
+    U[tid] = a.u[vbase + cell * NL + tid];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (has(f)) U[(1 + f) * NL + tid] = a.u[vbase + nbr(f) * NL + tid];
+    for (int e = tid; e < 16; e += NL) {
+      const int vx = cx - 1 + (e & 3), vy = cy - 1 + (e >> 2);
+      if (vx >= 0 && vx <= a.nx && vy >= 0 && vy <= a.ny) vb[e] = a.V[(int64_t)vy * (a.nx + 1) + vx];
+    }
+  }
+  __syncthreads();
+
+  // ---- P1: cell stage A; edge traces and reference normal-derivative lines; areas
+  if (active) {
+    const int q0 = tid % N1, i1 = tid / N1;
+    double sa = 0.0, sb = 0.0;
+#pragma unroll
+    for (int i0 = 0; i0 < N1; ++i0) {
+      const double v = U[i0 + N1 * i1];
+      sa = fma(Dq[q0 * N1 + i0], v, sa);
+      sb = fma(Vq[q0 * N1 + i0], v, sb);
+    }
+    tA[tid] = sa;
+    tB[tid] = sb;
+    for (int e = tid; e < 4 * N1; e += NL) {
+      const int f = e / N1, j = e % N1, t = f >> 1, side = f & 1;
+      const double* ds = dd + side * N1;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) s = fma(ds[m], U[lidx(t, m, j)], s);
+      trK[e] = U[lidx(t, side * K, j)];
+      dlK[e] = s;
+      if (has(f)) {
+        const double* UN = U + (1 + f) * NL;
+        const double* dn = dd + (1 - side) * N1;
+        double sn = 0.0;
+#pragma unroll
+        for (int m = 0; m < N1; ++m) sn = fma(dn[m], UN[lidx(t, m, j)], sn);
+        trN[e] = UN[lidx(t, (1 - side) * K, j)];
+        dlN[e] = sn;
+      }
+    }
+    for (int e = tid; e < 5; e += NL) {
+      if (e == 0) area[0] = quad_area(quad(0, 0));
+      else if (has(e - 1)) area[e] = quad_area(face_quad(e - 1));
+    }
+  }
+  __syncthreads();
+
+  // ---- P2: reference gradients at the Gauss points times the metric; edge-point coefficients
+  if (active) {
+    const Quad Q = quad(0, 0);
+    const int q0 = tid % N1, q1 = tid / N1;
+    double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) {
+      g0 = fma(Vq[q1 * N1 + i1], tA[q0 + N1 * i1], g0);
+      g1 = fma(Dq[q1 * N1 + i1], tB[q0 + N1 * i1], g1);
+    }
+    double Ji[4];
+    const double det = inverse_jacobian(Q, xq[q0], xq[q1], Ji);
+    const double w = wq[q0] * wq[q1] * fabs(det);
+    // C = w J^{-1} J^{-T}
+    const double c00 = w * (Ji[0] * Ji[0] + Ji[1] * Ji[1]);
+    const double c01 = w * (Ji[0] * Ji[2] + Ji[1] * Ji[3]);
+    const double c11 = w * (Ji[2] * Ji[2] + Ji[3] * Ji[3]);
+    F0[tid] = c00 * g0 + c01 * g1;
+    F1[tid] = c01 * g0 + c11 * g1;
+    for (int e = tid; e < 4 * N1; e += NL) {
+      const int f = e / N1, q = e % N1, t = f >> 1, side = f & 1;
+      const double* fl = trK + f * N1;
+      const double* dl = dlK + f * N1;
+      double uK = 0.0, dtK = 0.0, dtanK = 0.0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        uK = fma(Vq[q * N1 + j], fl[j], uK);
+        dtK = fma(Vq[q * N1 + j], dl[j], dtK);
+        dtanK = fma(Dq[q * N1 + j], fl[j], dtanK);
+      }
+      // edge of face f: t = 0 from v0 (side 0) / v1 to v2 / v3; t = 1 from v0 / v2 to v1 / v3
+      const double2 pa = t == 0 ? (side ? Q.v1 : Q.v0) : (side ? Q.v2 : Q.v0);
+      const double2 pb = t == 0 ? (side ? Q.v3 : Q.v2) : (side ? Q.v3 : Q.v1);
+      const double tx = pb.x - pa.x, ty = pb.y - pa.y;
+      const double le = sqrt(tx * tx + ty * ty);
+      double nx = t == 0 ? ty / le : -ty / le, ny = t == 0 ? -tx / le : tx / le;
+      if (side == 0) {
+        nx = -nx;
+        ny = -ny;
+      }
+      const double s = xq[q];
+      double JK[4];
+      inverse_jacobian(Q, t == 0 ? (double)side : s, t == 0 ? s : (double)side, JK);
+      const double aK0 = JK[0] * nx + JK[1] * ny, aK1 = JK[2] * nx + JK[3] * ny;   // J^{-1} n
+      const double dnK = t == 0 ? aK0 * dtK + aK1 * dtanK : aK0 * dtanK + aK1 * dtK;
+      const double Wq = wq[q] * le;
+      const double hK = area[0] / le;
+      double alpha, c1;
+      if (has(f)) {
+        const double* gl = trN + f * N1;
+        const double* gd = dlN + f * N1;
+        double uN = 0.0, dtN = 0.0, dtanN = 0.0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+          uN = fma(Vq[q * N1 + j], gl[j], uN);
+          dtN = fma(Vq[q * N1 + j], gd[j], dtN);
+          dtanN = fma(Dq[q * N1 + j], gl[j], dtanN);
+        }
+        const Quad QN = face_quad(f);
+        double JN[4];
+        inverse_jacobian(QN, t == 0 ? (double)(1 - side) : s, t == 0 ? s : (double)(1 - side), JN);
+        const double aN0 = JN[0] * nx + JN[1] * ny, aN1 = JN[2] * nx + JN[3] * ny;
+        const double dnN = t == 0 ? aN0 * dtN + aN1 * dtanN : aN0 * dtanN + aN1 * dtN;
+        const double hN = area[1 + f] / le;
+        const double gam = a.gpk * (1.0 / hK + 1.0 / hN);
+        const double jump = uK - uN;
+        alpha = Wq * (0.5 * gam * jump - 0.5 * (dnK + dnN));
+        c1 = -0.5 * Wq * jump;
+      } else {
+        const double gam = a.gpk * (2.0 / hK);
+        alpha = Wq * (gam * uK - dnK);
+        c1 = -Wq * uK;
+      }
+      al[e] = alpha;
+      be[e] = c1 * (t == 0 ? aK0 : aK1);    // times d_t v
+      de[e] = c1 * (t == 0 ? aK1 : aK0);    // times d_tan v
+    }
+  }
+  __syncthreads();
+
+  // ---- P3: cell stage C (test gradients, first direction); edge sums per test line
+  if (active) {
+    const int i0 = tid % N1, q1 = tid / N1;
+    double sa = 0.0, sb = 0.0;
+#pragma unroll
+    for (int q0 = 0; q0 < N1; ++q0) {
+      sa = fma(Dq[q0 * N1 + i0], F0[q0 + N1 * q1], sa);
+      sb = fma(Vq[q0 * N1 + i0], F1[q0 + N1 * q1], sb);
+    }
+    tA[tid] = sa;
+    tB[tid] = sb;
+    for (int e = tid; e < 4 * N1; e += NL) {
+      const int f = e / N1, j = e % N1;
+      double sbv = 0.0, sav = 0.0;
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        sbv = fma(Vq[q * N1 + j], be[f * N1 + q], sbv);
+        sav = fma(Vq[q * N1 + j], al[f * N1 + q], sav);
+        sav = fma(Dq[q * N1 + j], de[f * N1 + q], sav);
+      }
+      Bs[e] = sbv;
+      As[e] = sav;
+    }
+  }
+  __syncthreads();
+
+  // ---- P4: cell stage D and the edge contributions; write
+  if (active) {
+    const int i0 = tid % N1, i1 = tid / N1;
+    double v = 0.0;
+#pragma unroll
+    for (int q1 = 0; q1 < N1; ++q1) {
+      v = fma(Vq[q1 * N1 + i1], tA[i0 + N1 * q1], v);
+      v = fma(Dq[q1 * N1 + i1], tB[i0 + N1 * q1], v);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int t = f >> 1, side = f & 1;
+      const int it = t == 0 ? i0 : i1, j = t == 0 ? i1 : i0;
+      v = fma(dd[side * N1 + it], Bs[f * N1 + j], v);
+      if (it == side * K) v += As[f * N1 + j];
+    }
+    const int64_t gi = vbase + cell * NL + tid;
+    a.out[gi] = a.rhs ? a.rhs[gi] - v : v;
+  }
+}
+
+template <int N1>
+static tpss_status launch_mapped(tpss_ctx* ctx, const MappedOpArgs& a, int nrhs) {
+  using S = MappedShape<N1>;
+  static bool attr = false;
+  if (!attr) {
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_op_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::SMEM));
+    attr = true;
+  }
+  const dim3 grid((unsigned)((a.ncells + S::CPB - 1) / S::CPB), (unsigned)nrhs);
+  mapped_op_kernel<N1><<<grid, S::THREADS, S::SMEM, ctx->stream>>>(a);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+static double penalty_prefactor(const tpss_ctx* ctx) {
+  return ctx->gamma_hat * (ctx->penalty_poly == TPSS_PENALTY_KP1SQ ? (double)(ctx->n1 * ctx->n1)
+                                                                   : (double)(ctx->k * ctx->n1));
+}
+
+tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs) {
+  const Level& L = ctx->levels[level];
+  MappedOpArgs a{};
+  a.u = u;
+  a.out = out;
+  a.rhs = rhs;
+  a.V = reinterpret_cast<const double2*>(L.d_verts);
+  a.B = ctx->d_basis;
+  a.nx = L.nc[0];
+  a.ny = L.nc[1];
+  a.ncells = L.ncells;
+  a.ndofs = L.ndofs;
+  a.gpk = penalty_prefactor(ctx);
+  switch (ctx->n1) {
+    case 2: return launch_mapped<2>(ctx, a, nrhs);
+    case 3: return launch_mapped<3>(ctx, a, nrhs);
+    case 4: return launch_mapped<4>(ctx, a, nrhs);
+    case 5: return launch_mapped<5>(ctx, a, nrhs);
+    case 6: return launch_mapped<6>(ctx, a, nrhs);
+    case 7: return launch_mapped<7>(ctx, a, nrhs);
+    case 8: return launch_mapped<8>(ctx, a, nrhs);
+    default: break;
+  }
+  set_error("operator: meshes of quadrilaterals support degrees 1..7");
+  return TPSS_EINVAL;
+}
+
+// ------------------------------------------------- surrogate cell solvers
+// hbar[t][c] of eq. avglength (vertex distances)
+__global__ void surrogate_widths_kernel(const double2* __restrict__ V, int nx, int ny, double* __restrict__ h0,
+                                        double* __restrict__ h1) {
+  const int64_t nc = (int64_t)nx * ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)(c / nx);
+    const double2 v0 = V[(int64_t)j * (nx + 1) + i], v1 = V[(int64_t)j * (nx + 1) + i + 1];
+    const double2 v2 = V[(int64_t)(j + 1) * (nx + 1) + i], v3 = V[(int64_t)(j + 1) * (nx + 1) + i + 1];
+    h0[c] = 0.5 * (dist(v0, v1) + dist(v2, v3));
+    h1[c] = 0.5 * (dist(v0, v2) + dist(v1, v3));
+  }
+}
+
+// 1D matrices of cell c's surrogate along t: width hbar_t(c), neighbours'
+// hbar_t across the faces normal to t
+__global__ void surrogate_op1d_kernel(const Basis1D* __restrict__ B, const double* __restrict__ w, int nx, int ny,
+                                      int t, double gpk, double* __restrict__ M, double* __restrict__ A) {
+  const int n1 = B->n1;
+  const int64_t c = blockIdx.x;
+  const int i = (int)(c % nx), j = (int)(c / nx);
+  const bool has_l = t == 0 ? i > 0 : j > 0;
+  const bool has_r = t == 0 ? i + 1 < nx : j + 1 < ny;
+  const int64_t step = t == 0 ? 1 : nx;
+  const double h = w[c];
+  const double hl = has_l ? w[c - step] : h, hr = has_r ? w[c + step] : h;
+  for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x)
+    op1d_entry(B, h, hl, hr, has_l, has_r, gpk, e / n1, e % n1, &M[c * n1 * n1 + e], &A[c * n1 * n1 + e]);
+}
+
+// inv[c][i + n j] = 1 / (lambda^(0)_i(c) + lambda^(1)_j(c))
+__global__ void inv_table_cells_kernel(const double* __restrict__ l0, const double* __restrict__ l1, int n,
+                                       int64_t ncells, double* __restrict__ inv) {
+  const int64_t total = ncells * n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / (n * n);
+    const int loc = (int)(e % (n * n));
+    inv[e] = 1.0 / (l0[c * n + loc % n] + l1[c * n + loc / n]);
+  }
+}
+
+tpss_status mapped_cell_eigendata(tpss_ctx* ctx, tpss_patches* P, int* d_err) {
+  const Level& L = ctx->levels[P->level];
+  const int n = ctx->n1, nx = L.nc[0], ny = L.nc[1];
+  const int64_t nc = L.ncells;
+  const double2* V = reinterpret_cast<const double2*>(L.d_verts);
+  double* hb = nullptr;
+  TPSS_TRY(dalloc_t(&hb, 2 * (size_t)nc));
+  tpss_status st = TPSS_OK;
+  const int gb = (int)std::min<int64_t>((nc + 255) / 256, 4096);
+  surrogate_widths_kernel<<<gb, 256, 0, ctx->stream>>>(V, nx, ny, hb, hb + nc);
+  for (int t = 0; t < 2 && st == TPSS_OK; ++t) {
+    if ((st = dalloc_t(&P->d_A[t], (size_t)nc * n * n)) != TPSS_OK) break;
+    if ((st = dalloc_t(&P->d_M[t], (size_t)nc * n * n)) != TPSS_OK) break;
+    if ((st = dalloc_t(&P->d_Z[t], (size_t)nc * n * n)) != TPSS_OK) break;
+    if ((st = dalloc_t(&P->d_lam[t], (size_t)nc * n)) != TPSS_OK) break;
+    surrogate_op1d_kernel<<<(unsigned)nc, 64, 0, ctx->stream>>>(ctx->d_basis, hb + t * nc, nx, ny, t,
+                                                                penalty_prefactor(ctx), P->d_M[t], P->d_A[t]);
+    const int warps = 4;
+    const size_t smem = (size_t)warps * 3 * n * n * sizeof(double);
+    gen_eig_kernel<<<(unsigned)((nc + warps - 1) / warps), warps * 32, smem, ctx->stream>>>(
+        P->d_A[t], P->d_M[t], (int)nc, n, P->d_Z[t], P->d_lam[t], d_err);
+  }
+  if (st == TPSS_OK) st = dalloc_t(&P->d_inv, (size_t)nc * n * n);
+  if (st == TPSS_OK)
+    inv_table_cells_kernel<<<2048, 256, 0, ctx->stream>>>(P->d_lam[0], P->d_lam[1], n, nc, P->d_inv);
+  cudaError_t e = cudaGetLastError();
+  cudaStreamSynchronize(ctx->stream);   // hb is freed below
+  dfree(hb);
+  if (st != TPSS_OK) return st;
+  if (e != cudaSuccess) {
+    set_error(std::string("surrogate cell solvers: ") + cudaGetErrorString(e));
+    return TPSS_ECUDA;
+  }
+  return TPSS_OK;
+}
+
+// ------------------------------------------------------- right-hand side
+// kind 0: f = 2 pi^2 sin(pi x) sin(pi y), g = 0 on the mesh's boundary
+// (exact solution sin(pi x) sin(pi y) when the mesh covers the unit square),
+// integrated with the (k+2)-point Gauss rule per direction on the mapped cell.
+__global__ void mapped_rhs_kernel(const Basis1D* __restrict__ B, const double2* __restrict__ V, int nx,
+                                  double* __restrict__ b) {
+  extern __shared__ double sm[];
+  const int n1 = B->n1, nq = B->nq_rhs;
+  const int64_t c = blockIdx.x;
+  const int i = (int)(c % nx), j = (int)(c / nx);
+  Quad Q;
+  Q.v0 = V[(int64_t)j * (nx + 1) + i];
+  Q.v1 = V[(int64_t)j * (nx + 1) + i + 1];
+  Q.v2 = V[(int64_t)(j + 1) * (nx + 1) + i];
+  Q.v3 = V[(int64_t)(j + 1) * (nx + 1) + i + 1];
+  double* F = sm;            // nq^2
+  double* G = F + nq * nq;   // n1 nq
+  const double pi = 3.14159265358979323846;
+  for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
+    const double xa = B->xr[e % nq], xb = B->xr[e / nq];
+    double Ji[4];
+    const double det = inverse_jacobian(Q, xa, xb, Ji);
+    const double px = Q.v0.x * (1 - xa) * (1 - xb) + Q.v1.x * xa * (1 - xb) + Q.v2.x * (1 - xa) * xb + Q.v3.x * xa * xb;
+    const double py = Q.v0.y * (1 - xa) * (1 - xb) + Q.v1.y * xa * (1 - xb) + Q.v2.y * (1 - xa) * xb + Q.v3.y * xa * xb;
+    F[e] = B->wr[e % nq] * B->wr[e / nq] * fabs(det) * 2.0 * pi * pi * sin(pi * px) * sin(pi * py);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n1 * nq; e += blockDim.x) {
+    const int i0 = e % n1, q1 = e / n1;
+    double s = 0.0;
+    for (int q0 = 0; q0 < nq; ++q0) s += B->Vr[q0 * n1 + i0] * F[q0 + nq * q1];
+    G[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) {
+    const int i0 = e % n1, i1 = e / n1;
+    double s = 0.0;
+    for (int q1 = 0; q1 < nq; ++q1) s += B->Vr[q1 * n1 + i1] * G[i0 + n1 * q1];
+    b[c * n1 * n1 + e] = s;
+  }
+}
+
+tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b) {
+  TPSS_REQUIRE(kind == 0, "tpss_assemble_rhs: meshes of quadrilaterals support kind 0 only");
+  const Level& L = ctx->levels[level];
+  const int nq = ctx->n1 + 1;
+  const size_t smem = (size_t)(nq * nq + ctx->n1 * nq) * sizeof(double);
+  mapped_rhs_kernel<<<(unsigned)L.ncells, 128, smem, ctx->stream>>>(
+      ctx->d_basis, reinterpret_cast<const double2*>(L.d_verts), L.nc[0], b);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+}  // namespace tpss
+
+using namespace tpss;
+
+extern "C" tpss_status tpss_create_mapped(int degree, int nx, int ny, const double* vertices, int nlevels,
+                                          double gamma_hat, int penalty_poly, void* cuda_stream, tpss_ctx** out) {
+  clear_error();
+  TPSS_REQUIRE(vertices && out, "tpss_create_mapped: null argument");
+  *out = nullptr;
+  TPSS_REQUIRE(degree >= 1 && degree <= kMaxMappedDegree, "tpss_create_mapped: degree must be in 1..7");
+  TPSS_REQUIRE(nx >= 1 && ny >= 1, "tpss_create_mapped: nx and ny must be >= 1");
+  TPSS_REQUIRE(nlevels >= 1 && nlevels <= 12, "tpss_create_mapped: nlevels must be in 1..12");
+  TPSS_REQUIRE(((long long)nx << (nlevels - 1)) <= 1024 && ((long long)ny << (nlevels - 1)) <= 1024,
+               "tpss_create_mapped: at most 1024 cells per direction on the finest level");
+  const int sx = nx + 1;
+  for (int i = 0; i < 2 * sx * (ny + 1); ++i)
+    TPSS_REQUIRE(std::isfinite(vertices[i]), "tpss_create_mapped: vertices must be finite");
+  // every cell positively oriented and convex: det J > 0 at its four corners
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      auto P = [&](int a, int b) { return &vertices[2 * ((j + b) * sx + i + a)]; };
+      const double* c[4] = {P(0, 0), P(1, 0), P(0, 1), P(1, 1)};
+      // corner (a, b): J columns along the two edges leaving it (into the cell)
+      const int ca[4] = {0, 1, 0, 1}, cb[4] = {0, 0, 1, 1};
+      for (int q = 0; q < 4; ++q) {
+        const double* o = c[q];
+        const double* ea = c[(1 - ca[q]) + 2 * cb[q]];
+        const double* eb = c[ca[q] + 2 * (1 - cb[q])];
+        const double sa = ca[q] ? -1.0 : 1.0, sb = cb[q] ? -1.0 : 1.0;
+        const double det = sa * sb * ((ea[0] - o[0]) * (eb[1] - o[1]) - (ea[1] - o[1]) * (eb[0] - o[0]));
+        TPSS_REQUIRE(det > 0.0, "tpss_create_mapped: cells must be convex and counter-clockwise "
+                                "(v0, v1, v3, v2)");
+      }
+    }
+  std::vector<double> wx(nx, 1.0 / nx), wy(ny, 1.0 / ny);
+  tpss_problem_desc desc{};
+  desc.dim = 2;
+  desc.degree = degree;
+  desc.ncells[0] = nx;
+  desc.ncells[1] = ny;
+  desc.ncells[2] = 1;
+  desc.widths[0] = wx.data();
+  desc.widths[1] = wy.data();
+  desc.nlevels = nlevels;
+  desc.gamma_hat = gamma_hat;
+  desc.penalty_poly = penalty_poly;
+  tpss_ctx* ctx = nullptr;
+  TPSS_TRY(tpss_create(&desc, cuda_stream, &ctx));
+  ctx->mapped = 1;
+  auto fail = [&](tpss_status s) {
+    tpss_destroy(ctx);
+    return s;
+  };
+  tpss_status st;
+  for (int l = 0; l < nlevels; ++l) {
+    Level& L = ctx->levels[l];
+    const size_t nv = (size_t)(L.nc[0] + 1) * (L.nc[1] + 1);
+    if ((st = dalloc_t(&L.d_verts, 2 * nv)) != TPSS_OK) return fail(st);
+    if (l == 0) {
+      if (cudaMemcpyAsync(L.d_verts, vertices, 2 * nv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+          cudaSuccess) {
+        set_error("tpss_create_mapped: vertex upload failed");
+        return fail(TPSS_ECUDA);
+      }
+    } else {
+      const Level& C = ctx->levels[l - 1];
+      refine_vertices_kernel<<<(unsigned)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+          reinterpret_cast<const double2*>(C.d_verts), C.nc[0], C.nc[1], reinterpret_cast<double2*>(L.d_verts));
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    set_error("tpss_create_mapped: vertex refinement failed");
+    return fail(TPSS_ECUDA);
+  }
+  *out = ctx;
+  return TPSS_OK;
+}
+
+extern "C" tpss_status tpss_mapped_vertices(const tpss_ctx* ctx, int level, double* vertices) {
+  clear_error();
+  TPSS_REQUIRE(ctx && vertices, "tpss_mapped_vertices: null argument");
+  TPSS_REQUIRE(ctx->mapped, "tpss_mapped_vertices: not a mesh of quadrilaterals");
+  TPSS_REQUIRE(level >= 0 && level < ctx->nlevels, "tpss_mapped_vertices: level out of range");
+  const Level& L = ctx->levels[level];
+  const size_t nv = (size_t)(L.nc[0] + 1) * (L.nc[1] + 1);
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(vertices, L.d_verts, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TPSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TPSS_OK;
+}

@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(kBasisThreads) setup_basis_kernel(Basis1D* B, 
     Vq[e] = lagrange_val(nd, n1, i, B->xq[q]);
     Dq[e] = lagrange_der(nd, n1, i, B->xq[q]);
     for (int s2 = 0; s2 < 2; ++s2) B->Pc[s2][e] = lagrange_val(nd, n1, i, 0.5 * (nd[q] + s2));   // e = q*n1+i: row q, col i
+    B->Vq[e] = Vq[e];
+    B->Dq[e] = Dq[e];
   }
   for (int e = tid; e < (n1 + 1) * n1; e += kBasisThreads)
     B->Vr[e] = lagrange_val(nd, n1, e % n1, B->xr[e / n1]);
@@ -174,26 +176,16 @@ __global__ void __launch_bounds__(kBasisThreads) setup_basis_kernel(Basis1D* B, 
 __global__ void level_op1d_kernel(const Basis1D* __restrict__ B, const double* __restrict__ w,
                                   int nc, double gpk, double* __restrict__ M, double* __restrict__ A,
                                   double* __restrict__ F) {
-  const int n1 = B->n1, k = B->k;
+  const int n1 = B->n1;
   const int c = blockIdx.x;
   if (c >= nc) return;
   const double h = w[c];
   const bool has_l = c > 0, has_r = c + 1 < nc;
   const double hl = has_l ? w[c - 1] : h, hr = has_r ? w[c + 1] : h;
   const double gl = gpk * (1.0 / h + 1.0 / hl), gr = gpk * (1.0 / h + 1.0 / hr);
-  const double el = has_l ? 0.5 : 1.0, er = has_r ? 0.5 : 1.0;
-  for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) {
-    const int i = e / n1, j = e % n1;
-    M[(size_t)c * n1 * n1 + e] = h * B->Mhat[e];
-    double a = B->Lhat[e] / h;
-    // left face p = 0: G[i][j] = -eta/h phi_j'(0) phi_i(0)
-    a += el * gl * (i == 0 && j == 0 ? 1.0 : 0.0);
-    a += el / h * ((i == 0 ? B->d0[j] : 0.0) + (j == 0 ? B->d0[i] : 0.0));
-    // right face p = 1: G[i][j] = +eta/h phi_j'(1) phi_i(1)
-    a += er * gr * (i == k && j == k ? 1.0 : 0.0);
-    a -= er / h * ((i == k ? B->d1[j] : 0.0) + (j == k ? B->d1[i] : 0.0));
-    A[(size_t)c * n1 * n1 + e] = a;
-  }
+  for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x)
+    op1d_entry(B, h, hl, hr, has_l, has_r, gpk, e / n1, e % n1, &M[(size_t)c * n1 * n1 + e],
+               &A[(size_t)c * n1 * n1 + e]);
   if (threadIdx.x == 0) {
     double* f = F + (size_t)c * kFaceCoef;
     f[0] = has_r ? -0.5 * gr : 0.0;
@@ -463,6 +455,7 @@ static tpss_status build_level(tpss_ctx* ctx, int l) {
 }
 
 static void free_level(Level& L) {
+  dfree(L.d_verts);
   for (int t = 0; t < 3; ++t) {
     dfree(L.d_widths[t]);
     dfree(L.op64.M[t]); dfree(L.op64.A[t]); dfree(L.op64.F[t]);
@@ -695,7 +688,15 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
   int* d_err = nullptr;
   if ((st = dalloc_t(&d_err, 1)) != TPSS_OK) return fail(st);
   cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream);
-  for (int t = 0; t < d; ++t) {
+  if (ctx->mapped) {   // surrogate cell solvers, eigendata per cell (mapped.cu)
+    P->per_sub = 1;
+    P->mult_update = 0;
+    if ((st = mapped_cell_eigendata(ctx, P, d_err)) != TPSS_OK) {
+      dfree(d_err);
+      return fail(st);
+    }
+  }
+  for (int t = 0; t < d && !ctx->mapped; ++t) {
     const int np = P->npos[t];
     if ((st = dalloc_t(&P->d_A[t], (size_t)np * n * n)) != TPSS_OK) return fail(st);
     if ((st = dalloc_t(&P->d_M[t], (size_t)np * n * n)) != TPSS_OK) return fail(st);
@@ -720,7 +721,9 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
     }
   }
   const bool large = d == 3 && n > kMaxSharedPatchN;
-  if (large) {   // per-CTA tensor slabs of the large-patch kernel (no inverse table)
+  if (ctx->mapped) {
+    // inverse table already built per cell
+  } else if (large) {   // per-CTA tensor slabs of the large-patch kernel (no inverse table)
     if ((st = patch_large_ctas(n, ctx->num_sms, &P->scratch_ctas)) != TPSS_OK) return fail(st);
     if ((st = dalloc_t(&P->d_scratch, (size_t)P->scratch_ctas * n * n * n)) != TPSS_OK) return fail(st);
   } else if (precision == TPSS_FP64) {
@@ -811,6 +814,8 @@ extern "C" tpss_status tpss_setup_patches(tpss_ctx* ctx, int level, int kind, in
   TPSS_REQUIRE(precision >= TPSS_FP64 && precision <= TPSS_BF16, "tpss_setup_patches: unknown precision");
   TPSS_REQUIRE(precision == TPSS_FP64 || ctx->k <= kMaxMixedDegree,
                "tpss_setup_patches: FP32/TF32/BF16 smoothers support degrees up to 7");
+  TPSS_REQUIRE(!ctx->mapped || (kind == TPSS_CELL && precision == TPSS_FP64),
+               "tpss_setup_patches: meshes of quadrilaterals support FP64 cell patches (surrogate solvers) only");
   if (kind == TPSS_VERTEX_PATCH)
     for (int t = 0; t < ctx->dim; ++t)
       TPSS_REQUIRE(ctx->levels[level].nc[t] >= 2, "tpss_setup_patches: vertex patches need >= 2 cells per direction");
@@ -842,7 +847,8 @@ extern "C" tpss_status tpss_patches_eigendata(const tpss_patches* P, int t, int 
   clear_error();
   TPSS_REQUIRE(P, "tpss_patches_eigendata: null patches");
   TPSS_REQUIRE(t >= 0 && t < P->ctx->dim, "tpss_patches_eigendata: direction out of range");
-  TPSS_REQUIRE(pos >= 0 && pos < P->npos[t], "tpss_patches_eigendata: position out of range");
+  TPSS_REQUIRE(pos >= 0 && pos < (P->per_sub ? P->nsub : P->npos[t]),
+               "tpss_patches_eigendata: position out of range");
   const int n = P->n;
   const size_t off = (size_t)pos * n * n;
   cudaStream_t s = P->ctx->stream;
@@ -895,6 +901,8 @@ extern "C" tpss_status tpss_patches_set_mult_residual(tpss_patches* P, int mode)
   TPSS_REQUIRE(P, "tpss_patches_set_mult_residual: null patches");
   TPSS_REQUIRE(mode == TPSS_MULT_RESIDUAL_UPDATE || mode == TPSS_MULT_RESIDUAL_FULL,
                "tpss_patches_set_mult_residual: mode must be 0 (update) or 1 (full)");
+  TPSS_REQUIRE(!P->per_sub || mode == TPSS_MULT_RESIDUAL_FULL,
+               "tpss_patches_set_mult_residual: surrogate cell solvers recompute the full residual");
   P->mult_update = mode == TPSS_MULT_RESIDUAL_UPDATE ? 1 : 0;
   return TPSS_OK;
 }

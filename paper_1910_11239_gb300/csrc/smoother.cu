@@ -55,6 +55,7 @@ struct SmoothArgs {
   int nc0, nc1;        // cells per direction (x, y)
   int np0, np1;        // subdomain positions per direction (x, y)
   int64_t ndofs;
+  int per_sub;         // 1: Z, lam per subdomain (index sub), else per position along t
 };
 
 template <int DIM, int N>
@@ -112,14 +113,16 @@ patch_smooth_kernel(SmoothArgs<T> a) {
     pos[0] = unpack_x(packed);
     pos[1] = unpack_y(packed);
     pos[2] = unpack_z(packed);
+    const int64_t psub = pos[0] + (int64_t)a.np0 * (pos[1] + (int64_t)a.np1 * pos[2]);
     for (int e = line; e < DIM * N * N; e += S::LINES) {
       const int t = e / (N * N), i = e % (N * N);
-      const T z = a.Z[t][(size_t)pos[t] * N * N + i];
+      const T z = a.Z[t][(size_t)(a.per_sub ? psub : pos[t]) * N * N + i];
       Zs[t * N * N + i] = z;
       ZTs[t * N * N + (i % N) * N + i / N] = z;
     }
     if (sizeof(T) == 4)
-      for (int e = line; e < DIM * N; e += S::LINES) lams[e] = a.lam[e / N][(size_t)pos[e / N] * N + e % N];
+      for (int e = line; e < DIM * N; e += S::LINES)
+        lams[e] = a.lam[e / N][(size_t)(a.per_sub ? psub : pos[e / N]) * N + e % N];
     // gather R_j r
     for (int e = line; e < NCELL * NLOC1; e += S::LINES) {
       const int c = e / NLOC1, loc = e % NLOC1;
@@ -262,6 +265,7 @@ tpss_status patch_pass(tpss_patches* P, const int* list, int count, T omega, int
   a.np0 = P->npos[0];
   a.np1 = P->npos[1];
   a.ndofs = L.ndofs;
+  a.per_sub = P->per_sub;
   const bool v = P->kind == TPSS_VERTEX_PATCH;
   const int n = P->n;
 #define TPSS_SM_CASE(D, NN, V)                                                     \

@@ -367,9 +367,9 @@ static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
   const int64_t n = L0.ndofs;
   mg->n0 = n;
   int kind = TPSS_CELL;
-  const bool fd_ok = !mg->mixed && coarse_is_one_subdomain(ctx, &kind);
+  const bool fd_ok = !mg->mixed && !ctx->mapped && coarse_is_one_subdomain(ctx, &kind);
   const int choice = mg->params.coarse_solver;
-  if (choice == TPSS_COARSE_CHEBYSHEV) {
+  if (choice == TPSS_COARSE_CHEBYSHEV || (choice == TPSS_COARSE_AUTO && ctx->mapped && n > kDenseCoarseAuto)) {
     TPSS_REQUIRE(!mg->mixed, "tpss_mg_setup: the Chebyshev coarse solver needs an FP64 V-cycle");
     return chebyshev_setup(ctx, mg);
   }
@@ -449,10 +449,18 @@ static tpss_status smooth(tpss_ctx* ctx, MGState* mg, int l, const T* b, T* x, b
   tpss_patches* P = mg->patches[l];
   const int kind = mg->params.smoother;
   const T omega = (T)mg->params.omega;
-  if (kind == TPSS_ACS || kind == TPSS_AVS) return smooth_additive_t<T>(P, omega, 1, b, x, x_zero ? 1 : 0);
-  if (x_zero) TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)ctx->levels[l].ndofs * sizeof(T), ctx->stream));
-  const bool reverse = post && !mg->params.nonsymmetric;
-  return smooth_multiplicative_t<T>(P, omega, reverse ? 1 : 0, 1, b, x);
+  const int steps = mg->params.smoothing_steps > 0 ? mg->params.smoothing_steps : 1;   // m of Sec. 4
+  for (int m = 0; m < steps; ++m) {
+    const bool zero = x_zero && m == 0;
+    if (kind == TPSS_ACS || kind == TPSS_AVS) {
+      TPSS_TRY(smooth_additive_t<T>(P, omega, 1, b, x, zero ? 1 : 0));
+      continue;
+    }
+    if (zero) TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)ctx->levels[l].ndofs * sizeof(T), ctx->stream));
+    const bool reverse = post && !mg->params.nonsymmetric;
+    TPSS_TRY(smooth_multiplicative_t<T>(P, omega, reverse ? 1 : 0, 1, b, x));
+  }
+  return TPSS_OK;
 }
 
 // x_l = MG_l(0, b_l) (Alg. 1); b, x are level-l vectors.
@@ -683,6 +691,7 @@ extern "C" tpss_status tpss_assemble_rhs(tpss_ctx* ctx, int level, int kind, dou
   TPSS_REQUIRE(ctx && b, "tpss_assemble_rhs: null argument");
   TPSS_REQUIRE(level >= 0 && level < ctx->nlevels, "tpss_assemble_rhs: level out of range");
   TPSS_REQUIRE(kind == 0 || kind == 1, "tpss_assemble_rhs: kind must be 0 or 1");
+  if (ctx->mapped) return mapped_rhs(ctx, level, kind, b);
   const Level& L = ctx->levels[level];
   RhsArgs a{};
   a.B = ctx->d_basis;
@@ -719,7 +728,13 @@ extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params
                "tpss_mg_setup: unknown coarse solver");
   TPSS_REQUIRE(params->mult_residual == TPSS_MULT_RESIDUAL_UPDATE || params->mult_residual == TPSS_MULT_RESIDUAL_FULL,
                "tpss_mg_setup: mult_residual must be 0 (update) or 1 (full)");
+  TPSS_REQUIRE(params->smoothing_steps >= 0 && params->smoothing_steps <= 16,
+               "tpss_mg_setup: smoothing_steps must be in 0..16");
   const bool vertex = params->smoother == TPSS_AVS || params->smoother == TPSS_MVS;
+  TPSS_REQUIRE(!ctx->mapped || (!vertex && params->precision == TPSS_FP64 &&
+                                params->coarse_solver != TPSS_COARSE_FD),
+               "tpss_mg_setup: meshes of quadrilaterals support FP64 cell smoothers (ACS, MCS) with the dense or "
+               "Chebyshev coarse solver");
   if (vertex)
     for (int l = 1; l < ctx->nlevels; ++l)
       for (int t = 0; t < ctx->dim; ++t)
@@ -746,7 +761,9 @@ extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params
       return fail(st);
     if (params->mult_colors != 0 && (params->smoother == TPSS_MVS || params->smoother == TPSS_MCS))
       if ((st = tpss_patches_set_mult_colors(mg->patches[l], params->mult_colors)) != TPSS_OK) return fail(st);
-    mg->patches[l]->mult_update = params->mult_residual == TPSS_MULT_RESIDUAL_FULL ? 0 : 1;
+    // surrogate cell solvers (mapped meshes) always recompute the full residual
+    if (!mg->patches[l]->per_sub)
+      mg->patches[l]->mult_update = params->mult_residual == TPSS_MULT_RESIDUAL_FULL ? 0 : 1;
     if ((st = ensure_level_scratch(ctx, l, 1)) != TPSS_OK) return fail(st);
   }
   if ((st = ensure_level_scratch(ctx, 0, 1)) != TPSS_OK) return fail(st);

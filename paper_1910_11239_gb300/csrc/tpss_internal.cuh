@@ -73,8 +73,31 @@ struct Basis1D {
   double Mhat[kMaxN1 * kMaxN1];         // sum_q wq phi_i phi_j
   double Lhat[kMaxN1 * kMaxN1];         // sum_q wq phi_i' phi_j'
   double Pc[2][kMaxN1 * kMaxN1];        // Pc[s][i*n1+j] = phi_j((x_i + s)/2)
+  double Vq[kMaxN1 * kMaxN1];           // Vq[q*n1+i] = phi_i(xq_q)  (compact, stride n1)
+  double Dq[kMaxN1 * kMaxN1];           // Dq[q*n1+i] = phi_i'(xq_q)
   int status;                           // 0 ok, else Newton failed to converge
 };
+
+// 1D matrices of one cell of width h in a line of cells (eq. 1Dsipg with the
+// Nitsche terms of eq. 1Dnitsche): entry (i, j) of M and A.  hl / hr are the
+// neighbours' widths (h where absent), gpk = gamma_hat P(k) of eq. penalty;
+// eta = 1/2 on interior faces (the 1/sqrt(2) averages of eq. bfsipg), 1 on the
+// boundary.
+__device__ __forceinline__ void op1d_entry(const Basis1D* B, double h, double hl, double hr, bool has_l,
+                                           bool has_r, double gpk, int i, int j, double* m, double* a) {
+  const int n1 = B->n1, k = B->k;
+  const double gl = gpk * (1.0 / h + 1.0 / hl), gr = gpk * (1.0 / h + 1.0 / hr);
+  const double el = has_l ? 0.5 : 1.0, er = has_r ? 0.5 : 1.0;
+  *m = h * B->Mhat[i * n1 + j];
+  double v = B->Lhat[i * n1 + j] / h;
+  // left face p = 0: G[i][j] = -eta/h phi_j'(0) phi_i(0)
+  v += el * gl * (i == 0 && j == 0 ? 1.0 : 0.0);
+  v += el / h * ((i == 0 ? B->d0[j] : 0.0) + (j == 0 ? B->d0[i] : 0.0));
+  // right face p = 1: G[i][j] = +eta/h phi_j'(1) phi_i(1)
+  v += er * gr * (i == k && j == k ? 1.0 : 0.0);
+  v -= er / h * ((i == k ? B->d1[j] : 0.0) + (j == k ? B->d1[i] : 0.0));
+  *a = v;
+}
 
 // Number of face-coupling coefficients stored per cell position:
 // {cR0, cR1, cRd, cL0, cL1, cLd} (see operator.cu for their meaning).
@@ -98,6 +121,7 @@ struct Level {
   int64_t ndofs = 0;
   std::vector<double> widths[3];             // host copies
   double* d_widths[3] = {nullptr, nullptr, nullptr};
+  double* d_verts = nullptr;                 // mapped 2D meshes: [(nc1+1)][(nc0+1)] points (x, y)
   LevelOps<double> op64;
   LevelOps<float> op32;
   // scratch: operator intermediates and residual, nrhs_cap right-hand sides
@@ -143,12 +167,14 @@ struct tpss_ctx {
   double* d_scalars = nullptr;               // small device scratch for reductions
   double* d_partials = nullptr;
   int num_sms = 0;
+  int mapped = 0;                            // 1: 2D bilinear quadrilateral mesh (mapped.cu)
 };
 
 struct tpss_patches {
   tpss_ctx* ctx = nullptr;
   int level = 0, kind = 0, precision = 0;
   int n = 0;                       // 1D subdomain size
+  int per_sub = 0;                 // 1: eigendata per subdomain (mapped cells), not per position
   int npos[3] = {1, 1, 1};         // positions per direction
   int64_t nsub = 0;                // number of subdomains
   double* d_A[3] = {nullptr, nullptr, nullptr};   // [npos][n*n]
@@ -246,7 +272,16 @@ tpss_status prolongate_add_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* c
 template <typename T>
 tpss_status restrict_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* fine, T* coarse);
 
+// ---- mapped.cu (2D meshes of bilinear quadrilaterals, FP64)
+constexpr int kMaxMappedDegree = 7;
+tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs);
+// surrogate cell solvers: fills P->d_A, d_M, d_Z, d_lam (per cell) and d_inv
+tpss_status mapped_cell_eigendata(tpss_ctx* ctx, tpss_patches* P, int* d_err);
+tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b);
+
 // ---- setup.cu
+__global__ void gen_eig_kernel(const double* __restrict__ Aall, const double* __restrict__ Mall, int nprob, int n,
+                               double* __restrict__ Zall, double* __restrict__ lamall, int* __restrict__ err);
 tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tpss_patches** out);
 
 // ---- solver.cu

@@ -80,6 +80,25 @@ def operator_bytes(ncells, k, d=3, nrhs=1, word=8):
     return 2 * word * ndofs(ncells, k, d) * nrhs
 
 
+def mapped_operator_flops(ncells, k, nrhs=1):
+    """Matrix-free SIPG operator on 2D bilinear cells as the kernel computes it,
+    per cell (n1 = k+1, Gauss points = n1 per direction): 4 sum-factorization
+    stages of 2 n1^3 FMAs (reference gradients and their transposes) = 16 n1^3
+    flops; the metric J^{-1} J^{-T} |det J| w at n1^2 points (~30 flops each);
+    per edge (4, each evaluated from both of its cells) the normal-derivative
+    lines of both sides (2 n1^2 FMAs), 3 + 3 interpolations at n1 points
+    (6 n1^2 FMAs), the test sums (3 n1^2 FMAs) and ~60 flops of geometry per
+    point; the edge terms' scatter (~8 n1^2): 16 n1^3 + 126 n1^2 + 240 n1."""
+    n1 = k + 1
+    return num_cells(ncells) * (16 * n1 ** 3 + 126 * n1 ** 2 + 240 * n1) * nrhs
+
+
+def mapped_operator_bytes(ncells, k, nrhs=1):
+    """Minimal HBM traffic: read u, write A u, read the vertex array once."""
+    nx, ny = ncells
+    return 16 * nx * ny * (k + 1) ** 2 * nrhs + 16 * (nx + 1) * (ny + 1)
+
+
 def transfer_flops(coarse_ncells, k, d=3, nrhs=1):
     """Embedding of a parent's (k+1)^d values into its 2^d children by sum
     factorization, one direction after another: 2 n1^4 + 4 n1^4 + 8 n1^4

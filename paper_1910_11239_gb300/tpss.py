@@ -42,7 +42,7 @@ class ProblemDesc(ctypes.Structure):
 class MGParams(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("mult_colors", ctypes.c_int), ("flexible_cg", ctypes.c_int), ("nonsymmetric", ctypes.c_int),
-                ("coarse_solver", ctypes.c_int), ("mult_residual", ctypes.c_int)]
+                ("coarse_solver", ctypes.c_int), ("mult_residual", ctypes.c_int), ("smoothing_steps", ctypes.c_int)]
 
 
 _lib = None
@@ -51,6 +51,8 @@ _lib = None
 _VP, _I, _D, _F, _I64P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "tpss_create": [ctypes.POINTER(ProblemDesc), _VP, ctypes.POINTER(_VP)],
+    "tpss_create_mapped": [_I, _I, _I, _VP, _I, _D, _I, _VP, ctypes.POINTER(_VP)],
+    "tpss_mapped_vertices": [_VP, _I, _VP],
     "tpss_destroy": [_VP],
     "tpss_level_info": [_VP, _I, _I64P, ctypes.POINTER(ctypes.c_int)],
     "tpss_last_error": [],
@@ -149,6 +151,33 @@ class Problem:
         self.dim, self.degree, self.nlevels = dim, degree, nlevels
         self._patches = []
 
+    @classmethod
+    def mapped(cls, degree, vertices, nlevels=1, gamma_hat=4.0, penalty_poly=PENALTY_PAPER, stream=None):
+        """tpss_create_mapped: 2D mesh of bilinear quadrilaterals from a vertex
+        array of shape (ny+1, nx+1, 2) (x index fastest, Sec. 4)."""
+        import numpy as np
+        V = np.ascontiguousarray(vertices, dtype=np.float64)
+        if V.ndim != 3 or V.shape[2] != 2:
+            raise ValueError("vertices must have shape (ny+1, nx+1, 2)")
+        self = cls.__new__(cls)
+        self._keep = [V]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        handle = ctypes.c_void_p()
+        _check(lib().tpss_create_mapped(degree, V.shape[1] - 1, V.shape[0] - 1, ctypes.c_void_p(V.ctypes.data),
+                                        nlevels, gamma_hat, penalty_poly, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(handle)))
+        self.h = handle
+        self.dim, self.degree, self.nlevels = 2, degree, nlevels
+        self._patches = []
+        return self
+
+    def mapped_vertices(self, level):
+        import numpy as np
+        nc = self.level_info(level)[1]
+        out = np.empty((nc[1] + 1, nc[0] + 1, 2))
+        _check(lib().tpss_mapped_vertices(self.h, level, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             for p in self._patches:
@@ -217,8 +246,9 @@ class Problem:
         return b
 
     def mg_setup(self, smoother, omega, precision=FP64, mult_colors=0, flexible_cg=0, nonsymmetric=0,
-                 coarse_solver=COARSE_AUTO, mult_residual=MULT_RESIDUAL_UPDATE):
+                 coarse_solver=COARSE_AUTO, mult_residual=MULT_RESIDUAL_UPDATE, smoothing_steps=1):
         p = MGParams()
+        p.smoothing_steps = smoothing_steps
         p.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
         p.omega, p.precision, p.mult_colors, p.flexible_cg = omega, precision, mult_colors, flexible_cg
         p.nonsymmetric = int(bool(nonsymmetric))

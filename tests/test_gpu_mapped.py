@@ -1,0 +1,198 @@
+"""Sec. 4 on the GPU: SIPG on distorted meshes of bilinear quadrilaterals and
+the inexact cell smoothers on Cartesian surrogate cells, against the oracle
+(oracle/mapped.py): refined vertices, the matrix-free operator, the right-hand
+side, the per-cell surrogate 1D data, ACS / MCS sweeps and V-cycles; then the
+paper's iteration counts on its 25%-distorted 2D mesh."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import dev, paper_value, rel_err
+from oracle import schwarz
+from oracle.mapped import MappedHierarchy, MappedSIPG, refine, surrogate_cell_matrix, surrogate_solvers
+from paper_1910_11239_gb300 import perf, tpss, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _mesh(nx, ny, seed):
+    """A distorted nx x ny mesh: the unit-square recipe on max(nx, ny), cropped."""
+    n = max(nx, ny)
+    return workloads.vertices_distorted(n, seed)[:ny + 1, :nx + 1].copy()
+
+
+def test_refined_vertices_are_bit_exact():
+    V0 = _mesh(5, 3, 1)
+    prob = tpss.Problem.mapped(2, V0, nlevels=4)
+    V = V0
+    for l in range(4):
+        assert np.array_equal(prob.mapped_vertices(l), V)
+        V = refine(V)
+    prob.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7])
+def test_operator_matches_oracle(k):
+    """Several CTAs and a ragged last one: 6 x 5 cells on level 1 (12 x 10)."""
+    V0 = _mesh(6, 5, 10 + k)
+    prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+    for l, V in enumerate([V0, refine(V0)]):
+        A = MappedSIPG(V, k, gamma_hat=4.0).assemble()
+        n = A.shape[0]
+        assert prob.ndofs(l) == n
+        u = workloads.rhs_uniform(n, seed=k, nrhs=2)
+        out = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        prob.apply_operator(l, dev(u), out, nrhs=2)
+        ref = np.concatenate([A @ u[:n], A @ u[n:]])
+        assert rel_err(out, ref) < 1e-12
+        b = workloads.rhs_uniform(n, seed=100 + k)
+        r = torch.empty(n, dtype=torch.float64, device="cuda")
+        prob.residual(l, dev(b), dev(u[:n]), r)
+        assert rel_err(r, b - A @ u[:n]) < 1e-12
+    prob.close()
+
+
+def test_operator_on_cartesian_vertices_is_the_tensor_operator():
+    """A Cartesian vertex array through the mapped kernel equals the Cartesian context."""
+    widths = workloads.widths_random(7, 2, seed=3)
+    for k in (2, 5):
+        mp = tpss.Problem.mapped(k, workloads.vertices_cartesian(*widths), nlevels=1, gamma_hat=2.0)
+        cp = tpss.Problem(2, k, widths, nlevels=1, gamma_hat=2.0)
+        n = cp.ndofs(0)
+        u = dev(workloads.rhs_uniform(n, seed=5))
+        a, c = torch.empty_like(u), torch.empty_like(u)
+        mp.apply_operator(0, u, a)
+        cp.apply_operator(0, u, c)
+        assert rel_err(a, c.cpu().numpy()) < 1e-12
+        mp.close()
+        cp.close()
+
+
+def test_rhs_matches_oracle():
+    V0 = _mesh(4, 4, 6)
+    for k in (1, 3, 6):
+        prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+        S = MappedSIPG(refine(V0), k, gamma_hat=4.0)
+        f = lambda p: 2 * np.pi ** 2 * np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1])
+        ref = S.rhs(f, lambda p: np.zeros(len(p)))
+        b = torch.empty(S.ncells * S.nloc, dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(1, 0, b)
+        assert rel_err(b, ref) < 1e-12
+        with pytest.raises(tpss.TpssError):
+            prob.assemble_rhs(1, 1, b)
+        prob.close()
+
+
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_surrogate_1d_data_per_cell(k):
+    V0 = _mesh(5, 4, 20 + k)
+    prob = tpss.Problem.mapped(k, V0, nlevels=1, gamma_hat=4.0)
+    P = prob.setup_patches(0, tpss.CELL, tpss.FP64)
+    n1 = k + 1
+    for c in (0, 3, 7, 12, 19):
+        i, j = c % 5, c // 5
+        (A0, M0, Z0, l0), (A1, M1, Z1, l1) = P.eigendata(0, c), P.eigendata(1, c)
+        ref = surrogate_cell_matrix(V0, i, j, k, 4.0)
+        assert rel_err(np.kron(M1, A0) + np.kron(A1, M0), ref) < 1e-12
+        for A, M, Z, lam in ((A0, M0, Z0, l0), (A1, M1, Z1, l1)):
+            assert np.allclose(Z.T @ M @ Z, np.eye(n1), atol=1e-10)
+            assert np.allclose(Z.T @ A @ Z, np.diag(lam), atol=1e-9 * np.abs(lam).max())
+    prob.close()
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_surrogate_smoothers_match_oracle(k):
+    V0 = _mesh(6, 5, 30 + k)
+    V = refine(V0)
+    prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+    A = MappedSIPG(V, k, gamma_hat=4.0).assemble()
+    sol = surrogate_solvers(V, k, 4.0)
+    n = A.shape[0]
+    P = prob.setup_patches(1, tpss.CELL, tpss.FP64)
+    b = workloads.rhs_uniform(n, seed=1)
+    x0 = workloads.rhs_uniform(n, seed=2)
+    # additive, from x0 and from zero
+    x = dev(x0)
+    P.smooth_additive(0.5, dev(b), x)
+    assert rel_err(x, schwarz.additive_smoother(A, b, x0, sol, 0.5)) < 1e-11
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P.smooth_additive(0.5, dev(b), x, x_is_zero=True)
+    assert rel_err(x, schwarz.additive_smoother(A, b, np.zeros(n), sol, 0.5)) < 1e-11
+    # multiplicative, red-black, both orders
+    nx = V.shape[1] - 1
+    colors = [schwarz.color_multiplicative_cell((c % nx, c // nx)) for c in range(n // (k + 1) ** 2)]
+    for reverse in (False, True):
+        x = dev(x0)
+        P.smooth_multiplicative(0.75, dev(b), x, reverse_colors=reverse)
+        ref = schwarz.multiplicative_smoother(A, b, x0, sol, colors, 0.75, reverse=reverse)
+        assert rel_err(x, ref) < 1e-11
+    with pytest.raises(tpss.TpssError):
+        P.set_mult_residual(tpss.MULT_RESIDUAL_UPDATE)
+    prob.close()
+
+
+@pytest.mark.parametrize("smoother,omega,steps,k", [("ACS", 0.5, 1, 3), ("ACS", 0.5, 2, 2), ("MCS", 0.75, 1, 3),
+                                                    ("MCS", 0.5, 2, 4)])
+def test_vcycle_matches_oracle(smoother, omega, steps, k):
+    V0 = _mesh(3, 2, 40 + k)
+    H = MappedHierarchy(V0, k, 3, smoother, omega, steps=steps, gamma_hat=4.0)
+    prob = tpss.Problem.mapped(k, V0, nlevels=3, gamma_hat=4.0)
+    prob.mg_setup(smoother, omega, tpss.FP64, coarse_solver=tpss.COARSE_DENSE, smoothing_steps=steps)
+    n = H.A[-1].shape[0]
+    r = workloads.rhs_uniform(n, seed=steps)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    prob.vcycle(dev(r), z)
+    assert rel_err(z, H.precondition(r)) < 1e-10
+    prob.close()
+
+
+def test_mapped_contexts_reject_what_they_do_not_support():
+    prob = tpss.Problem.mapped(3, _mesh(4, 4, 2), nlevels=2)
+    with pytest.raises(tpss.TpssError):
+        prob.setup_patches(1, tpss.VERTEX_PATCH, tpss.FP64)
+    with pytest.raises(tpss.TpssError):
+        prob.setup_patches(1, tpss.CELL, tpss.FP32)
+    for smoother, prec in (("AVS", tpss.FP64), ("ACS", tpss.FP32)):
+        with pytest.raises(tpss.TpssError):
+            prob.mg_setup(smoother, 0.5, prec)
+    with pytest.raises(tpss.TpssError):
+        prob.mg_setup("ACS", 0.5, tpss.FP64, coarse_solver=tpss.COARSE_FD)
+    u = torch.zeros(prob.ndofs(1), dtype=torch.float32, device="cuda")
+    with pytest.raises(tpss.TpssError):
+        prob.apply_operator(1, u, torch.empty_like(u))
+    bad = workloads.vertices_cartesian(np.full(2, 0.5), np.full(2, 0.5))
+    bad[1, 1] = [0.1, 0.1]   # inside the triangle (0,0), (0.5,0), (0,0.5): a non-convex cell
+    with pytest.raises(tpss.TpssError, match="convex"):
+        tpss.Problem.mapped(2, bad)
+    with pytest.raises(tpss.TpssError):
+        tpss.Problem.mapped(8, _mesh(2, 2, 1))
+    prob.close()
+
+
+# Sec. 4 workload: 32 x 32 coarse cells of the unit square, 25% distortion,
+# gamma_hat = 4, L refinements; f = 2 pi^2 sin(pi x) sin(pi y), g = 0; PCG to
+# a relative residual of 1e-8 with the V-cycle (Chebyshev coarse solve), the
+# fractional count from the energy norm of the error (Sec. 2.4).
+def _distorted_count(smoother, omega, steps, k, L, seed=1):
+    prob = tpss.Problem.mapped(k, workloads.vertices_distorted(32, seed), nlevels=L + 1, gamma_hat=4.0)
+    prob.mg_setup(smoother, omega, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV, smoothing_steps=steps)
+    b = torch.empty(prob.ndofs(L), dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(L, 0, b)
+    errs = perf.cg_energy_errors(prob, b, rtol=1e-8, maxit=150)
+    prob.close()
+    return perf.fractional_iterations(errs, 1e-8)
+
+
+@pytest.mark.parametrize("key,smoother,omega,steps,k", [
+    ("dist2d_acs1_k3_L3", "ACS", 0.5, 1, 3),
+    ("dist2d_acs2_k3_L3", "ACS", 0.5, 2, 3),
+    ("dist2d_mcs1_k3_L3", "MCS", 0.75, 1, 3),
+    ("dist2d_mcs2_k3_L3", "MCS", 0.75, 2, 3),
+])
+def test_paper_counts_on_the_distorted_mesh(key, smoother, omega, steps, k):
+    """tab:cubedist25acp / tab:cubedist25mcp, 2D, L = 3.  The paper's mesh is
+    one random draw of the recipe and ours another, so the counts agree to
+    within 15%, not exactly."""
+    nu = _distorted_count(smoother, omega, steps, k, 3)
+    paper = paper_value(key)
+    assert abs(nu - paper) <= 0.15 * paper, (nu, paper)

@@ -7,10 +7,12 @@ import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import multigrid, schwarz
-from oracle.mapped import (MappedHierarchy, MappedSIPG, bilinear_map, cartesian_vertices, distorted_vertices,
-                           exact_solvers, refine, surrogate_cell_matrix, surrogate_solvers, surrogate_widths)
+from oracle.mapped import (MappedHierarchy, MappedSIPG, bilinear_map, exact_solvers, refine, surrogate_cell_matrix,
+                           surrogate_solvers, surrogate_widths)
 from oracle.mesh import TensorMesh
 from oracle.sipg import SIPG
+from paper_1910_11239_gb300.workloads import vertices_cartesian as cartesian_vertices
+from paper_1910_11239_gb300.workloads import vertices_distorted as distorted_vertices
 
 
 @pytest.mark.parametrize("k,gamma_hat", [(1, 1.0), (3, 4.0), (4, 2.5)])
