@@ -774,6 +774,11 @@ def run_distorted(tpss, workloads, perf, torch, steps):
             rec[f"{sm}1_pcg"] = {"omega": om, "vcycle_ms": ms, "iterations": res["iters"],
                                  "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
                                  "solve_s": t, "dofs_per_s": N / t}
+            if sm == "ACS":   # the coarse solve's share of the V-cycle (Chebyshev, CUDA graph)
+                b0 = torch.from_numpy(workloads.rhs_uniform(prob.ndofs(0), seed=5)).to("cuda")
+                x0 = torch.empty_like(b0)
+                rec["coarse_solve"] = {"ms": _time_calls(torch, lambda: prob.coarse_solve(b0, x0), 3),
+                                       "dofs": prob.ndofs(0), **prob.coarse_chebyshev_info()}
         prob.close()
         out[f"k{k}"] = rec
     its = {}

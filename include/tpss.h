@@ -334,6 +334,16 @@ tpss_status tpss_coarse_chebyshev_info(const tpss_ctx* ctx, double* a, double* b
 tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
                            int* iters, double* rel_res, double* res_hist);
 
+/* The energy norms of the errors of the same PCG iteration (the measure of
+ * Sec. 2.4 for CG): with xs the solution (a DEVICE vector, e.g. from
+ * tpss_pcg_solve to 1e-14), errs[k] = ||x_k - xs||_A for k = 0, 1, ...
+ * (HOST array of at least maxit+1 doubles), one PCG run stopped at the first
+ * errs[k] <= rtol errs[0] or after maxit steps; *count = number of values
+ * written, x = the last iterate (must not alias b or xs).  TPSS_ENOTCONV at
+ * maxit.  One extra operator application per step. */
+tpss_status tpss_pcg_energy_errors(tpss_ctx* ctx, const double* b, const double* xs, double* x, double rtol,
+                                   int maxit, int* count, double* errs);
+
 /* Mixed-precision iterative refinement (not in the paper): from x = 0, repeat
  *   r = b - A x (FP64);  solve A e = r / ||r|| approximately by PCG in FP32
  *   (the FP32 operator, the FP32 / TF32 / BF16 V-cycle of tpss_mg_setup,

@@ -11,9 +11,11 @@
 // are nested and the transfers are the Cartesian ones (transfer.cu).
 //
 // Operator (eq. bfsipg on mapped cells, matrix-free): one CTA handles CPB
-// cells, (k+1)^2 threads per cell.  The geometry is recomputed on the fly
-// from the 4 x 4 vertex block around the cell, so the kernel reads only
-// the DoF vectors and 32 doubles of vertices per cell.
+// cells, (k+1)^2 threads per cell.  The geometry (metric at the Gauss
+// points, J^{-1} n at the edge points, |e| and the penalty per edge) is
+// computed once per level; the kernel is bound by the FP64 pipe, and these
+// 3 (k+1)^2 + 8 (k+1) + 8 doubles per cell cost less HBM time than
+// recomputing them (two Jacobian inversions per edge point) costs FP64 time.
 //   cell term   sum_q w_q |det J| (J^{-1} J^{-T} g_u) . g_v with reference
 //               gradients g from sum factorization (Gauss points xq, k+1 per
 //               direction; Vq, Dq the basis values and derivatives there)
@@ -104,6 +106,75 @@ __global__ void refine_vertices_kernel(const double2* __restrict__ V, int nx, in
   }
 }
 
+// -------------------------------------------------------------- geometry
+// Per level and cell, computed once when the context is created (G doubles
+// per cell, GeoLayout):
+//   C[3][n1^2]   w_q0 w_q1 |det J| J^{-1} J^{-T} at the Gauss points (c00, c01, c11)
+//   A[4][2][n1]  J^{-1} n at the n1 Gauss points of edge f = 2 t + side, n the
+//                cell's outward unit normal (straight edges: one n per edge)
+//   S[4][2]      |e| and the penalty gamma_e of the edge (eq. penalty with
+//                h = |K| / |e|; interior: both cells, boundary: h^+ = h^-)
+struct GeoLayout {
+  int n1, nl, C, A, S, G;
+  __host__ __device__ explicit GeoLayout(int n) : n1(n), nl(n * n), C(0), A(3 * n * n), S(3 * n * n + 8 * n),
+                                                 G(3 * n * n + 8 * n + 8) {}
+};
+
+__global__ void mapped_geometry_kernel(const Basis1D* __restrict__ B, const double2* __restrict__ V, int nx, int ny,
+                                       double gpk, double* __restrict__ geo) {
+  const int n1 = B->n1;
+  const GeoLayout g(n1);
+  const int64_t c = blockIdx.x;
+  const int cx = (int)(c % nx), cy = (int)(c / nx);
+  auto quad = [&](int i, int j) {
+    Quad Q;
+    Q.v0 = V[(int64_t)j * (nx + 1) + i];
+    Q.v1 = V[(int64_t)j * (nx + 1) + i + 1];
+    Q.v2 = V[(int64_t)(j + 1) * (nx + 1) + i];
+    Q.v3 = V[(int64_t)(j + 1) * (nx + 1) + i + 1];
+    return Q;
+  };
+  const Quad Q = quad(cx, cy);
+  double* out = geo + c * g.G;
+  for (int e = threadIdx.x; e < g.nl; e += blockDim.x) {
+    const int q0 = e % n1, q1 = e / n1;
+    double Ji[4];
+    const double det = inverse_jacobian(Q, B->xq[q0], B->xq[q1], Ji);
+    const double w = B->wq[q0] * B->wq[q1] * fabs(det);
+    out[g.C + e] = w * (Ji[0] * Ji[0] + Ji[1] * Ji[1]);
+    out[g.C + g.nl + e] = w * (Ji[0] * Ji[2] + Ji[1] * Ji[3]);
+    out[g.C + 2 * g.nl + e] = w * (Ji[2] * Ji[2] + Ji[3] * Ji[3]);
+  }
+  for (int e = threadIdx.x; e < 4 * n1 + 4; e += blockDim.x) {
+    const int f = e < 4 * n1 ? e / n1 : e - 4 * n1, t = f >> 1, side = f & 1;
+    // edge of face f: t = 0 from v0 (side 0) / v1 to v2 / v3; t = 1 from v0 / v2 to v1 / v3
+    const double2 pa = t == 0 ? (side ? Q.v1 : Q.v0) : (side ? Q.v2 : Q.v0);
+    const double2 pb = t == 0 ? (side ? Q.v3 : Q.v2) : (side ? Q.v3 : Q.v1);
+    const double tx = pb.x - pa.x, ty = pb.y - pa.y;
+    const double le = sqrt(tx * tx + ty * ty);
+    double nxv = t == 0 ? ty / le : -ty / le, nyv = t == 0 ? -tx / le : tx / le;
+    if (side == 0) {
+      nxv = -nxv;
+      nyv = -nyv;
+    }
+    if (e < 4 * n1) {
+      const double s = B->xq[e % n1];
+      double Ji[4];
+      inverse_jacobian(Q, t == 0 ? (double)side : s, t == 0 ? s : (double)side, Ji);
+      out[g.A + f * 2 * n1 + e % n1] = Ji[0] * nxv + Ji[1] * nyv;
+      out[g.A + f * 2 * n1 + n1 + e % n1] = Ji[2] * nxv + Ji[3] * nyv;
+    } else {
+      const int ni = cx + (t == 0 ? (side ? 1 : -1) : 0), nj = cy + (t == 1 ? (side ? 1 : -1) : 0);
+      const double hK = quad_area(Q) / le;
+      double gam;
+      if (ni >= 0 && ni < nx && nj >= 0 && nj < ny) gam = gpk * (1.0 / hK + 1.0 / (quad_area(quad(ni, nj)) / le));
+      else gam = gpk * (2.0 / hK);
+      out[g.S + 2 * f] = le;
+      out[g.S + 2 * f + 1] = gam;
+    }
+  }
+}
+
 // -------------------------------------------------------------- operator
 template <int N1>
 struct MappedShape {
@@ -111,13 +182,14 @@ struct MappedShape {
   static constexpr int CPB_RAW = 256 / NL;
   static constexpr int CPB = CPB_RAW > 32 ? 32 : (CPB_RAW < 1 ? 1 : CPB_RAW);
   static constexpr int THREADS = CPB * NL;
-  // per-cell slot (doubles): 16 vertices (double2, 16-byte aligned: the slot
-  // and the tables have even lengths), 5 areas, U (own + 4 neighbours), tA,
-  // tB, F0, F1, 9 face arrays [4][N1]
-  static constexpr int VB = 0, AREA = 32, U = 38, TA = U + 5 * NL, TB = TA + NL, F0 = TB + NL, F1 = F0 + NL;
+  static constexpr int G = 3 * NL + 8 * N1 + 8;   // GeoLayout(N1).G
+  // per-cell slot (doubles): own geometry, the neighbours' J^{-1} n on the
+  // shared edges [4][2][N1], U (own + 4 neighbours), tA, tB, F0, F1 and 9
+  // edge arrays [4][N1]
+  static constexpr int GEO = 0, NA = G, U = NA + 8 * N1, TA = U + 5 * NL, TB = TA + NL, F0 = TB + NL, F1 = F0 + NL;
   static constexpr int FACE = F1 + NL;
-  static constexpr int SLOT = FACE + 9 * 4 * N1 + ((FACE + 9 * 4 * N1) & 1);
-  static constexpr int TABLES = 2 * NL + 4 * N1;   // even
+  static constexpr int SLOT = FACE + 9 * 4 * N1;
+  static constexpr int TABLES = 2 * NL + 4 * N1;
   static constexpr size_t SMEM = (size_t)(TABLES + CPB * SLOT) * sizeof(double);
 };
 
@@ -125,23 +197,22 @@ struct MappedOpArgs {
   const double* u;
   double* out;
   const double* rhs;   // not null: out = rhs - A u
-  const double2* V;
+  const double* geo;   // [ncells][G]
   const Basis1D* B;
   int nx, ny;
   int64_t ncells, ndofs;
-  double gpk;          // gamma_hat P(k)
 };
 
 template <int N1>
 __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(MappedOpArgs a) {
   using S = MappedShape<N1>;
-  constexpr int NL = N1 * N1, K = N1 - 1;
-  extern __shared__ __align__(16) double sm[];
+  constexpr int NL = N1 * N1, K = N1 - 1, G = S::G;
+  constexpr int GA = 3 * NL, GS = 3 * NL + 8 * N1;   // GeoLayout offsets
+  extern __shared__ double sm[];
   double* Vq = sm;
   double* Dq = Vq + NL;
   double* dd = Dq + NL;        // d0 then d1: phi_i'(0), phi_i'(1)
-  double* xq = dd + 2 * N1;
-  double* wq = xq + N1;
+  double* wq = dd + 2 * N1;
   for (int e = threadIdx.x; e < NL; e += S::THREADS) {
     Vq[e] = a.B->Vq[e];
     Dq[e] = a.B->Dq[e];
@@ -149,11 +220,12 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
   for (int e = threadIdx.x; e < N1; e += S::THREADS) {
     dd[e] = a.B->d0[e];
     dd[N1 + e] = a.B->d1[e];
-    xq[e] = a.B->xq[e];
     wq[e] = a.B->wq[e];
   }
   const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
   double* W = sm + S::TABLES + slot * S::SLOT;
+  double* geo = W + S::GEO;
+  double* na = W + S::NA;
   double* U = W + S::U;
   double* tA = W + S::TA;
   double* tB = W + S::TB;
@@ -168,8 +240,6 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
   double* de = be + 4 * N1;
   double* As = de + 4 * N1;
   double* Bs = As + 4 * N1;
-  double2* vb = reinterpret_cast<double2*>(W + S::VB);   // 4 x 4 vertex block around the cell
-  double* area = W + S::AREA;                            // own, then faces 0..3
   const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
   const bool active = cell < a.ncells;
   const int cx = active ? (int)(cell % a.nx) : 0, cy = active ? (int)(cell / a.nx) : 0;
@@ -180,34 +250,26 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
   auto nbr = [&](int f) -> int64_t {
     return cell + (f == 0 ? -1 : f == 1 ? 1 : f == 2 ? -a.nx : a.nx);
   };
-  auto quad = [&](int dx, int dy) -> Quad {
-    Quad Q;
-    Q.v0 = vb[(1 + dy) * 4 + 1 + dx];
-    Q.v1 = vb[(1 + dy) * 4 + 2 + dx];
-    Q.v2 = vb[(2 + dy) * 4 + 1 + dx];
-    Q.v3 = vb[(2 + dy) * 4 + 2 + dx];
-    return Q;
-  };
-  auto face_quad = [&](int f) -> Quad {
-    return f == 0 ? quad(-1, 0) : f == 1 ? quad(1, 0) : f == 2 ? quad(0, -1) : quad(0, 1);
-  };
   // local index of (i_t = it, the other index = j) for direction t
   auto lidx = [](int t, int it, int j) { return t == 0 ? it + N1 * j : j + N1 * it; };
 
-  // ---- P0: DoF values of the cell and its neighbours, vertex block
+  // ---- P0: DoF values of the cell and its neighbours; geometry
   if (active) {
     U[tid] = a.u[vbase + cell * NL + tid];
 #pragma unroll
     for (int f = 0; f < 4; ++f)
       if (has(f)) U[(1 + f) * NL + tid] = a.u[vbase + nbr(f) * NL + tid];
-    for (int e = tid; e < 16; e += NL) {
-      const int vx = cx - 1 + (e & 3), vy = cy - 1 + (e >> 2);
-      if (vx >= 0 && vx <= a.nx && vy >= 0 && vy <= a.ny) vb[e] = a.V[(int64_t)vy * (a.nx + 1) + vx];
+    const double* gc = a.geo + cell * G;
+    for (int e = tid; e < G; e += NL) geo[e] = gc[e];
+    // the neighbour across edge f sees it as its edge f ^ 1
+    for (int e = tid; e < 8 * N1; e += NL) {
+      const int f = e / (2 * N1);
+      if (has(f)) na[e] = a.geo[nbr(f) * G + GA + (f ^ 1) * 2 * N1 + e % (2 * N1)];
     }
   }
   __syncthreads();
 
-  // ---- P1: cell stage A; edge traces and reference normal-derivative lines; areas
+  // ---- P1: cell stage A; edge traces and reference normal-derivative lines
   if (active) {
     const int q0 = tid % N1, i1 = tid / N1;
     double sa = 0.0, sb = 0.0;
@@ -237,16 +299,11 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
         dlN[e] = sn;
       }
     }
-    for (int e = tid; e < 5; e += NL) {
-      if (e == 0) area[0] = quad_area(quad(0, 0));
-      else if (has(e - 1)) area[e] = quad_area(face_quad(e - 1));
-    }
   }
   __syncthreads();
 
   // ---- P2: reference gradients at the Gauss points times the metric; edge-point coefficients
   if (active) {
-    const Quad Q = quad(0, 0);
     const int q0 = tid % N1, q1 = tid / N1;
     double g0 = 0.0, g1 = 0.0;
 #pragma unroll
@@ -254,17 +311,11 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
       g0 = fma(Vq[q1 * N1 + i1], tA[q0 + N1 * i1], g0);
       g1 = fma(Dq[q1 * N1 + i1], tB[q0 + N1 * i1], g1);
     }
-    double Ji[4];
-    const double det = inverse_jacobian(Q, xq[q0], xq[q1], Ji);
-    const double w = wq[q0] * wq[q1] * fabs(det);
-    // C = w J^{-1} J^{-T}
-    const double c00 = w * (Ji[0] * Ji[0] + Ji[1] * Ji[1]);
-    const double c01 = w * (Ji[0] * Ji[2] + Ji[1] * Ji[3]);
-    const double c11 = w * (Ji[2] * Ji[2] + Ji[3] * Ji[3]);
-    F0[tid] = c00 * g0 + c01 * g1;
-    F1[tid] = c01 * g0 + c11 * g1;
+    const double c00 = geo[tid], c01 = geo[NL + tid], c11 = geo[2 * NL + tid];
+    F0[tid] = fma(c00, g0, c01 * g1);
+    F1[tid] = fma(c01, g0, c11 * g1);
     for (int e = tid; e < 4 * N1; e += NL) {
-      const int f = e / N1, q = e % N1, t = f >> 1, side = f & 1;
+      const int f = e / N1, q = e % N1, t = f >> 1;
       const double* fl = trK + f * N1;
       const double* dl = dlK + f * N1;
       double uK = 0.0, dtK = 0.0, dtanK = 0.0;
@@ -274,23 +325,9 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
         dtK = fma(Vq[q * N1 + j], dl[j], dtK);
         dtanK = fma(Dq[q * N1 + j], fl[j], dtanK);
       }
-      // edge of face f: t = 0 from v0 (side 0) / v1 to v2 / v3; t = 1 from v0 / v2 to v1 / v3
-      const double2 pa = t == 0 ? (side ? Q.v1 : Q.v0) : (side ? Q.v2 : Q.v0);
-      const double2 pb = t == 0 ? (side ? Q.v3 : Q.v2) : (side ? Q.v3 : Q.v1);
-      const double tx = pb.x - pa.x, ty = pb.y - pa.y;
-      const double le = sqrt(tx * tx + ty * ty);
-      double nx = t == 0 ? ty / le : -ty / le, ny = t == 0 ? -tx / le : tx / le;
-      if (side == 0) {
-        nx = -nx;
-        ny = -ny;
-      }
-      const double s = xq[q];
-      double JK[4];
-      inverse_jacobian(Q, t == 0 ? (double)side : s, t == 0 ? s : (double)side, JK);
-      const double aK0 = JK[0] * nx + JK[1] * ny, aK1 = JK[2] * nx + JK[3] * ny;   // J^{-1} n
-      const double dnK = t == 0 ? aK0 * dtK + aK1 * dtanK : aK0 * dtanK + aK1 * dtK;
-      const double Wq = wq[q] * le;
-      const double hK = area[0] / le;
+      const double aK0 = geo[GA + f * 2 * N1 + q], aK1 = geo[GA + f * 2 * N1 + N1 + q];   // J^{-1} n
+      const double dnK = t == 0 ? fma(aK0, dtK, aK1 * dtanK) : fma(aK0, dtanK, aK1 * dtK);
+      const double Wq = wq[q] * geo[GS + 2 * f], gam = geo[GS + 2 * f + 1];
       double alpha, c1;
       if (has(f)) {
         const double* gl = trN + f * N1;
@@ -302,18 +339,13 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
           dtN = fma(Vq[q * N1 + j], gd[j], dtN);
           dtanN = fma(Dq[q * N1 + j], gl[j], dtanN);
         }
-        const Quad QN = face_quad(f);
-        double JN[4];
-        inverse_jacobian(QN, t == 0 ? (double)(1 - side) : s, t == 0 ? s : (double)(1 - side), JN);
-        const double aN0 = JN[0] * nx + JN[1] * ny, aN1 = JN[2] * nx + JN[3] * ny;
-        const double dnN = t == 0 ? aN0 * dtN + aN1 * dtanN : aN0 * dtanN + aN1 * dtN;
-        const double hN = area[1 + f] / le;
-        const double gam = a.gpk * (1.0 / hK + 1.0 / hN);
+        // the neighbour's J^{-1} n_N with n_N = -n
+        const double aN0 = -na[f * 2 * N1 + q], aN1 = -na[f * 2 * N1 + N1 + q];
+        const double dnN = t == 0 ? fma(aN0, dtN, aN1 * dtanN) : fma(aN0, dtanN, aN1 * dtN);
         const double jump = uK - uN;
         alpha = Wq * (0.5 * gam * jump - 0.5 * (dnK + dnN));
         c1 = -0.5 * Wq * jump;
       } else {
-        const double gam = a.gpk * (2.0 / hK);
         alpha = Wq * (gam * uK - dnK);
         c1 = -Wq * uK;
       }
@@ -397,13 +429,12 @@ tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, do
   a.u = u;
   a.out = out;
   a.rhs = rhs;
-  a.V = reinterpret_cast<const double2*>(L.d_verts);
+  a.geo = L.d_geo;
   a.B = ctx->d_basis;
   a.nx = L.nc[0];
   a.ny = L.nc[1];
   a.ncells = L.ncells;
   a.ndofs = L.ndofs;
-  a.gpk = penalty_prefactor(ctx);
   switch (ctx->n1) {
     case 2: return launch_mapped<2>(ctx, a, nrhs);
     case 3: return launch_mapped<3>(ctx, a, nrhs);
@@ -618,8 +649,15 @@ extern "C" tpss_status tpss_create_mapped(int degree, int nx, int ny, const doub
           reinterpret_cast<const double2*>(C.d_verts), C.nc[0], C.nc[1], reinterpret_cast<double2*>(L.d_verts));
     }
   }
+  for (int l = 0; l < nlevels; ++l) {
+    Level& L = ctx->levels[l];
+    if ((st = dalloc_t(&L.d_geo, (size_t)L.ncells * GeoLayout(ctx->n1).G)) != TPSS_OK) return fail(st);
+    mapped_geometry_kernel<<<(unsigned)L.ncells, 64, 0, ctx->stream>>>(
+        ctx->d_basis, reinterpret_cast<const double2*>(L.d_verts), L.nc[0], L.nc[1], penalty_prefactor(ctx),
+        L.d_geo);
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-    set_error("tpss_create_mapped: vertex refinement failed");
+    set_error("tpss_create_mapped: vertex refinement or geometry setup failed");
     return fail(TPSS_ECUDA);
   }
   *out = ctx;

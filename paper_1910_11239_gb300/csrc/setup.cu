@@ -456,6 +456,7 @@ static tpss_status build_level(tpss_ctx* ctx, int l) {
 
 static void free_level(Level& L) {
   dfree(L.d_verts);
+  dfree(L.d_geo);
   for (int t = 0; t < 3; ++t) {
     dfree(L.d_widths[t]);
     dfree(L.op64.M[t]); dfree(L.op64.A[t]); dfree(L.op64.F[t]);

@@ -32,6 +32,8 @@ void destroy_mg(tpss_ctx* ctx) {
   if (mg->coarse_fd) tpss_patches_destroy(mg->coarse_fd);
   if (mg->coarse_acs) tpss_patches_destroy(mg->coarse_acs);
   dfree(mg->cheb_vec);
+  if (mg->cheb_exec) cudaGraphExecDestroy(mg->cheb_exec);
+  if (mg->cheb_capture) cudaStreamDestroy(mg->cheb_capture);
   dfree(mg->ir_vec);
   dfree(mg->coarse_inv);
   dfree(mg->gj_tmp);
@@ -41,6 +43,7 @@ void destroy_mg(tpss_ctx* ctx) {
   for (auto* v : mg->x32) dfree(v);
   dfree(mg->r); dfree(mg->z); dfree(mg->p); dfree(mg->q); dfree(mg->zold);
   dfree(mg->gm_V); dfree(mg->gm_Z); dfree(mg->gm_h);
+  dfree(mg->en_vec);
   delete mg;
   ctx->mg = nullptr;
 }
@@ -335,7 +338,7 @@ static tpss_status chebyshev_setup(tpss_ctx* ctx, MGState* mg) {
   return TPSS_OK;
 }
 
-static tpss_status chebyshev_apply(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
+static tpss_status chebyshev_body(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
   const int64_t n = mg->n0;
   cudaStream_t s = ctx->stream;
   double* r = mg->cheb_vec;
@@ -359,6 +362,48 @@ static tpss_status chebyshev_apply(tpss_ctx* ctx, MGState* mg, const double* f, 
     TPSS_CHECK_LAUNCH();
     rho = rho_new;
   }
+  return TPSS_OK;
+}
+
+// The m steps are ~3m small launches on level 0 (launch-bound): they are
+// captured once per (f, x) pair into a CUDA graph on a private stream (the
+// library's stream may be the legacy default stream, which cannot capture)
+// and replayed on the library's stream.  If capture is not possible the
+// steps run directly.
+static tpss_status chebyshev_apply(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
+  if (mg->cheb_m < 1) {
+    TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, mg->n0 * sizeof(double), ctx->stream));
+    return TPSS_OK;
+  }
+  if (!(mg->cheb_exec && mg->cheb_gf == f && mg->cheb_gx == x)) {
+    if (mg->cheb_exec) cudaGraphExecDestroy(mg->cheb_exec);
+    mg->cheb_exec = nullptr;
+    if (!mg->cheb_capture && cudaStreamCreateWithFlags(&mg->cheb_capture, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      mg->cheb_capture = nullptr;
+      return chebyshev_body(ctx, mg, f, x);
+    }
+    cudaStream_t orig = ctx->stream;
+    ctx->stream = mg->cheb_capture;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(mg->cheb_capture, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const tpss_status st = chebyshev_body(ctx, mg, f, x);
+      ok = cudaStreamEndCapture(mg->cheb_capture, &graph) == cudaSuccess && st == TPSS_OK;
+    }
+    ctx->stream = orig;
+    if (ok) ok = cudaGraphInstantiate(&mg->cheb_exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    clear_error();
+    if (!ok) {
+      mg->cheb_exec = nullptr;
+      return chebyshev_body(ctx, mg, f, x);
+    }
+    mg->cheb_gf = f;
+    mg->cheb_gx = x;
+  }
+  TPSS_CHECK_CUDA(cudaGraphLaunch(mg->cheb_exec, ctx->stream));
   return TPSS_OK;
 }
 
@@ -811,12 +856,19 @@ extern "C" tpss_status tpss_coarse_chebyshev_info(const tpss_ctx* ctx, double* a
   return TPSS_OK;
 }
 
-extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
-                                      int* iters, double* rel_res, double* res_hist) {
-  clear_error();
-  TPSS_REQUIRE(ctx && b && x && iters && rel_res, "tpss_pcg_solve: null argument");
-  TPSS_REQUIRE(ctx->mg, "tpss_pcg_solve: call tpss_mg_setup first");
-  TPSS_REQUIRE(rtol > 0.0 && maxit >= 1, "tpss_pcg_solve: rtol must be > 0 and maxit >= 1");
+// e = x - xs
+__global__ void diff_kernel(double* __restrict__ e, const double* __restrict__ x, const double* __restrict__ xs,
+                            int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    e[i] = x[i] - xs[i];
+}
+
+// PCG with the V-cycle from x = 0.  With xs (a device vector, the solution),
+// the A-norms of the errors ||x_k - xs||_A are recorded in errs and the
+// iteration stops at the first one <= rtol ||xs||_A instead of on the
+// residual.
+static tpss_status pcg_run(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit, int* iters,
+                           double* rel_res, double* res_hist, const double* xs, double* errs) {
   MGState* mg = ctx->mg;
   const int L = ctx->nlevels - 1;
   const int64_t n = ctx->levels[L].ndofs;
@@ -825,6 +877,20 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
   const int g = grid_for(ctx, n);
   *iters = 0;
   *rel_res = 1.0;
+  double e0 = 0.0;
+  if (xs) {
+    if (!mg->en_vec) TPSS_TRY(dalloc_t(&mg->en_vec, 2 * (size_t)n));
+    TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    diff_kernel<<<g, 256, 0, s>>>(mg->en_vec, x, xs, n);
+    TPSS_TRY(apply_operator_t<double>(ctx, L, 1, mg->en_vec, mg->en_vec + n, nullptr));
+    TPSS_TRY(dot(ctx, mg->en_vec, mg->en_vec + n, n, sc + 6));
+    double h0[8];
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(h0, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
+    e0 = std::sqrt(std::max(h0[6], 0.0));
+    errs[0] = e0;
+    if (e0 == 0.0) return TPSS_OK;
+  }
   TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   TPSS_CHECK_CUDA(cudaMemcpyAsync(mg->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 5));
@@ -850,6 +916,11 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
     TPSS_TRY(dot(ctx, mg->p, mg->q, n, sc + 1));
     cg_xr_kernel<double><<<g, 256, 0, s>>>(x, mg->r, mg->p, mg->q, n, sc);
     TPSS_TRY(dot(ctx, mg->r, mg->r, n, sc + 2));
+    if (xs) {
+      diff_kernel<<<g, 256, 0, s>>>(mg->en_vec, x, xs, n);
+      TPSS_TRY(apply_operator_t<double>(ctx, L, 1, mg->en_vec, mg->en_vec + n, nullptr));
+      TPSS_TRY(dot(ctx, mg->en_vec, mg->en_vec + n, n, sc + 6));
+    }
     TPSS_CHECK_CUDA(cudaMemcpyAsync(h, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
     const double rel = std::sqrt(std::max(h[2], 0.0) / rr0);
@@ -860,7 +931,12 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
       set_error("tpss_pcg_solve: breakdown (p^T A p <= 0 or non-finite residual)");
       return TPSS_EBREAKDOWN;
     }
-    if (rel <= rtol) return TPSS_OK;
+    if (xs) {
+      errs[it] = std::sqrt(std::max(h[6], 0.0));
+      if (errs[it] <= rtol * e0) return TPSS_OK;
+    } else if (rel <= rtol) {
+      return TPSS_OK;
+    }
     if (flex) std::swap(mg->z, mg->zold);
     TPSS_TRY(precondition(ctx, mg, mg->r, mg->z));
     TPSS_TRY(dot(ctx, mg->r, mg->z, n, sc + 3));
@@ -873,6 +949,30 @@ extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x,
   return TPSS_ENOTCONV;
 }
 
+extern "C" tpss_status tpss_pcg_solve(tpss_ctx* ctx, const double* b, double* x, double rtol, int maxit,
+                                      int* iters, double* rel_res, double* res_hist) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && x && iters && rel_res, "tpss_pcg_solve: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_pcg_solve: call tpss_mg_setup first");
+  TPSS_REQUIRE(rtol > 0.0 && maxit >= 1, "tpss_pcg_solve: rtol must be > 0 and maxit >= 1");
+  return pcg_run(ctx, b, x, rtol, maxit, iters, rel_res, res_hist, nullptr, nullptr);
+}
+
+extern "C" tpss_status tpss_pcg_energy_errors(tpss_ctx* ctx, const double* b, const double* xs, double* x,
+                                              double rtol, int maxit, int* count, double* errs) {
+  clear_error();
+  TPSS_REQUIRE(ctx && b && xs && x && count && errs, "tpss_pcg_energy_errors: null argument");
+  TPSS_REQUIRE(ctx->mg, "tpss_pcg_energy_errors: call tpss_mg_setup first");
+  TPSS_REQUIRE(rtol > 0.0 && maxit >= 1, "tpss_pcg_energy_errors: rtol must be > 0 and maxit >= 1");
+  TPSS_REQUIRE(x != xs && x != b, "tpss_pcg_energy_errors: x must not alias b or xs");
+  int it = 0;
+  double rel = 0.0;
+  *count = 0;
+  const tpss_status st = pcg_run(ctx, b, x, rtol, maxit, &it, &rel, nullptr, xs, errs);
+  *count = it + 1;
+  if (st == TPSS_ENOTCONV) set_error("tpss_pcg_energy_errors: error not reduced by rtol within maxit");
+  return st;
+}
 
 // Mixed-precision iterative refinement: FP64 residual outside, an FP32 PCG
 // with the FP32 V-cycle and the FP32 operator inside on the normalized
@@ -986,6 +1086,7 @@ extern "C" tpss_status tpss_gmres_solve(tpss_ctx* ctx, const double* b, double* 
   if (mg->gm_restart < restart) {
     TPSS_CHECK_CUDA(cudaStreamSynchronize(s));
     dfree(mg->gm_V); dfree(mg->gm_Z); dfree(mg->gm_h);
+  dfree(mg->en_vec);
     mg->gm_V = mg->gm_Z = mg->gm_h = nullptr;
     mg->gm_restart = 0;
     TPSS_TRY(dalloc_t(&mg->gm_V, (size_t)(restart + 1) * n));

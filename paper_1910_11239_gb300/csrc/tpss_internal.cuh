@@ -122,6 +122,7 @@ struct Level {
   std::vector<double> widths[3];             // host copies
   double* d_widths[3] = {nullptr, nullptr, nullptr};
   double* d_verts = nullptr;                 // mapped 2D meshes: [(nc1+1)][(nc0+1)] points (x, y)
+  double* d_geo = nullptr;                   // mapped 2D meshes: per-cell geometry (mapped.cu, GeoLayout)
   LevelOps<double> op64;
   LevelOps<float> op32;
   // scratch: operator intermediates and residual, nrhs_cap right-hand sides
@@ -150,7 +151,12 @@ struct MGState {
   double cheb_a = 0.0, cheb_b = 0.0;     // spectral interval of P A_0 used by the iteration
   int cheb_m = 0;                        // Chebyshev steps per coarse solve
   double* cheb_vec = nullptr;            // 4 level-0 vectors
+  cudaGraphExec_t cheb_exec = nullptr;   // captured steps for the (f, x) pair below
+  const double* cheb_gf = nullptr;
+  double* cheb_gx = nullptr;
+  cudaStream_t cheb_capture = nullptr;   // private non-blocking stream for the capture
   float* ir_vec = nullptr;               // iterative refinement: 5 finest-level FP32 vectors
+  double* en_vec = nullptr;              // energy-norm PCG: e and A e on the finest level
 };
 
 }  // namespace tpss

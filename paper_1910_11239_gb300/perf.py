@@ -82,21 +82,23 @@ def operator_bytes(ncells, k, d=3, nrhs=1, word=8):
 
 def mapped_operator_flops(ncells, k, nrhs=1):
     """Matrix-free SIPG operator on 2D bilinear cells as the kernel computes it,
-    per cell (n1 = k+1, Gauss points = n1 per direction): 4 sum-factorization
-    stages of 2 n1^3 FMAs (reference gradients and their transposes) = 16 n1^3
-    flops; the metric J^{-1} J^{-T} |det J| w at n1^2 points (~30 flops each);
-    per edge (4, each evaluated from both of its cells) the normal-derivative
-    lines of both sides (2 n1^2 FMAs), 3 + 3 interpolations at n1 points
-    (6 n1^2 FMAs), the test sums (3 n1^2 FMAs) and ~60 flops of geometry per
-    point; the edge terms' scatter (~8 n1^2): 16 n1^3 + 126 n1^2 + 240 n1."""
+    per cell (n1 = k+1 Gauss points per direction; geometry precomputed):
+    4 sum-factorization stages of 2 n1^3 FMAs (reference gradients and their
+    transposes) = 16 n1^3 flops; the metric at n1^2 points (6 each); per edge
+    (4, each evaluated from both of its cells) the normal-derivative lines of
+    both sides (2 n1^2 FMAs), 3 + 3 interpolations at n1 points (6 n1^2 FMAs)
+    and ~17 flops of coefficients per point, the test sums (3 n1^2 FMAs); the
+    edge terms' scatter (~10 n1^2): 16 n1^3 + 104 n1^2 + 68 n1."""
     n1 = k + 1
-    return num_cells(ncells) * (16 * n1 ** 3 + 126 * n1 ** 2 + 240 * n1) * nrhs
+    return num_cells(ncells) * (16 * n1 ** 3 + 104 * n1 ** 2 + 68 * n1) * nrhs
 
 
 def mapped_operator_bytes(ncells, k, nrhs=1):
-    """Minimal HBM traffic: read u, write A u, read the vertex array once."""
+    """Minimal HBM traffic: read u, write A u, read the per-cell geometry
+    (3 n1^2 + 8 n1 + 8 doubles)."""
     nx, ny = ncells
-    return 16 * nx * ny * (k + 1) ** 2 * nrhs + 16 * (nx + 1) * (ny + 1)
+    n1 = k + 1
+    return nx * ny * (16 * n1 ** 2 * nrhs + 8 * (3 * n1 ** 2 + 8 * n1 + 8))
 
 
 def transfer_flops(coarse_ncells, k, d=3, nrhs=1):
@@ -134,24 +136,11 @@ def fractional_iterations(hist, rtol):
 def cg_energy_errors(prob, b, rtol=1e-8, ref_rtol=1e-14, maxit=200):
     """Energy norms ||x* - x_k||_A of the PCG iterates k = 0, 1, ... on the
     finest level (Sec. 2.4 measures CG by these) until the first one at or
-    below rtol ||x*||_A: x* from PCG to ref_rtol, x_k as the iterate after k
-    steps (PCG from x_0 = 0 is deterministic, so the run with maxit = k stops
-    at the k-th iterate of the long run).  The V-cycle must be set up (FP64)."""
+    below rtol ||x*||_A: x* from PCG to ref_rtol, then one PCG run that
+    records the errors on the device (tpss_pcg_energy_errors).  The V-cycle
+    must be set up (FP64)."""
     import torch
-    L = prob.nlevels - 1
     xs = torch.empty_like(b)
     prob.pcg_solve(b, xs, rtol=ref_rtol, maxit=maxit)
-    Ae = torch.empty_like(b)
-
-    def enorm(e):
-        prob.apply_operator(L, e, Ae)
-        return float(torch.dot(e, Ae).clamp_min(0.0).sqrt())
-
-    errs = [enorm(xs)]
     x = torch.empty_like(b)
-    for k in range(1, maxit + 1):
-        prob.pcg_solve(b, x, rtol=1e-300, maxit=k)
-        errs.append(enorm(xs - x))
-        if errs[-1] <= rtol * errs[0]:
-            break
-    return errs
+    return prob.pcg_energy_errors(b, xs, x, rtol=rtol, maxit=maxit)

@@ -84,6 +84,7 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_int)],
     "tpss_pcg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                        _VP],
+    "tpss_pcg_energy_errors": [_VP, _VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP],
     "tpss_gmres_solve": [_VP, _VP, _VP, _D, _I, _I, _I, ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(ctypes.c_double), _VP],
     "tpss_batch_create": [ctypes.POINTER(ProblemDesc), _I, _I, ctypes.POINTER(MGParams), _I, _VP,
@@ -280,6 +281,17 @@ class Problem:
         a, b, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         _check(lib().tpss_coarse_chebyshev_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m)))
         return {"a": a.value, "b": b.value, "steps": m.value}
+    def pcg_energy_errors(self, b, xs, x, rtol=1e-8, maxit=200):
+        """||x_k - xs||_A of the PCG iterates in one run (tpss_pcg_energy_errors)."""
+        n = self.ndofs(self.nlevels - 1)
+        cnt = ctypes.c_int()
+        errs = (ctypes.c_double * (maxit + 1))()
+        st = lib().tpss_pcg_energy_errors(self.h, _ptr(b, torch.float64, n), _ptr(xs, torch.float64, n),
+                                          _ptr(x, torch.float64, n), rtol, maxit, ctypes.byref(cnt),
+                                          ctypes.cast(errs, ctypes.c_void_p))
+        _check(st, allow=(TPSS_OK, TPSS_ENOTCONV))
+        return list(errs[:cnt.value])
+
     def pcg_solve(self, b, x, rtol=1e-8, maxit=200, history=False):
         n = self.ndofs(self.nlevels - 1)
         it, rel = ctypes.c_int(), ctypes.c_double()

@@ -105,3 +105,34 @@ def test_2d_fractional_iterations_match_paper(k, L, smoother, paper, left):
     nu = perf.fractional_iterations(res["history"], 1e-8)
     assert abs(nu - paper) < (0.2 if left else 0.6), nu
     prob.close()
+
+
+@pytest.mark.parametrize("mapped", [False, True])
+def test_energy_errors_in_one_run_equal_the_reruns(mapped):
+    """tpss_pcg_energy_errors records ||x_k - x*||_A inside one PCG run; PCG from
+    x_0 = 0 is deterministic, so the k-th value equals that of a separate run
+    stopped after k steps (the way it is computed without the entry point)."""
+    if mapped:
+        prob = tpss.Problem.mapped(3, workloads.vertices_distorted(4, 3), nlevels=3, gamma_hat=4.0)
+        prob.mg_setup("ACS", 0.5, tpss.FP64)
+    else:
+        prob = tpss.Problem(3, 2, workloads.widths_uniform(2, 3), nlevels=3)
+        prob.mg_setup("ACS", 0.7, tpss.FP64)
+    L = prob.nlevels - 1
+    b = torch.empty(prob.ndofs(L), dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(L, 0, b)
+    xs, x = torch.empty_like(b), torch.empty_like(b)
+    prob.pcg_solve(b, xs, rtol=1e-14, maxit=200)
+    errs = prob.pcg_energy_errors(b, xs, x, rtol=1e-8, maxit=200)
+    Ae = torch.empty_like(b)
+    for k in range(len(errs)):
+        if k == 0:
+            e = xs.clone()
+        else:
+            prob.pcg_solve(b, x, rtol=1e-300, maxit=k)
+            e = xs - x
+        prob.apply_operator(L, e, Ae)
+        ref = float(torch.dot(e, Ae).clamp_min(0.0).sqrt())
+        assert abs(errs[k] - ref) <= 1e-9 * errs[0], (k, errs[k], ref)
+    assert errs[-1] <= 1e-8 * errs[0] < errs[-2]
+    prob.close()
