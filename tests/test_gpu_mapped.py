@@ -92,7 +92,7 @@ def test_surrogate_1d_data_per_cell(k):
     for c in (0, 3, 7, 12, 19):
         i, j = c % 5, c // 5
         (A0, M0, Z0, l0), (A1, M1, Z1, l1) = P.eigendata(0, c), P.eigendata(1, c)
-        ref = surrogate_cell_matrix(V0, i, j, k, 4.0)
+        ref = surrogate_cell_matrix(V0, (i, j), k, 4.0)
         assert rel_err(np.kron(M1, A0) + np.kron(A1, M0), ref) < 1e-12
         for A, M, Z, lam in ((A0, M0, Z0, l0), (A1, M1, Z1, l1)):
             assert np.allclose(Z.T @ M @ Z, np.eye(n1), atol=1e-10)

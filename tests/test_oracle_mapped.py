@@ -7,8 +7,8 @@ import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import multigrid, schwarz
-from oracle.mapped import (MappedHierarchy, MappedSIPG, bilinear_map, exact_solvers, refine, surrogate_cell_matrix,
-                           surrogate_solvers, surrogate_widths)
+from oracle.mapped import (MappedHierarchy, MappedSIPG, dlinear_map, exact_solvers, jacobians, refine,
+                           surrogate_cell_matrix, surrogate_solvers, surrogate_widths)
 from oracle.mesh import TensorMesh
 from oracle.sipg import SIPG
 from paper_1910_11239_gb300.workloads import vertices_cartesian as cartesian_vertices
@@ -111,14 +111,14 @@ def test_refinement_nests_the_bilinear_maps():
         for i in range(3):
             for sy in range(2):
                 for sx in range(2):
-                    child = bilinear_map(F, 2 * i + sx, 2 * j + sy, xi)
-                    parent = bilinear_map(V, i, j, (xi + np.array([sx, sy])) / 2)
+                    child = dlinear_map(F, (2 * i + sx, 2 * j + sy), xi)
+                    parent = dlinear_map(V, (i, j), (xi + np.array([sx, sy])) / 2)
                     assert np.allclose(child, parent, atol=1e-15)
 
 
 def test_surrogate_widths_are_the_mean_edge_lengths():
     V = np.array([[[0.0, 0.0], [2.0, 0.0]], [[0.0, 1.0], [3.0, 5.0]]])
-    h0, h1 = surrogate_widths(V, 0, 0)
+    h0, h1 = surrogate_widths(V, (0, 0))
     assert h0 == pytest.approx((2.0 + 5.0) / 2) and h1 == pytest.approx((1.0 + np.hypot(1.0, 5.0)) / 2)
 
 
@@ -129,8 +129,8 @@ def test_surrogate_of_a_cartesian_cell_is_the_exact_local_matrix():
     S = MappedSIPG(V, 3, 4.0)
     A = S.assemble().tocsr()
     for (i, j) in [(0, 0), (1, 1), (3, 2), (2, 0)]:
-        idx = schwarz.patch_dofs([S.cell_index(i, j)], S.nloc)
-        assert np.allclose(surrogate_cell_matrix(V, i, j, 3, 4.0), A[idx][:, idx].toarray(), rtol=1e-12, atol=1e-10)
+        idx = schwarz.patch_dofs([S.cell_index((i, j))], S.nloc)
+        assert np.allclose(surrogate_cell_matrix(V, (i, j), 3, 4.0), A[idx][:, idx].toarray(), rtol=1e-12, atol=1e-10)
 
 
 def test_surrogate_is_the_rectangle_of_mean_widths_on_a_distorted_cell():
@@ -139,10 +139,10 @@ def test_surrogate_is_the_rectangle_of_mean_widths_on_a_distorted_cell():
     is hbar_1/hbar_0 Lhat x Mhat + hbar_0/hbar_1 Mhat x Lhat, so two cells with
     equal mean widths have equal surrogates wherever their neighbours agree."""
     V = distorted_vertices(4, seed=8)
-    B = surrogate_cell_matrix(V, 1, 2, 2, 4.0)
-    h0, h1 = surrogate_widths(V, 1, 2)
-    wx = [surrogate_widths(V, i, 2)[0] for i in (0, 1, 2)]
-    wy = [surrogate_widths(V, 1, j)[1] for j in (1, 2, 3)]
+    B = surrogate_cell_matrix(V, (1, 2), 2, 4.0)
+    h0, h1 = surrogate_widths(V, (1, 2))
+    wx = [surrogate_widths(V, (i, 2))[0] for i in (0, 1, 2)]
+    wy = [surrogate_widths(V, (1, j))[1] for j in (1, 2, 3)]
     assert wx[1] == h0 and wy[1] == h1
     C = SIPG(TensorMesh([np.array(wx), np.array(wy)]), 2, 4.0).assemble([4]).toarray()
     assert np.allclose(B, C, rtol=1e-13, atol=1e-12)
@@ -183,3 +183,101 @@ def test_inexact_solvers_converge_with_damping_below_one():
         assert np.linalg.norm(b - H.A[-1] @ x) <= 1e-8 * np.linalg.norm(b) * 1.01
         its[local] = multigrid.fractional_iterations(hist, 1e-8)
     assert its["exact"] < its["surrogate"] < 1.8 * its["exact"], its
+
+
+# ------------------------------------------------------------------- 3D
+@pytest.mark.parametrize("k,gamma_hat", [(1, 1.0), (2, 4.0)])
+def test_cartesian_vertices_give_the_tensor_assembly_3d(k, gamma_hat):
+    rng = np.random.default_rng(20 + k)
+    w = [rng.uniform(0.5, 1.5, 2), rng.uniform(0.5, 1.5, 3), rng.uniform(0.5, 1.5, 2)]
+    A = MappedSIPG(cartesian_vertices(*w), k, gamma_hat).assemble()
+    B = SIPG(TensorMesh(w), k, gamma_hat).assemble()
+    assert abs(A - B).max() <= 1e-11 * abs(B).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_polynomials_are_reproduced_on_affine_hexahedra(k):
+    V = cartesian_vertices(*[np.full(2, 0.5)] * 3)
+    F = np.array([[1.1, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.05]])
+    S = MappedSIPG(V @ F.T + np.array([0.2, -0.1, 0.3]), k, gamma_hat=4.0)
+    A = S.assemble()
+    coef = {(a, b, c): (-1) ** (a + b + c) * (0.5 + 0.1 * a + 0.07 * b - 0.05 * c)
+            for a in range(k + 1) for b in range(k + 1 - a) for c in range(k + 1 - a - b)}
+    u = lambda p: sum(v * p[:, 0] ** a * p[:, 1] ** b * p[:, 2] ** c for (a, b, c), v in coef.items())
+
+    def lap(p):
+        out = np.zeros(len(p))
+        for (a, b, c), v in coef.items():
+            if a >= 2:
+                out += v * a * (a - 1) * p[:, 0] ** (a - 2) * p[:, 1] ** b * p[:, 2] ** c
+            if b >= 2:
+                out += v * b * (b - 1) * p[:, 0] ** a * p[:, 1] ** (b - 2) * p[:, 2] ** c
+            if c >= 2:
+                out += v * c * (c - 1) * p[:, 0] ** a * p[:, 1] ** b * p[:, 2] ** (c - 2)
+        return out
+
+    b = S.rhs(lambda p: -lap(p), u)
+    assert np.abs(A @ S.interpolate(u) - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_linear_functions_are_reproduced_on_distorted_hexahedra():
+    """A linear u is trilinear in the reference coordinates of every cell: it lies
+    in the mapped Q_1 space and is reproduced (operator's rule for the boundary terms)."""
+    S = MappedSIPG(distorted_vertices(3, seed=4, dim=3), 1, gamma_hat=4.0)
+    A = S.assemble()
+    u = lambda p: 0.3 - 1.1 * p[:, 0] + 0.6 * p[:, 1] + 0.9 * p[:, 2]
+    b = S.rhs(lambda p: np.zeros(len(p)), u, nq=2)
+    assert np.abs(A @ S.interpolate(u) - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_symmetric_positive_definite_3d():
+    S = MappedSIPG(distorted_vertices(2, seed=5, dim=3), 2, gamma_hat=4.0)
+    A = S.assemble().toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A)[0] > 0.0
+
+
+def test_refinement_nests_the_trilinear_maps():
+    V = distorted_vertices(2, seed=6, dim=3)
+    F = refine(V)
+    xi = np.random.default_rng(1).uniform(0, 1, (5, 3))
+    for c in range(8):
+        m = (c & 1, (c >> 1) & 1, c >> 2)
+        for s in range(8):
+            o = np.array([s & 1, (s >> 1) & 1, s >> 2])
+            child = dlinear_map(F, tuple(2 * np.array(m) + o), xi)
+            assert np.allclose(child, dlinear_map(V, m, (xi + o) / 2), atol=1e-15)
+
+
+def test_face_normals_and_measures_of_a_sheared_cube():
+    """Nanson's formula on an affine cell: the face of the parallelepiped spanned by
+    the columns of F at xi_2 = 1 has the normal (F e_0 x F e_1)/|..| and area |F e_0 x F e_1|."""
+    F = np.array([[1.0, 0.4, 0.1], [0.2, 1.3, -0.3], [0.0, 0.25, 0.8]])
+    V = cartesian_vertices(*[np.ones(1)] * 3) @ F.T
+    S = MappedSIPG(V, 2)
+    xi, W, n, area = S._face((0, 0, 0), 2, 1)
+    cr = np.cross(F[:, 0], F[:, 1])
+    assert np.allclose(n, cr / np.linalg.norm(cr)) and area == pytest.approx(np.linalg.norm(cr))
+    assert np.allclose(jacobians(V, (0, 0, 0), xi), F)
+
+
+def test_surrogate_of_a_cartesian_hexahedron_is_the_exact_block():
+    rng = np.random.default_rng(9)
+    w = [rng.uniform(0.5, 1.5, 3), rng.uniform(0.5, 1.5, 2), rng.uniform(0.5, 1.5, 2)]
+    V = cartesian_vertices(*w)
+    S = MappedSIPG(V, 2, 4.0)
+    A = S.assemble().tocsr()
+    for m in [(0, 0, 0), (1, 1, 0), (2, 0, 1)]:
+        idx = schwarz.patch_dofs([S.cell_index(m)], S.nloc)
+        assert np.allclose(surrogate_cell_matrix(V, m, 2, 4.0), A[idx][:, idx].toarray(), rtol=1e-12, atol=1e-10)
+    h = surrogate_widths(distorted_vertices(2, seed=3, dim=3), (1, 0, 1))
+    assert len(h) == 3 and all(0.3 < x < 0.8 for x in h)
+
+
+def test_hierarchy_on_cartesian_vertices_is_the_cartesian_vcycle_3d():
+    rng = np.random.default_rng(8)
+    widths = [rng.uniform(0.5, 1.5, 2) for _ in range(3)]
+    H = MappedHierarchy(cartesian_vertices(*widths), 1, 2, "MCS", 1.0, steps=1, gamma_hat=4.0)
+    C = multigrid.Hierarchy(widths, 1, 2, "MCS", 1.0, gamma_hat=4.0)
+    r = rng.uniform(-1, 1, H.A[-1].shape[0])
+    assert np.allclose(H.precondition(r), C.precondition(r), rtol=1e-10, atol=1e-12)
