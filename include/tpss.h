@@ -78,36 +78,39 @@ typedef struct {
 typedef struct tpss_ctx tpss_ctx;
 typedef struct tpss_patches tpss_patches;
 
-/* ------------------------------------------- meshes of quadrilaterals --
- * Sec. 4: a 2D mesh of bilinear quadrilaterals given by a structured
- * (nx+1) x (ny+1) vertex array, `vertices` a HOST array of (x, y) pairs with
- * the x index fastest: vertex (i, j) at vertices[2 (j (nx+1) + i)].  Cell
- * (i, j), numbered i + nx j, has the corners (i, j), (i+1, j), (i, j+1),
- * (i+1, j+1) at the reference corners (0,0), (1,0), (0,1), (1,1); every cell
- * must be convex and counter-clockwise (TPSS_EINVAL otherwise).  Level l+1
- * splits every cell of level l at its reference midpoints (edge midpoints
- * and the mean of the four corners as new vertices), so the spaces are
- * nested and the transfers are those of Cartesian meshes.
- * Operator: eq. bfsipg on the mapped cells (gradients through J^{-T}, the
- * edges' unit normals, the paper's 1/sqrt(2) averages), penalty of
- * eq. penalty with h^+- = |K^+-| / |e|; the paper takes gamma_hat = 4 on its
- * 25%-distorted meshes (Sec. 4).  FP64, degree 1..7.
- * Cell patches (tpss_setup_patches with TPSS_CELL, FP64) use the inexact
- * local solvers of eq. schwarzproj on the Cartesian surrogate of each cell
- * (eq. avglength: mean lengths of opposite edges, the neighbours' surrogate
- * widths across its faces), by fast diagonalization per cell.
+/* --------------------------------------------------------- mapped meshes --
+ * Sec. 4: a mesh of bilinear quadrilaterals (dim 2) or trilinear hexahedra
+ * (dim 3) given by a structured vertex array with ncells[t] + 1 vertices
+ * along t: `vertices` is a HOST array of dim-tuples with the x index fastest,
+ * vertex (i, j[, l]) at vertices[dim (i + (ncells[0]+1) (j + (ncells[1]+1) l))]
+ * (ncells[2] ignored for dim 2).  Cell (i, j[, l]), numbered i + ncells[0]
+ * (j + ncells[1] l), has the corners c = a0 + 2 a1 [+ 4 a2] at vertex
+ * (i + a0, j + a1[, l + a2]) and reference corner (a0, a1[, a2]); every cell
+ * must have det J > 0 at its corners (in 2D: convex, counter-clockwise;
+ * TPSS_EINVAL otherwise).  Level l+1 splits every cell of level l at its
+ * reference midpoints (the new vertices are means of 2, 4 or 8 old ones),
+ * so the spaces are nested and the transfers are those of Cartesian meshes.
+ * Operator: eq. bfsipg on the mapped cells (gradients through J^{-T}, outward
+ * unit normals J^{-T} e_t / |J^{-T} e_t| and Nanson's surface element, the
+ * paper's 1/sqrt(2) averages), penalty of eq. penalty with h^+- = |K^+-| / |e|;
+ * the paper takes gamma_hat = 4 on its 25%-distorted meshes.  FP64, degree
+ * 1..7.  Cell patches (tpss_setup_patches with TPSS_CELL, FP64) use the
+ * inexact local solvers of eq. schwarzproj on the Cartesian surrogate of each
+ * cell (eq. avglength: widths = mean lengths of the cell's edges per
+ * direction, the neighbours' surrogate widths across its faces), by fast
+ * diagonalization per cell.
  * Not available on these contexts (TPSS_EINVAL): vertex patches, FP32 / TF32
  * / BF16 operators and smoothers, tpss_ir_solve, kind 1 of
- * tpss_assemble_rhs, the per-color residual update of MCS (the full
- * residual is recomputed) and the fast-diagonalization coarse solver.
- * Every other call of this header works as on Cartesian contexts;
- * tpss_mg_setup's AUTO coarse solver takes the Chebyshev iteration above
- * 4096 coarse DoFs.  Release with tpss_destroy. */
-tpss_status tpss_create_mapped(int degree, int nx, int ny, const double* vertices, int nlevels, double gamma_hat,
-                               int penalty_poly, void* cuda_stream, tpss_ctx** out);
+ * tpss_assemble_rhs (kind 0 is f = d pi^2 prod sin(pi x_t), g = 0), the
+ * per-color residual update of MCS (the full residual is recomputed) and the
+ * fast-diagonalization coarse solver.  Every other call of this header works
+ * as on Cartesian contexts; tpss_mg_setup's AUTO coarse solver takes the
+ * Chebyshev iteration above 4096 coarse DoFs.  Release with tpss_destroy. */
+tpss_status tpss_create_mapped(int dim, int degree, const int ncells[3], const double* vertices, int nlevels,
+                               double gamma_hat, int penalty_poly, void* cuda_stream, tpss_ctx** out);
 
-/* Copy level `level`'s vertex array ((nc0+1)(nc1+1) (x, y) pairs) to the HOST
- * array `vertices`.  TPSS_EINVAL on a Cartesian context. */
+/* Copy level `level`'s vertex array (prod_t (nc_t + 1) dim-tuples, x index
+ * fastest) to the HOST array `vertices`.  TPSS_EINVAL on a Cartesian context. */
 tpss_status tpss_mapped_vertices(const tpss_ctx* ctx, int level, double* vertices);
 
 /* Create a context: copies the description, runs the 1D setup kernels (Gauss-

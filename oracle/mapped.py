@@ -202,7 +202,7 @@ class MappedSIPG:
         J = jacobians(self.V, multi, xi)
         Jinv = np.linalg.inv(J)                               # [Q, d, d]
         # grad phi = J^{-T} grad_ref phi: (J^{-T})[r, c] = Jinv[c, r]
-        return np.einsum("qcr,qic->qir", Jinv, G), np.abs(np.linalg.det(J))
+        return np.einsum("qcr,qic->qir", Jinv, G, optimize=True), np.abs(np.linalg.det(J))
 
     def volume(self, multi):
         q, w = self._tensor_points(self.qx, self.qw, self.d)
@@ -212,7 +212,7 @@ class MappedSIPG:
         q, w = self._tensor_points(self.qx, self.qw, self.d)
         _, G = self._basis(q)
         Gp, detj = self._physical_gradients(multi, q, G)
-        return np.einsum("q,qir,qjr->ij", w * detj, Gp, Gp)
+        return np.einsum("q,qir,qjr->ij", w * detj, Gp, Gp, optimize=True)
 
     def _face(self, multi, t, side, x=None, w=None):
         """Reference points on face (t, side) (the other coordinates a tensor
@@ -261,9 +261,9 @@ class MappedSIPG:
                 un = val[T][:, :, None] * normal[T][:, None, :] / SQRT2
                 vn = val[S][:, :, None] * normal[S][:, None, :] / SQRT2
                 gu, gv = grad[T] / SQRT2, grad[S] / SQRT2
-                blocks[(S, T)] = (gam * np.einsum("q,qir,qjr->ji", W, un, vn)
-                                  - np.einsum("q,qir,qjr->ji", W, gu, vn)
-                                  - np.einsum("q,qir,qjr->ji", W, un, gv))
+                blocks[(S, T)] = (gam * np.einsum("q,qir,qjr->ji", W, un, vn, optimize=True)
+                                  - np.einsum("q,qir,qjr->ji", W, gu, vn, optimize=True)
+                                  - np.einsum("q,qir,qjr->ji", W, un, gv, optimize=True))
         return blocks
 
     def boundary_face_block(self, multi, t, side):
@@ -272,8 +272,8 @@ class MappedSIPG:
         P, G = self._basis(xi)
         Gp, _ = self._physical_gradients(multi, xi, G)
         un = P[:, :, None] * n[:, None, :]
-        return (gam * np.einsum("q,qir,qjr->ji", W, un, un) - np.einsum("q,qir,qjr->ji", W, Gp, un)
-                - np.einsum("q,qir,qjr->ji", W, un, Gp))
+        return (gam * np.einsum("q,qir,qjr->ji", W, un, un, optimize=True) - np.einsum("q,qir,qjr->ji", W, Gp, un, optimize=True)
+                - np.einsum("q,qir,qjr->ji", W, un, Gp, optimize=True))
 
     def assemble(self):
         n = self.nloc
@@ -349,7 +349,7 @@ class MappedSIPG:
                     Pe, Ge = self._basis(xi)
                     Gp, _ = self._physical_gradients(m, xi, Ge)
                     gv = g(dlinear_map(self.V, m, xi))
-                    acc += Pe.T @ (W * gam * gv) - np.einsum("q,qir,qr->i", W * gv, Gp, n)
+                    acc += Pe.T @ (W * gam * gv) - np.einsum("q,qir,qr->i", W * gv, Gp, n, optimize=True)
             out[c * self.nloc:(c + 1) * self.nloc] = acc
         return out
 

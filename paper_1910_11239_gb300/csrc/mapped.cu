@@ -424,6 +424,7 @@ static double penalty_prefactor(const tpss_ctx* ctx) {
 }
 
 tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs) {
+  if (ctx->dim == 3) return mapped3_apply(ctx, level, nrhs, u, out, rhs);
   const Level& L = ctx->levels[level];
   MappedOpArgs a{};
   a.u = u;
@@ -466,13 +467,13 @@ __global__ void surrogate_widths_kernel(const double2* __restrict__ V, int nx, i
 // 1D matrices of cell c's surrogate along t: width hbar_t(c), neighbours'
 // hbar_t across the faces normal to t
 __global__ void surrogate_op1d_kernel(const Basis1D* __restrict__ B, const double* __restrict__ w, int nx, int ny,
-                                      int t, double gpk, double* __restrict__ M, double* __restrict__ A) {
+                                      int nz, int t, double gpk, double* __restrict__ M, double* __restrict__ A) {
   const int n1 = B->n1;
   const int64_t c = blockIdx.x;
-  const int i = (int)(c % nx), j = (int)(c / nx);
-  const bool has_l = t == 0 ? i > 0 : j > 0;
-  const bool has_r = t == 0 ? i + 1 < nx : j + 1 < ny;
-  const int64_t step = t == 0 ? 1 : nx;
+  const int ci[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((int64_t)nx * ny))};
+  const int nc[3] = {nx, ny, nz};
+  const bool has_l = ci[t] > 0, has_r = ci[t] + 1 < nc[t];
+  const int64_t step = t == 0 ? 1 : t == 1 ? nx : (int64_t)nx * ny;
   const double h = w[c];
   const double hl = has_l ? w[c - step] : h, hr = has_r ? w[c + step] : h;
   for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x)
@@ -492,29 +493,35 @@ __global__ void inv_table_cells_kernel(const double* __restrict__ l0, const doub
 
 tpss_status mapped_cell_eigendata(tpss_ctx* ctx, tpss_patches* P, int* d_err) {
   const Level& L = ctx->levels[P->level];
-  const int n = ctx->n1, nx = L.nc[0], ny = L.nc[1];
+  const int n = ctx->n1, nx = L.nc[0], ny = L.nc[1], d = ctx->dim;
   const int64_t nc = L.ncells;
-  const double2* V = reinterpret_cast<const double2*>(L.d_verts);
   double* hb = nullptr;
-  TPSS_TRY(dalloc_t(&hb, 2 * (size_t)nc));
+  TPSS_TRY(dalloc_t(&hb, (size_t)d * nc));
   tpss_status st = TPSS_OK;
-  const int gb = (int)std::min<int64_t>((nc + 255) / 256, 4096);
-  surrogate_widths_kernel<<<gb, 256, 0, ctx->stream>>>(V, nx, ny, hb, hb + nc);
-  for (int t = 0; t < 2 && st == TPSS_OK; ++t) {
+  if (d == 3) {
+    st = mapped3_surrogate_widths(ctx, P->level, hb);
+  } else {
+    const int gb = (int)std::min<int64_t>((nc + 255) / 256, 4096);
+    surrogate_widths_kernel<<<gb, 256, 0, ctx->stream>>>(reinterpret_cast<const double2*>(L.d_verts), nx, ny, hb,
+                                                         hb + nc);
+  }
+  for (int t = 0; t < d && st == TPSS_OK; ++t) {
     if ((st = dalloc_t(&P->d_A[t], (size_t)nc * n * n)) != TPSS_OK) break;
     if ((st = dalloc_t(&P->d_M[t], (size_t)nc * n * n)) != TPSS_OK) break;
     if ((st = dalloc_t(&P->d_Z[t], (size_t)nc * n * n)) != TPSS_OK) break;
     if ((st = dalloc_t(&P->d_lam[t], (size_t)nc * n)) != TPSS_OK) break;
-    surrogate_op1d_kernel<<<(unsigned)nc, 64, 0, ctx->stream>>>(ctx->d_basis, hb + t * nc, nx, ny, t,
+    surrogate_op1d_kernel<<<(unsigned)nc, 64, 0, ctx->stream>>>(ctx->d_basis, hb + t * nc, nx, ny, L.nc[2], t,
                                                                 penalty_prefactor(ctx), P->d_M[t], P->d_A[t]);
     const int warps = 4;
     const size_t smem = (size_t)warps * 3 * n * n * sizeof(double);
     gen_eig_kernel<<<(unsigned)((nc + warps - 1) / warps), warps * 32, smem, ctx->stream>>>(
         P->d_A[t], P->d_M[t], (int)nc, n, P->d_Z[t], P->d_lam[t], d_err);
   }
-  if (st == TPSS_OK) st = dalloc_t(&P->d_inv, (size_t)nc * n * n);
-  if (st == TPSS_OK)
-    inv_table_cells_kernel<<<2048, 256, 0, ctx->stream>>>(P->d_lam[0], P->d_lam[1], n, nc, P->d_inv);
+  if (st == TPSS_OK) st = dalloc_t(&P->d_inv, (size_t)nc * (d == 3 ? n * n * n : n * n));
+  if (st == TPSS_OK) {
+    if (d == 3) st = mapped3_inv_table(ctx, P);
+    else inv_table_cells_kernel<<<2048, 256, 0, ctx->stream>>>(P->d_lam[0], P->d_lam[1], n, nc, P->d_inv);
+  }
   cudaError_t e = cudaGetLastError();
   cudaStreamSynchronize(ctx->stream);   // hb is freed below
   dfree(hb);
@@ -569,7 +576,8 @@ __global__ void mapped_rhs_kernel(const Basis1D* __restrict__ B, const double2* 
 }
 
 tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b) {
-  TPSS_REQUIRE(kind == 0, "tpss_assemble_rhs: meshes of quadrilaterals support kind 0 only");
+  TPSS_REQUIRE(kind == 0, "tpss_assemble_rhs: mapped meshes support kind 0 only");
+  if (ctx->dim == 3) return mapped3_rhs(ctx, level, b);
   const Level& L = ctx->levels[level];
   const int nq = ctx->n1 + 1;
   const size_t smem = (size_t)(nq * nq + ctx->n1 * nq) * sizeof(double);
@@ -583,45 +591,66 @@ tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b) {
 
 using namespace tpss;
 
-extern "C" tpss_status tpss_create_mapped(int degree, int nx, int ny, const double* vertices, int nlevels,
-                                          double gamma_hat, int penalty_poly, void* cuda_stream, tpss_ctx** out) {
-  clear_error();
-  TPSS_REQUIRE(vertices && out, "tpss_create_mapped: null argument");
-  *out = nullptr;
-  TPSS_REQUIRE(degree >= 1 && degree <= kMaxMappedDegree, "tpss_create_mapped: degree must be in 1..7");
-  TPSS_REQUIRE(nx >= 1 && ny >= 1, "tpss_create_mapped: nx and ny must be >= 1");
-  TPSS_REQUIRE(nlevels >= 1 && nlevels <= 12, "tpss_create_mapped: nlevels must be in 1..12");
-  TPSS_REQUIRE(((long long)nx << (nlevels - 1)) <= 1024 && ((long long)ny << (nlevels - 1)) <= 1024,
-               "tpss_create_mapped: at most 1024 cells per direction on the finest level");
-  const int sx = nx + 1;
-  for (int i = 0; i < 2 * sx * (ny + 1); ++i)
-    TPSS_REQUIRE(std::isfinite(vertices[i]), "tpss_create_mapped: vertices must be finite");
-  // every cell positively oriented and convex: det J > 0 at its four corners
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      auto P = [&](int a, int b) { return &vertices[2 * ((j + b) * sx + i + a)]; };
-      const double* c[4] = {P(0, 0), P(1, 0), P(0, 1), P(1, 1)};
-      // corner (a, b): J columns along the two edges leaving it (into the cell)
-      const int ca[4] = {0, 1, 0, 1}, cb[4] = {0, 0, 1, 1};
-      for (int q = 0; q < 4; ++q) {
-        const double* o = c[q];
-        const double* ea = c[(1 - ca[q]) + 2 * cb[q]];
-        const double* eb = c[ca[q] + 2 * (1 - cb[q])];
-        const double sa = ca[q] ? -1.0 : 1.0, sb = cb[q] ? -1.0 : 1.0;
-        const double det = sa * sb * ((ea[0] - o[0]) * (eb[1] - o[1]) - (ea[1] - o[1]) * (eb[0] - o[0]));
-        TPSS_REQUIRE(det > 0.0, "tpss_create_mapped: cells must be convex and counter-clockwise "
-                                "(v0, v1, v3, v2)");
+// J of the d-linear map at reference point xi (host, for the validity check)
+static double host_det(int d, const double* const* c, const double* xi) {
+  double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < (1 << d); ++k)
+    for (int s2 = 0; s2 < d; ++s2) {
+      double g = 1.0;
+      for (int t = 0; t < d; ++t) {
+        const int a = (k >> t) & 1;
+        g *= t == s2 ? (a ? 1.0 : -1.0) : (a ? xi[t] : 1.0 - xi[t]);
       }
+      for (int r = 0; r < d; ++r) J[d * r + s2] += c[k][r] * g;
     }
-  std::vector<double> wx(nx, 1.0 / nx), wy(ny, 1.0 / ny);
+  if (d == 2) return J[0] * J[3] - J[1] * J[2];
+  return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+extern "C" tpss_status tpss_create_mapped(int dim, int degree, const int ncells[3], const double* vertices,
+                                          int nlevels, double gamma_hat, int penalty_poly, void* cuda_stream,
+                                          tpss_ctx** out) {
+  clear_error();
+  TPSS_REQUIRE(vertices && out && ncells, "tpss_create_mapped: null argument");
+  *out = nullptr;
+  TPSS_REQUIRE(dim == 2 || dim == 3, "tpss_create_mapped: dim must be 2 or 3");
+  TPSS_REQUIRE(degree >= 1 && degree <= kMaxMappedDegree, "tpss_create_mapped: degree must be in 1..7");
+  TPSS_REQUIRE(nlevels >= 1 && nlevels <= 12, "tpss_create_mapped: nlevels must be in 1..12");
+  int nc[3] = {1, 1, 1};
+  size_t nverts = 1;
+  for (int t = 0; t < dim; ++t) {
+    nc[t] = ncells[t];
+    TPSS_REQUIRE(nc[t] >= 1, "tpss_create_mapped: ncells must be >= 1");
+    TPSS_REQUIRE(((long long)nc[t] << (nlevels - 1)) <= 1024,
+                 "tpss_create_mapped: at most 1024 cells per direction on the finest level");
+    nverts *= (size_t)(nc[t] + 1);
+  }
+  for (size_t i = 0; i < (size_t)dim * nverts; ++i)
+    TPSS_REQUIRE(std::isfinite(vertices[i]), "tpss_create_mapped: vertices must be finite");
+  // every cell positively oriented: det J > 0 at its 2^d corners (for d = 2
+  // this is convexity with the corners v0, v1, v3, v2 counter-clockwise)
+  const int sx = nc[0] + 1, sy = nc[1] + 1;
+  for (int l = 0; l < nc[2]; ++l)
+    for (int j = 0; j < nc[1]; ++j)
+      for (int i = 0; i < nc[0]; ++i) {
+        const double* c[8];
+        for (int k = 0; k < (1 << dim); ++k)
+          c[k] = &vertices[(size_t)dim * (((size_t)(l + (k >> 2)) * sy + (j + ((k >> 1) & 1))) * sx + i + (k & 1))];
+        for (int k = 0; k < (1 << dim); ++k) {
+          const double xi[3] = {(double)(k & 1), (double)((k >> 1) & 1), (double)((k >> 2) & 1)};
+          TPSS_REQUIRE(host_det(dim, c, xi) > 0.0,
+                       "tpss_create_mapped: cells must be convex and positively oriented (det J > 0 at the corners)");
+        }
+      }
+  std::vector<double> w[3];
   tpss_problem_desc desc{};
-  desc.dim = 2;
+  desc.dim = dim;
   desc.degree = degree;
-  desc.ncells[0] = nx;
-  desc.ncells[1] = ny;
-  desc.ncells[2] = 1;
-  desc.widths[0] = wx.data();
-  desc.widths[1] = wy.data();
+  for (int t = 0; t < 3; ++t) {
+    desc.ncells[t] = nc[t];
+    w[t].assign(nc[t], 1.0 / nc[t]);
+    desc.widths[t] = w[t].data();
+  }
   desc.nlevels = nlevels;
   desc.gamma_hat = gamma_hat;
   desc.penalty_poly = penalty_poly;
@@ -635,22 +664,32 @@ extern "C" tpss_status tpss_create_mapped(int degree, int nx, int ny, const doub
   tpss_status st;
   for (int l = 0; l < nlevels; ++l) {
     Level& L = ctx->levels[l];
-    const size_t nv = (size_t)(L.nc[0] + 1) * (L.nc[1] + 1);
-    if ((st = dalloc_t(&L.d_verts, 2 * nv)) != TPSS_OK) return fail(st);
+    size_t nv = 1;
+    for (int t = 0; t < dim; ++t) nv *= (size_t)(L.nc[t] + 1);
+    if ((st = dalloc_t(&L.d_verts, dim * nv)) != TPSS_OK) return fail(st);
     if (l == 0) {
-      if (cudaMemcpyAsync(L.d_verts, vertices, 2 * nv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+      if (cudaMemcpyAsync(L.d_verts, vertices, dim * nv * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
           cudaSuccess) {
         set_error("tpss_create_mapped: vertex upload failed");
         return fail(TPSS_ECUDA);
       }
     } else {
       const Level& C = ctx->levels[l - 1];
-      refine_vertices_kernel<<<(unsigned)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, ctx->stream>>>(
-          reinterpret_cast<const double2*>(C.d_verts), C.nc[0], C.nc[1], reinterpret_cast<double2*>(L.d_verts));
+      if (dim == 3) {
+        if ((st = mapped3_refine(C.d_verts, C.nc[0], C.nc[1], C.nc[2], L.d_verts, ctx->stream)) != TPSS_OK)
+          return fail(st);
+      } else {
+        refine_vertices_kernel<<<(unsigned)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+            reinterpret_cast<const double2*>(C.d_verts), C.nc[0], C.nc[1], reinterpret_cast<double2*>(L.d_verts));
+      }
     }
   }
   for (int l = 0; l < nlevels; ++l) {
     Level& L = ctx->levels[l];
+    if (dim == 3) {
+      if ((st = mapped3_setup_level(ctx, l, penalty_prefactor(ctx))) != TPSS_OK) return fail(st);
+      continue;
+    }
     if ((st = dalloc_t(&L.d_geo, (size_t)L.ncells * GeoLayout(ctx->n1).G)) != TPSS_OK) return fail(st);
     mapped_geometry_kernel<<<(unsigned)L.ncells, 64, 0, ctx->stream>>>(
         ctx->d_basis, reinterpret_cast<const double2*>(L.d_verts), L.nc[0], L.nc[1], penalty_prefactor(ctx),
@@ -667,11 +706,13 @@ extern "C" tpss_status tpss_create_mapped(int degree, int nx, int ny, const doub
 extern "C" tpss_status tpss_mapped_vertices(const tpss_ctx* ctx, int level, double* vertices) {
   clear_error();
   TPSS_REQUIRE(ctx && vertices, "tpss_mapped_vertices: null argument");
-  TPSS_REQUIRE(ctx->mapped, "tpss_mapped_vertices: not a mesh of quadrilaterals");
+  TPSS_REQUIRE(ctx->mapped, "tpss_mapped_vertices: not a mapped mesh");
   TPSS_REQUIRE(level >= 0 && level < ctx->nlevels, "tpss_mapped_vertices: level out of range");
   const Level& L = ctx->levels[level];
-  const size_t nv = (size_t)(L.nc[0] + 1) * (L.nc[1] + 1);
-  TPSS_CHECK_CUDA(cudaMemcpyAsync(vertices, L.d_verts, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  size_t nv = 1;
+  for (int t = 0; t < ctx->dim; ++t) nv *= (size_t)(L.nc[t] + 1);
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(vertices, L.d_verts, ctx->dim * nv * sizeof(double), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
   TPSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   return TPSS_OK;
 }

@@ -279,11 +279,18 @@ template <typename T>
 tpss_status restrict_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* fine, T* coarse);
 
 // ---- mapped.cu (2D meshes of bilinear quadrilaterals, FP64)
-constexpr int kMaxMappedDegree = 7;
+constexpr int kMaxMappedDegree = 7;     // 2D and 3D mapped meshes
 tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs);
 // surrogate cell solvers: fills P->d_A, d_M, d_Z, d_lam (per cell) and d_inv
 tpss_status mapped_cell_eigendata(tpss_ctx* ctx, tpss_patches* P, int* d_err);
 tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b);
+// ---- mapped3.cu (3D meshes of trilinear hexahedra)
+tpss_status mapped3_refine(const double* coarse, int nx, int ny, int nz, double* fine, cudaStream_t s);
+tpss_status mapped3_setup_level(tpss_ctx* ctx, int level, double gpk);
+tpss_status mapped3_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs);
+tpss_status mapped3_surrogate_widths(tpss_ctx* ctx, int level, double* h);
+tpss_status mapped3_inv_table(tpss_ctx* ctx, tpss_patches* P);
+tpss_status mapped3_rhs(tpss_ctx* ctx, int level, double* b);
 
 // ---- setup.cu
 __global__ void gen_eig_kernel(const double* __restrict__ Aall, const double* __restrict__ Mall, int nprob, int n,

@@ -51,7 +51,7 @@ _lib = None
 _VP, _I, _D, _F, _I64P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "tpss_create": [ctypes.POINTER(ProblemDesc), _VP, ctypes.POINTER(_VP)],
-    "tpss_create_mapped": [_I, _I, _I, _VP, _I, _D, _I, _VP, ctypes.POINTER(_VP)],
+    "tpss_create_mapped": [_I, _I, ctypes.POINTER(ctypes.c_int), _VP, _I, _D, _I, _VP, ctypes.POINTER(_VP)],
     "tpss_mapped_vertices": [_VP, _I, _VP],
     "tpss_destroy": [_VP],
     "tpss_level_info": [_VP, _I, _I64P, ctypes.POINTER(ctypes.c_int)],
@@ -154,28 +154,30 @@ class Problem:
 
     @classmethod
     def mapped(cls, degree, vertices, nlevels=1, gamma_hat=4.0, penalty_poly=PENALTY_PAPER, stream=None):
-        """tpss_create_mapped: 2D mesh of bilinear quadrilaterals from a vertex
-        array of shape (ny+1, nx+1, 2) (x index fastest, Sec. 4)."""
+        """tpss_create_mapped: mesh of bilinear quadrilaterals / trilinear
+        hexahedra from a vertex array of shape (ny+1, nx+1, 2) or
+        (nz+1, ny+1, nx+1, 3) (x index fastest, Sec. 4)."""
         import numpy as np
         V = np.ascontiguousarray(vertices, dtype=np.float64)
-        if V.ndim != 3 or V.shape[2] != 2:
-            raise ValueError("vertices must have shape (ny+1, nx+1, 2)")
+        dim = V.shape[-1]
+        if dim not in (2, 3) or V.ndim != dim + 1:
+            raise ValueError("vertices must have shape (ny+1, nx+1, 2) or (nz+1, ny+1, nx+1, 3)")
+        nc = (ctypes.c_int * 3)(*([s - 1 for s in reversed(V.shape[:-1])] + [1] * (3 - dim)))
         self = cls.__new__(cls)
         self._keep = [V]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         handle = ctypes.c_void_p()
-        _check(lib().tpss_create_mapped(degree, V.shape[1] - 1, V.shape[0] - 1, ctypes.c_void_p(V.ctypes.data),
-                                        nlevels, gamma_hat, penalty_poly, ctypes.c_void_p(self.stream.cuda_stream),
-                                        ctypes.byref(handle)))
+        _check(lib().tpss_create_mapped(dim, degree, nc, ctypes.c_void_p(V.ctypes.data), nlevels, gamma_hat,
+                                        penalty_poly, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)))
         self.h = handle
-        self.dim, self.degree, self.nlevels = 2, degree, nlevels
+        self.dim, self.degree, self.nlevels = dim, degree, nlevels
         self._patches = []
         return self
 
     def mapped_vertices(self, level):
         import numpy as np
         nc = self.level_info(level)[1]
-        out = np.empty((nc[1] + 1, nc[0] + 1, 2))
+        out = np.empty(tuple(n + 1 for n in reversed(nc[:self.dim])) + (self.dim,))
         _check(lib().tpss_mapped_vertices(self.h, level, ctypes.c_void_p(out.ctypes.data)))
         return out
 

@@ -196,3 +196,138 @@ def test_paper_counts_on_the_distorted_mesh(key, smoother, omega, steps, k):
     nu = _distorted_count(smoother, omega, steps, k, 3)
     paper = paper_value(key)
     assert abs(nu - paper) <= 0.15 * paper, (nu, paper)
+
+
+# ------------------------------------------------------------------- 3D
+def _mesh3(nx, ny, nz, seed):
+    n = max(nx, ny, nz)
+    return workloads.vertices_distorted(n, seed, dim=3)[:nz + 1, :ny + 1, :nx + 1].copy()
+
+
+def test_refined_vertices_are_bit_exact_3d():
+    V0 = _mesh3(3, 2, 2, 1)
+    prob = tpss.Problem.mapped(1, V0, nlevels=3)
+    V = V0
+    for l in range(3):
+        assert np.array_equal(prob.mapped_vertices(l), V)
+        V = refine(V)
+    prob.close()
+
+
+@pytest.mark.parametrize("k,levels", [(1, 2), (2, 2), (3, 2), (4, 1), (5, 1), (6, 1), (7, 1)])
+def test_operator_matches_oracle_3d(k, levels):
+    """3 x 2 x 2 cells (and 6 x 4 x 4 on level 1 for k <= 3; several CTAs per launch)."""
+    V0 = _mesh3(3, 2, 2, 50 + k)
+    prob = tpss.Problem.mapped(k, V0, nlevels=levels, gamma_hat=4.0)
+    Vs = [V0, refine(V0)][:levels]
+    for l, V in enumerate(Vs):
+        A = MappedSIPG(V, k, gamma_hat=4.0).assemble()
+        n = A.shape[0]
+        assert prob.ndofs(l) == n
+        u = workloads.rhs_uniform(n, seed=k, nrhs=2)
+        out = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        prob.apply_operator(l, dev(u), out, nrhs=2)
+        assert rel_err(out, np.concatenate([A @ u[:n], A @ u[n:]])) < 1e-12
+        b = workloads.rhs_uniform(n, seed=100 + k)
+        r = torch.empty(n, dtype=torch.float64, device="cuda")
+        prob.residual(l, dev(b), dev(u[:n]), r)
+        assert rel_err(r, b - A @ u[:n]) < 1e-12
+    prob.close()
+
+
+def test_operator_on_cartesian_vertices_is_the_tensor_operator_3d():
+    widths = workloads.widths_random(4, 3, seed=4)
+    for k in (2, 4):
+        mp = tpss.Problem.mapped(k, workloads.vertices_cartesian(*widths), nlevels=1, gamma_hat=1.5)
+        cp = tpss.Problem(3, k, widths, nlevels=1, gamma_hat=1.5)
+        n = cp.ndofs(0)
+        u = dev(workloads.rhs_uniform(n, seed=6))
+        a, c = torch.empty_like(u), torch.empty_like(u)
+        mp.apply_operator(0, u, a)
+        cp.apply_operator(0, u, c)
+        assert rel_err(a, c.cpu().numpy()) < 1e-12
+        mp.close()
+        cp.close()
+
+
+def test_rhs_matches_oracle_3d():
+    V0 = _mesh3(2, 2, 2, 7)
+    for k in (1, 3):
+        prob = tpss.Problem.mapped(k, V0, nlevels=1, gamma_hat=4.0)
+        S = MappedSIPG(V0, k, gamma_hat=4.0)
+        f = lambda p: 3 * np.pi ** 2 * np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]) * np.sin(np.pi * p[:, 2])
+        b = torch.empty(S.ncells * S.nloc, dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(0, 0, b)
+        assert rel_err(b, S.rhs(f, lambda p: np.zeros(len(p)))) < 1e-12
+        prob.close()
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_surrogate_1d_data_per_cell_3d(k):
+    V0 = _mesh3(3, 2, 2, 60 + k)
+    prob = tpss.Problem.mapped(k, V0, nlevels=1, gamma_hat=4.0)
+    P = prob.setup_patches(0, tpss.CELL, tpss.FP64)
+    for c in (0, 4, 7, 11):
+        m = (c % 3, (c // 3) % 2, c // 6)
+        (A0, M0, _, _), (A1, M1, _, _), (A2, M2, _, _) = (P.eigendata(t, c) for t in range(3))
+        K = np.kron(M2, np.kron(M1, A0)) + np.kron(M2, np.kron(A1, M0)) + np.kron(A2, np.kron(M1, M0))
+        assert rel_err(K, surrogate_cell_matrix(V0, m, k, 4.0)) < 1e-12
+    prob.close()
+
+
+def test_surrogate_smoothers_match_oracle_3d():
+    k = 2
+    V0 = _mesh3(3, 2, 2, 70)
+    V = refine(V0)
+    prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+    A = MappedSIPG(V, k, gamma_hat=4.0).assemble()
+    sol = surrogate_solvers(V, k, 4.0)
+    n = A.shape[0]
+    P = prob.setup_patches(1, tpss.CELL, tpss.FP64)
+    b = workloads.rhs_uniform(n, seed=1)
+    x0 = workloads.rhs_uniform(n, seed=2)
+    x = dev(x0)
+    P.smooth_additive(0.55, dev(b), x)
+    assert rel_err(x, schwarz.additive_smoother(A, b, x0, sol, 0.55)) < 1e-11
+    nc = (6, 4, 4)
+    colors = [schwarz.color_multiplicative_cell((c % 6, (c // 6) % 4, c // 24)) for c in range(96)]
+    for reverse in (False, True):
+        x = dev(x0)
+        P.smooth_multiplicative(0.95, dev(b), x, reverse_colors=reverse)
+        ref = schwarz.multiplicative_smoother(A, b, x0, sol, colors, 0.95, reverse=reverse)
+        assert rel_err(x, ref) < 1e-11
+    prob.close()
+
+
+@pytest.mark.parametrize("smoother,omega,steps", [("ACS", 0.55, 1), ("MCS", 0.95, 2)])
+def test_vcycle_matches_oracle_3d(smoother, omega, steps):
+    k = 2
+    V0 = _mesh3(2, 2, 2, 80)
+    H = MappedHierarchy(V0, k, 2, smoother, omega, steps=steps, gamma_hat=4.0)
+    prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+    prob.mg_setup(smoother, omega, tpss.FP64, coarse_solver=tpss.COARSE_DENSE, smoothing_steps=steps)
+    n = H.A[-1].shape[0]
+    r = workloads.rhs_uniform(n, seed=3)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    prob.vcycle(dev(r), z)
+    assert rel_err(z, H.precondition(r)) < 1e-10
+    prob.close()
+
+
+# Sec. 4, 3D: 8^3 coarse cells of the unit cube, 25% distortion, gamma_hat = 4,
+# f = 3 pi^2 sin sin sin, Chebyshev coarse solve, energy-norm fractional count.
+@pytest.mark.parametrize("key,smoother,omega,steps,k,L", [
+    ("dist3d_acs1_k3_L1", "ACS", 0.55, 1, 3, 1),
+    ("dist3d_acs2_k3_L1", "ACS", 0.55, 2, 3, 1),
+    ("dist3d_mcs1_k3_L1", "MCS", 0.95, 1, 3, 1),
+    ("dist3d_mcs2_k3_L1", "MCS", 0.95, 2, 3, 1),
+])
+def test_paper_counts_on_the_distorted_cube(key, smoother, omega, steps, k, L):
+    prob = tpss.Problem.mapped(k, workloads.vertices_distorted(8, 1, dim=3), nlevels=L + 1, gamma_hat=4.0)
+    prob.mg_setup(smoother, omega, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV, smoothing_steps=steps)
+    b = torch.empty(prob.ndofs(L), dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(L, 0, b)
+    nu = perf.fractional_iterations(perf.cg_energy_errors(prob, b, rtol=1e-8, maxit=150), 1e-8)
+    prob.close()
+    paper = paper_value(key)
+    assert abs(nu - paper) <= 0.15 * paper, (nu, paper)
