@@ -423,7 +423,7 @@ def main():
         if high is not None:
             line["high_degree_k15"] = high
         if distorted is not None:
-            line["distorted_2d"] = distorted
+            line["distorted"] = distorted
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -724,75 +724,87 @@ def run_high_degree(tpss, workloads, perf, torch, steps):
     return out
 
 
-# tab:cubedist25acp / tab:cubedist25mcp, 2D, L = 3 (32 x 32 coarse cells, 25% distortion)
-PAPER_NU_DIST2D_L3 = {("ACS", 1, 3): 38.7, ("ACS", 2, 3): 24.3, ("MCS", 1, 3): 24.7, ("MCS", 2, 3): 15.3,
-                      ("ACS", 1, 7): 47.7, ("MCS", 1, 7): 43.5}
+# tab:cubedist25acp / tab:cubedist25mcp: (smoother, m, k) -> printed nu_frac;
+# 2D at L = 3 (32 x 32 coarse cells), 3D at L = 1 (8^3 coarse cells), 25% distortion
+PAPER_NU_DIST = {2: {("ACS", 1, 3): 38.7, ("ACS", 2, 3): 24.3, ("MCS", 1, 3): 24.7, ("MCS", 2, 3): 15.3,
+                     ("ACS", 1, 7): 47.7, ("MCS", 1, 7): 43.5},
+                 3: {("ACS", 1, 3): 34.4, ("ACS", 2, 3): 24.5, ("MCS", 1, 3): 24.7, ("MCS", 2, 3): 14.4,
+                     ("ACS", 1, 7): 49.7, ("MCS", 1, 7): 37.7}}
+# relaxation of those columns: ACS (k = 3, 7), MCS (k = 3, 7)
+PAPER_OMEGA_DIST = {2: {("ACS", 3): 0.5, ("ACS", 7): 0.5, ("MCS", 3): 0.75, ("MCS", 7): 0.5},
+                    3: {("ACS", 3): 0.55, ("ACS", 7): 0.5, ("MCS", 3): 0.95, ("MCS", 7): 0.7}}
 DIST_SEED = 1
 
 
 def run_distorted(tpss, workloads, perf, torch, steps):
-    """Sec. 4: the 32 x 32 mesh of the unit square with 25% vertex distortion
-    (seed DIST_SEED), gamma_hat = 4, refined to about 16.7 M DoFs (k = 3: L = 5,
-    1024^2 cells; k = 7: L = 4, 512^2 cells): the matrix-free operator, one
-    ACS and one MCS sweep with Cartesian-surrogate cell solvers, the V-cycle and
-    a PCG solve to 1e-8 (f = 2 pi^2 sin(pi x) sin(pi y), Chebyshev coarse
-    solve), timed with CUDA events; and the energy-norm fractional counts of
-    the paper's L = 3 columns."""
-    V0 = workloads.vertices_distorted(32, DIST_SEED)
-    out = {"workload": f"2D, 32^2 coarse cells of [0,1]^2, 25% distortion (seed {DIST_SEED}), gamma_hat 4, FP64"}
+    """Sec. 4: the unit square (32^2 cells) / cube (8^3 cells) with 25% vertex
+    distortion (seed DIST_SEED), gamma_hat = 4, refined to about 16.8 M DoFs
+    (2D k = 3: L = 5; k = 7: L = 4; 3D k = 3: L = 3; k = 7: L = 2): the
+    matrix-free operator, one ACS and one MCS sweep with Cartesian-surrogate
+    cell solvers, the V-cycle and PCG to 1e-8 (f = d pi^2 prod sin(pi x_t),
+    Chebyshev coarse solve), timed with CUDA events; and the energy-norm
+    fractional counts of the paper's columns (2D L = 3, 3D L = 1)."""
+    out = {"workload": f"unit square 32^2 / cube 8^3 coarse cells, 25% distortion (seed {DIST_SEED}), "
+                       "gamma_hat 4, FP64"}
     fp64 = perf.fp64_peak_flops()
-    for k, L, om_a, om_m in ((3, 5, 0.5, 0.75), (7, 4, 0.5, 0.5)):
-        prob = tpss.Problem.mapped(k, V0, nlevels=L + 1, gamma_hat=4.0)
-        N, nc = prob.level_info(L)
-        u = torch.from_numpy(workloads.rhs_uniform(N, seed=3)).to("cuda")
-        au = torch.empty_like(u)
-        ms = _time_calls(torch, lambda: prob.apply_operator(L, u, au), steps)
-        fl = perf.mapped_operator_flops(nc[:2], k)
-        rec = {"L": L, "cells": nc[0] * nc[1], "dofs": N,
-               "operator": {"kernel": f"mapped_op_kernel<{k + 1}>", "ms": ms, "dofs_per_s": N / (ms / 1e3),
-                            "tflops": fl / ms / 1e9, "frac_fp64_peak": fl / (ms / 1e3) / fp64,
-                            "algorithmic_gbs": perf.mapped_operator_bytes(nc[:2], k) / ms / 1e6}}
-        b = torch.empty(N, dtype=torch.float64, device="cuda")
-        prob.assemble_rhs(L, 0, b)
-        x = torch.zeros_like(b)
-        P = prob.setup_patches(L, tpss.CELL)
-        ms = _time_calls(torch, lambda: P.smooth_additive(om_a, b, x, x_is_zero=True), steps)
-        rec["acs_sweep"] = {"ms": ms, "dofs_per_s": N / (ms / 1e3), "note": "residual (operator) + local solves"}
-        ms = _time_calls(torch, lambda: P.smooth_multiplicative(om_m, b, x), max(2, steps // 2))
-        rec["mcs_sweep"] = {"ms": ms, "dofs_per_s": N / (ms / 1e3), "note": "2 colors, full residual per color"}
-        P.close()
-        for sm, om in (("ACS", om_a), ("MCS", om_m)):
-            prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV)
-            z = torch.empty_like(b)
-            ms = _time_calls(torch, lambda: prob.vcycle(b, z), max(2, steps // 2))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            res = prob.pcg_solve(b, x, rtol=1e-8, maxit=200, history=True)
-            e1.record()
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 1e3
-            rec[f"{sm}1_pcg"] = {"omega": om, "vcycle_ms": ms, "iterations": res["iters"],
-                                 "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
-                                 "solve_s": t, "dofs_per_s": N / t}
-            if sm == "ACS":   # the coarse solve's share of the V-cycle (Chebyshev, CUDA graph)
-                b0 = torch.from_numpy(workloads.rhs_uniform(prob.ndofs(0), seed=5)).to("cuda")
-                x0 = torch.empty_like(b0)
-                rec["coarse_solve"] = {"ms": _time_calls(torch, lambda: prob.coarse_solve(b0, x0), 3),
-                                       "dofs": prob.ndofs(0), **prob.coarse_chebyshev_info()}
-        prob.close()
-        out[f"k{k}"] = rec
-    its = {}
-    for (sm, m, k), paper in PAPER_NU_DIST2D_L3.items():
-        om = 0.5 if sm == "ACS" or k == 7 else 0.75
-        prob = tpss.Problem.mapped(k, V0, nlevels=4, gamma_hat=4.0)
-        prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV, smoothing_steps=m)
-        b = torch.empty(prob.ndofs(3), dtype=torch.float64, device="cuda")
-        prob.assemble_rhs(3, 0, b)
-        errs = perf.cg_energy_errors(prob, b, rtol=1e-8, maxit=150)
-        prob.close()
-        its[f"{sm}{m}_k{k}_L3"] = {"omega": om, "nu_frac_energy": perf.fractional_iterations(errs, 1e-8),
-                                   "paper_nu_frac": paper}
-    out["paper_iterations_L3"] = its
+    for dim, n0, runs, Lp in ((2, 32, ((3, 5), (7, 4)), 3), (3, 8, ((3, 3), (7, 2)), 1)):
+        V0 = workloads.vertices_distorted(n0, DIST_SEED, dim=dim)
+        rec_d = {}
+        for k, L in runs:
+            om_a, om_m = PAPER_OMEGA_DIST[dim][("ACS", k)], PAPER_OMEGA_DIST[dim][("MCS", k)]
+            prob = tpss.Problem.mapped(k, V0, nlevels=L + 1, gamma_hat=4.0)
+            N, nc = prob.level_info(L)
+            u = torch.from_numpy(workloads.rhs_uniform(N, seed=3)).to("cuda")
+            au = torch.empty_like(u)
+            ms = _time_calls(torch, lambda: prob.apply_operator(L, u, au), steps)
+            fl = (perf.mapped_operator_flops(nc[:2], k) if dim == 2 else perf.mapped3_operator_flops(nc, k))
+            by = (perf.mapped_operator_bytes(nc[:2], k) if dim == 2 else perf.mapped3_operator_bytes(nc, k))
+            rec = {"L": L, "cells": nc[0] * nc[1] * (nc[2] if dim == 3 else 1), "dofs": N,
+                   "operator": {"kernel": f"mapped{'' if dim == 2 else '3'}_op_kernel<{k + 1}>", "ms": ms,
+                                "dofs_per_s": N / (ms / 1e3), "tflops": fl / ms / 1e9,
+                                "frac_fp64_peak": fl / (ms / 1e3) / fp64, "algorithmic_gbs": by / ms / 1e6}}
+            b = torch.empty(N, dtype=torch.float64, device="cuda")
+            prob.assemble_rhs(L, 0, b)
+            x = torch.zeros_like(b)
+            P = prob.setup_patches(L, tpss.CELL)
+            ms = _time_calls(torch, lambda: P.smooth_additive(om_a, b, x, x_is_zero=True), steps)
+            rec["acs_sweep_x0"] = {"ms": ms, "dofs_per_s": N / (ms / 1e3), "note": "x = 0: local solves only"}
+            ms = _time_calls(torch, lambda: P.smooth_multiplicative(om_m, b, x), max(2, steps // 2))
+            rec["mcs_sweep"] = {"ms": ms, "dofs_per_s": N / (ms / 1e3), "note": "2 colors, full residual per color"}
+            P.close()
+            for sm, om in (("ACS", om_a), ("MCS", om_m)):
+                prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV)
+                z = torch.empty_like(b)
+                ms = _time_calls(torch, lambda: prob.vcycle(b, z), max(2, steps // 2))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                res = prob.pcg_solve(b, x, rtol=1e-8, maxit=200, history=True)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 1e3
+                rec[f"{sm}1_pcg"] = {"omega": om, "vcycle_ms": ms, "iterations": res["iters"],
+                                     "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
+                                     "solve_s": t, "dofs_per_s": N / t}
+                if sm == "ACS":   # the coarse solve's share of the V-cycle (Chebyshev, CUDA graph)
+                    b0 = torch.from_numpy(workloads.rhs_uniform(prob.ndofs(0), seed=5)).to("cuda")
+                    x0 = torch.empty_like(b0)
+                    rec["coarse_solve"] = {"ms": _time_calls(torch, lambda: prob.coarse_solve(b0, x0), 3),
+                                           "dofs": prob.ndofs(0), **prob.coarse_chebyshev_info()}
+            prob.close()
+            rec_d[f"k{k}"] = rec
+        its = {}
+        for (sm, m, k), paper in PAPER_NU_DIST[dim].items():
+            om = PAPER_OMEGA_DIST[dim][(sm, k)]
+            prob = tpss.Problem.mapped(k, V0, nlevels=Lp + 1, gamma_hat=4.0)
+            prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV, smoothing_steps=m)
+            b = torch.empty(prob.ndofs(Lp), dtype=torch.float64, device="cuda")
+            prob.assemble_rhs(Lp, 0, b)
+            errs = perf.cg_energy_errors(prob, b, rtol=1e-8, maxit=150)
+            prob.close()
+            its[f"{sm}{m}_k{k}_L{Lp}"] = {"omega": om, "nu_frac_energy": perf.fractional_iterations(errs, 1e-8),
+                                          "paper_nu_frac": paper}
+        rec_d[f"paper_iterations_L{Lp}"] = its
+        out[f"{dim}d"] = rec_d
     return out
 
 

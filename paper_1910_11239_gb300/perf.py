@@ -93,6 +93,24 @@ def mapped_operator_flops(ncells, k, nrhs=1):
     return num_cells(ncells) * (16 * n1 ** 3 + 104 * n1 ** 2 + 68 * n1) * nrhs
 
 
+def mapped3_operator_flops(ncells, k, nrhs=1):
+    """The 3D kernel on trilinear hexahedra, per cell (n1 = k+1): 6 sum-
+    factorization stages of 2 + 3 + 3 (and transposed) arrays of n1^4 FMAs
+    (32 n1^4 flops), the metric (15 n1^3); per face (6, both sides each
+    evaluated from both cells) the normal-derivative planes (2 n1^3 FMAs),
+    two interpolation stages (6 + 8 n1^3 FMAs, both sides), ~30 flops of
+    coefficients per point (180 n1^2 in total), two test stages (4 + 3 n1^3
+    FMAs); the scatter (12 n1^3): 32 n1^4 + 303 n1^3 + 180 n1^2."""
+    n1 = k + 1
+    return num_cells(ncells) * (32 * n1 ** 4 + 303 * n1 ** 3 + 180 * n1 ** 2) * nrhs
+
+
+def mapped3_operator_bytes(ncells, k, nrhs=1):
+    """Read u, write A u, read the per-cell geometry (6 n1^3 + 24 n1^2 + 6 doubles)."""
+    n1 = k + 1
+    return num_cells(ncells) * (16 * n1 ** 3 * nrhs + 8 * (6 * n1 ** 3 + 24 * n1 ** 2 + 6))
+
+
 def mapped_operator_bytes(ncells, k, nrhs=1):
     """Minimal HBM traffic: read u, write A u, read the per-cell geometry
     (3 n1^2 + 8 n1 + 8 doubles)."""
