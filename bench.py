@@ -804,6 +804,27 @@ def run_distorted(tpss, workloads, perf, torch, steps):
             its[f"{sm}{m}_k{k}_L{Lp}"] = {"omega": om, "nu_frac_energy": perf.fractional_iterations(errs, 1e-8),
                                           "paper_nu_frac": paper}
         rec_d[f"paper_iterations_L{Lp}"] = its
+        if dim == 2:   # tab:cubedist25varydamp: k = 3, L = 3, one smoothing step, omega swept
+            sweep = {}
+            prob = tpss.Problem.mapped(3, V0, nlevels=4, gamma_hat=4.0)
+            b = torch.empty(prob.ndofs(3), dtype=torch.float64, device="cuda")
+            prob.assemble_rhs(3, 0, b)
+            xs, xw = torch.empty_like(b), torch.empty_like(b)
+            prob.mg_setup("ACS", 0.5, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV)
+            prob.pcg_solve(b, xs, rtol=1e-14, maxit=300)   # x* once, with a convergent V-cycle
+            for sm, omegas, paper in (("ACS", (0.65, 0.6, 0.55, 0.5, 0.45, 0.4), (">100", 54.4, 40.7, 38.7, 42.9, 48.6)),
+                                      ("MCS", (0.85, 0.8, 0.75, 0.7, 0.65, 0.6), (23.4, 23.6, 24.7, 25.8, 27.6, 29.6))):
+                for om, pv in zip(omegas, paper):
+                    prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV)
+                    try:
+                        errs = prob.pcg_energy_errors(b, xs, xw, rtol=1e-8, maxit=150)
+                    except tpss.TpssError:
+                        errs = [1.0, 1.0]
+                    ok = errs[-1] <= 1e-8 * errs[0]
+                    sweep[f"{sm}_w{om:.2f}"] = {"nu_frac_energy": perf.fractional_iterations(errs, 1e-8) if ok
+                                                else ">150", "paper_nu_frac": pv}
+            prob.close()
+            rec_d["damping_sweep_k3_L3"] = sweep
         out[f"{dim}d"] = rec_d
     return out
 
