@@ -203,27 +203,35 @@ struct MappedOpArgs {
   int64_t ncells, ndofs;
 };
 
+// tables of the 2D kernels in shared memory: Vq, Dq (n1^2), d0, d1, wq (n1)
 template <int N1>
-__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(MappedOpArgs a) {
+__device__ __forceinline__ void mapped_tables(const Basis1D* __restrict__ B, double* sm) {
+  constexpr int NL = N1 * N1;
+  for (int e = threadIdx.x; e < NL; e += blockDim.x) {
+    sm[e] = B->Vq[e];
+    sm[NL + e] = B->Dq[e];
+  }
+  for (int e = threadIdx.x; e < N1; e += blockDim.x) {
+    sm[2 * NL + e] = B->d0[e];
+    sm[2 * NL + N1 + e] = B->d1[e];
+    sm[2 * NL + 2 * N1 + e] = B->wq[e];
+  }
+}
+
+// (A u)_K at the local DoF tid of cell `cell` (a.u read, nothing written to
+// global memory).  Every thread of the CTA calls it (it synchronizes the
+// CTA); the tables must have been written (they become visible at its first
+// barrier); W is the cell's slot, and W + S::U keeps u_K afterwards.
+template <int N1>
+__device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, double* sm, double* W, int64_t cell,
+                                                    bool active, int tid) {
   using S = MappedShape<N1>;
   constexpr int NL = N1 * N1, K = N1 - 1, G = S::G;
   constexpr int GA = 3 * NL, GS = 3 * NL + 8 * N1;   // GeoLayout offsets
-  extern __shared__ double sm[];
   double* Vq = sm;
   double* Dq = Vq + NL;
   double* dd = Dq + NL;        // d0 then d1: phi_i'(0), phi_i'(1)
   double* wq = dd + 2 * N1;
-  for (int e = threadIdx.x; e < NL; e += S::THREADS) {
-    Vq[e] = a.B->Vq[e];
-    Dq[e] = a.B->Dq[e];
-  }
-  for (int e = threadIdx.x; e < N1; e += S::THREADS) {
-    dd[e] = a.B->d0[e];
-    dd[N1 + e] = a.B->d1[e];
-    wq[e] = a.B->wq[e];
-  }
-  const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
-  double* W = sm + S::TABLES + slot * S::SLOT;
   double* geo = W + S::GEO;
   double* na = W + S::NA;
   double* U = W + S::U;
@@ -240,8 +248,6 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
   double* de = be + 4 * N1;
   double* As = de + 4 * N1;
   double* Bs = As + 4 * N1;
-  const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
-  const bool active = cell < a.ncells;
   const int cx = active ? (int)(cell % a.nx) : 0, cy = active ? (int)(cell / a.nx) : 0;
   const int64_t vbase = (int64_t)blockIdx.y * a.ndofs;
   // face f = 2 t + side: neighbour along t at -1 (side 0) / +1 (side 1)
@@ -398,9 +404,131 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
       v = fma(dd[side * N1 + it], Bs[f * N1 + j], v);
       if (it == side * K) v += As[f * N1 + j];
     }
-    const int64_t gi = vbase + cell * NL + tid;
+    return v;
+  }
+  return 0.0;
+}
+
+template <int N1>
+__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(MappedOpArgs a) {
+  using S = MappedShape<N1>;
+  constexpr int NL = N1 * N1;
+  extern __shared__ double sm[];
+  mapped_tables<N1>(a.B, sm);
+  const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
+  const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
+  const bool active = cell < a.ncells;
+  const double v = mapped_cell_apply<N1>(a, sm, sm + S::TABLES + slot * S::SLOT, cell, active, tid);
+  if (active) {
+    const int64_t gi = (int64_t)blockIdx.y * a.ndofs + cell * NL + tid;
     a.out[gi] = a.rhs ? a.rhs[gi] - v : v;
   }
+}
+
+// Residual, surrogate cell solve and update fused, for the cells of `list`
+// (packed positions; null: all cells):
+//   r = b - (A x)_K,  z = Z_1 x Z_0 diag(1/(lambda_i + lambda_j)) (Z_1 x Z_0)^T r,
+//   mode 0:  out_K = x_K + omega z
+//   mode 1:  d_K = c1 d_K + c2 z,  out_K = x_K + d_K   (a Chebyshev step)
+// out may equal x when no listed cell is a face neighbour of another (one
+// color of the red-black sweep); otherwise out is a different vector.
+struct MappedFusedArgs {
+  MappedOpArgs op;     // op.u = x
+  const double* b;
+  double* out;
+  double* d;
+  const int* list;
+  int64_t count;
+  const double* Z[3];  // per cell and direction [N1 * N1], column j = eigenvector j
+  const double* inv;   // per cell [N1^dim]
+  int mode;
+  double omega, c1, c2;
+};
+
+template <int N1>
+__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_fused_kernel(MappedFusedArgs f) {
+  using S = MappedShape<N1>;
+  constexpr int NL = N1 * N1, SL = S::SLOT + 2 * NL;
+  extern __shared__ double sm[];
+  mapped_tables<N1>(f.op.B, sm);
+  const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
+  const int64_t idx = (int64_t)blockIdx.x * S::CPB + slot;
+  const bool active = idx < f.count;
+  int64_t cell = 0;
+  if (active) {
+    if (f.list) {
+      const int p = f.list[idx];
+      cell = unpack_x(p) + (int64_t)f.op.nx * unpack_y(p);
+    } else {
+      cell = idx;
+    }
+  }
+  double* W = sm + S::TABLES + slot * SL;
+  double* Zs = W + S::SLOT;   // Z_0, Z_1 of the cell
+  if (active) {
+    Zs[tid] = f.Z[0][cell * NL + tid];
+    Zs[NL + tid] = f.Z[1][cell * NL + tid];
+  }
+  const double v = mapped_cell_apply<N1>(f.op, sm, W, cell, active, tid);
+  const int64_t gi = (int64_t)blockIdx.y * f.op.ndofs + cell * NL + tid;
+  const double xo = active ? W[S::U + tid] : 0.0;
+  double* R = W + S::TA;
+  double* T1 = W + S::TB;
+  double* T2 = W + S::F0;
+  double* T3 = W + S::F1;
+  const int i0 = tid % N1, i1 = tid / N1;
+  __syncthreads();   // the operator's last stage read these arrays
+  if (active) R[tid] = f.b[gi] - v;
+  __syncthreads();
+  if (active) {   // Z_0^T along x
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Zs[m * N1 + i0], R[m + N1 * i1], s);
+    T1[tid] = s;
+  }
+  __syncthreads();
+  if (active) {   // Z_1^T along y, then 1 / (lambda_i + lambda_j)
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Zs[NL + m * N1 + i1], T1[i0 + N1 * m], s);
+    T2[tid] = s * f.inv[cell * NL + tid];
+  }
+  __syncthreads();
+  if (active) {   // Z_1 along y
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Zs[NL + i1 * N1 + m], T2[i0 + N1 * m], s);
+    T3[tid] = s;
+  }
+  __syncthreads();
+  if (active) {   // Z_0 along x, update
+    double z = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) z = fma(Zs[i0 * N1 + m], T3[m + N1 * i1], z);
+    if (f.mode == 0) {
+      f.out[gi] = fma(f.omega, z, xo);
+    } else {
+      const double dn = fma(f.c1, f.d[gi], f.c2 * z);
+      f.d[gi] = dn;
+      f.out[gi] = xo + dn;
+    }
+  }
+}
+
+template <int N1>
+static tpss_status launch_fused(tpss_ctx* ctx, const MappedFusedArgs& a, int nrhs) {
+  using S = MappedShape<N1>;
+  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 2 * N1 * N1)) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_fused_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    attr = true;
+  }
+  const dim3 grid((unsigned)((a.count + S::CPB - 1) / S::CPB), (unsigned)nrhs);
+  mapped_fused_kernel<N1><<<grid, S::THREADS, smem, ctx->stream>>>(a);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
 }
 
 template <int N1>
@@ -416,6 +544,45 @@ static tpss_status launch_mapped(tpss_ctx* ctx, const MappedOpArgs& a, int nrhs)
   mapped_op_kernel<N1><<<grid, S::THREADS, S::SMEM, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
+}
+
+tpss_status mapped_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
+                         double* out, double* d, int mode, double omega, double c1, double c2) {
+  tpss_ctx* ctx = P->ctx;
+  if (ctx->dim == 3) return mapped3_fused(P, list, count, nrhs, x, b, out, d, mode, omega, c1, c2);
+  const Level& L = ctx->levels[P->level];
+  MappedFusedArgs a{};
+  a.op.u = x;
+  a.op.geo = L.d_geo;
+  a.op.B = ctx->d_basis;
+  a.op.nx = L.nc[0];
+  a.op.ny = L.nc[1];
+  a.op.ncells = L.ncells;
+  a.op.ndofs = L.ndofs;
+  a.b = b;
+  a.out = out;
+  a.d = d;
+  a.list = list;
+  a.count = count;
+  a.Z[0] = P->d_Z[0];
+  a.Z[1] = P->d_Z[1];
+  a.inv = P->d_inv;
+  a.mode = mode;
+  a.omega = omega;
+  a.c1 = c1;
+  a.c2 = c2;
+  switch (ctx->n1) {
+    case 2: return launch_fused<2>(ctx, a, nrhs);
+    case 3: return launch_fused<3>(ctx, a, nrhs);
+    case 4: return launch_fused<4>(ctx, a, nrhs);
+    case 5: return launch_fused<5>(ctx, a, nrhs);
+    case 6: return launch_fused<6>(ctx, a, nrhs);
+    case 7: return launch_fused<7>(ctx, a, nrhs);
+    case 8: return launch_fused<8>(ctx, a, nrhs);
+    default: break;
+  }
+  set_error("smoother: meshes of quadrilaterals support degrees 1..7");
+  return TPSS_EINVAL;
 }
 
 static double penalty_prefactor(const tpss_ctx* ctx) {

@@ -266,31 +266,35 @@ struct Mapped3Args {
   int64_t ncells, ndofs;
 };
 
+// tables in shared memory: Vq, Dq (n1^2), d0, d1 (n1)
 template <int N1>
-__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_op_kernel(Mapped3Args a) {
+__device__ __forceinline__ void mapped3_tables(const Basis1D* __restrict__ B, double* sm) {
+  constexpr int NF = N1 * N1;
+  for (int e = threadIdx.x; e < NF; e += blockDim.x) {
+    sm[e] = B->Vq[e];
+    sm[NF + e] = B->Dq[e];
+  }
+  for (int e = threadIdx.x; e < N1; e += blockDim.x) {
+    sm[2 * NF + e] = B->d0[e];
+    sm[2 * NF + N1 + e] = B->d1[e];
+  }
+}
+
+// (A u)_K at the local DoF tid of cell `cell`; every thread of the CTA calls
+// it (it synchronizes the CTA), Wk is the cell's slot (Wk + S::U keeps u_K)
+template <int N1>
+__device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, double* sm, double* Wk, int64_t cell,
+                                                     bool active, int tid) {
   using S = Mapped3Shape<N1>;
   constexpr int NV = S::NV, NF = S::NF, K = N1 - 1, G = S::G;
   constexpr int GA = 6 * NV, GW = 6 * NV + 18 * NF, GS = 6 * NV + 24 * NF;   // Geo3Layout offsets
-  extern __shared__ double sm[];
   double* Vq = sm;
   double* Dq = Vq + NF;
   double* dd = Dq + NF;   // d0 then d1
-  for (int e = threadIdx.x; e < NF; e += S::THREADS) {
-    Vq[e] = a.B->Vq[e];
-    Dq[e] = a.B->Dq[e];
-  }
-  for (int e = threadIdx.x; e < N1; e += S::THREADS) {
-    dd[e] = a.B->d0[e];
-    dd[N1 + e] = a.B->d1[e];
-  }
-  const int slot = threadIdx.x / NV, tid = threadIdx.x % NV;
-  double* Wk = sm + S::TABLES + slot * S::SLOT;
   double* U = Wk + S::U;
   double* sc = Wk + S::SC;       // 6 x NV
   double* fa = Wk + S::FA;       // 6 x 6 NF
   double* fb = Wk + S::FB;       // 4 x 6 NF
-  const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
-  const bool active = cell < a.ncells;
   const int ci0 = active ? (int)(cell % a.nx) : 0, ci1 = active ? (int)((cell / a.nx) % a.ny) : 0;
   const int ci2 = active ? (int)(cell / ((int64_t)a.nx * a.ny)) : 0;
   const int hasm = (ci0 > 0 ? 1 : 0) | (ci0 + 1 < a.nx ? 2 : 0) | (ci1 > 0 ? 4 : 0) | (ci1 + 1 < a.ny ? 8 : 0) |
@@ -553,9 +557,177 @@ __global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_op_kernel(M
       v = fma(dd[side * N1 + ii[t]], fb[f * NF + p], v);
       if (ii[t] == side * K) v += fb[6 * NF + f * NF + p];
     }
-    const int64_t gi = vbase + cell * NV + tid;
+    return v;
+  }
+  return 0.0;
+}
+
+template <int N1>
+__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_op_kernel(Mapped3Args a) {
+  using S = Mapped3Shape<N1>;
+  constexpr int NV = S::NV;
+  extern __shared__ double sm[];
+  mapped3_tables<N1>(a.B, sm);
+  const int slot = threadIdx.x / NV, tid = threadIdx.x % NV;
+  const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
+  const bool active = cell < a.ncells;
+  const double v = mapped3_cell_apply<N1>(a, sm, sm + S::TABLES + slot * S::SLOT, cell, active, tid);
+  if (active) {
+    const int64_t gi = (int64_t)blockIdx.y * a.ndofs + cell * NV + tid;
     a.out[gi] = a.rhs ? a.rhs[gi] - v : v;
   }
+}
+
+// Residual, surrogate cell solve and update fused (see mapped.cu, 2D):
+//   r = b - (A x)_K, z = (Z_2 x Z_1 x Z_0) Lambda^{-1} (Z_2 x Z_1 x Z_0)^T r,
+//   mode 0: out_K = x_K + omega z;  mode 1: d_K = c1 d_K + c2 z, out_K = x_K + d_K
+struct Mapped3FusedArgs {
+  Mapped3Args op;
+  const double* b;
+  double* out;
+  double* d;
+  const int* list;
+  int64_t count;
+  const double* Z[3];
+  const double* inv;
+  int mode;
+  double omega, c1, c2;
+};
+
+template <int N1>
+__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_fused_kernel(Mapped3FusedArgs f) {
+  using S = Mapped3Shape<N1>;
+  constexpr int NV = S::NV, NF = S::NF, SL = S::SLOT + 3 * NF;
+  extern __shared__ double sm[];
+  mapped3_tables<N1>(f.op.B, sm);
+  const int slot = threadIdx.x / NV, tid = threadIdx.x % NV;
+  const int64_t idx = (int64_t)blockIdx.x * S::CPB + slot;
+  const bool active = idx < f.count;
+  int64_t cell = 0;
+  if (active) {
+    if (f.list) {
+      const int p = f.list[idx];
+      cell = unpack_x(p) + (int64_t)f.op.nx * (unpack_y(p) + (int64_t)f.op.ny * unpack_z(p));
+    } else {
+      cell = idx;
+    }
+  }
+  double* Wk = sm + S::TABLES + slot * SL;
+  double* Zs = Wk + S::SLOT;   // Z_0, Z_1, Z_2 of the cell
+  if (active)
+    for (int e = tid; e < 3 * NF; e += NV) Zs[e] = f.Z[e / NF][cell * NF + e % NF];
+  const double v = mapped3_cell_apply<N1>(f.op, sm, Wk, cell, active, tid);
+  const int64_t gi = (int64_t)blockIdx.y * f.op.ndofs + cell * NV + tid;
+  const double xo = active ? Wk[S::U + tid] : 0.0;
+  double* sc = Wk + S::SC;
+  const int i0 = tid % N1, i1 = (tid / N1) % N1, i2 = tid / NF;
+  const double* Z0 = Zs;
+  const double* Z1 = Zs + NF;
+  const double* Z2 = Zs + 2 * NF;
+  __syncthreads();   // the operator's last stage read sc
+  if (active) sc[tid] = f.b[gi] - v;
+  __syncthreads();
+  if (active) {   // Z_0^T along x
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Z0[m * N1 + i0], sc[m + N1 * i1 + NF * i2], s);
+    sc[NV + tid] = s;
+  }
+  __syncthreads();
+  if (active) {   // Z_1^T along y
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Z1[m * N1 + i1], sc[NV + i0 + N1 * m + NF * i2], s);
+    sc[2 * NV + tid] = s;
+  }
+  __syncthreads();
+  if (active) {   // Z_2^T along z, then 1 / (lambda_i + lambda_j + lambda_l)
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Z2[m * N1 + i2], sc[2 * NV + i0 + N1 * i1 + NF * m], s);
+    sc[3 * NV + tid] = s * f.inv[cell * NV + tid];
+  }
+  __syncthreads();
+  if (active) {   // Z_2 along z
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Z2[i2 * N1 + m], sc[3 * NV + i0 + N1 * i1 + NF * m], s);
+    sc[4 * NV + tid] = s;
+  }
+  __syncthreads();
+  if (active) {   // Z_1 along y
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) s = fma(Z1[i1 * N1 + m], sc[4 * NV + i0 + N1 * m + NF * i2], s);
+    sc[5 * NV + tid] = s;
+  }
+  __syncthreads();
+  if (active) {   // Z_0 along x, update
+    double z = 0.0;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) z = fma(Z0[i0 * N1 + m], sc[5 * NV + m + N1 * i1 + NF * i2], z);
+    if (f.mode == 0) {
+      f.out[gi] = fma(f.omega, z, xo);
+    } else {
+      const double dn = fma(f.c1, f.d[gi], f.c2 * z);
+      f.d[gi] = dn;
+      f.out[gi] = xo + dn;
+    }
+  }
+}
+
+template <int N1>
+static tpss_status launch_fused3(tpss_ctx* ctx, const Mapped3FusedArgs& a, int nrhs) {
+  using S = Mapped3Shape<N1>;
+  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 3 * S::NF)) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_fused_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    attr = true;
+  }
+  const dim3 grid((unsigned)((a.count + S::CPB - 1) / S::CPB), (unsigned)nrhs);
+  mapped3_fused_kernel<N1><<<grid, S::THREADS, smem, ctx->stream>>>(a);
+  TPSS_CHECK_LAUNCH();
+  return TPSS_OK;
+}
+
+tpss_status mapped3_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
+                          double* out, double* d, int mode, double omega, double c1, double c2) {
+  tpss_ctx* ctx = P->ctx;
+  const Level& L = ctx->levels[P->level];
+  Mapped3FusedArgs a{};
+  a.op.u = x;
+  a.op.geo = L.d_geo;
+  a.op.B = ctx->d_basis;
+  a.op.nx = L.nc[0];
+  a.op.ny = L.nc[1];
+  a.op.nz = L.nc[2];
+  a.op.ncells = L.ncells;
+  a.op.ndofs = L.ndofs;
+  a.b = b;
+  a.out = out;
+  a.d = d;
+  a.list = list;
+  a.count = count;
+  for (int t = 0; t < 3; ++t) a.Z[t] = P->d_Z[t];
+  a.inv = P->d_inv;
+  a.mode = mode;
+  a.omega = omega;
+  a.c1 = c1;
+  a.c2 = c2;
+  switch (ctx->n1) {
+    case 2: return launch_fused3<2>(ctx, a, nrhs);
+    case 3: return launch_fused3<3>(ctx, a, nrhs);
+    case 4: return launch_fused3<4>(ctx, a, nrhs);
+    case 5: return launch_fused3<5>(ctx, a, nrhs);
+    case 6: return launch_fused3<6>(ctx, a, nrhs);
+    case 7: return launch_fused3<7>(ctx, a, nrhs);
+    case 8: return launch_fused3<8>(ctx, a, nrhs);
+    default: break;
+  }
+  set_error("smoother: meshes of hexahedra support degrees 1..7");
+  return TPSS_EINVAL;
 }
 
 template <int N1>

@@ -316,6 +316,17 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
   cudaStream_t s = ctx->stream;
   Level& L = ctx->levels[P->level];
   const T* r = b;
+  if constexpr (sizeof(T) == 8) {
+    // surrogate cell solvers (mapped meshes): residual, local solves and the
+    // update in one launch, into a scratch vector (neighbours read x)
+    if (P->per_sub && !x_is_zero) {
+      TPSS_TRY(ensure_level_scratch(ctx, P->level, nrhs));
+      T* rb = residual_buffer<T>(L);
+      TPSS_TRY(mapped_fused(P, nullptr, P->nsub, nrhs, x, b, rb, nullptr, 0, omega, 0.0, 0.0));
+      TPSS_CHECK_CUDA(cudaMemcpyAsync(x, rb, (size_t)L.ndofs * nrhs * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      return TPSS_OK;
+    }
+  }
   if (x_is_zero) {
     TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)L.ndofs * nrhs * sizeof(T), s));
   } else {
@@ -404,6 +415,15 @@ tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int n
     const int c = reverse ? nc - 1 - i : i;
     const int o = offs[c], cnt = offs[c + 1] - o;
     if (cnt == 0) continue;
+    if constexpr (sizeof(T) == 8) {
+      // surrogate cell solvers (mapped meshes): the residual on the color's
+      // cells only, local solves and update in one launch, in place (no two
+      // cells of a red-black color share a face)
+      if (P->per_sub) {
+        TPSS_TRY(mapped_fused(P, list + o, cnt, nrhs, x, b, x, nullptr, 0, omega, 0.0, 0.0));
+        continue;
+      }
+    }
     TPSS_TRY(apply_operator_t<T>(ctx, P->level, nrhs, x, rb, b));
     TPSS_TRY(patch_pass<T>(P, list + o, cnt, omega, nrhs, rb, x, s));
   }

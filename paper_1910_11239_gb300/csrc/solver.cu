@@ -354,6 +354,21 @@ static tpss_status chebyshev_body(tpss_ctx* ctx, MGState* mg, const double* f, d
   }
   TPSS_TRY(smooth_additive_t<double>(mg->coarse_acs, 1.0 / theta, 1, f, d, 1));   // d_0 = P f / theta
   TPSS_CHECK_CUDA(cudaMemcpyAsync(x, d, n * sizeof(double), cudaMemcpyDeviceToDevice, s));   // x_1
+  if (ctx->mapped) {
+    // one launch per step (residual, surrogate cell solves, recurrence), the
+    // iterate alternating between x and r
+    double* xc = x;
+    double* xn = r;
+    for (int k = 1; k < mg->cheb_m; ++k) {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      TPSS_TRY(mapped_fused(mg->coarse_acs, nullptr, mg->coarse_acs->nsub, 1, xc, f, xn, d, 1, 0.0, rho_new * rho,
+                            2.0 * rho_new / delta));
+      std::swap(xc, xn);
+      rho = rho_new;
+    }
+    if (xc != x) TPSS_CHECK_CUDA(cudaMemcpyAsync(x, xc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return TPSS_OK;
+  }
   for (int k = 1; k < mg->cheb_m; ++k) {
     TPSS_TRY(apply_operator_t<double>(ctx, 0, 1, x, r, f));                // r_k = f - A x_k
     TPSS_TRY(smooth_additive_t<double>(mg->coarse_acs, 1.0, 1, r, z, 1));  // z = P r_k

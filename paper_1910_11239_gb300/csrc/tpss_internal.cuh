@@ -284,6 +284,12 @@ tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, do
 // surrogate cell solvers: fills P->d_A, d_M, d_Z, d_lam (per cell) and d_inv
 tpss_status mapped_cell_eigendata(tpss_ctx* ctx, tpss_patches* P, int* d_err);
 tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b);
+// residual + surrogate cell solve + update, one launch, for the cells of
+// `list` (packed positions; null: all cells of the level): mode 0 out = x +
+// omega z, mode 1 d = c1 d + c2 z and out = x + d, z = P_K (b - A x)_K; out
+// may alias x only for cells that are not face neighbours of one another
+tpss_status mapped_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
+                         double* out, double* d, int mode, double omega, double c1, double c2);
 // ---- mapped3.cu (3D meshes of trilinear hexahedra)
 tpss_status mapped3_refine(const double* coarse, int nx, int ny, int nz, double* fine, cudaStream_t s);
 tpss_status mapped3_setup_level(tpss_ctx* ctx, int level, double gpk);
@@ -291,6 +297,8 @@ tpss_status mapped3_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, d
 tpss_status mapped3_surrogate_widths(tpss_ctx* ctx, int level, double* h);
 tpss_status mapped3_inv_table(tpss_ctx* ctx, tpss_patches* P);
 tpss_status mapped3_rhs(tpss_ctx* ctx, int level, double* b);
+tpss_status mapped3_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
+                          double* out, double* d, int mode, double omega, double c1, double c2);
 
 // ---- setup.cu
 __global__ void gen_eig_kernel(const double* __restrict__ Aall, const double* __restrict__ Mall, int nprob, int n,
