@@ -785,6 +785,18 @@ def run_distorted(tpss, workloads, perf, torch, steps):
                 rec[f"{sm}1_pcg"] = {"omega": om, "vcycle_ms": ms, "iterations": res["iters"],
                                      "nu_frac_residual": perf.fractional_iterations(res["history"], 1e-8),
                                      "solve_s": t, "dofs_per_s": N / t}
+                # the same solve with the FP32 V-cycle (flexible PCG in FP64)
+                prob.mg_setup(sm, om, tpss.FP32, flexible_cg=1, coarse_solver=tpss.COARSE_CHEBYSHEV)
+                z = torch.empty_like(b)
+                ms32 = _time_calls(torch, lambda: prob.vcycle(b, z), max(2, steps // 2))
+                e0.record()
+                res32 = prob.pcg_solve(b, x, rtol=1e-8, maxit=200)
+                e1.record()
+                torch.cuda.synchronize()
+                t32 = e0.elapsed_time(e1) / 1e3
+                rec[f"{sm}1_pcg_fp32_vcycle"] = {"vcycle_ms": ms32, "iterations": res32["iters"], "solve_s": t32,
+                                                 "dofs_per_s": N / t32, "speedup_vs_fp64": t / t32}
+                prob.mg_setup(sm, om, tpss.FP64, coarse_solver=tpss.COARSE_CHEBYSHEV)
                 if sm == "ACS":   # the coarse solve's share of the V-cycle (Chebyshev, CUDA graph)
                     b0 = torch.from_numpy(workloads.rhs_uniform(prob.ndofs(0), seed=5)).to("cuda")
                     x0 = torch.empty_like(b0)

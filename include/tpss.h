@@ -99,13 +99,18 @@ typedef struct tpss_patches tpss_patches;
  * cell (eq. avglength: widths = mean lengths of the cell's edges per
  * direction, the neighbours' surrogate widths across its faces), by fast
  * diagonalization per cell.
- * Not available on these contexts (TPSS_EINVAL): vertex patches, FP32 / TF32
- * / BF16 operators and smoothers, tpss_ir_solve, kind 1 of
- * tpss_assemble_rhs (kind 0 is f = d pi^2 prod sin(pi x_t), g = 0), the
- * per-color residual update of MCS (the full residual is recomputed) and the
- * fast-diagonalization coarse solver.  Every other call of this header works
- * as on Cartesian contexts; tpss_mg_setup's AUTO coarse solver takes the
- * Chebyshev iteration above 4096 coarse DoFs.  Release with tpss_destroy. */
+ * FP32 (tpss_apply_operator_f32, FP32 cell patches, tpss_mg_setup with
+ * precision TPSS_FP32: an FP32 V-cycle with FP32 geometry and surrogate data,
+ * FP32 Chebyshev coarse steps, inside FP64 flexible PCG) is available.  The
+ * smoothers compute the residual, the surrogate cell solves and the update
+ * in one kernel per color (the multiplicative colors only on their own
+ * cells).  Not available on these contexts (TPSS_EINVAL): vertex patches,
+ * TF32 / BF16, kind 1 of tpss_assemble_rhs (kind 0 is f = d pi^2 prod
+ * sin(pi x_t), g = 0), the per-color residual update of MCS (the residual
+ * is formed per color on the color's cells) and the fast-diagonalization
+ * coarse solver.  Every other call of this header works as on Cartesian
+ * contexts; tpss_mg_setup's AUTO coarse solver takes the Chebyshev iteration
+ * above 4096 coarse DoFs.  Release with tpss_destroy. */
 tpss_status tpss_create_mapped(int dim, int degree, const int ncells[3], const double* vertices, int nlevels,
                                double gamma_hat, int penalty_poly, void* cuda_stream, tpss_ctx** out);
 
@@ -223,6 +228,10 @@ tpss_status tpss_smooth_additive_f32(tpss_patches* patches, float omega, int nrh
  *   r = b - A x;   x <- x + omega * sum_{j in J_c} R_j^T A_j^{-1} R_j r. */
 tpss_status tpss_smooth_multiplicative(tpss_patches* patches, double omega, int reverse_colors,
                                        int nrhs, const double* b, double* x);
+/* The same sweep with FP32 vectors, operator and local solves (patches set up
+ * with FP32, TF32 or BF16; the multiplicative mixed V-cycle uses it). */
+tpss_status tpss_smooth_multiplicative_f32(tpss_patches* patches, float omega, int reverse_colors, int nrhs,
+                                           const float* b, float* x);
 
 /* ------------------------------------------------------------- operators --
  * Matrix-free SIPG operator Au = A_l u (eq. bfsipg) by sum factorization over

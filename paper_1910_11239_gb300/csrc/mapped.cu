@@ -80,6 +80,11 @@ __device__ __forceinline__ double dist(double2 a, double2 b) {
 
 }  // namespace
 
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
 // ---------------------------------------------------------------- meshes
 // F = refinement of V (nx x ny cells): edge midpoints 0.5 (a + b), cell
 // centres 0.25 (((a + b) + c) + d) -- the images of the reference midpoints.
@@ -190,31 +195,31 @@ struct MappedShape {
   static constexpr int FACE = F1 + NL;
   static constexpr int SLOT = FACE + 9 * 4 * N1;
   static constexpr int TABLES = 2 * NL + 4 * N1;
-  static constexpr size_t SMEM = (size_t)(TABLES + CPB * SLOT) * sizeof(double);
 };
 
-struct MappedOpArgs {
-  const double* u;
-  double* out;
-  const double* rhs;   // not null: out = rhs - A u
-  const double* geo;   // [ncells][G]
+template <typename T>
+struct MappedOpArgsT {
+  const T* u;
+  T* out;
+  const T* rhs;        // not null: out = rhs - A u
+  const T* geo;        // [ncells][G]
   const Basis1D* B;
   int nx, ny;
   int64_t ncells, ndofs;
 };
 
 // tables of the 2D kernels in shared memory: Vq, Dq (n1^2), d0, d1, wq (n1)
-template <int N1>
-__device__ __forceinline__ void mapped_tables(const Basis1D* __restrict__ B, double* sm) {
+template <int N1, typename T>
+__device__ __forceinline__ void mapped_tables(const Basis1D* __restrict__ B, T* sm) {
   constexpr int NL = N1 * N1;
   for (int e = threadIdx.x; e < NL; e += blockDim.x) {
-    sm[e] = B->Vq[e];
-    sm[NL + e] = B->Dq[e];
+    sm[e] = (T)B->Vq[e];
+    sm[NL + e] = (T)B->Dq[e];
   }
   for (int e = threadIdx.x; e < N1; e += blockDim.x) {
-    sm[2 * NL + e] = B->d0[e];
-    sm[2 * NL + N1 + e] = B->d1[e];
-    sm[2 * NL + 2 * N1 + e] = B->wq[e];
+    sm[2 * NL + e] = (T)B->d0[e];
+    sm[2 * NL + N1 + e] = (T)B->d1[e];
+    sm[2 * NL + 2 * N1 + e] = (T)B->wq[e];
   }
 }
 
@@ -222,32 +227,32 @@ __device__ __forceinline__ void mapped_tables(const Basis1D* __restrict__ B, dou
 // global memory).  Every thread of the CTA calls it (it synchronizes the
 // CTA); the tables must have been written (they become visible at its first
 // barrier); W is the cell's slot, and W + S::U keeps u_K afterwards.
-template <int N1>
-__device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, double* sm, double* W, int64_t cell,
-                                                    bool active, int tid) {
+template <int N1, typename T>
+__device__ __forceinline__ T mapped_cell_apply(const MappedOpArgsT<T>& a, T* sm, T* W, int64_t cell, bool active,
+                                               int tid) {
   using S = MappedShape<N1>;
   constexpr int NL = N1 * N1, K = N1 - 1, G = S::G;
   constexpr int GA = 3 * NL, GS = 3 * NL + 8 * N1;   // GeoLayout offsets
-  double* Vq = sm;
-  double* Dq = Vq + NL;
-  double* dd = Dq + NL;        // d0 then d1: phi_i'(0), phi_i'(1)
-  double* wq = dd + 2 * N1;
-  double* geo = W + S::GEO;
-  double* na = W + S::NA;
-  double* U = W + S::U;
-  double* tA = W + S::TA;
-  double* tB = W + S::TB;
-  double* F0 = W + S::F0;
-  double* F1 = W + S::F1;
-  double* trK = W + S::FACE;
-  double* dlK = trK + 4 * N1;
-  double* trN = dlK + 4 * N1;
-  double* dlN = trN + 4 * N1;
-  double* al = dlN + 4 * N1;
-  double* be = al + 4 * N1;
-  double* de = be + 4 * N1;
-  double* As = de + 4 * N1;
-  double* Bs = As + 4 * N1;
+  T* Vq = sm;
+  T* Dq = Vq + NL;
+  T* dd = Dq + NL;        // d0 then d1: phi_i'(0), phi_i'(1)
+  T* wq = dd + 2 * N1;
+  T* geo = W + S::GEO;
+  T* na = W + S::NA;
+  T* U = W + S::U;
+  T* tA = W + S::TA;
+  T* tB = W + S::TB;
+  T* F0 = W + S::F0;
+  T* F1 = W + S::F1;
+  T* trK = W + S::FACE;
+  T* dlK = trK + 4 * N1;
+  T* trN = dlK + 4 * N1;
+  T* dlN = trN + 4 * N1;
+  T* al = dlN + 4 * N1;
+  T* be = al + 4 * N1;
+  T* de = be + 4 * N1;
+  T* As = de + 4 * N1;
+  T* Bs = As + 4 * N1;
   const int cx = active ? (int)(cell % a.nx) : 0, cy = active ? (int)(cell / a.nx) : 0;
   const int64_t vbase = (int64_t)blockIdx.y * a.ndofs;
   // face f = 2 t + side: neighbour along t at -1 (side 0) / +1 (side 1)
@@ -265,7 +270,7 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
 #pragma unroll
     for (int f = 0; f < 4; ++f)
       if (has(f)) U[(1 + f) * NL + tid] = a.u[vbase + nbr(f) * NL + tid];
-    const double* gc = a.geo + cell * G;
+    const T* gc = a.geo + cell * G;
     for (int e = tid; e < G; e += NL) geo[e] = gc[e];
     // the neighbour across edge f sees it as its edge f ^ 1
     for (int e = tid; e < 8 * N1; e += NL) {
@@ -278,10 +283,10 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
   // ---- P1: cell stage A; edge traces and reference normal-derivative lines
   if (active) {
     const int q0 = tid % N1, i1 = tid / N1;
-    double sa = 0.0, sb = 0.0;
+    T sa = T(0), sb = T(0);
 #pragma unroll
     for (int i0 = 0; i0 < N1; ++i0) {
-      const double v = U[i0 + N1 * i1];
+      const T v = U[i0 + N1 * i1];
       sa = fma(Dq[q0 * N1 + i0], v, sa);
       sb = fma(Vq[q0 * N1 + i0], v, sb);
     }
@@ -289,16 +294,16 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
     tB[tid] = sb;
     for (int e = tid; e < 4 * N1; e += NL) {
       const int f = e / N1, j = e % N1, t = f >> 1, side = f & 1;
-      const double* ds = dd + side * N1;
-      double s = 0.0;
+      const T* ds = dd + side * N1;
+      T s = T(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) s = fma(ds[m], U[lidx(t, m, j)], s);
       trK[e] = U[lidx(t, side * K, j)];
       dlK[e] = s;
       if (has(f)) {
-        const double* UN = U + (1 + f) * NL;
-        const double* dn = dd + (1 - side) * N1;
-        double sn = 0.0;
+        const T* UN = U + (1 + f) * NL;
+        const T* dn = dd + (1 - side) * N1;
+        T sn = T(0);
 #pragma unroll
         for (int m = 0; m < N1; ++m) sn = fma(dn[m], UN[lidx(t, m, j)], sn);
         trN[e] = UN[lidx(t, (1 - side) * K, j)];
@@ -311,34 +316,34 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
   // ---- P2: reference gradients at the Gauss points times the metric; edge-point coefficients
   if (active) {
     const int q0 = tid % N1, q1 = tid / N1;
-    double g0 = 0.0, g1 = 0.0;
+    T g0 = T(0), g1 = T(0);
 #pragma unroll
     for (int i1 = 0; i1 < N1; ++i1) {
       g0 = fma(Vq[q1 * N1 + i1], tA[q0 + N1 * i1], g0);
       g1 = fma(Dq[q1 * N1 + i1], tB[q0 + N1 * i1], g1);
     }
-    const double c00 = geo[tid], c01 = geo[NL + tid], c11 = geo[2 * NL + tid];
+    const T c00 = geo[tid], c01 = geo[NL + tid], c11 = geo[2 * NL + tid];
     F0[tid] = fma(c00, g0, c01 * g1);
     F1[tid] = fma(c01, g0, c11 * g1);
     for (int e = tid; e < 4 * N1; e += NL) {
       const int f = e / N1, q = e % N1, t = f >> 1;
-      const double* fl = trK + f * N1;
-      const double* dl = dlK + f * N1;
-      double uK = 0.0, dtK = 0.0, dtanK = 0.0;
+      const T* fl = trK + f * N1;
+      const T* dl = dlK + f * N1;
+      T uK = T(0), dtK = T(0), dtanK = T(0);
 #pragma unroll
       for (int j = 0; j < N1; ++j) {
         uK = fma(Vq[q * N1 + j], fl[j], uK);
         dtK = fma(Vq[q * N1 + j], dl[j], dtK);
         dtanK = fma(Dq[q * N1 + j], fl[j], dtanK);
       }
-      const double aK0 = geo[GA + f * 2 * N1 + q], aK1 = geo[GA + f * 2 * N1 + N1 + q];   // J^{-1} n
-      const double dnK = t == 0 ? fma(aK0, dtK, aK1 * dtanK) : fma(aK0, dtanK, aK1 * dtK);
-      const double Wq = wq[q] * geo[GS + 2 * f], gam = geo[GS + 2 * f + 1];
-      double alpha, c1;
+      const T aK0 = geo[GA + f * 2 * N1 + q], aK1 = geo[GA + f * 2 * N1 + N1 + q];   // J^{-1} n
+      const T dnK = t == 0 ? fma(aK0, dtK, aK1 * dtanK) : fma(aK0, dtanK, aK1 * dtK);
+      const T Wq = wq[q] * geo[GS + 2 * f], gam = geo[GS + 2 * f + 1];
+      T alpha, c1;
       if (has(f)) {
-        const double* gl = trN + f * N1;
-        const double* gd = dlN + f * N1;
-        double uN = 0.0, dtN = 0.0, dtanN = 0.0;
+        const T* gl = trN + f * N1;
+        const T* gd = dlN + f * N1;
+        T uN = T(0), dtN = T(0), dtanN = T(0);
 #pragma unroll
         for (int j = 0; j < N1; ++j) {
           uN = fma(Vq[q * N1 + j], gl[j], uN);
@@ -346,11 +351,11 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
           dtanN = fma(Dq[q * N1 + j], gl[j], dtanN);
         }
         // the neighbour's J^{-1} n_N with n_N = -n
-        const double aN0 = -na[f * 2 * N1 + q], aN1 = -na[f * 2 * N1 + N1 + q];
-        const double dnN = t == 0 ? fma(aN0, dtN, aN1 * dtanN) : fma(aN0, dtanN, aN1 * dtN);
-        const double jump = uK - uN;
-        alpha = Wq * (0.5 * gam * jump - 0.5 * (dnK + dnN));
-        c1 = -0.5 * Wq * jump;
+        const T aN0 = -na[f * 2 * N1 + q], aN1 = -na[f * 2 * N1 + N1 + q];
+        const T dnN = t == 0 ? fma(aN0, dtN, aN1 * dtanN) : fma(aN0, dtanN, aN1 * dtN);
+        const T jump = uK - uN;
+        alpha = Wq * (T(0.5) * gam * jump - T(0.5) * (dnK + dnN));
+        c1 = -T(0.5) * Wq * jump;
       } else {
         alpha = Wq * (gam * uK - dnK);
         c1 = -Wq * uK;
@@ -365,7 +370,7 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
   // ---- P3: cell stage C (test gradients, first direction); edge sums per test line
   if (active) {
     const int i0 = tid % N1, q1 = tid / N1;
-    double sa = 0.0, sb = 0.0;
+    T sa = T(0), sb = T(0);
 #pragma unroll
     for (int q0 = 0; q0 < N1; ++q0) {
       sa = fma(Dq[q0 * N1 + i0], F0[q0 + N1 * q1], sa);
@@ -375,7 +380,7 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
     tB[tid] = sb;
     for (int e = tid; e < 4 * N1; e += NL) {
       const int f = e / N1, j = e % N1;
-      double sbv = 0.0, sav = 0.0;
+      T sbv = T(0), sav = T(0);
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
         sbv = fma(Vq[q * N1 + j], be[f * N1 + q], sbv);
@@ -391,7 +396,7 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
   // ---- P4: cell stage D and the edge contributions; write
   if (active) {
     const int i0 = tid % N1, i1 = tid / N1;
-    double v = 0.0;
+    T v = T(0);
 #pragma unroll
     for (int q1 = 0; q1 < N1; ++q1) {
       v = fma(Vq[q1 * N1 + i1], tA[i0 + N1 * q1], v);
@@ -406,19 +411,20 @@ __device__ __forceinline__ double mapped_cell_apply(const MappedOpArgs& a, doubl
     }
     return v;
   }
-  return 0.0;
+  return T(0);
 }
 
-template <int N1>
-__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(MappedOpArgs a) {
+template <int N1, typename T>
+__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(MappedOpArgsT<T> a) {
   using S = MappedShape<N1>;
   constexpr int NL = N1 * N1;
-  extern __shared__ double sm[];
-  mapped_tables<N1>(a.B, sm);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  mapped_tables<N1, T>(a.B, sm);
   const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
   const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
   const bool active = cell < a.ncells;
-  const double v = mapped_cell_apply<N1>(a, sm, sm + S::TABLES + slot * S::SLOT, cell, active, tid);
+  const T v = mapped_cell_apply<N1, T>(a, sm, sm + S::TABLES + slot * S::SLOT, cell, active, tid);
   if (active) {
     const int64_t gi = (int64_t)blockIdx.y * a.ndofs + cell * NL + tid;
     a.out[gi] = a.rhs ? a.rhs[gi] - v : v;
@@ -432,25 +438,27 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_op_kernel(Map
 //   mode 1:  d_K = c1 d_K + c2 z,  out_K = x_K + d_K   (a Chebyshev step)
 // out may equal x when no listed cell is a face neighbour of another (one
 // color of the red-black sweep); otherwise out is a different vector.
-struct MappedFusedArgs {
-  MappedOpArgs op;     // op.u = x
-  const double* b;
-  double* out;
-  double* d;
+template <typename T>
+struct MappedFusedArgsT {
+  MappedOpArgsT<T> op;  // op.u = x
+  const T* b;
+  T* out;
+  T* d;
   const int* list;
   int64_t count;
-  const double* Z[3];  // per cell and direction [N1 * N1], column j = eigenvector j
-  const double* inv;   // per cell [N1^dim]
+  const T* Z[3];       // per cell and direction [N1 * N1], column j = eigenvector j
+  const T* inv;        // per cell [N1^dim]
   int mode;
-  double omega, c1, c2;
+  T omega, c1, c2;
 };
 
-template <int N1>
-__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_fused_kernel(MappedFusedArgs f) {
+template <int N1, typename T>
+__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_fused_kernel(MappedFusedArgsT<T> f) {
   using S = MappedShape<N1>;
   constexpr int NL = N1 * N1, SL = S::SLOT + 2 * NL;
-  extern __shared__ double sm[];
-  mapped_tables<N1>(f.op.B, sm);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  mapped_tables<N1, T>(f.op.B, sm);
   const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
   const int64_t idx = (int64_t)blockIdx.x * S::CPB + slot;
   const bool active = idx < f.count;
@@ -463,97 +471,99 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_fused_kernel(
       cell = idx;
     }
   }
-  double* W = sm + S::TABLES + slot * SL;
-  double* Zs = W + S::SLOT;   // Z_0, Z_1 of the cell
+  T* W = sm + S::TABLES + slot * SL;
+  T* Zs = W + S::SLOT;   // Z_0, Z_1 of the cell
   if (active) {
     Zs[tid] = f.Z[0][cell * NL + tid];
     Zs[NL + tid] = f.Z[1][cell * NL + tid];
   }
-  const double v = mapped_cell_apply<N1>(f.op, sm, W, cell, active, tid);
+  const T v = mapped_cell_apply<N1, T>(f.op, sm, W, cell, active, tid);
   const int64_t gi = (int64_t)blockIdx.y * f.op.ndofs + cell * NL + tid;
-  const double xo = active ? W[S::U + tid] : 0.0;
-  double* R = W + S::TA;
-  double* T1 = W + S::TB;
-  double* T2 = W + S::F0;
-  double* T3 = W + S::F1;
+  const T xo = active ? W[S::U + tid] : T(0);
+  T* R = W + S::TA;
+  T* T1 = W + S::TB;
+  T* T2 = W + S::F0;
+  T* T3 = W + S::F1;
   const int i0 = tid % N1, i1 = tid / N1;
   __syncthreads();   // the operator's last stage read these arrays
   if (active) R[tid] = f.b[gi] - v;
   __syncthreads();
   if (active) {   // Z_0^T along x
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Zs[m * N1 + i0], R[m + N1 * i1], s);
     T1[tid] = s;
   }
   __syncthreads();
   if (active) {   // Z_1^T along y, then 1 / (lambda_i + lambda_j)
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Zs[NL + m * N1 + i1], T1[i0 + N1 * m], s);
     T2[tid] = s * f.inv[cell * NL + tid];
   }
   __syncthreads();
   if (active) {   // Z_1 along y
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Zs[NL + i1 * N1 + m], T2[i0 + N1 * m], s);
     T3[tid] = s;
   }
   __syncthreads();
   if (active) {   // Z_0 along x, update
-    double z = 0.0;
+    T z = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) z = fma(Zs[i0 * N1 + m], T3[m + N1 * i1], z);
     if (f.mode == 0) {
       f.out[gi] = fma(f.omega, z, xo);
     } else {
-      const double dn = fma(f.c1, f.d[gi], f.c2 * z);
+      const T dn = fma(f.c1, f.d[gi], f.c2 * z);
       f.d[gi] = dn;
       f.out[gi] = xo + dn;
     }
   }
 }
 
-template <int N1>
-static tpss_status launch_fused(tpss_ctx* ctx, const MappedFusedArgs& a, int nrhs) {
+template <int N1, typename T>
+static tpss_status launch_fused(tpss_ctx* ctx, const MappedFusedArgsT<T>& a, int nrhs) {
   using S = MappedShape<N1>;
-  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 2 * N1 * N1)) * sizeof(double);
+  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 2 * N1 * N1)) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_fused_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_fused_kernel<N1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     attr = true;
   }
   const dim3 grid((unsigned)((a.count + S::CPB - 1) / S::CPB), (unsigned)nrhs);
-  mapped_fused_kernel<N1><<<grid, S::THREADS, smem, ctx->stream>>>(a);
+  mapped_fused_kernel<N1, T><<<grid, S::THREADS, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
 
-template <int N1>
-static tpss_status launch_mapped(tpss_ctx* ctx, const MappedOpArgs& a, int nrhs) {
+template <int N1, typename T>
+static tpss_status launch_mapped(tpss_ctx* ctx, const MappedOpArgsT<T>& a, int nrhs) {
   using S = MappedShape<N1>;
+  const size_t smem = (size_t)(S::TABLES + S::CPB * S::SLOT) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_op_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM));
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_op_kernel<N1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
     attr = true;
   }
   const dim3 grid((unsigned)((a.ncells + S::CPB - 1) / S::CPB), (unsigned)nrhs);
-  mapped_op_kernel<N1><<<grid, S::THREADS, S::SMEM, ctx->stream>>>(a);
+  mapped_op_kernel<N1, T><<<grid, S::THREADS, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
 
-tpss_status mapped_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
-                         double* out, double* d, int mode, double omega, double c1, double c2) {
+template <typename T>
+tpss_status mapped_fused_t(tpss_patches* P, const int* list, int64_t count, int nrhs, const T* x, const T* b, T* out,
+                           T* d, int mode, T omega, T c1, T c2) {
   tpss_ctx* ctx = P->ctx;
-  if (ctx->dim == 3) return mapped3_fused(P, list, count, nrhs, x, b, out, d, mode, omega, c1, c2);
+  if (ctx->dim == 3) return mapped3_fused_t<T>(P, list, count, nrhs, x, b, out, d, mode, omega, c1, c2);
   const Level& L = ctx->levels[P->level];
-  MappedFusedArgs a{};
+  MappedFusedArgsT<T> a{};
   a.op.u = x;
-  a.op.geo = L.d_geo;
+  a.op.geo = geo_of<T>(L);
   a.op.B = ctx->d_basis;
   a.op.nx = L.nc[0];
   a.op.ny = L.nc[1];
@@ -564,58 +574,68 @@ tpss_status mapped_fused(tpss_patches* P, const int* list, int64_t count, int nr
   a.d = d;
   a.list = list;
   a.count = count;
-  a.Z[0] = P->d_Z[0];
-  a.Z[1] = P->d_Z[1];
-  a.inv = P->d_inv;
+  for (int t = 0; t < 2; ++t) a.Z[t] = patch_Z<T>(P, t);
+  a.inv = patch_inv<T>(P);
   a.mode = mode;
   a.omega = omega;
   a.c1 = c1;
   a.c2 = c2;
+  if (!a.op.geo || !a.Z[0] || !a.inv) {
+    set_error("smoother: surrogate cell data missing for this precision");
+    return TPSS_EINVAL;
+  }
   switch (ctx->n1) {
-    case 2: return launch_fused<2>(ctx, a, nrhs);
-    case 3: return launch_fused<3>(ctx, a, nrhs);
-    case 4: return launch_fused<4>(ctx, a, nrhs);
-    case 5: return launch_fused<5>(ctx, a, nrhs);
-    case 6: return launch_fused<6>(ctx, a, nrhs);
-    case 7: return launch_fused<7>(ctx, a, nrhs);
-    case 8: return launch_fused<8>(ctx, a, nrhs);
+    case 2: return launch_fused<2, T>(ctx, a, nrhs);
+    case 3: return launch_fused<3, T>(ctx, a, nrhs);
+    case 4: return launch_fused<4, T>(ctx, a, nrhs);
+    case 5: return launch_fused<5, T>(ctx, a, nrhs);
+    case 6: return launch_fused<6, T>(ctx, a, nrhs);
+    case 7: return launch_fused<7, T>(ctx, a, nrhs);
+    case 8: return launch_fused<8, T>(ctx, a, nrhs);
     default: break;
   }
   set_error("smoother: meshes of quadrilaterals support degrees 1..7");
   return TPSS_EINVAL;
 }
+template tpss_status mapped_fused_t<double>(tpss_patches*, const int*, int64_t, int, const double*, const double*,
+                                            double*, double*, int, double, double, double);
+template tpss_status mapped_fused_t<float>(tpss_patches*, const int*, int64_t, int, const float*, const float*, float*,
+                                           float*, int, float, float, float);
 
 static double penalty_prefactor(const tpss_ctx* ctx) {
   return ctx->gamma_hat * (ctx->penalty_poly == TPSS_PENALTY_KP1SQ ? (double)(ctx->n1 * ctx->n1)
                                                                    : (double)(ctx->k * ctx->n1));
 }
 
-tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs) {
-  if (ctx->dim == 3) return mapped3_apply(ctx, level, nrhs, u, out, rhs);
+template <typename T>
+tpss_status mapped_apply_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out, const T* rhs) {
+  if (ctx->dim == 3) return mapped3_apply_t<T>(ctx, level, nrhs, u, out, rhs);
   const Level& L = ctx->levels[level];
-  MappedOpArgs a{};
+  MappedOpArgsT<T> a{};
   a.u = u;
   a.out = out;
   a.rhs = rhs;
-  a.geo = L.d_geo;
+  a.geo = geo_of<T>(L);
   a.B = ctx->d_basis;
   a.nx = L.nc[0];
   a.ny = L.nc[1];
   a.ncells = L.ncells;
   a.ndofs = L.ndofs;
   switch (ctx->n1) {
-    case 2: return launch_mapped<2>(ctx, a, nrhs);
-    case 3: return launch_mapped<3>(ctx, a, nrhs);
-    case 4: return launch_mapped<4>(ctx, a, nrhs);
-    case 5: return launch_mapped<5>(ctx, a, nrhs);
-    case 6: return launch_mapped<6>(ctx, a, nrhs);
-    case 7: return launch_mapped<7>(ctx, a, nrhs);
-    case 8: return launch_mapped<8>(ctx, a, nrhs);
+    case 2: return launch_mapped<2, T>(ctx, a, nrhs);
+    case 3: return launch_mapped<3, T>(ctx, a, nrhs);
+    case 4: return launch_mapped<4, T>(ctx, a, nrhs);
+    case 5: return launch_mapped<5, T>(ctx, a, nrhs);
+    case 6: return launch_mapped<6, T>(ctx, a, nrhs);
+    case 7: return launch_mapped<7, T>(ctx, a, nrhs);
+    case 8: return launch_mapped<8, T>(ctx, a, nrhs);
     default: break;
   }
   set_error("operator: meshes of quadrilaterals support degrees 1..7");
   return TPSS_EINVAL;
 }
+template tpss_status mapped_apply_t<double>(tpss_ctx*, int, int, const double*, double*, const double*);
+template tpss_status mapped_apply_t<float>(tpss_ctx*, int, int, const float*, float*, const float*);
 
 // ------------------------------------------------- surrogate cell solvers
 // hbar[t][c] of eq. avglength (vertex distances)
@@ -861,6 +881,13 @@ extern "C" tpss_status tpss_create_mapped(int dim, int degree, const int ncells[
     mapped_geometry_kernel<<<(unsigned)L.ncells, 64, 0, ctx->stream>>>(
         ctx->d_basis, reinterpret_cast<const double2*>(L.d_verts), L.nc[0], L.nc[1], penalty_prefactor(ctx),
         L.d_geo);
+  }
+  for (int l = 0; l < nlevels; ++l) {   // FP32 copy for the mixed-precision V-cycle
+    Level& L = ctx->levels[l];
+    const size_t g = (size_t)L.ncells * (dim == 3 ? (size_t)(6 * ctx->n1 + 24) * ctx->n1 * ctx->n1 + 6
+                                                   : (size_t)GeoLayout(ctx->n1).G);
+    if ((st = dalloc_t(&L.d_geo32, g)) != TPSS_OK) return fail(st);
+    to_float_kernel<<<(unsigned)std::min<size_t>((g + 255) / 256, 4096), 256, 0, ctx->stream>>>(L.d_geo, L.d_geo32, g);
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     set_error("tpss_create_mapped: vertex refinement or geometry setup failed");

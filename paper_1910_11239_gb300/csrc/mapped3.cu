@@ -248,53 +248,53 @@ struct Mapped3Shape {
   static constexpr int CPB = 256 / NV > 0 ? 256 / NV : 1;
   static constexpr int THREADS = CPB * NV;
   static constexpr int G = 6 * NV + 24 * NF + 6;    // Geo3Layout(N1).G
-  // per-cell slot (doubles): U (own + 6 neighbours), 6 cell scratch arrays,
+  // per-cell slot (Ts): U (own + 6 neighbours), 6 cell scratch arrays,
   // face arrays: set A (6 x [6][NF]) and set B (4 x [6][NF])
   static constexpr int U = 0, SC = 7 * NV, FA = 13 * NV, FB = 13 * NV + 36 * NF;
   static constexpr int SLOT = 13 * NV + 60 * NF;
   static constexpr int TABLES = 2 * NF + 4 * N1;
-  static constexpr size_t SMEM = (size_t)(TABLES + CPB * SLOT) * sizeof(double);
 };
 
-struct Mapped3Args {
-  const double* u;
-  double* out;
-  const double* rhs;   // not null: out = rhs - A u
-  const double* geo;   // [ncells][G]
+template <typename T>
+struct Mapped3ArgsT {
+  const T* u;
+  T* out;
+  const T* rhs;        // not null: out = rhs - A u
+  const T* geo;        // [ncells][G]
   const Basis1D* B;
   int nx, ny, nz;
   int64_t ncells, ndofs;
 };
 
 // tables in shared memory: Vq, Dq (n1^2), d0, d1 (n1)
-template <int N1>
-__device__ __forceinline__ void mapped3_tables(const Basis1D* __restrict__ B, double* sm) {
+template <int N1, typename T>
+__device__ __forceinline__ void mapped3_tables(const Basis1D* __restrict__ B, T* sm) {
   constexpr int NF = N1 * N1;
   for (int e = threadIdx.x; e < NF; e += blockDim.x) {
-    sm[e] = B->Vq[e];
-    sm[NF + e] = B->Dq[e];
+    sm[e] = (T)B->Vq[e];
+    sm[NF + e] = (T)B->Dq[e];
   }
   for (int e = threadIdx.x; e < N1; e += blockDim.x) {
-    sm[2 * NF + e] = B->d0[e];
-    sm[2 * NF + N1 + e] = B->d1[e];
+    sm[2 * NF + e] = (T)B->d0[e];
+    sm[2 * NF + N1 + e] = (T)B->d1[e];
   }
 }
 
 // (A u)_K at the local DoF tid of cell `cell`; every thread of the CTA calls
 // it (it synchronizes the CTA), Wk is the cell's slot (Wk + S::U keeps u_K)
-template <int N1>
-__device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, double* sm, double* Wk, int64_t cell,
-                                                     bool active, int tid) {
+template <int N1, typename T>
+__device__ __forceinline__ T mapped3_cell_apply(const Mapped3ArgsT<T>& a, T* sm, T* Wk, int64_t cell, bool active,
+                                                int tid) {
   using S = Mapped3Shape<N1>;
   constexpr int NV = S::NV, NF = S::NF, K = N1 - 1, G = S::G;
   constexpr int GA = 6 * NV, GW = 6 * NV + 18 * NF, GS = 6 * NV + 24 * NF;   // Geo3Layout offsets
-  double* Vq = sm;
-  double* Dq = Vq + NF;
-  double* dd = Dq + NF;   // d0 then d1
-  double* U = Wk + S::U;
-  double* sc = Wk + S::SC;       // 6 x NV
-  double* fa = Wk + S::FA;       // 6 x 6 NF
-  double* fb = Wk + S::FB;       // 4 x 6 NF
+  T* Vq = sm;
+  T* Dq = Vq + NF;
+  T* dd = Dq + NF;   // d0 then d1
+  T* U = Wk + S::U;
+  T* sc = Wk + S::SC;       // 6 x NV
+  T* fa = Wk + S::FA;       // 6 x 6 NF
+  T* fb = Wk + S::FB;       // 4 x 6 NF
   const int ci0 = active ? (int)(cell % a.nx) : 0, ci1 = active ? (int)((cell / a.nx) % a.ny) : 0;
   const int ci2 = active ? (int)(cell / ((int64_t)a.nx * a.ny)) : 0;
   const int hasm = (ci0 > 0 ? 1 : 0) | (ci0 + 1 < a.nx ? 2 : 0) | (ci1 > 0 ? 4 : 0) | (ci1 + 1 < a.ny ? 8 : 0) |
@@ -310,7 +310,7 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
     return t == 0 ? it + N1 * (j + N1 * l) : t == 1 ? j + N1 * (it + N1 * l) : j + N1 * (l + N1 * it);
   };
   const int64_t vbase = (int64_t)blockIdx.y * a.ndofs;
-  const double* gc = a.geo + cell * G;
+  const T* gc = a.geo + cell * G;
   const int i0 = tid % N1, i1 = (tid / N1) % N1, i2 = tid / NF;
 
   // ---- P0: DoF values of the cell and its 6 neighbours
@@ -324,10 +324,10 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
 
   // ---- P1: x stage (D, V); traces and normal-derivative planes of both sides
   if (active) {
-    double sd = 0.0, sv = 0.0;   // thread = (q0, i1, i2)
+    T sd = T(0), sv = T(0);   // thread = (q0, i1, i2)
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      const double v = U[m + N1 * (i1 + N1 * i2)];
+      const T v = U[m + N1 * (i1 + N1 * i2)];
       sd = fma(Dq[i0 * N1 + m], v, sd);
       sv = fma(Vq[i0 * N1 + m], v, sv);
     }
@@ -335,16 +335,16 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
     sc[1 * NV + tid] = sv;
     for (int e = tid; e < 6 * NF; e += NV) {
       const int f = e / NF, p = e % NF, t = f >> 1, side = f & 1, j = p % N1, l = p / N1;
-      const double* ds = dd + side * N1;
-      double s = 0.0;
+      const T* ds = dd + side * N1;
+      T s = T(0);
 #pragma unroll
       for (int m = 0; m < N1; ++m) s = fma(ds[m], U[lidx(t, m, j, l)], s);
       fb[0 * 6 * NF + e] = U[lidx(t, side * K, j, l)];
       fb[1 * 6 * NF + e] = s;
       if (has(f)) {
-        const double* UN = U + (1 + f) * NV;
-        const double* dn = dd + (1 - side) * N1;
-        double sn = 0.0;
+        const T* UN = U + (1 + f) * NV;
+        const T* dn = dd + (1 - side) * N1;
+        T sn = T(0);
 #pragma unroll
         for (int m = 0; m < N1; ++m) sn = fma(dn[m], UN[lidx(t, m, j, l)], sn);
         fb[2 * 6 * NF + e] = UN[lidx(t, (1 - side) * K, j, l)];
@@ -356,10 +356,10 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
 
   // ---- P2: y stage (V, D, V); face stage along u (both sides)
   if (active) {
-    double dv = 0.0, vd = 0.0, vv = 0.0;   // thread = (q0, q1, i2)
+    T dv = T(0), vd = T(0), vv = T(0);   // thread = (q0, q1, i2)
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      const double xd = sc[0 * NV + i0 + N1 * (m + N1 * i2)], xv = sc[1 * NV + i0 + N1 * (m + N1 * i2)];
+      const T xd = sc[0 * NV + i0 + N1 * (m + N1 * i2)], xv = sc[1 * NV + i0 + N1 * (m + N1 * i2)];
       dv = fma(Vq[i1 * N1 + m], xd, dv);
       vd = fma(Dq[i1 * N1 + m], xv, vd);
       vv = fma(Vq[i1 * N1 + m], xv, vv);
@@ -369,9 +369,9 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
     sc[4 * NV + tid] = vv;
     for (int e = tid; e < 6 * NF; e += NV) {
       const int f = e / NF, p = e % NF, pu = p % N1, l = p / N1;
-      const double* tr = fb + f * NF;
-      const double* dl = fb + 6 * NF + f * NF;
-      double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      const T* tr = fb + f * NF;
+      const T* dl = fb + 6 * NF + f * NF;
+      T t1 = T(0), t2 = T(0), t3 = T(0);
 #pragma unroll
       for (int j = 0; j < N1; ++j) {
         t1 = fma(Vq[pu * N1 + j], tr[j + N1 * l], t1);
@@ -382,9 +382,9 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
       fa[1 * 6 * NF + e] = t2;
       fa[2 * 6 * NF + e] = t3;
       if (has(f)) {
-        const double* trn = fb + 12 * NF + f * NF;
-        const double* dln = fb + 18 * NF + f * NF;
-        double n1v = 0.0, n2v = 0.0, n3v = 0.0;
+        const T* trn = fb + 12 * NF + f * NF;
+        const T* dln = fb + 18 * NF + f * NF;
+        T n1v = T(0), n2v = T(0), n3v = T(0);
 #pragma unroll
         for (int j = 0; j < N1; ++j) {
           n1v = fma(Vq[pu * N1 + j], trn[j + N1 * l], n1v);
@@ -401,7 +401,7 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
 
   // ---- P3: z stage (V, V, D) and the metric; face stage along v and the edge coefficients
   if (active) {
-    double g0 = 0.0, g1 = 0.0, g2 = 0.0;   // thread = (q0, q1, q2)
+    T g0 = T(0), g1 = T(0), g2 = T(0);   // thread = (q0, q1, q2)
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const int o = i0 + N1 * (i1 + N1 * m);
@@ -409,63 +409,63 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
       g1 = fma(Vq[i2 * N1 + m], sc[3 * NV + o], g1);
       g2 = fma(Dq[i2 * N1 + m], sc[4 * NV + o], g2);
     }
-    const double c00 = gc[0 * NV + tid], c01 = gc[1 * NV + tid], c02 = gc[2 * NV + tid];
-    const double c11 = gc[3 * NV + tid], c12 = gc[4 * NV + tid], c22 = gc[5 * NV + tid];
+    const T c00 = gc[0 * NV + tid], c01 = gc[1 * NV + tid], c02 = gc[2 * NV + tid];
+    const T c11 = gc[3 * NV + tid], c12 = gc[4 * NV + tid], c22 = gc[5 * NV + tid];
     sc[0 * NV + tid] = fma(c00, g0, fma(c01, g1, c02 * g2));
     sc[1 * NV + tid] = fma(c01, g0, fma(c11, g1, c12 * g2));
     sc[5 * NV + tid] = fma(c02, g0, fma(c12, g1, c22 * g2));
     for (int e = tid; e < 6 * NF; e += NV) {
       const int f = e / NF, p = e % NF, pu = p % N1, pv = p / N1, t = f >> 1;
       const int u = t == 0 ? 1 : 0, v = t == 2 ? 1 : 2;
-      const double* T1 = fa + f * NF;
-      const double* T2 = fa + 6 * NF + f * NF;
-      const double* T3 = fa + 12 * NF + f * NF;
-      double uK = 0.0, duK = 0.0, dtK = 0.0, dvK = 0.0;
+      const T* T1 = fa + f * NF;
+      const T* T2 = fa + 6 * NF + f * NF;
+      const T* T3 = fa + 12 * NF + f * NF;
+      T uK = T(0), duK = T(0), dtK = T(0), dvK = T(0);
 #pragma unroll
       for (int l = 0; l < N1; ++l) {
-        const double vq = Vq[pv * N1 + l];
+        const T vq = Vq[pv * N1 + l];
         uK = fma(vq, T1[pu + N1 * l], uK);
         duK = fma(vq, T2[pu + N1 * l], duK);
         dtK = fma(vq, T3[pu + N1 * l], dtK);
         dvK = fma(Dq[pv * N1 + l], T1[pu + N1 * l], dvK);
       }
-      double gK[3];
+      T gK[3];
       gK[t] = dtK;
       gK[u] = duK;
       gK[v] = dvK;
-      const double aK0 = gc[GA + (f * 3 + 0) * NF + p], aK1 = gc[GA + (f * 3 + 1) * NF + p];
-      const double aK2 = gc[GA + (f * 3 + 2) * NF + p];
-      const double dnK = fma(aK0, gK[0], fma(aK1, gK[1], aK2 * gK[2]));
-      const double Wq = gc[GW + f * NF + p], gam = gc[GS + f];
-      double alpha, c1;
+      const T aK0 = gc[GA + (f * 3 + 0) * NF + p], aK1 = gc[GA + (f * 3 + 1) * NF + p];
+      const T aK2 = gc[GA + (f * 3 + 2) * NF + p];
+      const T dnK = fma(aK0, gK[0], fma(aK1, gK[1], aK2 * gK[2]));
+      const T Wq = gc[GW + f * NF + p], gam = gc[GS + f];
+      T alpha, c1;
       if (has(f)) {
-        const double* N1p = fa + 18 * NF + f * NF;
-        const double* N2p = fa + 24 * NF + f * NF;
-        const double* N3p = fa + 30 * NF + f * NF;
-        double uN = 0.0, duN = 0.0, dtN = 0.0, dvN = 0.0;
+        const T* N1p = fa + 18 * NF + f * NF;
+        const T* N2p = fa + 24 * NF + f * NF;
+        const T* N3p = fa + 30 * NF + f * NF;
+        T uN = T(0), duN = T(0), dtN = T(0), dvN = T(0);
 #pragma unroll
         for (int l = 0; l < N1; ++l) {
-          const double vq = Vq[pv * N1 + l];
+          const T vq = Vq[pv * N1 + l];
           uN = fma(vq, N1p[pu + N1 * l], uN);
           duN = fma(vq, N2p[pu + N1 * l], duN);
           dtN = fma(vq, N3p[pu + N1 * l], dtN);
           dvN = fma(Dq[pv * N1 + l], N1p[pu + N1 * l], dvN);
         }
-        double gN[3];
+        T gN[3];
         gN[t] = dtN;
         gN[u] = duN;
         gN[v] = dvN;
         // the neighbour's J^{-1} n_N on its face f ^ 1, n_N = -n
-        const double* gnb = a.geo + nbr(f) * G + GA + ((f ^ 1) * 3) * NF + p;
-        const double dnN = -fma(gnb[0], gN[0], fma(gnb[NF], gN[1], gnb[2 * NF] * gN[2]));
-        const double jump = uK - uN;
-        alpha = Wq * (0.5 * gam * jump - 0.5 * (dnK + dnN));
-        c1 = -0.5 * Wq * jump;
+        const T* gnb = a.geo + nbr(f) * G + GA + ((f ^ 1) * 3) * NF + p;
+        const T dnN = -fma(gnb[0], gN[0], fma(gnb[NF], gN[1], gnb[2 * NF] * gN[2]));
+        const T jump = uK - uN;
+        alpha = Wq * (T(0.5) * gam * jump - T(0.5) * (dnK + dnN));
+        c1 = -T(0.5) * Wq * jump;
       } else {
         alpha = Wq * (gam * uK - dnK);
         c1 = -Wq * uK;
       }
-      const double aK[3] = {aK0, aK1, aK2};
+      const T aK[3] = {aK0, aK1, aK2};
       fb[0 * 6 * NF + e] = alpha;
       fb[1 * 6 * NF + e] = c1 * aK[t];
       fb[2 * 6 * NF + e] = c1 * aK[u];
@@ -476,7 +476,7 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
 
   // ---- P4: transposed z stage; test stage along v
   if (active) {
-    double bdv = 0.0, bvd = 0.0, bvv = 0.0;   // thread = (q0, q1, i2)
+    T bdv = T(0), bvd = T(0), bvv = T(0);   // thread = (q0, q1, i2)
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const int o = i0 + N1 * (i1 + N1 * m);
@@ -489,14 +489,14 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
     sc[4 * NV + tid] = bvv;
     for (int e = tid; e < 6 * NF; e += NV) {
       const int f = e / NF, p = e % NF, pu = p % N1, l = p / N1;
-      const double* al = fb + f * NF;
-      const double* bt = fb + 6 * NF + f * NF;
-      const double* bu = fb + 12 * NF + f * NF;
-      const double* bv = fb + 18 * NF + f * NF;
-      double qt = 0.0, qa = 0.0, qu = 0.0;
+      const T* al = fb + f * NF;
+      const T* bt = fb + 6 * NF + f * NF;
+      const T* bu = fb + 12 * NF + f * NF;
+      const T* bv = fb + 18 * NF + f * NF;
+      T qt = T(0), qa = T(0), qu = T(0);
 #pragma unroll
       for (int pv = 0; pv < N1; ++pv) {
-        const double vq = Vq[pv * N1 + l];
+        const T vq = Vq[pv * N1 + l];
         qt = fma(vq, bt[pu + N1 * pv], qt);
         qu = fma(vq, bu[pu + N1 * pv], qu);
         qa = fma(vq, al[pu + N1 * pv], qa);
@@ -511,7 +511,7 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
 
   // ---- P5: transposed y stage; test stage along u
   if (active) {
-    double yd = 0.0, yv = 0.0;   // thread = (q0, i1, i2)
+    T yd = T(0), yv = T(0);   // thread = (q0, i1, i2)
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const int o = i0 + N1 * (m + N1 * i2);
@@ -523,10 +523,10 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
     sc[1 * NV + tid] = yv;
     for (int e = tid; e < 6 * NF; e += NV) {
       const int f = e / NF, p = e % NF, j = p % N1, l = p / N1;
-      const double* qt = fa + f * NF;
-      const double* qa = fa + 6 * NF + f * NF;
-      const double* qu = fa + 12 * NF + f * NF;
-      double bt = 0.0, as = 0.0;
+      const T* qt = fa + f * NF;
+      const T* qa = fa + 6 * NF + f * NF;
+      const T* qu = fa + 12 * NF + f * NF;
+      T bt = T(0), as = T(0);
 #pragma unroll
       for (int pu = 0; pu < N1; ++pu) {
         bt = fma(Vq[pu * N1 + j], qt[pu + N1 * l], bt);
@@ -541,7 +541,7 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
 
   // ---- P6: transposed x stage and the face contributions; write
   if (active) {
-    double v = 0.0;   // thread = (i0, i1, i2)
+    T v = T(0);   // thread = (i0, i1, i2)
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const int o = m + N1 * (i1 + N1 * i2);
@@ -559,19 +559,20 @@ __device__ __forceinline__ double mapped3_cell_apply(const Mapped3Args& a, doubl
     }
     return v;
   }
-  return 0.0;
+  return T(0);
 }
 
-template <int N1>
-__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_op_kernel(Mapped3Args a) {
+template <int N1, typename T>
+__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_op_kernel(Mapped3ArgsT<T> a) {
   using S = Mapped3Shape<N1>;
   constexpr int NV = S::NV;
-  extern __shared__ double sm[];
-  mapped3_tables<N1>(a.B, sm);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  mapped3_tables<N1, T>(a.B, sm);
   const int slot = threadIdx.x / NV, tid = threadIdx.x % NV;
   const int64_t cell = (int64_t)blockIdx.x * S::CPB + slot;
   const bool active = cell < a.ncells;
-  const double v = mapped3_cell_apply<N1>(a, sm, sm + S::TABLES + slot * S::SLOT, cell, active, tid);
+  const T v = mapped3_cell_apply<N1, T>(a, sm, sm + S::TABLES + slot * S::SLOT, cell, active, tid);
   if (active) {
     const int64_t gi = (int64_t)blockIdx.y * a.ndofs + cell * NV + tid;
     a.out[gi] = a.rhs ? a.rhs[gi] - v : v;
@@ -581,25 +582,27 @@ __global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_op_kernel(M
 // Residual, surrogate cell solve and update fused (see mapped.cu, 2D):
 //   r = b - (A x)_K, z = (Z_2 x Z_1 x Z_0) Lambda^{-1} (Z_2 x Z_1 x Z_0)^T r,
 //   mode 0: out_K = x_K + omega z;  mode 1: d_K = c1 d_K + c2 z, out_K = x_K + d_K
-struct Mapped3FusedArgs {
-  Mapped3Args op;
-  const double* b;
-  double* out;
-  double* d;
+template <typename T>
+struct Mapped3FusedArgsT {
+  Mapped3ArgsT<T> op;
+  const T* b;
+  T* out;
+  T* d;
   const int* list;
   int64_t count;
-  const double* Z[3];
-  const double* inv;
+  const T* Z[3];
+  const T* inv;
   int mode;
-  double omega, c1, c2;
+  T omega, c1, c2;
 };
 
-template <int N1>
-__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_fused_kernel(Mapped3FusedArgs f) {
+template <int N1, typename T>
+__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_fused_kernel(Mapped3FusedArgsT<T> f) {
   using S = Mapped3Shape<N1>;
   constexpr int NV = S::NV, NF = S::NF, SL = S::SLOT + 3 * NF;
-  extern __shared__ double sm[];
-  mapped3_tables<N1>(f.op.B, sm);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  mapped3_tables<N1, T>(f.op.B, sm);
   const int slot = threadIdx.x / NV, tid = threadIdx.x % NV;
   const int64_t idx = (int64_t)blockIdx.x * S::CPB + slot;
   const bool active = idx < f.count;
@@ -612,93 +615,94 @@ __global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_fused_kerne
       cell = idx;
     }
   }
-  double* Wk = sm + S::TABLES + slot * SL;
-  double* Zs = Wk + S::SLOT;   // Z_0, Z_1, Z_2 of the cell
+  T* Wk = sm + S::TABLES + slot * SL;
+  T* Zs = Wk + S::SLOT;   // Z_0, Z_1, Z_2 of the cell
   if (active)
     for (int e = tid; e < 3 * NF; e += NV) Zs[e] = f.Z[e / NF][cell * NF + e % NF];
-  const double v = mapped3_cell_apply<N1>(f.op, sm, Wk, cell, active, tid);
+  const T v = mapped3_cell_apply<N1, T>(f.op, sm, Wk, cell, active, tid);
   const int64_t gi = (int64_t)blockIdx.y * f.op.ndofs + cell * NV + tid;
-  const double xo = active ? Wk[S::U + tid] : 0.0;
-  double* sc = Wk + S::SC;
+  const T xo = active ? Wk[S::U + tid] : T(0);
+  T* sc = Wk + S::SC;
   const int i0 = tid % N1, i1 = (tid / N1) % N1, i2 = tid / NF;
-  const double* Z0 = Zs;
-  const double* Z1 = Zs + NF;
-  const double* Z2 = Zs + 2 * NF;
+  const T* Z0 = Zs;
+  const T* Z1 = Zs + NF;
+  const T* Z2 = Zs + 2 * NF;
   __syncthreads();   // the operator's last stage read sc
   if (active) sc[tid] = f.b[gi] - v;
   __syncthreads();
   if (active) {   // Z_0^T along x
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Z0[m * N1 + i0], sc[m + N1 * i1 + NF * i2], s);
     sc[NV + tid] = s;
   }
   __syncthreads();
   if (active) {   // Z_1^T along y
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Z1[m * N1 + i1], sc[NV + i0 + N1 * m + NF * i2], s);
     sc[2 * NV + tid] = s;
   }
   __syncthreads();
   if (active) {   // Z_2^T along z, then 1 / (lambda_i + lambda_j + lambda_l)
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Z2[m * N1 + i2], sc[2 * NV + i0 + N1 * i1 + NF * m], s);
     sc[3 * NV + tid] = s * f.inv[cell * NV + tid];
   }
   __syncthreads();
   if (active) {   // Z_2 along z
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Z2[i2 * N1 + m], sc[3 * NV + i0 + N1 * i1 + NF * m], s);
     sc[4 * NV + tid] = s;
   }
   __syncthreads();
   if (active) {   // Z_1 along y
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) s = fma(Z1[i1 * N1 + m], sc[4 * NV + i0 + N1 * m + NF * i2], s);
     sc[5 * NV + tid] = s;
   }
   __syncthreads();
   if (active) {   // Z_0 along x, update
-    double z = 0.0;
+    T z = T(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) z = fma(Z0[i0 * N1 + m], sc[5 * NV + m + N1 * i1 + NF * i2], z);
     if (f.mode == 0) {
       f.out[gi] = fma(f.omega, z, xo);
     } else {
-      const double dn = fma(f.c1, f.d[gi], f.c2 * z);
+      const T dn = fma(f.c1, f.d[gi], f.c2 * z);
       f.d[gi] = dn;
       f.out[gi] = xo + dn;
     }
   }
 }
 
-template <int N1>
-static tpss_status launch_fused3(tpss_ctx* ctx, const Mapped3FusedArgs& a, int nrhs) {
+template <int N1, typename T>
+static tpss_status launch_fused3(tpss_ctx* ctx, const Mapped3FusedArgsT<T>& a, int nrhs) {
   using S = Mapped3Shape<N1>;
-  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 3 * S::NF)) * sizeof(double);
+  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 3 * S::NF)) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_fused_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_fused_kernel<N1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     attr = true;
   }
   const dim3 grid((unsigned)((a.count + S::CPB - 1) / S::CPB), (unsigned)nrhs);
-  mapped3_fused_kernel<N1><<<grid, S::THREADS, smem, ctx->stream>>>(a);
+  mapped3_fused_kernel<N1, T><<<grid, S::THREADS, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
 
-tpss_status mapped3_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
-                          double* out, double* d, int mode, double omega, double c1, double c2) {
+template <typename T>
+tpss_status mapped3_fused_t(tpss_patches* P, const int* list, int64_t count, int nrhs, const T* x, const T* b, T* out,
+                            T* d, int mode, T omega, T c1, T c2) {
   tpss_ctx* ctx = P->ctx;
   const Level& L = ctx->levels[P->level];
-  Mapped3FusedArgs a{};
+  Mapped3FusedArgsT<T> a{};
   a.op.u = x;
-  a.op.geo = L.d_geo;
+  a.op.geo = geo_of<T>(L);
   a.op.B = ctx->d_basis;
   a.op.nx = L.nc[0];
   a.op.ny = L.nc[1];
@@ -710,48 +714,58 @@ tpss_status mapped3_fused(tpss_patches* P, const int* list, int64_t count, int n
   a.d = d;
   a.list = list;
   a.count = count;
-  for (int t = 0; t < 3; ++t) a.Z[t] = P->d_Z[t];
-  a.inv = P->d_inv;
+  for (int t = 0; t < 3; ++t) a.Z[t] = patch_Z<T>(P, t);
+  a.inv = patch_inv<T>(P);
   a.mode = mode;
   a.omega = omega;
   a.c1 = c1;
   a.c2 = c2;
+  if (!a.op.geo || !a.Z[0] || !a.inv) {
+    set_error("smoother: surrogate cell data missing for this precision");
+    return TPSS_EINVAL;
+  }
   switch (ctx->n1) {
-    case 2: return launch_fused3<2>(ctx, a, nrhs);
-    case 3: return launch_fused3<3>(ctx, a, nrhs);
-    case 4: return launch_fused3<4>(ctx, a, nrhs);
-    case 5: return launch_fused3<5>(ctx, a, nrhs);
-    case 6: return launch_fused3<6>(ctx, a, nrhs);
-    case 7: return launch_fused3<7>(ctx, a, nrhs);
-    case 8: return launch_fused3<8>(ctx, a, nrhs);
+    case 2: return launch_fused3<2, T>(ctx, a, nrhs);
+    case 3: return launch_fused3<3, T>(ctx, a, nrhs);
+    case 4: return launch_fused3<4, T>(ctx, a, nrhs);
+    case 5: return launch_fused3<5, T>(ctx, a, nrhs);
+    case 6: return launch_fused3<6, T>(ctx, a, nrhs);
+    case 7: return launch_fused3<7, T>(ctx, a, nrhs);
+    case 8: return launch_fused3<8, T>(ctx, a, nrhs);
     default: break;
   }
   set_error("smoother: meshes of hexahedra support degrees 1..7");
   return TPSS_EINVAL;
 }
+template tpss_status mapped3_fused_t<double>(tpss_patches*, const int*, int64_t, int, const double*, const double*,
+                                             double*, double*, int, double, double, double);
+template tpss_status mapped3_fused_t<float>(tpss_patches*, const int*, int64_t, int, const float*, const float*,
+                                            float*, float*, int, float, float, float);
 
-template <int N1>
-static tpss_status launch_mapped3(tpss_ctx* ctx, const Mapped3Args& a, int nrhs) {
+template <int N1, typename T>
+static tpss_status launch_mapped3(tpss_ctx* ctx, const Mapped3ArgsT<T>& a, int nrhs) {
   using S = Mapped3Shape<N1>;
+  const size_t smem = (size_t)(S::TABLES + S::CPB * S::SLOT) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_op_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM));
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_op_kernel<N1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
     attr = true;
   }
   const dim3 grid((unsigned)((a.ncells + S::CPB - 1) / S::CPB), (unsigned)nrhs);
-  mapped3_op_kernel<N1><<<grid, S::THREADS, S::SMEM, ctx->stream>>>(a);
+  mapped3_op_kernel<N1, T><<<grid, S::THREADS, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
 }
 
-tpss_status mapped3_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs) {
+template <typename T>
+tpss_status mapped3_apply_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out, const T* rhs) {
   const Level& L = ctx->levels[level];
-  Mapped3Args a{};
+  Mapped3ArgsT<T> a{};
   a.u = u;
   a.out = out;
   a.rhs = rhs;
-  a.geo = L.d_geo;
+  a.geo = geo_of<T>(L);
   a.B = ctx->d_basis;
   a.nx = L.nc[0];
   a.ny = L.nc[1];
@@ -759,18 +773,20 @@ tpss_status mapped3_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, d
   a.ncells = L.ncells;
   a.ndofs = L.ndofs;
   switch (ctx->n1) {
-    case 2: return launch_mapped3<2>(ctx, a, nrhs);
-    case 3: return launch_mapped3<3>(ctx, a, nrhs);
-    case 4: return launch_mapped3<4>(ctx, a, nrhs);
-    case 5: return launch_mapped3<5>(ctx, a, nrhs);
-    case 6: return launch_mapped3<6>(ctx, a, nrhs);
-    case 7: return launch_mapped3<7>(ctx, a, nrhs);
-    case 8: return launch_mapped3<8>(ctx, a, nrhs);
+    case 2: return launch_mapped3<2, T>(ctx, a, nrhs);
+    case 3: return launch_mapped3<3, T>(ctx, a, nrhs);
+    case 4: return launch_mapped3<4, T>(ctx, a, nrhs);
+    case 5: return launch_mapped3<5, T>(ctx, a, nrhs);
+    case 6: return launch_mapped3<6, T>(ctx, a, nrhs);
+    case 7: return launch_mapped3<7, T>(ctx, a, nrhs);
+    case 8: return launch_mapped3<8, T>(ctx, a, nrhs);
     default: break;
   }
   set_error("operator: meshes of hexahedra support degrees 1..7");
   return TPSS_EINVAL;
 }
+template tpss_status mapped3_apply_t<double>(tpss_ctx*, int, int, const double*, double*, const double*);
+template tpss_status mapped3_apply_t<float>(tpss_ctx*, int, int, const float*, float*, const float*);
 
 // ------------------------------------------------- surrogate cell solvers
 // hbar[t][c]: the mean length of the cell's 4 edges along t (eq. avglength)

@@ -215,11 +215,7 @@ float* const* tmp_of<float>(const Level& L) { return L.t32; }
 
 template <typename T>
 tpss_status apply_operator_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out, const T* rhs) {
-  if (ctx->mapped) {
-    if constexpr (sizeof(T) == sizeof(double)) return mapped_apply(ctx, level, nrhs, u, out, rhs);
-    set_error("operator: meshes of quadrilaterals have an FP64 operator only");
-    return TPSS_EINVAL;
-  }
+  if (ctx->mapped) return mapped_apply_t<T>(ctx, level, nrhs, u, out, rhs);
   TPSS_TRY(ensure_level_scratch(ctx, level, nrhs));
   Level& L = ctx->levels[level];
   const LevelOps<T>& op = ops_of<T>(L);
@@ -247,7 +243,7 @@ tpss_status apply_operator_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* 
 // ndofs * nrhs doubles); used by the allocation-free entry point.
 tpss_status apply_operator_into(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out,
                                 double* const* tmp) {
-  if (ctx->mapped) return mapped_apply(ctx, level, nrhs, u, out, nullptr);
+  if (ctx->mapped) return mapped_apply_t<double>(ctx, level, nrhs, u, out, nullptr);
   Level& L = ctx->levels[level];
   const LevelOps<double>& op = L.op64;
 #define TPSS_OPI_CASE(D, N)                                                  \

@@ -457,6 +457,7 @@ static tpss_status build_level(tpss_ctx* ctx, int l) {
 static void free_level(Level& L) {
   dfree(L.d_verts);
   dfree(L.d_geo);
+  dfree(L.d_geo32);
   for (int t = 0; t < 3; ++t) {
     dfree(L.d_widths[t]);
     dfree(L.op64.M[t]); dfree(L.op64.A[t]); dfree(L.op64.F[t]);
@@ -497,6 +498,7 @@ static void free_patches(tpss_patches* P) {
     dfree(P->d_Z32[t]); dfree(P->d_lam32[t]);
   }
   dfree(P->d_inv);
+  dfree(P->d_inv32);
   dfree(P->d_scratch);
   dfree(P->d_add_list);
   dfree(P->d_mul_list);
@@ -696,6 +698,17 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
       dfree(d_err);
       return fail(st);
     }
+    if (precision != TPSS_FP64) {   // FP32 copies: the SIMT patch kernel (x = 0) and the fused kernel
+      const size_t nn = (size_t)P->nsub * n * n, vol = (size_t)P->nsub * (d == 3 ? n * n * n : n * n);
+      for (int t = 0; t < d; ++t) {
+        if ((st = dalloc_t(&P->d_Z32[t], nn)) != TPSS_OK) return fail(st);
+        if ((st = dalloc_t(&P->d_lam32[t], (size_t)P->nsub * n)) != TPSS_OK) return fail(st);
+        convert(P->d_Z[t], P->d_Z32[t], nn, ctx->stream);
+        convert(P->d_lam[t], P->d_lam32[t], (size_t)P->nsub * n, ctx->stream);
+      }
+      if ((st = dalloc_t(&P->d_inv32, vol)) != TPSS_OK) return fail(st);
+      convert(P->d_inv, P->d_inv32, vol, ctx->stream);
+    }
   }
   for (int t = 0; t < d && !ctx->mapped; ++t) {
     const int np = P->npos[t];
@@ -815,8 +828,8 @@ extern "C" tpss_status tpss_setup_patches(tpss_ctx* ctx, int level, int kind, in
   TPSS_REQUIRE(precision >= TPSS_FP64 && precision <= TPSS_BF16, "tpss_setup_patches: unknown precision");
   TPSS_REQUIRE(precision == TPSS_FP64 || ctx->k <= kMaxMixedDegree,
                "tpss_setup_patches: FP32/TF32/BF16 smoothers support degrees up to 7");
-  TPSS_REQUIRE(!ctx->mapped || (kind == TPSS_CELL && precision == TPSS_FP64),
-               "tpss_setup_patches: meshes of quadrilaterals support FP64 cell patches (surrogate solvers) only");
+  TPSS_REQUIRE(!ctx->mapped || (kind == TPSS_CELL && (precision == TPSS_FP64 || precision == TPSS_FP32)),
+               "tpss_setup_patches: mapped meshes support FP64 and FP32 cell patches (surrogate solvers) only");
   if (kind == TPSS_VERTEX_PATCH)
     for (int t = 0; t < ctx->dim; ++t)
       TPSS_REQUIRE(ctx->levels[level].nc[t] >= 2, "tpss_setup_patches: vertex patches need >= 2 cells per direction");

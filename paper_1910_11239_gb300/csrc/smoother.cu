@@ -316,16 +316,14 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
   cudaStream_t s = ctx->stream;
   Level& L = ctx->levels[P->level];
   const T* r = b;
-  if constexpr (sizeof(T) == 8) {
-    // surrogate cell solvers (mapped meshes): residual, local solves and the
-    // update in one launch, into a scratch vector (neighbours read x)
-    if (P->per_sub && !x_is_zero) {
-      TPSS_TRY(ensure_level_scratch(ctx, P->level, nrhs));
-      T* rb = residual_buffer<T>(L);
-      TPSS_TRY(mapped_fused(P, nullptr, P->nsub, nrhs, x, b, rb, nullptr, 0, omega, 0.0, 0.0));
-      TPSS_CHECK_CUDA(cudaMemcpyAsync(x, rb, (size_t)L.ndofs * nrhs * sizeof(T), cudaMemcpyDeviceToDevice, s));
-      return TPSS_OK;
-    }
+  // surrogate cell solvers (mapped meshes): residual, local solves and the
+  // update in one launch, into a scratch vector (neighbours read x)
+  if (P->per_sub && !x_is_zero) {
+    TPSS_TRY(ensure_level_scratch(ctx, P->level, nrhs));
+    T* rb = residual_buffer<T>(L);
+    TPSS_TRY(mapped_fused_t<T>(P, nullptr, P->nsub, nrhs, x, b, rb, nullptr, 0, omega, T(0), T(0)));
+    TPSS_CHECK_CUDA(cudaMemcpyAsync(x, rb, (size_t)L.ndofs * nrhs * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return TPSS_OK;
   }
   if (x_is_zero) {
     TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)L.ndofs * nrhs * sizeof(T), s));
@@ -415,14 +413,12 @@ tpss_status smooth_multiplicative_t(tpss_patches* P, T omega, int reverse, int n
     const int c = reverse ? nc - 1 - i : i;
     const int o = offs[c], cnt = offs[c + 1] - o;
     if (cnt == 0) continue;
-    if constexpr (sizeof(T) == 8) {
-      // surrogate cell solvers (mapped meshes): the residual on the color's
-      // cells only, local solves and update in one launch, in place (no two
-      // cells of a red-black color share a face)
-      if (P->per_sub) {
-        TPSS_TRY(mapped_fused(P, list + o, cnt, nrhs, x, b, x, nullptr, 0, omega, 0.0, 0.0));
-        continue;
-      }
+    // surrogate cell solvers (mapped meshes): the residual on the color's
+    // cells only, local solves and update in one launch, in place (no two
+    // cells of a red-black color share a face)
+    if (P->per_sub) {
+      TPSS_TRY(mapped_fused_t<T>(P, list + o, cnt, nrhs, x, b, x, nullptr, 0, omega, T(0), T(0)));
+      continue;
     }
     TPSS_TRY(apply_operator_t<T>(ctx, P->level, nrhs, x, rb, b));
     TPSS_TRY(patch_pass<T>(P, list + o, cnt, omega, nrhs, rb, x, s));
@@ -467,4 +463,14 @@ extern "C" tpss_status tpss_smooth_multiplicative(tpss_patches* P, double omega,
   TPSS_REQUIRE(nrhs >= 1 && nrhs <= 65535, "tpss_smooth_multiplicative: nrhs out of range");
   TPSS_REQUIRE((const void*)b != (const void*)x, "tpss_smooth_multiplicative: b and x must not alias");
   return smooth_multiplicative_t<double>(P, omega, reverse_colors, nrhs, b, x);
+}
+
+extern "C" tpss_status tpss_smooth_multiplicative_f32(tpss_patches* P, float omega, int reverse_colors, int nrhs,
+                                                      const float* b, float* x) {
+  clear_error();
+  TPSS_REQUIRE(P && b && x, "tpss_smooth_multiplicative_f32: null argument");
+  TPSS_REQUIRE(P->precision != TPSS_FP64, "tpss_smooth_multiplicative_f32: patches were set up for FP64");
+  TPSS_REQUIRE(nrhs >= 1 && nrhs <= 65535, "tpss_smooth_multiplicative_f32: nrhs out of range");
+  TPSS_REQUIRE((const void*)b != (const void*)x, "tpss_smooth_multiplicative_f32: b and x must not alias");
+  return smooth_multiplicative_t<float>(P, omega, reverse_colors, nrhs, b, x);
 }

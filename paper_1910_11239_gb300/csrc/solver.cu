@@ -31,6 +31,9 @@ void destroy_mg(tpss_ctx* ctx) {
     if (P) tpss_patches_destroy(P);
   if (mg->coarse_fd) tpss_patches_destroy(mg->coarse_fd);
   if (mg->coarse_acs) tpss_patches_destroy(mg->coarse_acs);
+  if (mg->coarse_acs32) tpss_patches_destroy(mg->coarse_acs32);
+  dfree(mg->cheb_vec32);
+  if (mg->cheb_exec32) cudaGraphExecDestroy(mg->cheb_exec32);
   dfree(mg->cheb_vec);
   if (mg->cheb_exec) cudaGraphExecDestroy(mg->cheb_exec);
   if (mg->cheb_capture) cudaStreamDestroy(mg->cheb_capture);
@@ -338,7 +341,11 @@ static tpss_status chebyshev_setup(tpss_ctx* ctx, MGState* mg) {
   return TPSS_OK;
 }
 
-static tpss_status chebyshev_body(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
+template <typename T>
+static tpss_status chebyshev_body(tpss_ctx* ctx, MGState* mg, const T* f, T* x);
+
+template <>
+tpss_status chebyshev_body<double>(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
   const int64_t n = mg->n0;
   cudaStream_t s = ctx->stream;
   double* r = mg->cheb_vec;
@@ -361,8 +368,8 @@ static tpss_status chebyshev_body(tpss_ctx* ctx, MGState* mg, const double* f, d
     double* xn = r;
     for (int k = 1; k < mg->cheb_m; ++k) {
       const double rho_new = 1.0 / (2.0 * sigma - rho);
-      TPSS_TRY(mapped_fused(mg->coarse_acs, nullptr, mg->coarse_acs->nsub, 1, xc, f, xn, d, 1, 0.0, rho_new * rho,
-                            2.0 * rho_new / delta));
+      TPSS_TRY(mapped_fused_t<double>(mg->coarse_acs, nullptr, mg->coarse_acs->nsub, 1, xc, f, xn, d, 1, 0.0,
+                                      rho_new * rho, 2.0 * rho_new / delta));
       std::swap(xc, xn);
       rho = rho_new;
     }
@@ -380,45 +387,93 @@ static tpss_status chebyshev_body(tpss_ctx* ctx, MGState* mg, const double* f, d
   return TPSS_OK;
 }
 
-// The m steps are ~3m small launches on level 0 (launch-bound): they are
-// captured once per (f, x) pair into a CUDA graph on a private stream (the
-// library's stream may be the legacy default stream, which cannot capture)
-// and replayed on the library's stream.  If capture is not possible the
-// steps run directly.
-static tpss_status chebyshev_apply(tpss_ctx* ctx, MGState* mg, const double* f, double* x) {
+// FP32 steps for the mixed V-cycle on mapped meshes: the FP64 interval and
+// step count with the FP32 surrogate cell solvers and operator
+template <>
+tpss_status chebyshev_body<float>(tpss_ctx* ctx, MGState* mg, const float* f, float* x) {
+  const int64_t n = mg->n0;
+  cudaStream_t s = ctx->stream;
+  float* r = mg->cheb_vec32;
+  float* d = r + 2 * n;
+  const double a = mg->cheb_a, b = mg->cheb_b;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  double rho = 1.0 / sigma;
   if (mg->cheb_m < 1) {
-    TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, mg->n0 * sizeof(double), ctx->stream));
+    TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(float), s));
     return TPSS_OK;
   }
-  if (!(mg->cheb_exec && mg->cheb_gf == f && mg->cheb_gx == x)) {
-    if (mg->cheb_exec) cudaGraphExecDestroy(mg->cheb_exec);
-    mg->cheb_exec = nullptr;
+  TPSS_TRY(smooth_additive_t<float>(mg->coarse_acs32, (float)(1.0 / theta), 1, f, d, 1));   // d_0 = P f / theta
+  TPSS_CHECK_CUDA(cudaMemcpyAsync(x, d, n * sizeof(float), cudaMemcpyDeviceToDevice, s));     // x_1
+  float* xc = x;
+  float* xn = r;
+  for (int k = 1; k < mg->cheb_m; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    TPSS_TRY(mapped_fused_t<float>(mg->coarse_acs32, nullptr, mg->coarse_acs32->nsub, 1, xc, f, xn, d, 1, 0.0f,
+                                   (float)(rho_new * rho), (float)(2.0 * rho_new / delta)));
+    std::swap(xc, xn);
+    rho = rho_new;
+  }
+  if (xc != x) TPSS_CHECK_CUDA(cudaMemcpyAsync(x, xc, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return TPSS_OK;
+}
+
+template <typename T>
+struct ChebGraph;
+template <>
+struct ChebGraph<double> {
+  static cudaGraphExec_t& exec(MGState* m) { return m->cheb_exec; }
+  static const void*& f(MGState* m) { return m->cheb_gf; }
+  static void*& x(MGState* m) { return m->cheb_gx; }
+};
+template <>
+struct ChebGraph<float> {
+  static cudaGraphExec_t& exec(MGState* m) { return m->cheb_exec32; }
+  static const void*& f(MGState* m) { return m->cheb_gf32; }
+  static void*& x(MGState* m) { return m->cheb_gx32; }
+};
+
+// The m steps are ~m to 3m small launches on level 0 (launch-bound): they
+// are captured once per (f, x) pair into a CUDA graph on a private stream
+// (the library's stream may be the legacy default stream, which cannot
+// capture) and replayed on the library's stream.  If capture is not possible
+// the steps run directly.
+template <typename T>
+static tpss_status chebyshev_apply(tpss_ctx* ctx, MGState* mg, const T* f, T* x) {
+  using Gr = ChebGraph<T>;
+  if (mg->cheb_m < 1) {
+    TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, mg->n0 * sizeof(T), ctx->stream));
+    return TPSS_OK;
+  }
+  cudaGraphExec_t& exec = Gr::exec(mg);
+  if (!(exec && Gr::f(mg) == f && Gr::x(mg) == x)) {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
     if (!mg->cheb_capture && cudaStreamCreateWithFlags(&mg->cheb_capture, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       mg->cheb_capture = nullptr;
-      return chebyshev_body(ctx, mg, f, x);
+      return chebyshev_body<T>(ctx, mg, f, x);
     }
     cudaStream_t orig = ctx->stream;
     ctx->stream = mg->cheb_capture;
     cudaGraph_t graph = nullptr;
     bool ok = cudaStreamBeginCapture(mg->cheb_capture, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      const tpss_status st = chebyshev_body(ctx, mg, f, x);
+      const tpss_status st = chebyshev_body<T>(ctx, mg, f, x);
       ok = cudaStreamEndCapture(mg->cheb_capture, &graph) == cudaSuccess && st == TPSS_OK;
     }
     ctx->stream = orig;
-    if (ok) ok = cudaGraphInstantiate(&mg->cheb_exec, graph, 0) == cudaSuccess;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     clear_error();
     if (!ok) {
-      mg->cheb_exec = nullptr;
-      return chebyshev_body(ctx, mg, f, x);
+      exec = nullptr;
+      return chebyshev_body<T>(ctx, mg, f, x);
     }
-    mg->cheb_gf = f;
-    mg->cheb_gx = x;
+    Gr::f(mg) = f;
+    Gr::x(mg) = x;
   }
-  TPSS_CHECK_CUDA(cudaGraphLaunch(mg->cheb_exec, ctx->stream));
+  TPSS_CHECK_CUDA(cudaGraphLaunch(exec, ctx->stream));
   return TPSS_OK;
 }
 
@@ -430,8 +485,14 @@ static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
   const bool fd_ok = !mg->mixed && !ctx->mapped && coarse_is_one_subdomain(ctx, &kind);
   const int choice = mg->params.coarse_solver;
   if (choice == TPSS_COARSE_CHEBYSHEV || (choice == TPSS_COARSE_AUTO && ctx->mapped && n > kDenseCoarseAuto)) {
-    TPSS_REQUIRE(!mg->mixed, "tpss_mg_setup: the Chebyshev coarse solver needs an FP64 V-cycle");
-    return chebyshev_setup(ctx, mg);
+    TPSS_REQUIRE(!mg->mixed || ctx->mapped,
+                 "tpss_mg_setup: the Chebyshev coarse solver needs an FP64 V-cycle on Cartesian meshes");
+    TPSS_TRY(chebyshev_setup(ctx, mg));
+    if (mg->mixed) {   // mapped meshes: the same iteration in FP32 inside the FP32 V-cycle
+      TPSS_TRY(create_patches(ctx, 0, TPSS_CELL, TPSS_FP32, &mg->coarse_acs32));
+      TPSS_TRY(dalloc_t(&mg->cheb_vec32, 3 * (size_t)n));
+    }
+    return TPSS_OK;
   }
   if (choice == TPSS_COARSE_FD || (choice == TPSS_COARSE_AUTO && fd_ok && n > kDenseCoarseAuto)) {
     TPSS_REQUIRE(fd_ok, "tpss_mg_setup: the fast-diagonalization coarse solve needs an FP64 V-cycle and "
@@ -468,10 +529,13 @@ static tpss_status coarse_setup(tpss_ctx* ctx, MGState* mg) {
 
 template <typename S, typename D>
 static tpss_status coarse_apply(tpss_ctx* ctx, MGState* mg, const S* b, D* x) {
-  if (mg->coarse_fd || mg->coarse_acs) {   // FP64 only (set up for FP64 V-cycles)
+  if (mg->coarse_fd || mg->coarse_acs) {   // FP64, or FP32 Chebyshev on mapped meshes
     if constexpr (sizeof(S) == sizeof(double) && sizeof(D) == sizeof(double)) {
       if (mg->coarse_fd) return smooth_additive_t<double>(mg->coarse_fd, 1.0, 1, b, x, 1);
-      return chebyshev_apply(ctx, mg, b, x);
+      return chebyshev_apply<double>(ctx, mg, b, x);
+    }
+    if constexpr (sizeof(S) == sizeof(float) && sizeof(D) == sizeof(float)) {
+      if (mg->coarse_acs32) return chebyshev_apply<float>(ctx, mg, b, x);
     }
     set_error("coarse solve: the fast-diagonalization and Chebyshev coarse solvers are FP64 only");
     return TPSS_EINVAL;
@@ -791,9 +855,9 @@ extern "C" tpss_status tpss_mg_setup(tpss_ctx* ctx, const tpss_mg_params* params
   TPSS_REQUIRE(params->smoothing_steps >= 0 && params->smoothing_steps <= 16,
                "tpss_mg_setup: smoothing_steps must be in 0..16");
   const bool vertex = params->smoother == TPSS_AVS || params->smoother == TPSS_MVS;
-  TPSS_REQUIRE(!ctx->mapped || (!vertex && params->precision == TPSS_FP64 &&
+  TPSS_REQUIRE(!ctx->mapped || (!vertex && (params->precision == TPSS_FP64 || params->precision == TPSS_FP32) &&
                                 params->coarse_solver != TPSS_COARSE_FD),
-               "tpss_mg_setup: meshes of quadrilaterals support FP64 cell smoothers (ACS, MCS) with the dense or "
+               "tpss_mg_setup: mapped meshes support FP64 and FP32 cell smoothers (ACS, MCS) with the dense or "
                "Chebyshev coarse solver");
   if (vertex)
     for (int l = 1; l < ctx->nlevels; ++l)

@@ -122,7 +122,8 @@ struct Level {
   std::vector<double> widths[3];             // host copies
   double* d_widths[3] = {nullptr, nullptr, nullptr};
   double* d_verts = nullptr;                 // mapped 2D meshes: [(nc1+1)][(nc0+1)] points (x, y)
-  double* d_geo = nullptr;                   // mapped 2D meshes: per-cell geometry (mapped.cu, GeoLayout)
+  double* d_geo = nullptr;                   // mapped meshes: per-cell geometry (GeoLayout / Geo3Layout)
+  float* d_geo32 = nullptr;                  // its FP32 copy (mixed-precision V-cycle)
   LevelOps<double> op64;
   LevelOps<float> op32;
   // scratch: operator intermediates and residual, nrhs_cap right-hand sides
@@ -152,8 +153,13 @@ struct MGState {
   int cheb_m = 0;                        // Chebyshev steps per coarse solve
   double* cheb_vec = nullptr;            // 4 level-0 vectors
   cudaGraphExec_t cheb_exec = nullptr;   // captured steps for the (f, x) pair below
-  const double* cheb_gf = nullptr;
-  double* cheb_gx = nullptr;
+  const void* cheb_gf = nullptr;
+  void* cheb_gx = nullptr;
+  tpss_patches* coarse_acs32 = nullptr;  // mixed V-cycle on mapped meshes: FP32 Chebyshev steps
+  float* cheb_vec32 = nullptr;           // 3 level-0 vectors
+  cudaGraphExec_t cheb_exec32 = nullptr;
+  const void* cheb_gf32 = nullptr;
+  void* cheb_gx32 = nullptr;
   cudaStream_t cheb_capture = nullptr;   // private non-blocking stream for the capture
   float* ir_vec = nullptr;               // iterative refinement: 5 finest-level FP32 vectors
   double* en_vec = nullptr;              // energy-norm PCG: e and A e on the finest level
@@ -190,6 +196,7 @@ struct tpss_patches {
   float* d_Z32[3] = {nullptr, nullptr, nullptr};
   float* d_lam32[3] = {nullptr, nullptr, nullptr};
   double* d_inv = nullptr;         // [nsub][n^d] 1/(sum of lambdas), FP64 path (n <= 16 in 3D)
+  float* d_inv32 = nullptr;        // FP32 copy, surrogate cell solvers (mapped meshes) in FP32
   double* d_scratch = nullptr;     // 3D FP64 n > 16: [scratch_ctas][n^3] tensor slabs (one per cluster)
   int scratch_ctas = 0;
   int large_cluster = 0;           // CTAs per subdomain in that kernel: 0 = chosen per launch
@@ -280,7 +287,8 @@ tpss_status restrict_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* fine, T
 
 // ---- mapped.cu (2D meshes of bilinear quadrilaterals, FP64)
 constexpr int kMaxMappedDegree = 7;     // 2D and 3D mapped meshes
-tpss_status mapped_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs);
+template <typename T>
+tpss_status mapped_apply_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out, const T* rhs);
 // surrogate cell solvers: fills P->d_A, d_M, d_Z, d_lam (per cell) and d_inv
 tpss_status mapped_cell_eigendata(tpss_ctx* ctx, tpss_patches* P, int* d_err);
 tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b);
@@ -288,17 +296,39 @@ tpss_status mapped_rhs(tpss_ctx* ctx, int level, int kind, double* b);
 // `list` (packed positions; null: all cells of the level): mode 0 out = x +
 // omega z, mode 1 d = c1 d + c2 z and out = x + d, z = P_K (b - A x)_K; out
 // may alias x only for cells that are not face neighbours of one another
-tpss_status mapped_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
-                         double* out, double* d, int mode, double omega, double c1, double c2);
+template <typename T>
+tpss_status mapped_fused_t(tpss_patches* P, const int* list, int64_t count, int nrhs, const T* x, const T* b, T* out,
+                           T* d, int mode, T omega, T c1, T c2);
 // ---- mapped3.cu (3D meshes of trilinear hexahedra)
 tpss_status mapped3_refine(const double* coarse, int nx, int ny, int nz, double* fine, cudaStream_t s);
 tpss_status mapped3_setup_level(tpss_ctx* ctx, int level, double gpk);
-tpss_status mapped3_apply(tpss_ctx* ctx, int level, int nrhs, const double* u, double* out, const double* rhs);
+template <typename T>
+tpss_status mapped3_apply_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out, const T* rhs);
 tpss_status mapped3_surrogate_widths(tpss_ctx* ctx, int level, double* h);
 tpss_status mapped3_inv_table(tpss_ctx* ctx, tpss_patches* P);
 tpss_status mapped3_rhs(tpss_ctx* ctx, int level, double* b);
-tpss_status mapped3_fused(tpss_patches* P, const int* list, int64_t count, int nrhs, const double* x, const double* b,
-                          double* out, double* d, int mode, double omega, double c1, double c2);
+template <typename T>
+tpss_status mapped3_fused_t(tpss_patches* P, const int* list, int64_t count, int nrhs, const T* x, const T* b, T* out,
+                            T* d, int mode, T omega, T c1, T c2);
+// per-precision views of the mapped data (nullptr where not built)
+template <typename T>
+inline const T* geo_of(const Level& L);
+template <>
+inline const double* geo_of<double>(const Level& L) { return L.d_geo; }
+template <>
+inline const float* geo_of<float>(const Level& L) { return L.d_geo32; }
+template <typename T>
+inline const T* patch_Z(const tpss_patches* P, int t);
+template <>
+inline const double* patch_Z<double>(const tpss_patches* P, int t) { return P->d_Z[t]; }
+template <>
+inline const float* patch_Z<float>(const tpss_patches* P, int t) { return P->d_Z32[t]; }
+template <typename T>
+inline const T* patch_inv(const tpss_patches* P);
+template <>
+inline const double* patch_inv<double>(const tpss_patches* P) { return P->d_inv; }
+template <>
+inline const float* patch_inv<float>(const tpss_patches* P) { return P->d_inv32; }
 
 // ---- setup.cu
 __global__ void gen_eig_kernel(const double* __restrict__ Aall, const double* __restrict__ Mall, int nprob, int n,

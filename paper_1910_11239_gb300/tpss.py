@@ -68,6 +68,7 @@ SIGNATURES = {
     "tpss_smooth_additive": [_VP, _D, _I, _VP, _VP, _I],
     "tpss_smooth_additive_f32": [_VP, _F, _I, _VP, _VP, _I],
     "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
+    "tpss_smooth_multiplicative_f32": [_VP, _F, _I, _I, _VP, _VP],
     "tpss_apply_operator": [_VP, _I, _I, _VP, _VP],
     "tpss_apply_operator_f32": [_VP, _I, _I, _VP, _VP],
     "tpss_apply_operator_noalloc": [_VP, _I, _I, _VP, _VP],
@@ -375,8 +376,12 @@ class Patches:
 
     def smooth_multiplicative(self, omega, b, x, reverse_colors=False, nrhs=1):
         n = self.problem.ndofs(self.level) * nrhs
-        _check(lib().tpss_smooth_multiplicative(self.h, omega, int(bool(reverse_colors)), nrhs,
-                                                _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+        if self.precision == FP64:
+            _check(lib().tpss_smooth_multiplicative(self.h, omega, int(bool(reverse_colors)), nrhs,
+                                                    _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+        else:
+            _check(lib().tpss_smooth_multiplicative_f32(self.h, omega, int(bool(reverse_colors)), nrhs,
+                                                        _ptr(b, torch.float32, n), _ptr(x, torch.float32, n)))
         return x
 
 

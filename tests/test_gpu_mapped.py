@@ -150,16 +150,14 @@ def test_mapped_contexts_reject_what_they_do_not_support():
     prob = tpss.Problem.mapped(3, _mesh(4, 4, 2), nlevels=2)
     with pytest.raises(tpss.TpssError):
         prob.setup_patches(1, tpss.VERTEX_PATCH, tpss.FP64)
-    with pytest.raises(tpss.TpssError):
-        prob.setup_patches(1, tpss.CELL, tpss.FP32)
-    for smoother, prec in (("AVS", tpss.FP64), ("ACS", tpss.FP32)):
+    for prec in (tpss.TF32, tpss.BF16):
+        with pytest.raises(tpss.TpssError):
+            prob.setup_patches(1, tpss.CELL, prec)
+    for smoother, prec in (("AVS", tpss.FP64), ("ACS", tpss.BF16), ("MCS", tpss.TF32)):
         with pytest.raises(tpss.TpssError):
             prob.mg_setup(smoother, 0.5, prec)
     with pytest.raises(tpss.TpssError):
         prob.mg_setup("ACS", 0.5, tpss.FP64, coarse_solver=tpss.COARSE_FD)
-    u = torch.zeros(prob.ndofs(1), dtype=torch.float32, device="cuda")
-    with pytest.raises(tpss.TpssError):
-        prob.apply_operator(1, u, torch.empty_like(u))
     bad = workloads.vertices_cartesian(np.full(2, 0.5), np.full(2, 0.5))
     bad[1, 1] = [0.1, 0.1]   # inside the triangle (0,0), (0.5,0), (0,0.5): a non-convex cell
     with pytest.raises(tpss.TpssError, match="convex"):
@@ -361,3 +359,60 @@ def test_damping_sweep_on_the_distorted_mesh():
     assert abs(nu[("MCS", 0.75)] - paper_value("damp2d_mcs_L3_w0.75")) <= 0.15 * paper_value("damp2d_mcs_L3_w0.75")
     assert nu[("ACS", 0.65)] > 1.5 * nu[("ACS", 0.5)], nu
     assert nu[("ACS", 0.4)] > nu[("ACS", 0.5)] and nu[("MCS", 0.6)] > nu[("MCS", 0.75)], nu
+
+
+# ------------------------------------------------- mixed precision (FP32)
+@pytest.mark.parametrize("dim,k", [(2, 3), (2, 7), (3, 2), (3, 4)])
+def test_fp32_operator_and_sweeps_match_oracle(dim, k):
+    """The FP32 mapped operator and the FP32 fused sweeps (FP32 geometry and
+    surrogate data) against the FP64 oracle, at FP32 accuracy."""
+    V0 = _mesh(6, 5, 90 + k) if dim == 2 else _mesh3(3, 2, 2, 90 + k)
+    V = refine(V0)
+    prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+    A = MappedSIPG(V, k, gamma_hat=4.0).assemble()
+    n = A.shape[0]
+    u = workloads.rhs_uniform(n, seed=1)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    prob.apply_operator(1, dev(u, torch.float32), out)
+    assert rel_err(out.double(), A @ u.astype(np.float32).astype(np.float64)) < 2e-5
+    sol = surrogate_solvers(V, k, 4.0)
+    P = prob.setup_patches(1, tpss.CELL, tpss.FP32)
+    b = workloads.rhs_uniform(n, seed=2)
+    x0 = workloads.rhs_uniform(n, seed=3)
+    b32, x032 = b.astype(np.float32).astype(np.float64), x0.astype(np.float32).astype(np.float64)
+    x = dev(x0, torch.float32)
+    P.smooth_additive(0.5, dev(b, torch.float32), x)
+    assert rel_err(x.double(), schwarz.additive_smoother(A, b32, x032, sol, 0.5)) < 1e-4
+    nc = (12, 10) if dim == 2 else (6, 4, 4)
+    cells = int(np.prod(nc))
+    colors = [schwarz.color_multiplicative_cell(tuple((c // int(np.prod(nc[:t]))) % nc[t] for t in range(dim)))
+              for c in range(cells)]
+    x = dev(x0, torch.float32)
+    P.smooth_multiplicative(0.75, dev(b, torch.float32), x)
+    assert rel_err(x.double(), schwarz.multiplicative_smoother(A, b32, x032, sol, colors, 0.75)) < 1e-4
+    prob.close()
+
+
+@pytest.mark.parametrize("dim,k,L,smoother,omega", [(2, 3, 3, "ACS", 0.5), (2, 3, 3, "MCS", 0.75),
+                                                    (3, 3, 1, "ACS", 0.55), (3, 3, 1, "MCS", 0.95)])
+def test_mixed_precision_pcg_on_distorted_meshes(dim, k, L, smoother, omega):
+    """FP32 V-cycle (FP32 operator, fused FP32 sweeps, transfers and FP32
+    Chebyshev coarse steps) inside FP64 flexible PCG: the FP64 residual
+    reaches 1e-8 in about the FP64 number of iterations."""
+    V0 = workloads.vertices_distorted(32 if dim == 2 else 8, 1, dim=dim)
+    its = {}
+    for prec in (tpss.FP64, tpss.FP32):
+        prob = tpss.Problem.mapped(k, V0, nlevels=L + 1, gamma_hat=4.0)
+        prob.mg_setup(smoother, omega, prec, flexible_cg=1, coarse_solver=tpss.COARSE_CHEBYSHEV)
+        b = torch.empty(prob.ndofs(L), dtype=torch.float64, device="cuda")
+        prob.assemble_rhs(L, 0, b)
+        x = torch.empty_like(b)
+        res = prob.pcg_solve(b, x, rtol=1e-8, maxit=200)
+        assert res["converged"]
+        r = torch.empty_like(b)
+        prob.residual(L, b, x, r)
+        assert float(r.norm() / b.norm()) <= 1.01e-8
+        its[prec] = res["iters"]
+        prob.close()
+    # the FP32 V-cycle is a slightly perturbed preconditioner (not exactly symmetric)
+    assert its[tpss.FP32] <= 1.35 * its[tpss.FP64] + 2, its
