@@ -747,6 +747,8 @@ def run_distorted(tpss, workloads, perf, torch, steps):
     out = {"workload": f"unit square 32^2 / cube 8^3 coarse cells, 25% distortion (seed {DIST_SEED}), "
                        "gamma_hat 4, FP64"}
     fp64 = perf.fp64_peak_flops()
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    HBM_GBS = json.load(open(peaks)).get("hbm_gbs", 6800.0) if os.path.exists(peaks) else 6800.0
     for dim, n0, runs, Lp in ((2, 32, ((3, 5), (7, 4)), 3), (3, 8, ((3, 3), (7, 2)), 1)):
         V0 = workloads.vertices_distorted(n0, DIST_SEED, dim=dim)
         rec_d = {}
@@ -763,6 +765,13 @@ def run_distorted(tpss, workloads, perf, torch, steps):
                    "operator": {"kernel": f"mapped{'' if dim == 2 else '3'}_op_kernel<{k + 1}>", "ms": ms,
                                 "dofs_per_s": N / (ms / 1e3), "tflops": fl / ms / 1e9,
                                 "frac_fp64_peak": fl / (ms / 1e3) / fp64, "algorithmic_gbs": by / ms / 1e6}}
+            u32, au32 = u.float(), torch.empty(N, dtype=torch.float32, device="cuda")
+            ms32 = _time_calls(torch, lambda: prob.apply_operator(L, u32, au32), steps)
+            by32 = (perf.mapped_operator_bytes(nc[:2], k, word=4) if dim == 2
+                    else perf.mapped3_operator_bytes(nc, k, word=4))
+            rec["operator_fp32"] = {"ms": ms32, "dofs_per_s": N / (ms32 / 1e3), "tflops": fl / ms32 / 1e9,
+                                    "frac_fp32_peak": fl / (ms32 / 1e3) / perf.fp32_peak_flops(),
+                                    "algorithmic_gbs": by32 / ms32 / 1e6, "frac_hbm": by32 / ms32 / 1e6 / HBM_GBS}
             b = torch.empty(N, dtype=torch.float64, device="cuda")
             prob.assemble_rhs(L, 0, b)
             x = torch.zeros_like(b)

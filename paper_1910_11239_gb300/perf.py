@@ -105,18 +105,18 @@ def mapped3_operator_flops(ncells, k, nrhs=1):
     return num_cells(ncells) * (32 * n1 ** 4 + 303 * n1 ** 3 + 180 * n1 ** 2) * nrhs
 
 
-def mapped3_operator_bytes(ncells, k, nrhs=1):
-    """Read u, write A u, read the per-cell geometry (6 n1^3 + 24 n1^2 + 6 doubles)."""
+def mapped3_operator_bytes(ncells, k, nrhs=1, word=8):
+    """Read u, write A u, read the per-cell geometry (6 n1^3 + 24 n1^2 + 6 words)."""
     n1 = k + 1
-    return num_cells(ncells) * (16 * n1 ** 3 * nrhs + 8 * (6 * n1 ** 3 + 24 * n1 ** 2 + 6))
+    return num_cells(ncells) * word * (2 * n1 ** 3 * nrhs + 6 * n1 ** 3 + 24 * n1 ** 2 + 6)
 
 
-def mapped_operator_bytes(ncells, k, nrhs=1):
+def mapped_operator_bytes(ncells, k, nrhs=1, word=8):
     """Minimal HBM traffic: read u, write A u, read the per-cell geometry
-    (3 n1^2 + 8 n1 + 8 doubles)."""
+    (3 n1^2 + 8 n1 + 8 words)."""
     nx, ny = ncells
     n1 = k + 1
-    return nx * ny * (16 * n1 ** 2 * nrhs + 8 * (3 * n1 ** 2 + 8 * n1 + 8))
+    return nx * ny * word * (2 * n1 ** 2 * nrhs + 3 * n1 ** 2 + 8 * n1 + 8)
 
 
 def transfer_flops(coarse_ncells, k, d=3, nrhs=1):
