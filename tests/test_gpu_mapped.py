@@ -416,3 +416,19 @@ def test_mixed_precision_pcg_on_distorted_meshes(dim, k, L, smoother, omega):
         prob.close()
     # the FP32 V-cycle is a slightly perturbed preconditioner (not exactly symmetric)
     assert its[tpss.FP32] <= 1.35 * its[tpss.FP64] + 2, its
+
+
+def test_iterative_refinement_on_a_distorted_mesh():
+    """tpss_ir_solve (FP64 residual, FP32 inner PCG with the FP32 mapped operator
+    and V-cycle) reaches the FP64 relative residual 1e-8."""
+    prob = tpss.Problem.mapped(3, workloads.vertices_distorted(16, 2), nlevels=3, gamma_hat=4.0)
+    prob.mg_setup("ACS", 0.5, tpss.FP32, flexible_cg=1, coarse_solver=tpss.COARSE_CHEBYSHEV)
+    b = torch.empty(prob.ndofs(2), dtype=torch.float64, device="cuda")
+    prob.assemble_rhs(2, 0, b)
+    x = torch.empty_like(b)
+    res = prob.ir_solve(b, x, rtol=1e-8)
+    assert res["converged"] and res["rel_res"] <= 1e-8
+    r = torch.empty_like(b)
+    prob.residual(2, b, x, r)
+    assert float(r.norm() / b.norm()) <= 1.01e-8
+    prob.close()
