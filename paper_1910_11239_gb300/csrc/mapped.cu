@@ -452,15 +452,17 @@ struct MappedFusedArgsT {
   T omega, c1, c2;
 };
 
-template <int N1, typename T>
-__global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_fused_kernel(MappedFusedArgsT<T> f) {
+// CPB: cells per CTA (the shape's default, or fewer on small levels so that
+// the work of a launch spreads over more SMs)
+template <int N1, typename T, int CPB>
+__global__ void __launch_bounds__(CPB * MappedShape<N1>::NL) mapped_fused_kernel(MappedFusedArgsT<T> f) {
   using S = MappedShape<N1>;
   constexpr int NL = N1 * N1, SL = S::SLOT + 2 * NL;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   mapped_tables<N1, T>(f.op.B, sm);
   const int slot = threadIdx.x / NL, tid = threadIdx.x % NL;
-  const int64_t idx = (int64_t)blockIdx.x * S::CPB + slot;
+  const int64_t idx = (int64_t)blockIdx.x * CPB + slot;
   const bool active = idx < f.count;
   int64_t cell = 0;
   if (active) {
@@ -523,20 +525,31 @@ __global__ void __launch_bounds__(MappedShape<N1>::THREADS) mapped_fused_kernel(
   }
 }
 
-template <int N1, typename T>
-static tpss_status launch_fused(tpss_ctx* ctx, const MappedFusedArgsT<T>& a, int nrhs) {
+template <int N1, typename T, int CPB>
+static tpss_status launch_fused_cpb(tpss_ctx* ctx, const MappedFusedArgsT<T>& a, int nrhs) {
   using S = MappedShape<N1>;
-  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 2 * N1 * N1)) * sizeof(T);
+  const size_t smem = (size_t)(S::TABLES + CPB * (S::SLOT + 2 * N1 * N1)) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_fused_kernel<N1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped_fused_kernel<N1, T, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     attr = true;
   }
-  const dim3 grid((unsigned)((a.count + S::CPB - 1) / S::CPB), (unsigned)nrhs);
-  mapped_fused_kernel<N1, T><<<grid, S::THREADS, smem, ctx->stream>>>(a);
+  const dim3 grid((unsigned)((a.count + CPB - 1) / CPB), (unsigned)nrhs);
+  mapped_fused_kernel<N1, T, CPB><<<grid, CPB * N1 * N1, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
+}
+
+// launches of fewer than two CTAs per SM (the coarse levels) take CTAs of
+// about 64 threads
+template <int N1, typename T>
+static tpss_status launch_fused(tpss_ctx* ctx, const MappedFusedArgsT<T>& a, int nrhs) {
+  using S = MappedShape<N1>;
+  constexpr int SMALL = N1 * N1 >= 64 ? 1 : 64 / (N1 * N1);
+  if (SMALL < S::CPB && (a.count + S::CPB - 1) / S::CPB * nrhs < 2 * (int64_t)ctx->num_sms)
+    return launch_fused_cpb<N1, T, SMALL>(ctx, a, nrhs);
+  return launch_fused_cpb<N1, T, S::CPB>(ctx, a, nrhs);
 }
 
 template <int N1, typename T>

@@ -596,15 +596,17 @@ struct Mapped3FusedArgsT {
   T omega, c1, c2;
 };
 
-template <int N1, typename T>
-__global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_fused_kernel(Mapped3FusedArgsT<T> f) {
+// CPB: cells per CTA (the shape's default, or fewer on small levels so that
+// the work of a launch spreads over more SMs)
+template <int N1, typename T, int CPB>
+__global__ void __launch_bounds__(CPB * Mapped3Shape<N1>::NV) mapped3_fused_kernel(Mapped3FusedArgsT<T> f) {
   using S = Mapped3Shape<N1>;
   constexpr int NV = S::NV, NF = S::NF, SL = S::SLOT + 3 * NF;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   mapped3_tables<N1, T>(f.op.B, sm);
   const int slot = threadIdx.x / NV, tid = threadIdx.x % NV;
-  const int64_t idx = (int64_t)blockIdx.x * S::CPB + slot;
+  const int64_t idx = (int64_t)blockIdx.x * CPB + slot;
   const bool active = idx < f.count;
   int64_t cell = 0;
   if (active) {
@@ -679,20 +681,31 @@ __global__ void __launch_bounds__(Mapped3Shape<N1>::THREADS) mapped3_fused_kerne
   }
 }
 
-template <int N1, typename T>
-static tpss_status launch_fused3(tpss_ctx* ctx, const Mapped3FusedArgsT<T>& a, int nrhs) {
+template <int N1, typename T, int CPB>
+static tpss_status launch_fused3_cpb(tpss_ctx* ctx, const Mapped3FusedArgsT<T>& a, int nrhs) {
   using S = Mapped3Shape<N1>;
-  const size_t smem = (size_t)(S::TABLES + S::CPB * (S::SLOT + 3 * S::NF)) * sizeof(T);
+  const size_t smem = (size_t)(S::TABLES + CPB * (S::SLOT + 3 * S::NF)) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_fused_kernel<N1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(mapped3_fused_kernel<N1, T, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     attr = true;
   }
-  const dim3 grid((unsigned)((a.count + S::CPB - 1) / S::CPB), (unsigned)nrhs);
-  mapped3_fused_kernel<N1, T><<<grid, S::THREADS, smem, ctx->stream>>>(a);
+  const dim3 grid((unsigned)((a.count + CPB - 1) / CPB), (unsigned)nrhs);
+  mapped3_fused_kernel<N1, T, CPB><<<grid, CPB * S::NV, smem, ctx->stream>>>(a);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
+}
+
+// launches of fewer than two CTAs per SM (the coarse levels) take CTAs of
+// about 64 threads
+template <int N1, typename T>
+static tpss_status launch_fused3(tpss_ctx* ctx, const Mapped3FusedArgsT<T>& a, int nrhs) {
+  using S = Mapped3Shape<N1>;
+  constexpr int SMALL = S::NV >= 64 ? 1 : 64 / (S::NV);
+  if (SMALL < S::CPB && (a.count + S::CPB - 1) / S::CPB * nrhs < 2 * (int64_t)ctx->num_sms)
+    return launch_fused3_cpb<N1, T, SMALL>(ctx, a, nrhs);
+  return launch_fused3_cpb<N1, T, S::CPB>(ctx, a, nrhs);
 }
 
 template <typename T>
