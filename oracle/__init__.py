@@ -24,7 +24,13 @@ Galerkin methods"), in FP64, with no Kronecker shortcuts:
 * ``transfer``  -- prolongation as the embedding V_{l-1} in V_l and restriction
                    as its transpose (Sec. 2.2).
 * ``multigrid`` -- V-cycle (Alg. 1) with an exact coarse solve, preconditioned
-                   CG and the fractional iteration count (Sec. 2.4).
+                   CG, flexible and left-preconditioned GMRES and the
+                   fractional iteration count (Sec. 2.4).
+* ``chebyshev`` -- the Chebyshev coarse solver with the additive cell smoother
+                   as preconditioner (Sec. 2.4).
+* ``mapped``    -- SIPG on distorted meshes of bilinear / trilinear cells and
+                   the Cartesian-surrogate local solvers (Sec. 4, eq.
+                   schwarzproj, eq. avglength), with their multigrid hierarchy.
 
 Each function below states whether parity for it is pinned by the tests under
 ``tests/test_oracle_*.py``.  All functions are pinned (no "parity unpinned"
