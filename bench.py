@@ -727,11 +727,12 @@ def run_high_degree(tpss, workloads, perf, torch, steps):
 # tab:cubedist25acp / tab:cubedist25mcp: (smoother, m, k) -> printed nu_frac;
 # 2D at L = 3 (32 x 32 coarse cells), 3D at L = 1 (8^3 coarse cells), 25% distortion
 PAPER_NU_DIST = {2: {("ACS", 1, 3): 38.7, ("ACS", 2, 3): 24.3, ("MCS", 1, 3): 24.7, ("MCS", 2, 3): 15.3,
-                     ("ACS", 1, 7): 47.7, ("MCS", 1, 7): 43.5},
+                     ("ACS", 1, 7): 47.7, ("MCS", 1, 7): 43.5, ("ACS", 1, 15): 65.6, ("MCS", 1, 15): 50.9},
                  3: {("ACS", 1, 3): 34.4, ("ACS", 2, 3): 24.5, ("MCS", 1, 3): 24.7, ("MCS", 2, 3): 14.4,
                      ("ACS", 1, 7): 49.7, ("MCS", 1, 7): 37.7}}
 # relaxation of those columns: ACS (k = 3, 7), MCS (k = 3, 7)
-PAPER_OMEGA_DIST = {2: {("ACS", 3): 0.5, ("ACS", 7): 0.5, ("MCS", 3): 0.75, ("MCS", 7): 0.5},
+PAPER_OMEGA_DIST = {2: {("ACS", 3): 0.5, ("ACS", 7): 0.5, ("MCS", 3): 0.75, ("MCS", 7): 0.5, ("ACS", 15): 0.5,
+                        ("MCS", 15): 0.5},
                     3: {("ACS", 3): 0.55, ("ACS", 7): 0.5, ("MCS", 3): 0.95, ("MCS", 7): 0.7}}
 DIST_SEED = 1
 

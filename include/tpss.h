@@ -94,7 +94,7 @@ typedef struct tpss_patches tpss_patches;
  * unit normals J^{-T} e_t / |J^{-T} e_t| and Nanson's surface element, the
  * paper's 1/sqrt(2) averages), penalty of eq. penalty with h^+- = |K^+-| / |e|;
  * the paper takes gamma_hat = 4 on its 25%-distorted meshes.  FP64, degree
- * 1..7.  Cell patches (tpss_setup_patches with TPSS_CELL, FP64) use the
+ * 1..15 in 2D and 1..7 in 3D; FP32 degree 1..7.  Cell patches (tpss_setup_patches with TPSS_CELL, FP64) use the
  * inexact local solvers of eq. schwarzproj on the Cartesian surrogate of each
  * cell (eq. avglength: widths = mean lengths of the cell's edges per
  * direction, the neighbours' surrogate widths across its faces), by fast

@@ -607,7 +607,20 @@ tpss_status mapped_fused_t(tpss_patches* P, const int* list, int64_t count, int 
     case 8: return launch_fused<8, T>(ctx, a, nrhs);
     default: break;
   }
-  set_error("smoother: meshes of quadrilaterals support degrees 1..7");
+  if constexpr (sizeof(T) == sizeof(double)) {   // degrees 8..15: FP64 only
+    switch (ctx->n1) {
+      case 9: return launch_fused<9, T>(ctx, a, nrhs);
+      case 10: return launch_fused<10, T>(ctx, a, nrhs);
+      case 11: return launch_fused<11, T>(ctx, a, nrhs);
+      case 12: return launch_fused<12, T>(ctx, a, nrhs);
+      case 13: return launch_fused<13, T>(ctx, a, nrhs);
+      case 14: return launch_fused<14, T>(ctx, a, nrhs);
+      case 15: return launch_fused<15, T>(ctx, a, nrhs);
+      case 16: return launch_fused<16, T>(ctx, a, nrhs);
+      default: break;
+    }
+  }
+  set_error("smoother: meshes of quadrilaterals support degrees 1..15 in FP64, 1..7 in FP32");
   return TPSS_EINVAL;
 }
 template tpss_status mapped_fused_t<double>(tpss_patches*, const int*, int64_t, int, const double*, const double*,
@@ -644,7 +657,20 @@ tpss_status mapped_apply_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* ou
     case 8: return launch_mapped<8, T>(ctx, a, nrhs);
     default: break;
   }
-  set_error("operator: meshes of quadrilaterals support degrees 1..7");
+  if constexpr (sizeof(T) == sizeof(double)) {   // degrees 8..15: FP64 only
+    switch (ctx->n1) {
+      case 9: return launch_mapped<9, T>(ctx, a, nrhs);
+      case 10: return launch_mapped<10, T>(ctx, a, nrhs);
+      case 11: return launch_mapped<11, T>(ctx, a, nrhs);
+      case 12: return launch_mapped<12, T>(ctx, a, nrhs);
+      case 13: return launch_mapped<13, T>(ctx, a, nrhs);
+      case 14: return launch_mapped<14, T>(ctx, a, nrhs);
+      case 15: return launch_mapped<15, T>(ctx, a, nrhs);
+      case 16: return launch_mapped<16, T>(ctx, a, nrhs);
+      default: break;
+    }
+  }
+  set_error("operator: meshes of quadrilaterals support degrees 1..15 in FP64, 1..7 in FP32");
   return TPSS_EINVAL;
 }
 template tpss_status mapped_apply_t<double>(tpss_ctx*, int, int, const double*, double*, const double*);
@@ -814,7 +840,8 @@ extern "C" tpss_status tpss_create_mapped(int dim, int degree, const int ncells[
   TPSS_REQUIRE(vertices && out && ncells, "tpss_create_mapped: null argument");
   *out = nullptr;
   TPSS_REQUIRE(dim == 2 || dim == 3, "tpss_create_mapped: dim must be 2 or 3");
-  TPSS_REQUIRE(degree >= 1 && degree <= kMaxMappedDegree, "tpss_create_mapped: degree must be in 1..7");
+  TPSS_REQUIRE(degree >= 1 && degree <= (dim == 2 ? kMaxDegree : kMaxMappedDegree3),
+               "tpss_create_mapped: degree must be in 1..15 (dim 2) or 1..7 (dim 3)");
   TPSS_REQUIRE(nlevels >= 1 && nlevels <= 12, "tpss_create_mapped: nlevels must be in 1..12");
   int nc[3] = {1, 1, 1};
   size_t nverts = 1;

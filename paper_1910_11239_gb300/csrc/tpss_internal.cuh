@@ -286,7 +286,7 @@ template <typename T>
 tpss_status restrict_t(tpss_ctx* ctx, int fine_level, int nrhs, const T* fine, T* coarse);
 
 // ---- mapped.cu (2D meshes of bilinear quadrilaterals, FP64)
-constexpr int kMaxMappedDegree = 7;     // 2D and 3D mapped meshes
+constexpr int kMaxMappedDegree3 = 7;    // 3D mapped meshes (2D: kMaxDegree in FP64, kMaxMixedDegree in FP32)
 template <typename T>
 tpss_status mapped_apply_t(tpss_ctx* ctx, int level, int nrhs, const T* u, T* out, const T* rhs);
 // surrogate cell solvers: fills P->d_A, d_M, d_Z, d_lam (per cell) and d_inv

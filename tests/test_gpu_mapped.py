@@ -163,7 +163,7 @@ def test_mapped_contexts_reject_what_they_do_not_support():
     with pytest.raises(tpss.TpssError, match="convex"):
         tpss.Problem.mapped(2, bad)
     with pytest.raises(tpss.TpssError):
-        tpss.Problem.mapped(8, _mesh(2, 2, 1))
+        tpss.Problem.mapped(16, _mesh(2, 2, 1))
     prob.close()
 
 
@@ -432,3 +432,42 @@ def test_iterative_refinement_on_a_distorted_mesh():
     prob.residual(2, b, x, r)
     assert float(r.norm() / b.norm()) <= 1.01e-8
     prob.close()
+
+
+# ------------------------------------------- 2D, degrees 8..15 (FP64)
+@pytest.mark.parametrize("k", [9, 12, 15])
+def test_high_degree_operator_and_sweeps_match_oracle(k):
+    V0 = _mesh(4, 3, 110 + k)
+    prob = tpss.Problem.mapped(k, V0, nlevels=1, gamma_hat=4.0)
+    A = MappedSIPG(V0, k, gamma_hat=4.0).assemble()
+    n = A.shape[0]
+    u = workloads.rhs_uniform(n, seed=k)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    prob.apply_operator(0, dev(u), out)
+    assert rel_err(out, A @ u) < 1e-12
+    sol = surrogate_solvers(V0, k, 4.0)
+    P = prob.setup_patches(0, tpss.CELL, tpss.FP64)
+    b = workloads.rhs_uniform(n, seed=2)
+    x0 = workloads.rhs_uniform(n, seed=3)
+    x = dev(x0)
+    P.smooth_additive(0.5, dev(b), x)
+    assert rel_err(x, schwarz.additive_smoother(A, b, x0, sol, 0.5)) < 1e-10
+    colors = [schwarz.color_multiplicative_cell((c % 4, c // 4)) for c in range(12)]
+    x = dev(x0)
+    P.smooth_multiplicative(0.5, dev(b), x, reverse_colors=True)
+    assert rel_err(x, schwarz.multiplicative_smoother(A, b, x0, sol, colors, 0.5, reverse=True)) < 1e-10
+    with pytest.raises(tpss.TpssError):
+        prob.setup_patches(0, tpss.CELL, tpss.FP32)
+    prob.close()
+    with pytest.raises(tpss.TpssError):
+        tpss.Problem.mapped(8, _mesh3(2, 2, 2, 1))
+
+
+def test_paper_count_at_k15_on_the_distorted_mesh():
+    """Context, not parity (parity is the V-cycle against the oracle): in 2D our
+    ACS counts rise faster with the degree than the printed ones (k = 3: -7%,
+    k = 7: +15%, k = 15: +18%; 3D k = 7 within 2%), so the band is 25% here;
+    MCS at k = 15 (72 against 50.9) is reported by the benchmark, not pinned."""
+    nu = _distorted_count("ACS", 0.5, 1, 15, 3)
+    paper = paper_value("dist2d_acs1_k15_L3")
+    assert abs(nu - paper) <= 0.25 * paper, (nu, paper)
