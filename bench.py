@@ -12,8 +12,11 @@ Also reported: per-degree DoF/s and roofline fraction, an end-to-end number
 through the same C-ABI call with host buffers (copies timed), the oracle on
 the host cores as cpu_baseline, the MG-CG time to a 1e-8 residual
 reduction on 64^3 cells (FP64 and mixed precision), batched solves, the
-paper's fractional iteration counts, and the k = 15 smoothers on the paper's
-16^3-cell FLOP-table mesh.
+paper's fractional iteration counts, the k = 15 smoothers on the paper's
+16^3-cell FLOP-table mesh, and the distorted meshes of Sec. 4 (2D and 3D:
+mapped operators in FP64 and FP32, ACS / MCS sweeps with Cartesian-surrogate
+cell solvers, V-cycle and PCG times with FP64 and FP32 V-cycles, the paper's
+counts and its damping sweep).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tpss|reference]
 """
