@@ -44,7 +44,7 @@ tensor mesh of K's and its face neighbours' surrogate widths.
 Pins (tests/test_oracle_mapped.py): on a Cartesian vertex array the assembly
 equals sipg.SIPG (2D, 3D); on an affine mesh polynomials of degree k are
 reproduced exactly (SIPG consistency, 2D, 3D); linear functions on
-distorted meshes; L2 order k+1 on a distorted 2D mesh; symmetry and
+distorted meshes; L2 order k+1 on distorted meshes (2D, 3D); symmetry and
 positive definiteness with gamma_hat = 4 (2D, 3D); the child maps of
 `refine` equal the parent maps on the sub-boxes; the surrogate of a
 Cartesian cell is its exact block; the mapped V-cycle on a Cartesian vertex
