@@ -163,7 +163,6 @@ __global__ void hex_volume_kernel(const Basis1D* __restrict__ B, const double3* 
 
 __global__ void mapped3_geometry_kernel(const Basis1D* __restrict__ B, const double3* __restrict__ V, int nx, int ny,
                                         int nz, double gpk, const double* __restrict__ vol, double* __restrict__ geo) {
-  __shared__ double area[6];
   const int n1 = B->n1;
   const Geo3Layout g(n1);
   const int64_t c = blockIdx.x;
@@ -208,7 +207,6 @@ __global__ void mapped3_geometry_kernel(const Basis1D* __restrict__ B, const dou
     const int f = threadIdx.x, t = f >> 1, side = f & 1;
     double a = 0.0;
     for (int p = 0; p < g.nf; ++p) a += out[g.W + f * g.nf + p];
-    area[f] = a;
     int nb[3] = {ci[0], ci[1], ci[2]};
     nb[t] += side ? 1 : -1;
     const bool interior = nb[t] >= 0 && nb[t] < nc[t];
