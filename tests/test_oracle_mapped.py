@@ -305,3 +305,32 @@ def test_mcs_vcycle_is_symmetric_on_distorted_hexahedra():
     rng = np.random.default_rng(4)
     x, y = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
     assert abs(x @ H.precondition(y) - y @ H.precondition(x)) <= 1e-11 * abs(x @ H.precondition(x))
+
+
+def test_local_stability_of_the_surrogate_solvers():
+    """eq. localstab: a(u, u) <= eta a~(u, u) on every cell subspace with eta
+    independent of the cell.  The spectrum of (A~_j)^{-1} A_j is exactly {1} on
+    a Cartesian mesh, stays in a fixed interval on distorted meshes, narrows as
+    the distortion shrinks, and hardly depends on the degree."""
+    import scipy.linalg as sla
+
+    def spectrum(V, k):
+        S = MappedSIPG(V, k, 4.0)
+        A = S.assemble().tocsr()
+        lo, hi = np.inf, 0.0
+        for c in range(S.ncells):
+            idx = schwarz.patch_dofs([c], S.nloc)
+            ev = sla.eigh(A[idx][:, idx].toarray(), surrogate_cell_matrix(V, S.cell_multi(c), k, 4.0),
+                          eigvals_only=True)
+            lo, hi = min(lo, ev[0]), max(hi, ev[-1])
+        return lo, hi
+
+    lo, hi = spectrum(cartesian_vertices(np.full(5, 0.2), np.full(5, 0.2)), 3)
+    assert abs(lo - 1) < 1e-10 and abs(hi - 1) < 1e-10
+    eta = {}
+    for k in (1, 3):
+        lo25, hi25 = spectrum(distorted_vertices(6, seed=3), k)
+        lo10, hi10 = spectrum(distorted_vertices(6, seed=3, alpha=0.1), k)
+        assert 0.4 < lo25 < lo10 < 1.0 < hi10 < hi25 < 2.5, (k, lo25, lo10, hi10, hi25)
+        eta[k] = hi25
+    assert eta[3] < 1.2 * eta[1], eta
