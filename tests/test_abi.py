@@ -55,3 +55,40 @@ def test_null_arguments_rejected_without_gpu(libpath):
     assert b"null" in L.tpss_last_error()
     assert L.tpss_smooth_additive(None, 0.7, 1, None, None, 1) == -1
     assert L.tpss_pcg_solve(None, None, None, 1e-8, 10, None, None, None) == -1
+
+
+def test_mapped_mesh_arguments_are_checked_on_the_host(libpath):
+    """tpss_create_mapped rejects bad arguments and invalid meshes before any
+    device work (so this runs without a GPU): a non-convex cell, a degree
+    outside the range of the dimension, non-finite vertices, a bad dim."""
+    import numpy as np
+    from paper_1910_11239_gb300 import tpss, workloads
+    L = tpss.lib()
+    EINVAL = -1   # TPSS_EINVAL in include/tpss.h
+
+    def create(dim, degree, V):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        nc = (ctypes.c_int * 3)(*([s - 1 for s in reversed(V.shape[:-1])] + [1] * (3 - V.shape[-1])))
+        h = ctypes.c_void_p()
+        st = L.tpss_create_mapped(dim, degree, nc, ctypes.c_void_p(V.ctypes.data), 1, 4.0, 0, None,
+                                  ctypes.byref(h))
+        return st, L.tpss_last_error().decode()
+
+    good2 = workloads.vertices_distorted(3, 1)
+    bad2 = workloads.vertices_cartesian(np.full(2, 0.5), np.full(2, 0.5))
+    bad2[1, 1] = [0.1, 0.1]                    # inside the triangle of cell (0, 0): not convex
+    st, msg = create(2, 3, bad2)
+    assert st == EINVAL and "convex" in msg
+    flipped = good2[:, ::-1].copy()            # mirrored x: clockwise cells
+    st, msg = create(2, 3, flipped)
+    assert st == EINVAL and "convex" in msg
+    st, msg = create(2, 16, good2)
+    assert st == EINVAL and "degree" in msg
+    st, msg = create(3, 8, workloads.vertices_distorted(2, 1, dim=3))
+    assert st == EINVAL and "degree" in msg
+    nan = good2.copy()
+    nan[1, 1, 0] = np.nan
+    st, msg = create(2, 3, nan)
+    assert st == EINVAL and "finite" in msg
+    st, msg = create(4, 3, good2)
+    assert st == EINVAL and "dim" in msg
