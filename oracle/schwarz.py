@@ -28,7 +28,9 @@ mesh T_0 the additive vertex patch smoother with omega = 1 is an exact solve;
 on a one-cell mesh the cell smoother is an exact solve; the colored
 multiplicative smoother equals the literal product of eq. multschwarz1 taken in
 the same patch order (which holds only if same-color patches are A-orthogonal);
-the coloring is checked for shared cells and shared faces by brute force.
+the coloring is checked for shared cells and shared faces by brute force;
+additive_local_sum equals omega times the densely assembled
+sum_j R_j^T (R_j A R_j^T)^{-1} R_j (tests/test_oracle_checkers.py).
 """
 import itertools
 

@@ -27,7 +27,8 @@ integrated with k+2 Gauss points per direction.
 Pins (tests/test_oracle_sipg.py): symmetry, positive definiteness, exact
 reproduction of polynomial solutions in Q_k (SIPG consistency), O(h^(k+1))
 L2 convergence, and agreement with the Kronecker-sum form assembled from the
-paper's 1D matrices (tests/test_oracle_kron.py).
+paper's 1D matrices (tests/test_oracle_kron.py); apply_rows equals the rows of
+the assembled matrix (tests/test_oracle_checkers.py).
 """
 import itertools
 
