@@ -248,8 +248,10 @@ tpss_status tpss_apply_operator_f32(tpss_ctx* ctx, int level, int nrhs, const fl
  * first time a level is used with a larger nrhs.  Same result as
  * tpss_apply_operator; the operator's intermediates live in one static device
  * array of 4 * 2^19 doubles (16 MiB, held by every GPU that loads the library
- * until the process exits).  Limit: ndofs(level) * nrhs <= 2^19, else
- * TPSS_EINVAL with a message.  The first call on a device looks up the
+ * until the process exits).  Limit on Cartesian meshes: ndofs(level) * nrhs
+ * <= 2^19, else TPSS_EINVAL with a message; on a mesh of quadrilaterals or
+ * hexahedra (tpss_create_mapped) the operator needs no intermediates, so
+ * there is no limit and the array is not touched.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.
  * All calls share the array, so calls that overlap on the GPU (e.g. on two
  * streams) race; serialize them.  Calls no allocating routine. */

@@ -66,6 +66,9 @@ extern "C" tpss_status tpss_apply_operator_noalloc(tpss_ctx* ctx, int level, int
   TPSS_REQUIRE(level >= 0 && level < ctx->nlevels, "tpss_apply_operator_noalloc: level out of range");
   TPSS_REQUIRE(nrhs >= 1, "tpss_apply_operator_noalloc: nrhs must be >= 1");
   TPSS_REQUIRE(u != Au, "tpss_apply_operator_noalloc: u and Au must not alias");
+  // A mesh of quadrilaterals / hexahedra uses a single-pass operator with no
+  // intermediates at all: no scratch, hence no size limit.
+  if (ctx->mapped) return apply_operator_into(ctx, level, nrhs, u, Au, nullptr);
   const int64_t entries = ctx->levels[level].ndofs * (int64_t)nrhs;
   if (entries > kNoAllocMaxEntries) {
     set_error("tpss_apply_operator_noalloc: ndofs * nrhs = " + std::to_string(entries) +

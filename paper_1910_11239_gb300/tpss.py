@@ -222,7 +222,7 @@ class Problem:
     def apply_operator_noalloc(self, level, u, out, nrhs=1):
         """tpss_apply_operator_noalloc: same result as apply_operator, no device
         allocation (intermediates in the library's fixed 16 MiB array;
-        ndofs * nrhs <= 2^19)."""
+        ndofs * nrhs <= 2^19 on Cartesian meshes; no limit on mapped meshes)."""
         n = self.ndofs(level) * nrhs
         _check(lib().tpss_apply_operator_noalloc(self.h, level, nrhs, _ptr(u, torch.float64, n),
                                                  _ptr(out, torch.float64, n)))

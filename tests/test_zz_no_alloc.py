@@ -60,3 +60,23 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     assert "exceeds" in str(e.value)
     prob.apply_operator_noalloc(0, u[:2 * N], out[:2 * N], nrhs=2)  # 524288 == 2^19 is allowed
     prob.close()
+
+
+@pytest.mark.parametrize("dim,k,n0,nrhs", [(2, 3, 64, 3), (3, 2, 14, 1)])
+def test_noalloc_on_mapped_meshes_has_no_scratch_limit(dim, k, n0, nrhs):
+    # On a mesh of quadrilaterals / hexahedra the operator is one pass with no
+    # intermediates: the call must match tpss_apply_operator even where
+    # ndofs * nrhs is above the Cartesian scratch limit of 2^19.
+    V0 = workloads.vertices_distorted(n0, 7, dim=dim)
+    prob = tpss.Problem.mapped(k, V0, nlevels=2, gamma_hat=4.0)
+    N = prob.ndofs(1)
+    assert N * nrhs > 2 ** 19
+    for seed in (1, 2):   # two calls in a row
+        u = dev(workloads.rhs_uniform(N, seed=seed, nrhs=nrhs))
+        ref = torch.empty_like(u)
+        got = torch.full_like(u, np.nan)
+        prob.apply_operator(1, u, ref, nrhs=nrhs)
+        prob.apply_operator_noalloc(1, u, got, nrhs=nrhs)
+        torch.cuda.synchronize()
+        assert rel_err(got, ref.cpu().numpy()) < TOL64
+    prob.close()
