@@ -66,7 +66,6 @@ def parse():
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
     p.add_argument("--mixed", default="fp32,tf32,bf16", help="low-precision smoother variants to time")
     p.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
-    p.add_argument("--cpu-scale", type=float, default=1.0, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -131,10 +130,50 @@ def clocks_stop(proc, f, path, gpu_index):
 
 
 # -------------------------------------------------------------- cpu oracle
-def cpu_sample(ks, per_k, offset, scale=1.0):
-    """Time the oracle (dense-LU local solves assembled from the bilinear form)
-    on a bounded sample of vertex patches per degree; returns per-k seconds per
-    patch (all 8 right-hand sides) and a description."""
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def fd_sample(ks, colors, threads):
+    """Time the fast-diagonalization oracle (oracle/fd_smoother.c, FP64,
+    OpenMP) on the bench workload restricted to the vertex patches of the
+    given additive colors, 8 RHS, per degree.  Returns {k: (seconds, patches
+    solved)}; the 1D eigendata are computed before the clock starts."""
+    import numpy as np
+
+    from oracle import fastdiag
+    from paper_1910_11239_gb300 import workloads
+
+    widths = workloads.widths_random(NC, 3, WIDTH_SEED)
+    out = {}
+    for k in ks:
+        eig = fastdiag.eigendata(widths, k, True)
+        b = workloads.rhs_batch(dofs(k), SEEDS)
+        t0 = time.perf_counter()
+        fastdiag.additive_local_sum(widths, k, True, b, OMEGA, nrhs=len(SEEDS), threads=threads, eig=eig,
+                                    colors=colors)
+        out[k] = (time.perf_counter() - t0, sum(fastdiag.count_color((NC, NC, NC), c) for c in colors))
+    return out
+
+
+def lu_sample(k, m, seed):
+    """Time the dense-LU oracle (local matrices assembled from the bilinear
+    form, LU with partial pivoting, one core) on m random vertex patches at
+    degree k, 8 RHS; returns (seconds, m)."""
     import numpy as np
     import scipy.linalg as sla
 
@@ -143,76 +182,113 @@ def cpu_sample(ks, per_k, offset, scale=1.0):
     from oracle.sipg import SIPG
     from paper_1910_11239_gb300 import workloads
 
-    widths = workloads.widths_random(NC, 3, WIDTH_SEED)
-    mesh = TensorMesh(widths)
+    mesh = TensorMesh(workloads.widths_random(NC, 3, WIDTH_SEED))
     patches = schwarz.vertex_patches(mesh)
-    out = {}
-    for k in ks:
-        S = SIPG(mesh, k)
-        m = max(1, int(round(per_k[k] * scale)))
-        rng = np.random.default_rng(1000 + k + offset)
-        pick = rng.choice(len(patches), size=m, replace=False)
-        N = mesh.num_cells * S.nloc
-        b = workloads.rhs_batch(N, SEEDS).reshape(len(SEEDS), N)
-        y = np.zeros_like(b)
-        t0 = time.perf_counter()
-        for j in pick:
-            cells = patches[j][1]
-            idx = schwarz.patch_dofs(cells, S.nloc)
-            lu = sla.lu_factor(S.assemble(cells).toarray())
-            y[:, idx] += OMEGA * sla.lu_solve(lu, b[:, idx].T).T
-        out[k] = (time.perf_counter() - t0) / m
-    desc = ", ".join(f"k={k}: {max(1, int(round(per_k[k] * scale)))}" for k in ks)
-    return out, f"{desc} of {len(patches)} vertex patches per degree, 8 RHS each; time per patch x 29791"
-
-
-CPU_PER_K = {2: 48, 3: 24, 4: 8, 5: 4, 6: 2, 7: 1}
-
-
-def cpu_baseline_subprocess(ks, scale):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-worker", "1", "--ks", ",".join(map(str, ks)),
-           "--cpu-scale", str(scale)]
-    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
-    if res.returncode != 0:
-        return {"error": res.stderr[-400:]}
-    return json.loads(res.stdout.strip().splitlines()[-1])
+    S = SIPG(mesh, k)
+    pick = np.random.default_rng(seed).choice(len(patches), size=m, replace=False)
+    N = mesh.num_cells * S.nloc
+    b = workloads.rhs_batch(N, SEEDS).reshape(len(SEEDS), N)
+    y = np.zeros_like(b)
+    t0 = time.perf_counter()
+    for j in pick:
+        idx = schwarz.patch_dofs(patches[j][1], S.nloc)
+        lu = sla.lu_factor(S.assemble(patches[j][1]).toarray())
+        y[:, idx] += OMEGA * sla.lu_solve(lu, b[:, idx].T).T
+    return time.perf_counter() - t0, m
 
 
 def dofs(k):
     return NC ** 3 * (k + 1) ** 3
 
 
-def cpu_value(per_patch, ks):
-    npatch = (NC - 1) ** 3
-    total_t = sum(per_patch[k] * npatch for k in ks)
-    return sum(dofs(k) * len(SEEDS) for k in ks) / total_t
+def npatches():
+    return (NC - 1) ** 3
+
+
+def sample_rate(per_k):
+    """DoF/s of a sample: each degree contributes ndofs * 8 RHS scaled by the
+    fraction of the patches solved, over the summed time."""
+    work = sum(dofs(k) * len(SEEDS) * m / npatches() for k, (t, m) in per_k.items())
+    return work / sum(t for t, _ in per_k.values())
+
+
+def full_step_estimate_ms(per_k):
+    """Time one whole step (every patch of every degree) would take at the
+    sampled per-patch rate (reported beside the timed sample, never as it)."""
+    return 1e3 * sum(t * npatches() / m for t, m in per_k.values())
+
+
+CPU_COLORS = [0]             # one of the 8 additive colors: about 1/8 of the patches
+CPU_ONE_CORE_KS = [2, 3, 4]  # the one-core run stays bounded
+LU_K, LU_PATCHES = 2, 24     # dense LU (the non-tensor sACS approach), context only
+
+
+def cpu_worker(ks):
+    """The cpu_baseline measurement (run in a child process before any CUDA
+    call): the fast-diagonalization oracle on all host cores and on one core,
+    and the dense-LU oracle on one core, each on a bounded sample."""
+    from oracle import fastdiag
+    fastdiag.lib()
+    fd_sample(ks[:1], CPU_COLORS, 0)   # warm-up (page in, thread pool)
+    allc = fd_sample(ks, CPU_COLORS, 0)
+    one_ks = [k for k in ks if k in CPU_ONE_CORE_KS] or ks[:1]
+    one = fd_sample(one_ks, CPU_COLORS, 1)
+    same = {k: allc[k] for k in one_ks}
+    lu = {LU_K: lu_sample(LU_K, LU_PATCHES, 1000)}
+    ncol = ", ".join(f"k={k}: {m}" for k, (t, m) in allc.items())
+    return {
+        "value": sample_rate(allc), "unit": "DoF/s", "cores": fastdiag.max_threads(), "kind": "oracle",
+        "sample": (f"fast-diagonalization oracle (oracle/fd_smoother.c, FP64, OpenMP over the patches of one "
+                   f"color), the vertex patches of additive color {CPU_COLORS} ({ncol} of {npatches()}), 8 RHS "
+                   f"each; DoF/s = ndofs x 8 x solved/total patches / time"),
+        "timed_s": sum(t for t, _ in allc.values()), "full_step_estimate_ms": full_step_estimate_ms(allc),
+        "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+        "per_degree_s": {str(k): t for k, (t, _) in allc.items()},
+        "one_core": {"value": sample_rate(one), "degrees": one_ks, "cores": 1,
+                     "all_cores_same_degrees": sample_rate(same)},
+        "dense_lu_one_core": {"value": sample_rate(lu), "degree": LU_K,
+                              "sample": f"{LU_PATCHES} random vertex patches at k={LU_K}, 8 RHS"}}
+
+
+def cpu_baseline_subprocess(ks):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    env.pop("OMP_NUM_THREADS", None)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-worker", "1", "--ks", ",".join(map(str, ks))]
+    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if res.returncode != 0:
+        return {"error": res.stderr[-400:]}
+    return json.loads(res.stdout.strip().splitlines()[-1])
 
 
 # --------------------------------------------------------------- reference
 def run_reference(args):
+    """The reference arm: the oracle (fast diagonalization in plain C with
+    OpenMP on all host cores) on the same workload, each step a bounded sample
+    (the vertex patches of one additive color, cycling through the 8 colors,
+    at every degree).  ms_per_step is the timed interval of a step; value is
+    the DoFs the sampled patches account for over that time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import fastdiag
+    fastdiag.lib()
     ks = [int(x) for x in args.ks.split(",")]
-    # one step = a bounded sample of the workload (about a third of CPU_PER_K)
     for w in range(args.warmup):
-        cpu_sample(ks, CPU_PER_K, offset=w, scale=0.34)
-    tot = {k: 0.0 for k in ks}
-    desc = ""
+        fd_sample(ks, [w % 8], 0)
+    steps = []
     for s in range(args.steps):
-        per, desc = cpu_sample(ks, CPU_PER_K, offset=100 + s, scale=0.34)
-        for k in ks:
-            tot[k] += per[k]
-    per_patch = {k: tot[k] / args.steps for k in ks}
-    val = cpu_value(per_patch, ks)
-    step_ms = 1e3 * sum(dofs(k) * len(SEEDS) for k in ks) / val
+        steps.append(fd_sample(ks, [s % 8], 0))
+    tot = {k: (sum(st[k][0] for st in steps), sum(st[k][1] for st in steps)) for k in ks}
+    val = sample_rate(tot)
+    step_ms = 1e3 * sum(t for t, _ in tot.values()) / max(1, args.steps)
+    desc = (f"fast-diagonalization oracle (oracle/fd_smoother.c, FP64, OpenMP), per step the vertex patches of "
+            f"one additive color (step s: color s mod 8, about 1/8 of {npatches()}) at k={ks[0]}..{ks[-1]}, 8 RHS")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DoF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
-            "cpu_baseline": {"value": val, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step " + desc},
+            "full_step_estimate_ms": full_step_estimate_ms(tot),
+            "cpu_baseline": {"value": val, "unit": "DoF/s", "cores": fastdiag.max_threads(), "kind": "oracle",
+                             "sample": desc, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": val, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -227,9 +303,7 @@ def main():
         CONFIG["cells"] = [NC, NC, NC]
         CONFIG["workload"] = CONFIG["workload"].replace("32^3", f"{NC}^3").replace("/32", f"/{NC}")
     if args.cpu_worker:
-        ks = [int(x) for x in args.ks.split(",")]
-        per, desc = cpu_sample(ks, CPU_PER_K, offset=0, scale=args.cpu_scale)
-        print(json.dumps({"per_patch_s": {str(k): v for k, v in per.items()}, "sample": desc}))
+        print(json.dumps(cpu_worker([int(x) for x in args.ks.split(",")])))
         return
     if args.impl == "reference":
         run_reference(args)
@@ -247,7 +321,7 @@ def main():
     ks = [int(x) for x in args.ks.split(",")]
     cpu_res = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_res = cpu_baseline_subprocess(ks, 1.0)   # before the first CUDA call
+        cpu_res = cpu_baseline_subprocess(ks)   # before the first CUDA call
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -373,63 +447,52 @@ def main():
         probs[k].close()
     del bdev, xdev, bhost, xhost
 
-    mixed = {}
-    for prec in [p for p in args.mixed.split(",") if p]:
-        mixed[prec] = run_low_precision_smoother(prec, ks, widths, args.steps, tpss, workloads, perf, torch)
+    def leg(name, fn):
+        """Run one extra leg and print it as its own JSON line (rank 0)."""
+        t0 = time.perf_counter()
+        res = fn()
+        if rank == 0:
+            print(json.dumps({"leg": name, "wall_s": time.perf_counter() - t0, "result": res}), flush=True)
 
-    mgcg = None
+    for prec in [p for p in args.mixed.split(",") if p]:
+        leg(f"mixed_smoother_{prec}",
+            lambda: run_low_precision_smoother(prec, ks, widths, args.steps, tpss, workloads, perf, torch))
     if not args.no_mgcg:
-        mgcg = run_mgcg(tpss, workloads, torch, MGCG_CASES)
-    paper_its = None
-    if not args.no_mgcg:
-        paper_its = run_paper_iterations(tpss, workloads, perf, torch)
-    batch = None
+        leg("mg_cg", lambda: run_mgcg(tpss, workloads, torch, MGCG_CASES))
+        leg("paper_iterations", lambda: run_paper_iterations(tpss, workloads, perf, torch))
     if not args.no_batch:
-        batch = run_batch(tpss, workloads, perf, torch, args.steps)
-    kernels = None
+        leg("batched", lambda: run_batch(tpss, workloads, perf, torch, args.steps))
     if not args.no_kernels:
-        kernels = run_kernels(tpss, workloads, perf, torch, max(3, min(args.steps, 10)))
-    high = None
+        leg("kernels", lambda: run_kernels(tpss, workloads, perf, torch, max(3, min(args.steps, 10))))
     if not args.no_high_degree:
-        high = run_high_degree(tpss, workloads, perf, torch, max(2, min(args.steps, 5)))
-    distorted = None
+        leg("high_degree_k15", lambda: run_high_degree(tpss, workloads, perf, torch, max(2, min(args.steps, 5))))
     if not args.no_distorted:
-        distorted = run_distorted(tpss, workloads, perf, torch, max(3, min(args.steps, 10)))
+        leg("distorted", lambda: run_distorted(tpss, workloads, perf, torch, max(3, min(args.steps, 10))))
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
-                "warmup": nwarm, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic (seeded widths and right-hand sides)", "config": CONFIG,
-                "gpu_launches": args.steps * len(ks) * 8, "roofline": roofline, "e2e": e2e,
-                "clocks": clocks, "per_degree": per_k}
-        if world > 1:
-            line["config"] = dict(CONFIG, parallelism=f"replicas x{world}")
-        if cpu_res is not None:
-            if "per_patch_s" in cpu_res:
-                pp = {int(k): v for k, v in cpu_res["per_patch_s"].items()}
-                line["cpu_baseline"] = {"value": cpu_value(pp, ks), "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                                        "sample": cpu_res["sample"]}
-            else:
-                line["cpu_baseline"] = {"value": None, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                                        "sample": "failed: " + cpu_res.get("error", "")}
-        if mixed:
-            line["mixed_smoother"] = mixed
-        if mgcg is not None:
-            line["mg_cg"] = mgcg
-        if batch is not None:
-            line["batched"] = batch
-        if paper_its is not None:
-            line["paper_iterations"] = paper_its
-        if kernels is not None:
-            line["kernels"] = kernels
-        if high is not None:
-            line["high_degree_k15"] = high
-        if distorted is not None:
-            line["distorted"] = distorted
-        print(json.dumps(line))
+        print(json.dumps(headline_line(value, ms / args.steps, world, args.steps, nwarm, roofline, e2e, clocks,
+                                       per_k, cpu_res, args.steps * len(ks) * 8)), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def headline_line(value, ms_per_step, world, steps, warmup, roofline, e2e, clocks, per_k, cpu_res, launches):
+    """The bench's contract line (printed last, a few KB): the FP64 smoother
+    headline with its roofline, end-to-end number, clocks, per-degree rates
+    and the CPU baseline.  The extra legs are printed on earlier lines."""
+    line = {"impl": "tpss", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded widths and right-hand sides)",
+            "config": dict(CONFIG, parallelism=f"replicas x{world}") if world > 1 else CONFIG,
+            "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "clocks": clocks, "per_degree": per_k}
+    if cpu_res is None:
+        pass
+    elif "value" in cpu_res:
+        line["cpu_baseline"] = cpu_res
+    else:
+        line["cpu_baseline"] = {"value": None, "unit": "DoF/s", "cores": None, "kind": "oracle",
+                                "sample": "failed: " + str(cpu_res.get("error", ""))[-300:]}
+    return line
 
 
 def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, torch):

@@ -28,6 +28,11 @@ Galerkin methods"), in FP64, with no Kronecker shortcuts:
                    fractional iteration count (Sec. 2.4).
 * ``chebyshev`` -- the Chebyshev coarse solver with the additive cell smoother
                    as preconditioner (Sec. 2.4).
+* ``fastdiag``  -- the same local solvers by fast diagonalization (Sec. 3.2,
+                   eq. KDseparable, eq. generalizedEVP, eq. fastinverse): 1D
+                   factors from the 1D bilinear form, scipy eigh, and the
+                   additive sweep in plain C with OpenMP (``fd_smoother.c``),
+                   the timed CPU baseline.
 * ``mapped``    -- SIPG on distorted meshes of bilinear / trilinear cells and
                    the Cartesian-surrogate local solvers (Sec. 4, eq.
                    schwarzproj, eq. avglength), with their multigrid hierarchy.

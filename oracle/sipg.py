@@ -110,7 +110,10 @@ class SIPG:
         of the (d-1)-dimensional Gauss rule over the face."""
         d, nq = self.d, len(self.qx)
         others = [s for s in range(d) if s != t]
-        qm = np.array(list(itertools.product(range(nq), repeat=d - 1))).reshape(-1, d - 1)  # [Q, d-1]
+        if d == 1:   # a face of a 1D cell is a point: one "quadrature point", weight 1
+            qm = np.zeros((1, 0), dtype=int)
+        else:
+            qm = np.array(list(itertools.product(range(nq), repeat=d - 1))).reshape(-1, d - 1)  # [Q, d-1]
         im = np.array(self.multi)
         nQ = len(qm)
         vals, ders = [], []

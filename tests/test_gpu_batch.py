@@ -113,3 +113,99 @@ def test_batch_pcg_converges_every_system(prec, stream):
                 assert ((x[seg] - x64).norm() / x64.norm()).item() < 1e-6
             prob.close()
         B.close()
+
+
+# The batched workload's large patch sizes: k = 5 (n = 12) and k = 7 (n = 16),
+# beside a k = 2 problem, each on a 2^3 coarse mesh refined once (4^3 cells).
+SPECS_LARGE = [(5, 2, 2, 21), (7, 2, 2, 22), (2, 2, 2, 23)]
+
+
+def large_problems():
+    return [(k, workloads.widths_random(c, 3, seed), nl) for k, c, nl, seed in SPECS_LARGE]
+
+
+def fine_widths(widths, nlevels):
+    """Per-direction widths after nlevels - 1 bisections."""
+    out = []
+    for w in widths:
+        for _ in range(nlevels - 1):
+            w = np.repeat(np.asarray(w) / 2.0, 2)
+        out.append(np.asarray(w))
+    return out
+
+
+# error bars against the FP64 oracle (as for the single-problem mixed smoothers)
+BATCH_TOL = {"fp32": 1e-4, "bf16": 5e-2}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_smoother_large_patches_match_oracle(prec, stream):
+    # each routine is forced by the batch precision: FP32 -> batch_group<n>,
+    # BF16 -> batch_group_bf16<n>; n = 12 and 16 are the k = 5 and k = 7 items
+    from oracle import fastdiag
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec])
+        b = rhs_for(B, 4)
+        x = torch.full((B.total,), float("nan"), dtype=torch.float32, device="cuda")
+        B.smooth_additive(dev(b, torch.float32), x)
+        torch.cuda.synchronize()
+        xs = x.double().cpu().numpy()
+        for p, (k, widths, nl) in enumerate(large_problems()):
+            info = B.info(p)
+            n = info["ndofs"]
+            fw = fine_widths(widths, nl)
+            for r in range(2):
+                seg = slice(info["offset"] + r * n, info["offset"] + (r + 1) * n)
+                ref = fastdiag.additive_local_sum(fw, k, True, b[seg], OMEGA)
+                assert rel_err(xs[seg], ref) < BATCH_TOL[prec], (p, k, r)
+        B.close()
+
+
+_LARGE_HIERARCHIES = {}
+
+
+def _large_hierarchy(p):
+    # the oracle hierarchy (dense-LU local solvers, up to 4096 x 4096 at k = 7)
+    # is built once per problem and shared by both precisions
+    if p not in _LARGE_HIERARCHIES:
+        k, widths, nl = large_problems()[p]
+        _LARGE_HIERARCHIES[p] = Hierarchy(widths, k, nl, smoother="AVS", omega=OMEGA)
+    return _LARGE_HIERARCHIES[p]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_vcycle_large_patches_match_oracle(prec, stream):
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec])
+        b = rhs_for(B, 5)
+        x = torch.empty(B.total, dtype=torch.float64, device="cuda")
+        B.vcycle(dev(b), x)
+        torch.cuda.synchronize()
+        xs = x.cpu().numpy()
+        for p, (k, widths, nl) in enumerate(large_problems()):
+            info = B.info(p)
+            n = info["ndofs"]
+            H = _large_hierarchy(p)
+            for r in range(2):
+                seg = slice(info["offset"] + r * n, info["offset"] + (r + 1) * n)
+                assert rel_err(xs[seg], H.precondition(b[seg])) < BATCH_TOL[prec], (p, k, r)
+        B.close()
+
+
+def test_batch_vcycle_every_problem_matches_oracle(stream):
+    # the small uneven batch: every problem and right-hand side, not only the first
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(problems(), nrhs=2, omega=OMEGA, stream=stream)
+        b = rhs_for(B, 6)
+        x = torch.empty(B.total, dtype=torch.float64, device="cuda")
+        B.vcycle(dev(b), x)
+        torch.cuda.synchronize()
+        xs = x.cpu().numpy()
+        for p, (k, widths, nl) in enumerate(problems()):
+            info = B.info(p)
+            n = info["ndofs"]
+            H = Hierarchy(widths, k, nl, smoother="AVS", omega=OMEGA)
+            for r in range(2):
+                seg = slice(info["offset"] + r * n, info["offset"] + (r + 1) * n)
+                assert rel_err(xs[seg], H.precondition(b[seg])) < 1e-4, (p, r)
+        B.close()
