@@ -505,8 +505,9 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
     hbm = peaks.get("hbm_gbs", 6800.0)
     nr = len(SEEDS)
     out = {"dtype": prec, "accumulate": "fp32", "per_degree": {}}
-    out["schedule"] = ("colored launches (default); plane-by-plane" +
-                       (" and single-launch atomic" if prec == "bf16" else "") + " schedules timed beside it")
+    out["schedule"] = ("column streaming (default; 4 launches, r read and x written once per parity class); "
+                       "colored, plane-by-plane and single-launch atomic schedules timed beside it" if prec == "bf16"
+                       else "colored launches (default); plane-by-plane schedule timed beside it")
     total_ms = 0.0
     for k in ks:
         prob = tpss.Problem(3, k, widths)
@@ -528,9 +529,11 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
         byt = perf.smoother_bytes((NC, NC, NC), k, nrhs=nr, word=4)
         out["per_degree"][str(k)] = {"dofs_per_s": dofs(k) * nr / (ms / 1e3), "ms_per_call": ms,
                                      "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
-        # the other schedules of the same smoother (default: colored launches)
-        for name, sch in (("planes", tpss.ADDITIVE_PLANES), ("atomic", tpss.ADDITIVE_ATOMIC)):
-            if sch == tpss.ADDITIVE_ATOMIC and prec != "bf16":
+        # the other schedules of the same smoother (default: column streaming
+        # for BF16, colored launches otherwise)
+        for name, sch in (("colors", tpss.ADDITIVE_COLORS), ("planes", tpss.ADDITIVE_PLANES),
+                          ("atomic", tpss.ADDITIVE_ATOMIC)):
+            if sch != tpss.ADDITIVE_PLANES and prec != "bf16":
                 continue
             P.set_additive_schedule(sch)
             P.smooth_additive(OMEGA, b, x, x_is_zero=True, nrhs=nr)
@@ -541,7 +544,6 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
             e1.record()
             torch.cuda.synchronize()
             out["per_degree"][str(k)][f"{name}_ms_per_call"] = e0.elapsed_time(e1) / steps
-        P.set_additive_schedule(tpss.ADDITIVE_COLORS)
         prob.close()
     out["dofs_per_s"] = sum(dofs(k) * nr for k in ks) / (total_ms / 1e3)
     out["vs_fp64_note"] = "same workload, FP32 vectors; compare with the line's FP64 value"
@@ -1027,9 +1029,12 @@ MGCG_CASES = [
     (4, "AVS", 0.7, ["fp64"]),
     (4, "AVS", 0.125, ["fp64", "fp32", "tf32", "bf16"]),
     (4, "MVS", 1.0, ["fp64", "fp64+full", "fp64+8colors", "fp32", "tf32", "bf16"]),
-    (3, "MVS", 1.0, ["fp64", "tf32"]),
-    (5, "MVS", 1.0, ["fp64", "tf32"]),
-    (7, "MVS", 1.0, ["fp64", "fp64+full", "tf32"]),
+    (3, "MVS", 1.0, ["fp64", "fp32", "tf32", "bf16"]),
+    (5, "MVS", 1.0, ["fp64", "fp32", "tf32", "bf16"]),
+    (7, "MVS", 1.0, ["fp64", "fp64+full", "fp32", "tf32", "bf16"]),
+    (3, "AVS", 0.125, ["fp64", "fp32", "bf16"]),
+    (5, "AVS", 0.125, ["fp64", "fp32", "bf16"]),
+    (7, "AVS", 0.125, ["fp64", "fp32", "bf16"]),
 ]
 
 

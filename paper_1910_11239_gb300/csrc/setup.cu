@@ -675,6 +675,9 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
   P->level = level;
   P->kind = kind;
   P->precision = precision;
+  // BF16 3D vertex patches stream columns of patches by default
+  if (precision == TPSS_BF16 && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped)
+    P->additive_schedule = TPSS_ADDITIVE_COLUMNS;
   P->n = kind == TPSS_VERTEX_PATCH ? 2 * n1 : n1;
   const int n = P->n;
   P->nsub = 1;
@@ -904,7 +907,7 @@ extern "C" tpss_status tpss_patches_set_additive_schedule(tpss_patches* P, int s
   clear_error();
   TPSS_REQUIRE(P, "tpss_patches_set_additive_schedule: null patches");
   TPSS_REQUIRE(schedule == TPSS_ADDITIVE_COLORS || schedule == TPSS_ADDITIVE_PLANES ||
-                   schedule == TPSS_ADDITIVE_ATOMIC,
+                   schedule == TPSS_ADDITIVE_ATOMIC || schedule == TPSS_ADDITIVE_COLUMNS,
                "tpss_patches_set_additive_schedule: unknown schedule");
   P->additive_schedule = schedule;
   return TPSS_OK;

@@ -325,6 +325,28 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
     TPSS_CHECK_CUDA(cudaMemcpyAsync(x, rb, (size_t)L.ndofs * nrhs * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return TPSS_OK;
   }
+  if constexpr (sizeof(T) == 4) {
+    // BF16 3D vertex patches, column-streaming schedule: writes x itself
+    if (P->precision == TPSS_BF16 && P->additive_schedule == TPSS_ADDITIVE_COLUMNS) {
+      if (!x_is_zero) {
+        TPSS_TRY(ensure_level_scratch(ctx, P->level, nrhs));
+        T* rb = residual_buffer<T>(L);
+        TPSS_TRY(apply_operator_t<T>(ctx, P->level, nrhs, x, rb, b));
+        r = rb;
+      }
+      const tpss_status st = patch_pass_bf16_stream(P, (float)omega, nrhs, reinterpret_cast<const float*>(r),
+                                                    reinterpret_cast<float*>(x), x_is_zero, s);
+      if (st != TPSS_EINVAL) return st;   // else: shape or alignment not covered, colored launches
+      if (!x_is_zero) {                   // r already holds the residual
+        const int nc = (int)P->add_offsets.size() - 1;
+        for (int c = 0; c < nc; ++c) {
+          const int o = P->add_offsets[c], cnt = P->add_offsets[c + 1] - o;
+          TPSS_TRY(patch_pass<T>(P, P->d_add_list + o, cnt, omega, nrhs, r, x, s));
+        }
+        return TPSS_OK;
+      }
+    }
+  }
   if (x_is_zero) {
     TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, (size_t)L.ndofs * nrhs * sizeof(T), s));
   } else {

@@ -216,7 +216,7 @@ struct tpss_patches {
   // present in plane p_z
   int* d_plane_list = nullptr;
   std::vector<int> plane_offsets;
-  int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule
+  int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule (BF16 3D vertex: COLUMNS)
   // per multiplicative color: cells outside the color with a face to it,
   // {cell index, face mask (bit 2t+side: neighbour at -1 / +1 along t)}
   int2* d_flux_list = nullptr;
@@ -267,6 +267,10 @@ tpss_status patch_pass_bf16(tpss_patches* P, const int* list, int count, float o
                             float* x, cudaStream_t s, float* d = nullptr, int rpc = 0);
 tpss_status patch_pass_bf16_atomic(tpss_patches* P, const int* list, int count, float omega, int nrhs,
                                    const float* r, float* x, cudaStream_t s);
+// ---- smoother_stream.cu (3D BF16 vertex patches, column-streaming schedule:
+// the whole additive pass, x written without clearing when x_is_zero)
+tpss_status patch_pass_bf16_stream(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
+                                   cudaStream_t s);
 
 // ---- smoother_large.cu (3D FP64 vertex patches with n > 16, per-CTA scratch slabs)
 tpss_status patch_large_ctas(int n, int num_sms, int* max_ctas);

@@ -1,0 +1,111 @@
+"""The column-streaming schedule of the BF16 additive vertex-patch smoother
+(3D; the default for BF16 vertex patches): parity with the FP64 oracle at the
+BF16 bound on ragged meshes (odd and even cell counts, so that every parity
+class is first for some cells), with x = 0 and x != 0, several right-hand
+sides, determinism, and the full 32^3 bench mesh at k = 7."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import dev, make, oracle_solvers, oracle_sipg, rel_err
+from oracle import fastdiag, schwarz
+from paper_1910_11239_gb300 import tpss, workloads
+
+pytestmark = pytest.mark.gpu
+
+# BF16 operands (unit roundoff 2^-8) in 6 contractions with FP32 accumulation:
+# relative max-norm errors of a few 1e-3 (the colored schedule's bound, 5e-2,
+# is kept as the bar)
+TOL_BF16 = 5e-2
+
+
+def _smooth(prob, k, schedule, b, nrhs, x0=None, omega=0.7):
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH, tpss.BF16)
+    if schedule is not None:
+        P.set_additive_schedule(schedule)
+    x = torch.full((b.size,), float("nan"), dtype=torch.float32, device="cuda")
+    if x0 is None:
+        P.smooth_additive(omega, dev(b, torch.float32), x, x_is_zero=True, nrhs=nrhs)
+    else:
+        x.copy_(dev(x0, torch.float32))
+        P.smooth_additive(omega, dev(b, torch.float32), x, x_is_zero=False, nrhs=nrhs)
+    torch.cuda.synchronize()
+    out = x.double().cpu().numpy()
+    P.close()
+    return out
+
+
+@pytest.mark.parametrize("k,cells", [(1, (5, 4, 3)), (2, (3, 6, 5)), (3, (7, 2, 4)), (4, (4, 5, 3)),
+                                     (5, (3, 3, 4)), (6, (2, 3, 3)), (7, (3, 4, 2))])
+def test_columns_x0_matches_oracle(k, cells):
+    widths = [workloads.widths_random(n, 1, seed=70 + 3 * k + i)[0] for i, n in enumerate(cells)]
+    prob = make(3, k, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=71 + k, nrhs=2)
+    got = _smooth(prob, k, None, b, 2)
+    for r in range(2):
+        br = b[r * N:(r + 1) * N].astype(np.float32).astype(np.float64)
+        ref = fastdiag.additive_local_sum(widths, k, True, br, 0.7)
+        assert rel_err(got[r * N:(r + 1) * N], ref) < TOL_BF16, r
+    prob.close()
+
+
+@pytest.mark.parametrize("k,cells", [(2, (5, 3, 4)), (3, (4, 4, 3))])
+def test_columns_x0_matches_dense_lu_oracle(k, cells):
+    # the same check against the dense-LU local solvers of the oracle
+    widths = [workloads.widths_random(n, 1, seed=80 + i)[0] for i, n in enumerate(cells)]
+    prob = make(3, k, widths)
+    S = oracle_sipg(widths, k)
+    A = S.assemble().tocsr()
+    _, sol = oracle_solvers(S, A, "vertex")
+    N = A.shape[0]
+    b = workloads.rhs_uniform(N, seed=81)
+    got = _smooth(prob, k, tpss.ADDITIVE_COLUMNS, b, 1)
+    ref = schwarz.additive_local_sum(b.astype(np.float32).astype(np.float64), sol, 0.7)
+    assert rel_err(got, ref) < TOL_BF16
+    prob.close()
+
+
+@pytest.mark.parametrize("k,cells", [(3, (5, 4, 3)), (7, (3, 3, 2))])
+def test_columns_nonzero_x_matches_oracle(k, cells):
+    widths = [workloads.widths_random(n, 1, seed=90 + i)[0] for i, n in enumerate(cells)]
+    prob = make(3, k, widths)
+    S = oracle_sipg(widths, k)
+    A = S.assemble().tocsr()
+    N = A.shape[0]
+    b = workloads.rhs_uniform(N, seed=91, nrhs=2)
+    x0 = workloads.rhs_uniform(N, seed=92, nrhs=2)
+    got = _smooth(prob, k, None, b, 2, x0=x0, omega=0.3)
+    for r in range(2):
+        sl = slice(r * N, (r + 1) * N)
+        bb = b[sl].astype(np.float32).astype(np.float64)
+        xx = x0[sl].astype(np.float32).astype(np.float64)
+        ref = xx + fastdiag.additive_local_sum(widths, k, True, bb - A @ xx, 0.3)
+        assert rel_err(got[sl] - xx, ref - xx) < TOL_BF16, r
+    prob.close()
+
+
+def test_columns_is_default_deterministic_and_close_to_colors():
+    widths = workloads.widths_random(5, 3, seed=95)
+    prob = make(3, 5, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=96, nrhs=3)
+    d1 = _smooth(prob, 5, None, b, 3)
+    d2 = _smooth(prob, 5, tpss.ADDITIVE_COLUMNS, b, 3)
+    assert np.array_equal(d1, d2)            # the default is COLUMNS, and runs repeat bit for bit
+    col = _smooth(prob, 5, tpss.ADDITIVE_COLORS, b, 3)
+    assert rel_err(d1, col) < 2e-2           # two BF16 schedules, different rounding of the last contraction
+    prob.close()
+
+
+def test_columns_full_size_k7():
+    # the 32^3 bench mesh, k = 7, one right-hand side: every DoF against the
+    # fast-diagonalization oracle (pinned to the dense-LU solvers)
+    widths = workloads.widths_random(32, 3, 2)
+    prob = make(3, 7, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=100)
+    got = _smooth(prob, 7, None, b, 1)
+    ref = fastdiag.additive_local_sum(widths, 7, True, b.astype(np.float32).astype(np.float64), 0.7)
+    assert rel_err(got, ref) < TOL_BF16
+    prob.close()
