@@ -532,7 +532,8 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
         # the other schedules of the same smoother (default: column streaming
         # for BF16, colored launches otherwise)
         for name, sch in (("colors", tpss.ADDITIVE_COLORS), ("planes", tpss.ADDITIVE_PLANES),
-                          ("atomic", tpss.ADDITIVE_ATOMIC)):
+                          ("atomic", tpss.ADDITIVE_ATOMIC), ("columns_mma_sync", tpss.ADDITIVE_COLUMNS),
+                          ("columns_tcgen05", tpss.ADDITIVE_TCGEN05)):
             if sch != tpss.ADDITIVE_PLANES and prec != "bf16":
                 continue
             P.set_additive_schedule(sch)

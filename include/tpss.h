@@ -212,12 +212,19 @@ tpss_status tpss_patches_set_large_cluster(tpss_patches* patches, int ctas);
  *     in FP32 in shared memory until both of its patches in the column are
  *     done; the 4 parity classes of (p_x, p_y) share no cell and are 4
  *     launches; deterministic; x is written without being cleared first.
+ *   TCGEN05 (same patch sets): the COLUMNS schedule with the six mode
+ *     contractions of each local solve as tcgen05 MMAs (BF16 operands in
+ *     shared memory, FP32 accumulators in tensor memory).  Its waits for MMA
+ *     completion are bounded (about a second); if one expires the kernel
+ *     stops, frees its tensor memory, and the next additive smoother call on
+ *     the patch set returns TPSS_ETIMEOUT (the earlier result is invalid).
  * Schedules that do not apply to a patch set fall back to COLORS. */
 typedef enum {
   TPSS_ADDITIVE_COLORS = 0,
   TPSS_ADDITIVE_PLANES = 1,
   TPSS_ADDITIVE_ATOMIC = 2,
-  TPSS_ADDITIVE_COLUMNS = 3
+  TPSS_ADDITIVE_COLUMNS = 3,
+  TPSS_ADDITIVE_TCGEN05 = 4
 } tpss_additive_schedule;
 tpss_status tpss_patches_set_additive_schedule(tpss_patches* patches, int schedule);
 

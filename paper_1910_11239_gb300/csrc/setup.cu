@@ -506,6 +506,7 @@ static void free_patches(tpss_patches* P) {
   dfree(P->d_flux_list);
   dfree(P->d_lex_list);
   dfree(P->d_plane_list);
+  if (P->h_fail_flag) cudaFreeHost(P->h_fail_flag);
 }
 
 // Is cell m in a subdomain of multiplicative color `color`?  (The same rule
@@ -907,7 +908,8 @@ extern "C" tpss_status tpss_patches_set_additive_schedule(tpss_patches* P, int s
   clear_error();
   TPSS_REQUIRE(P, "tpss_patches_set_additive_schedule: null patches");
   TPSS_REQUIRE(schedule == TPSS_ADDITIVE_COLORS || schedule == TPSS_ADDITIVE_PLANES ||
-                   schedule == TPSS_ADDITIVE_ATOMIC || schedule == TPSS_ADDITIVE_COLUMNS,
+                   schedule == TPSS_ADDITIVE_ATOMIC || schedule == TPSS_ADDITIVE_COLUMNS ||
+                   schedule == TPSS_ADDITIVE_TCGEN05,
                "tpss_patches_set_additive_schedule: unknown schedule");
   P->additive_schedule = schedule;
   return TPSS_OK;

@@ -327,15 +327,20 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
   }
   if constexpr (sizeof(T) == 4) {
     // BF16 3D vertex patches, column-streaming schedule: writes x itself
-    if (P->precision == TPSS_BF16 && P->additive_schedule == TPSS_ADDITIVE_COLUMNS) {
+    if (P->precision == TPSS_BF16 && (P->additive_schedule == TPSS_ADDITIVE_COLUMNS ||
+                                      P->additive_schedule == TPSS_ADDITIVE_TCGEN05)) {
       if (!x_is_zero) {
         TPSS_TRY(ensure_level_scratch(ctx, P->level, nrhs));
         T* rb = residual_buffer<T>(L);
         TPSS_TRY(apply_operator_t<T>(ctx, P->level, nrhs, x, rb, b));
         r = rb;
       }
-      const tpss_status st = patch_pass_bf16_stream(P, (float)omega, nrhs, reinterpret_cast<const float*>(r),
-                                                    reinterpret_cast<float*>(x), x_is_zero, s);
+      const float* rf = reinterpret_cast<const float*>(r);
+      float* xf = reinterpret_cast<float*>(x);
+      tpss_status st = TPSS_EINVAL;
+      if (P->additive_schedule == TPSS_ADDITIVE_TCGEN05)
+        st = patch_pass_bf16_tc05(P, (float)omega, nrhs, rf, xf, x_is_zero, s);
+      if (st == TPSS_EINVAL) st = patch_pass_bf16_stream(P, (float)omega, nrhs, rf, xf, x_is_zero, s);
       if (st != TPSS_EINVAL) return st;   // else: shape or alignment not covered, colored launches
       if (!x_is_zero) {                   // r already holds the residual
         const int nc = (int)P->add_offsets.size() - 1;

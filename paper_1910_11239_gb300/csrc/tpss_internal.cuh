@@ -217,6 +217,8 @@ struct tpss_patches {
   int* d_plane_list = nullptr;
   std::vector<int> plane_offsets;
   int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule (BF16 3D vertex: COLUMNS)
+  int* h_fail_flag = nullptr;      // tcgen05 smoother: host-mapped word set when an MMA wait expires
+  int* d_fail_flag = nullptr;      // its device address
   // per multiplicative color: cells outside the color with a face to it,
   // {cell index, face mask (bit 2t+side: neighbour at -1 / +1 along t)}
   int2* d_flux_list = nullptr;
@@ -271,6 +273,10 @@ tpss_status patch_pass_bf16_atomic(tpss_patches* P, const int* list, int count, 
 // the whole additive pass, x written without clearing when x_is_zero)
 tpss_status patch_pass_bf16_stream(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
                                    cudaStream_t s);
+// ---- smoother_tc05.cu (the same schedule with tcgen05 MMAs; TPSS_ETIMEOUT
+// if an earlier launch on P gave up waiting for its MMAs)
+tpss_status patch_pass_bf16_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
+                                 cudaStream_t s);
 
 // ---- smoother_large.cu (3D FP64 vertex patches with n > 16, per-CTA scratch slabs)
 tpss_status patch_large_ctas(int n, int num_sms, int* max_ctas);

@@ -21,7 +21,7 @@ FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PENALTY_PAPER, PENALTY_KP1SQ = 0, 1
 COARSE_AUTO, COARSE_DENSE, COARSE_FD, COARSE_CHEBYSHEV = 0, 1, 2, 3
 MULT_RESIDUAL_UPDATE, MULT_RESIDUAL_FULL = 0, 1
-ADDITIVE_COLORS, ADDITIVE_PLANES, ADDITIVE_ATOMIC, ADDITIVE_COLUMNS = 0, 1, 2, 3
+ADDITIVE_COLORS, ADDITIVE_PLANES, ADDITIVE_ATOMIC, ADDITIVE_COLUMNS, ADDITIVE_TCGEN05 = 0, 1, 2, 3, 4
 ACS, AVS, MCS, MVS = 0, 1, 2, 3
 SMOOTHERS = {"ACS": ACS, "AVS": AVS, "MCS": MCS, "MVS": MVS}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}

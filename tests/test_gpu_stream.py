@@ -1,5 +1,6 @@
-"""The column-streaming schedule of the BF16 additive vertex-patch smoother
-(3D; the default for BF16 vertex patches): parity with the FP64 oracle at the
+"""The column-streaming schedules of the BF16 additive vertex-patch smoother
+(3D): COLUMNS (mma.sync contractions) and TCGEN05 (the same walk with tcgen05
+MMAs and tensor-memory accumulators).  Parity with the FP64 oracle at the
 BF16 bound on ragged meshes (odd and even cell counts, so that every parity
 class is first for some cells), with x = 0 and x != 0, several right-hand
 sides, determinism, and the full 32^3 bench mesh at k = 7."""
@@ -35,14 +36,18 @@ def _smooth(prob, k, schedule, b, nrhs, x0=None, omega=0.7):
     return out
 
 
+SCHEDULES = [tpss.ADDITIVE_COLUMNS, tpss.ADDITIVE_TCGEN05]
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("k,cells", [(1, (5, 4, 3)), (2, (3, 6, 5)), (3, (7, 2, 4)), (4, (4, 5, 3)),
                                      (5, (3, 3, 4)), (6, (2, 3, 3)), (7, (3, 4, 2))])
-def test_columns_x0_matches_oracle(k, cells):
+def test_columns_x0_matches_oracle(k, cells, schedule):
     widths = [workloads.widths_random(n, 1, seed=70 + 3 * k + i)[0] for i, n in enumerate(cells)]
     prob = make(3, k, widths)
     N = prob.ndofs(0)
     b = workloads.rhs_uniform(N, seed=71 + k, nrhs=2)
-    got = _smooth(prob, k, None, b, 2)
+    got = _smooth(prob, k, schedule, b, 2)
     for r in range(2):
         br = b[r * N:(r + 1) * N].astype(np.float32).astype(np.float64)
         ref = fastdiag.additive_local_sum(widths, k, True, br, 0.7)
@@ -50,8 +55,9 @@ def test_columns_x0_matches_oracle(k, cells):
     prob.close()
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("k,cells", [(2, (5, 3, 4)), (3, (4, 4, 3))])
-def test_columns_x0_matches_dense_lu_oracle(k, cells):
+def test_columns_x0_matches_dense_lu_oracle(k, cells, schedule):
     # the same check against the dense-LU local solvers of the oracle
     widths = [workloads.widths_random(n, 1, seed=80 + i)[0] for i, n in enumerate(cells)]
     prob = make(3, k, widths)
@@ -60,14 +66,15 @@ def test_columns_x0_matches_dense_lu_oracle(k, cells):
     _, sol = oracle_solvers(S, A, "vertex")
     N = A.shape[0]
     b = workloads.rhs_uniform(N, seed=81)
-    got = _smooth(prob, k, tpss.ADDITIVE_COLUMNS, b, 1)
+    got = _smooth(prob, k, schedule, b, 1)
     ref = schwarz.additive_local_sum(b.astype(np.float32).astype(np.float64), sol, 0.7)
     assert rel_err(got, ref) < TOL_BF16
     prob.close()
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("k,cells", [(3, (5, 4, 3)), (7, (3, 3, 2))])
-def test_columns_nonzero_x_matches_oracle(k, cells):
+def test_columns_nonzero_x_matches_oracle(k, cells, schedule):
     widths = [workloads.widths_random(n, 1, seed=90 + i)[0] for i, n in enumerate(cells)]
     prob = make(3, k, widths)
     S = oracle_sipg(widths, k)
@@ -75,7 +82,7 @@ def test_columns_nonzero_x_matches_oracle(k, cells):
     N = A.shape[0]
     b = workloads.rhs_uniform(N, seed=91, nrhs=2)
     x0 = workloads.rhs_uniform(N, seed=92, nrhs=2)
-    got = _smooth(prob, k, None, b, 2, x0=x0, omega=0.3)
+    got = _smooth(prob, k, schedule, b, 2, x0=x0, omega=0.3)
     for r in range(2):
         sl = slice(r * N, (r + 1) * N)
         bb = b[sl].astype(np.float32).astype(np.float64)
@@ -85,27 +92,39 @@ def test_columns_nonzero_x_matches_oracle(k, cells):
     prob.close()
 
 
-def test_columns_is_default_deterministic_and_close_to_colors():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_columns_deterministic_and_close_to_colors(schedule):
     widths = workloads.widths_random(5, 3, seed=95)
     prob = make(3, 5, widths)
     N = prob.ndofs(0)
     b = workloads.rhs_uniform(N, seed=96, nrhs=3)
-    d1 = _smooth(prob, 5, None, b, 3)
-    d2 = _smooth(prob, 5, tpss.ADDITIVE_COLUMNS, b, 3)
-    assert np.array_equal(d1, d2)            # the default is COLUMNS, and runs repeat bit for bit
+    d1 = _smooth(prob, 5, schedule, b, 3)
+    d2 = _smooth(prob, 5, schedule, b, 3)
+    assert np.array_equal(d1, d2)            # runs repeat bit for bit
     col = _smooth(prob, 5, tpss.ADDITIVE_COLORS, b, 3)
     assert rel_err(d1, col) < 2e-2           # two BF16 schedules, different rounding of the last contraction
     prob.close()
 
 
-def test_columns_full_size_k7():
+def test_bf16_vertex_default_schedule_is_streamed():
+    widths = workloads.widths_random(4, 3, seed=97)
+    prob = make(3, 3, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=98)
+    default = _smooth(prob, 3, None, b, 1)
+    assert any(np.array_equal(default, _smooth(prob, 3, s, b, 1)) for s in SCHEDULES)
+    prob.close()
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_columns_full_size_k7(schedule):
     # the 32^3 bench mesh, k = 7, one right-hand side: every DoF against the
     # fast-diagonalization oracle (pinned to the dense-LU solvers)
     widths = workloads.widths_random(32, 3, 2)
     prob = make(3, 7, widths)
     N = prob.ndofs(0)
     b = workloads.rhs_uniform(N, seed=100)
-    got = _smooth(prob, 7, None, b, 1)
+    got = _smooth(prob, 7, schedule, b, 1)
     ref = fastdiag.additive_local_sum(widths, 7, True, b.astype(np.float32).astype(np.float64), 0.7)
     assert rel_err(got, ref) < TOL_BF16
     prob.close()
