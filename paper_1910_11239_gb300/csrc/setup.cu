@@ -506,6 +506,7 @@ static void free_patches(tpss_patches* P) {
   dfree(P->d_flux_list);
   dfree(P->d_lex_list);
   dfree(P->d_plane_list);
+  dfree(P->d_bop);
   if (P->h_fail_flag) cudaFreeHost(P->h_fail_flag);
 }
 
@@ -738,6 +739,8 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
       convert(P->d_lam[t], P->d_lam32[t], (size_t)np * n, ctx->stream);
     }
   }
+  // operands of the tcgen05 smoother (every direction's FP32 eigenvectors are converted by now)
+  if (!ctx->mapped && precision == TPSS_BF16 && (st = tc05_prepare(P)) != TPSS_OK) return fail(st);
   const bool large = d == 3 && n > kMaxSharedPatchN;
   if (ctx->mapped) {
     // inverse table already built per cell

@@ -4,8 +4,8 @@
 //
 // Schedule: as the COLUMNS schedule (smoother_stream.cu): one CTA per column
 // of vertex patches (p_x, p_y) and right-hand side walks p_z, r staged one
-// cell plane at a time with cp.async, x accumulated per cell plane in FP32
-// shared memory and written once per parity class of (p_x, p_y).
+// cell plane ahead with cp.async, each cell plane of x written once per
+// parity class of (p_x, p_y) when both of its patches in the column are done.
 //
 // Local solve (eq. fastinverse, eq. eigenvectormatvec): the six mode
 // contractions of (Z_z x Z_y x Z_x) Lambda^{-1} (Z_z x Z_y x Z_x)^T are six
@@ -13,24 +13,34 @@
 // BF16 operands from shared memory, FP32 accumulation in TMEM.  Every index
 // is padded to 16, so the patch tensor has 256 "lines" (slow index s, fast
 // index f, row m = 16 s + f).  A is the tensor with the contracted index as
-// K; B holds the 1D eigenvector matrix (K-major, 16 x 16, zero padded).
-// After each MMA every thread reads its TMEM rows (row m = thread + 128 b)
-// and writes them back to shared memory as the next A, rotating the indices
-// so that the next contracted index becomes K:
+// K; B is the 1D eigenvector matrix (K-major 16 x 16, zero padded, prepared
+// once per position at setup and staged with cp.async).  After each MMA every
+// thread reads its TMEM rows (row m = thread + 128 b) and writes them back to
+// shared memory as the next A, rotating the indices so that the next
+// contracted index becomes K:
 //
 //   A0[(z,y)][x]  --Zx^T--> D1[(z,y)][a] -> A1[(z,a)][y]   (MN-major write)
 //   A1            --Zy^T--> D2[(z,a)][b] -> A2[(a,b)][z]   (MN-major)
 //   A2            --Zz^T--> D3[(a,b)][c] -> scaled by 1/(lx_a + ly_b + lz_c) -> A3[(a,b)][c] (K-major)
 //   A3            --Zz----> D4[(a,b)][z] -> A4[(a,z)][b]   (MN-major)
 //   A4            --Zy----> D5[(a,z)][y] -> A5[(z,y)][a]   (MN-major)
-//   A5            --Zx----> D6[(z,y)][x] -> omega * D6 added to the plane accumulators
+//   A5            --Zx----> D6[(z,y)][x] -> omega * D6, the patch's correction
 //
-// so each thread's TMEM row is stored as two 16-byte rows of core matrices.
-// One thread issues the MMAs and a tcgen05.commit arrives on an mbarrier;
-// the wait for it is bounded (about a second); on expiry the kernel records
-// the failure in a host-visible flag, waits for its own copies, frees its
-// TMEM and returns, and the next smoother call on the patch set reports
-// TPSS_ETIMEOUT.
+// so each thread's TMEM row goes back as two 16-byte rows of core matrices.
+// The core matrices of A sit 144 bytes apart along M (not 128) so that these
+// writes are free of shared-memory bank conflicts.
+//
+// Output: with k = 7 (16 points per direction) a thread's two rows of D6 are
+// the same (y, z) line of the patch's lower and upper cell plane; the upper
+// one is kept in registers until the next patch of the column adds the lower
+// one of that plane, and the finished line (two cell rows) goes straight to
+// x.  Other degrees accumulate in FP32 plane buffers in shared memory and
+// write each finished plane.
+//
+// One thread issues the MMAs; a tcgen05.commit arrives on an mbarrier.  The
+// wait for it is bounded (about a second): on expiry the kernel records the
+// failure in a host-visible flag, waits for its own copies, frees its TMEM and
+// returns, and the next smoother call on the patch set reports TPSS_ETIMEOUT.
 #include "tc05.cuh"
 #include "tpss_internal.cuh"
 
@@ -39,37 +49,56 @@ namespace tcs {
 
 constexpr int kThreads = 128;
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+constexpr int kMStride = 144;                     // bytes between core matrices along M
+constexpr int kKStride = 32 * kMStride;           // bytes between the two K halves (256 rows)
+constexpr int kOpABytes = 2 * kKStride;
 
-// byte offsets of the operand layouts (see tc05.cuh): 256 rows x 16 K of BF16
-// in core matrices of 8 rows x 16 bytes; K-direction stride 4096 bytes,
-// M-direction stride 128 bytes
-__device__ __forceinline__ int off_k(int m) { return (m & 7) * 16 + (m >> 3) * 128; }   // + 4096 for k >= 8
-__device__ __forceinline__ int off_mn(int slow, int k) { return (k & 7) * 16 + slow * 256 + (k >> 3) * 4096; }
+// byte offset of row m of a K-major A (K half 0; + kKStride for K half 1)
+__device__ __forceinline__ int off_k(int m) { return (m & 7) * 16 + (m >> 3) * kMStride; }
+// byte offset of the run of rows 16 slow .. 16 slow + 7 at column k of an
+// MN-major A (rows 16 slow + 8 .. + 15: + kMStride)
+__device__ __forceinline__ int off_mn(int slow, int k) {
+  return (k & 7) * 16 + slow * 2 * kMStride + (k >> 3) * kKStride;
+}
 
 template <int N>
 struct Smem {
   static constexpr int N1 = N / 2;
   static constexpr int NLOC1 = N1 * N1 * N1;
-  static constexpr int NP = 4 * NLOC1;                 // floats of one column plane (4 cells)
-  static constexpr size_t OPA = 0;                     // 8192 bytes: operand A
-  static constexpr size_t OPB = 8192;                  // 6 x 512 bytes: operands B
-  static constexpr size_t SB = OPB + 6 * 512;          // 3 staged planes of r (FP32)
-  static constexpr size_t ACC = SB + 3 * (size_t)NP * 4;   // 2 plane accumulators (FP32)
-  static constexpr size_t BYTES = ACC + 2 * (size_t)NP * 4;
+  static constexpr int NP = 4 * NLOC1;                       // floats of one column plane (4 cells)
+  static constexpr bool CARRY = (N == 16);                   // finished lines kept in registers
+  static constexpr size_t OPA = 0;
+  static constexpr size_t OPB = kOpABytes;                   // 8 x 512 bytes: operands B
+  static constexpr size_t SB = OPB + 8 * 512;                // 3 staged planes of r (FP32)
+  static constexpr size_t ACC = SB + 3 * (size_t)NP * 4;     // 2 plane accumulators (FP32) unless CARRY
+  static constexpr size_t BYTES = ACC + (CARRY ? 0 : 2 * (size_t)NP * 4);
 };
+// B operand slots (pairs as stored per position: Z^T-apply, Z-apply): 0 / 1 x,
+// 2 / 3 y, 4 + 2q / 5 + 2q z of the patch with p_z & 1 == q.  Stage s (1..6)
+// of patch p_z uses:
+__device__ __forceinline__ int b_slot(int s, int q) {
+  return s == 1 ? 0 : s == 2 ? 2 : s == 3 ? 4 + 2 * q : s == 4 ? 5 + 2 * q : s == 5 ? 3 : 1;
+}
+// A layout of the MMA of stage s (0 K-major, 1 MN-major)
+__device__ __forceinline__ int a_major(int s) { return (s == 1 || s == 4) ? 0 : 1; }
 
-// B operand s (16 x 16, K-major) from the 1D eigenvector matrix Z (node-major
-// Z[i * N + mode]): forward (Z^T applied): B[n][k] = Z[k][n]; back (Z
-// applied): B[n][k] = Z[n][k]; zero outside N x N.
-template <int N>
-__device__ __forceinline__ void write_b(unsigned char* ob, const float* __restrict__ Z, bool back, int tid) {
-  __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(ob);
-  for (int e = tid; e < 256; e += kThreads) {
-    const int n = e >> 4, k = e & 15;
+// Global B operands: [t][position][apply Z^T (0) / Z (1)][512 bytes], the
+// 16 x 16 K-major BF16 matrix B[n][k] = Z[k][n] (0) or Z[n][k] (1), Z[node][mode].
+__global__ void prepare_bop_kernel(const float* __restrict__ Z, int npos, int n, __nv_bfloat16* __restrict__ out) {
+  const int p = blockIdx.x, back = blockIdx.y;
+  if (p >= npos) return;
+  const float* Zp = Z + (size_t)p * n * n;
+  __nv_bfloat16* o = out + ((size_t)p * 2 + back) * 256;
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    const int nn = e >> 4, k = e & 15;
     float v = 0.f;
-    if (n < N && k < N) v = back ? __ldg(Z + n * N + k) : __ldg(Z + k * N + n);
-    b[((n & 7) * 16 + (n >> 3) * 128 + (k >> 3) * 256 + (k & 7) * 2) / 2] = __float2bfloat16(v);
+    if (nn < n && k < n) v = back ? Zp[nn * n + k] : Zp[k * n + nn];
+    o[((nn & 7) * 16 + (nn >> 3) * 128 + (k >> 3) * 256 + (k & 7) * 2) / 2] = __float2bfloat16(v);
   }
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
 }
 
 template <int NLOC1>
@@ -83,8 +112,7 @@ __device__ __forceinline__ void stage_plane(float* dst, const float* __restrict_
     constexpr int CH = NLOC1 / 4;
     for (int e = tid; e < 4 * CH; e += kThreads) {
       const int c2 = e / CH, o = (e % CH) * 4;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d + 4u * (c2 * NLOC1 + o)),
-                   "l"(src + cell0(c2) + o) : "memory");
+      cp16(d + 4u * (c2 * NLOC1 + o), src + cell0(c2) + o);
     }
   } else {
     for (int e = tid; e < 4 * NLOC1; e += kThreads) {
@@ -93,6 +121,11 @@ __device__ __forceinline__ void stage_plane(float* dst, const float* __restrict_
                    "l"(src + cell0(c2) + o) : "memory");
     }
   }
+}
+
+// 1 KB of B operands (two matrices) -> shared memory
+__device__ __forceinline__ void stage_b2(unsigned char* dst, const __nv_bfloat16* src, int tid) {
+  if (tid < 64) cp16(tc05::smem_u32(dst) + 16u * tid, reinterpret_cast<const unsigned char*>(src) + 16 * tid);
 }
 
 __device__ __forceinline__ int first_class(int cx, int cy, int nc0, int nc1) {
@@ -132,15 +165,13 @@ __device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, i
   }
 }
 
-// stage s (1..6): A layout of the MMA's operand (0 K-major, 1 MN-major)
-__device__ __forceinline__ int a_major(int s) { return (s == 1 || s == 4) ? 0 : 1; }
-
 template <int N>
 __global__ void __launch_bounds__(kThreads, 4)
-patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__ Z1, const float* __restrict__ Z2,
-                         const float* __restrict__ L0, const float* __restrict__ L1, const float* __restrict__ L2,
-                         const float* __restrict__ r, float* __restrict__ x, float omega, int nc0, int nc1, int nc2,
-                         int64_t ndofs, int cls, int ncolx, int x_is_zero, volatile int* fail_flag) {
+patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat16* __restrict__ B1,
+                         const __nv_bfloat16* __restrict__ B2, const float* __restrict__ L0,
+                         const float* __restrict__ L1, const float* __restrict__ L2, const float* __restrict__ r,
+                         float* __restrict__ x, float omega, int nc0, int nc1, int nc2, int64_t ndofs, int cls,
+                         int ncolx, int x_is_zero, volatile int* fail_flag) {
   using M = Smem<N>;
   constexpr int N1 = N / 2;
   constexpr int NLOC1 = M::NLOC1;
@@ -161,17 +192,18 @@ patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__
   x += (int64_t)blockIdx.y * ndofs;
   const uint32_t mb = tc05::smem_u32(&mbar);
 
+  // prologue: planes 0 and 1, the column's x and y operands, patch 0's z operands
   stage_plane<NLOC1>(SB, r, px, py, 0, nc0, nc1, tid);
   stage_plane<NLOC1>(SB + NP, r, px, py, 1, nc0, nc1, tid);
+  stage_b2(opb + 0 * 512, B0 + (size_t)px * 512, tid);   // slots 0, 1
+  stage_b2(opb + 2 * 512, B1 + (size_t)py * 512, tid);   // slots 2, 3
+  stage_b2(opb + 4 * 512, B2, tid);                      // patch 0: slots 4, 5
   asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int e = tid; e < 8192 / 16; e += kThreads) reinterpret_cast<uint4*>(opa)[e] = make_uint4(0, 0, 0, 0);
-  for (int e = tid; e < 2 * NP; e += kThreads) ACC[e] = 0.f;
+  for (int e = tid; e < kOpABytes / 16; e += kThreads) reinterpret_cast<uint4*>(opa)[e] = make_uint4(0, 0, 0, 0);
+  if constexpr (!M::CARRY)
+    for (int e = tid; e < 2 * NP; e += kThreads) ACC[e] = 0.f;
   if (tid < 32) lam[tid] = (tid < 16) ? (tid < N ? L0[(size_t)px * N + tid] : 0.f)
                                       : (tid - 16 < N ? L1[(size_t)py * N + tid - 16] : 0.f);
-  write_b<N>(opb + 0 * 512, Z0 + (size_t)px * N * N, false, tid);
-  write_b<N>(opb + 1 * 512, Z1 + (size_t)py * N * N, false, tid);
-  write_b<N>(opb + 4 * 512, Z1 + (size_t)py * N * N, true, tid);
-  write_b<N>(opb + 5 * 512, Z0 + (size_t)px * N * N, true, tid);
   if (tid == 0) tc05::mbar_init(mb, 1);
   if (warp == 0) tc05::alloc(tc05::smem_u32(&tslot), 32);
   tc05::fence_before_sync();
@@ -183,16 +215,50 @@ patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__
   uint32_t phase = 0;
   bool failed = false;
 
+  // CARRY (k = 7): this thread's line (y = tid & 15, local z = tid >> 4) of the
+  // two cells (sx = 0, 1) at (p_x + sx, p_y + y / 8)
+  const int ly = tid & 15, liz = tid >> 4;
+  float carry[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) carry[j] = 0.f;
+  bool store_cell[2] = {false, false};
+  int64_t line_off[2] = {0, 0};
+  if constexpr (M::CARRY) {
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx) {
+      const int cx = px + sx, cy = py + (ly >> 3);
+      store_cell[sx] = x_is_zero && first_class(cx, cy, nc0, nc1) == cls;
+      line_off[sx] = (cx + (int64_t)nc0 * cy) * NLOC1 + 8 * ((ly & 7) + 8 * liz);
+    }
+  }
+  const int64_t plane_stride = (int64_t)nc0 * nc1 * NLOC1;
+
   for (int pz = 0; pz + 1 < nc2 && !failed; ++pz) {
     asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();   // planes pz, pz + 1 staged; the previous patch is done with the operands and slot (pz + 2) % 3
+    __syncthreads();   // planes pz, pz + 1 and patch pz's z operands staged; patch pz - 1 is done
     if (pz + 2 < nc2) {
       stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
+      stage_b2(opb + (4 + 2 * ((pz + 1) & 1)) * 512, B2 + (size_t)(pz + 1) * 512, tid);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
     if (tid < 16) lam[32 + tid] = tid < N ? L2[(size_t)pz * N + tid] : 0.f;
-    write_b<N>(opb + 2 * 512, Z2 + (size_t)pz * N * N, false, tid);
-    write_b<N>(opb + 3 * 512, Z2 + (size_t)pz * N * N, true, tid);
+    // previous values of this thread's line of plane pz (read-modify-write classes)
+    float xold[16];
+    if constexpr (M::CARRY) {
+#pragma unroll
+      for (int sx = 0; sx < 2; ++sx) {
+        const float* src = x + line_off[sx] + pz * plane_stride;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (!store_cell[sx]) v = *reinterpret_cast<const float4*>(src + 4 * q);
+          xold[8 * sx + 4 * q] = v.x;
+          xold[8 * sx + 4 * q + 1] = v.y;
+          xold[8 * sx + 4 * q + 2] = v.z;
+          xold[8 * sx + 4 * q + 3] = v.w;
+        }
+      }
+    }
     // gather: A0[(z, y)][x] (K-major), zero outside the patch
     const float* lo = SB + (pz % 3) * NP;
     const float* hi = SB + ((pz + 1) % 3) * NP;
@@ -200,15 +266,26 @@ patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__
     for (int b = 0; b < NB; ++b) {
       const int m = tid + 128 * b, z = m >> 4, y = m & 15;
       float v[16];
+      if constexpr (N1 == 8) {
+        const float* src = (b ? hi : lo) + 2 * (y >> 3) * NLOC1 + 8 * ((y & 7) + 8 * (z & 7));
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = 0.f;
-      if (z < N && y < N) {
-        const float* src = (z >= N1 ? hi : lo) + 2 * (y / N1) * NLOC1 + N1 * ((y % N1) + N1 * (z % N1));
+        for (int sx = 0; sx < 2; ++sx) {
+          const float4 a0 = *reinterpret_cast<const float4*>(src + sx * NLOC1);
+          const float4 a1 = *reinterpret_cast<const float4*>(src + sx * NLOC1 + 4);
+          v[8 * sx] = a0.x; v[8 * sx + 1] = a0.y; v[8 * sx + 2] = a0.z; v[8 * sx + 3] = a0.w;
+          v[8 * sx + 4] = a1.x; v[8 * sx + 5] = a1.y; v[8 * sx + 6] = a1.z; v[8 * sx + 7] = a1.w;
+        }
+      } else {
 #pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = src[(j / N1) * NLOC1 + (j % N1)];
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        if (z < N && y < N) {
+          const float* src = (z >= N1 ? hi : lo) + 2 * (y / N1) * NLOC1 + N1 * ((y % N1) + N1 * (z % N1));
+#pragma unroll
+          for (int j = 0; j < N; ++j) v[j] = src[(j / N1) * NLOC1 + (j % N1)];
+        }
       }
       tc05::st_row8(opa + off_k(m), v);
-      tc05::st_row8(opa + off_k(m) + 4096, v + 8);
+      tc05::st_row8(opa + off_k(m) + kKStride, v + 8);
     }
     tc05::fence_proxy_async();
     tc05::fence_before_sync();
@@ -218,10 +295,10 @@ patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__
     for (int s = 1; s <= 6; ++s) {
       if (tid == 0) {
         const uint32_t idesc = tc05::idesc_bf16(128, 16, a_major(s), 0);
-        const uint64_t bdesc = tc05::desc(b_base + 512 * (s - 1), 256, 128);
+        const uint64_t bdesc = tc05::desc(b_base + 512 * b_slot(s, pz & 1), 256, 128);
 #pragma unroll
         for (int b = 0; b < NB; ++b)
-          tc05::mma(tmem + 16 * b, tc05::desc(a_base + 2048 * b, 4096, 128), bdesc, idesc, 0);
+          tc05::mma(tmem + 16 * b, tc05::desc(a_base + 16 * kMStride * b, kKStride, kMStride), bdesc, idesc, 0);
         tc05::commit(mb);
       }
       const bool ok = tc05::mbar_wait_bounded(mb, phase, kWaitCycles);
@@ -233,33 +310,50 @@ patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__
       } else {
         tc05::ld16(trow, v);
       }
+      if (s == 6 && M::CARRY) {
+        // rows: block 0 = line (liz, ly) of plane pz (lower cells), block 1 = plane pz + 1
 #pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int m = tid + 128 * b, sl = m >> 4, fa = m & 15;
-        float* w = v + 16 * b;
-        if (s == 1 || s == 4) {          // D1[(z,y)][a] -> A1[(z,a)][y];  D4[(a,b)][z] -> A4[(a,z)][b]
-          if (NB == 2 || sl < 8) {
-            tc05::st_row8(opa + off_mn(sl, fa), w);
-            tc05::st_row8(opa + off_mn(sl, fa) + 128, w + 8);
-          }
-        } else if (s == 2 || s == 5) {   // D2[(z,a)][b] -> A2[(a,b)][z];  D5[(a,z)][y] -> A5[(z,y)][a]
-          if (NB == 2 || fa < 8) {
-            tc05::st_row8(opa + off_mn(fa, sl), w);
-            tc05::st_row8(opa + off_mn(fa, sl) + 128, w + 8);
-          }
-        } else if (s == 3) {             // D3[(a,b)][c] / (lx_a + ly_b + lz_c) -> A3[(a,b)][c]
-          const float sab = lam[sl] + lam[16 + fa];
+        for (int j = 0; j < 16; ++j) {
+          xold[j] += carry[j] + omega * v[j];
+          carry[j] = omega * v[16 + j];
+        }
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            w[j] = (sl < N && fa < N && j < N) ? __fdividef(w[j], sab + lam[32 + j]) : 0.f;
-          tc05::st_row8(opa + off_k(m), w);
-          tc05::st_row8(opa + off_k(m) + 4096, w + 8);
-        } else {                         // D6[(z,y)][x]: omega * line -> plane accumulators
-          if (sl < N && fa < N) {
-            const int sz = sl / N1, iz = sl % N1, sy = fa / N1, iy = fa % N1;
-            float* acc = ACC + ((pz + sz) & 1) * NP + 2 * sy * NLOC1 + N1 * (iy + N1 * iz);
+        for (int sx = 0; sx < 2; ++sx) {
+          float* dst = x + line_off[sx] + pz * plane_stride;
+          *reinterpret_cast<float4*>(dst) = make_float4(xold[8 * sx], xold[8 * sx + 1], xold[8 * sx + 2],
+                                                        xold[8 * sx + 3]);
+          *reinterpret_cast<float4*>(dst + 4) = make_float4(xold[8 * sx + 4], xold[8 * sx + 5],
+                                                            xold[8 * sx + 6], xold[8 * sx + 7]);
+        }
+      } else {
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[(j / N1) * NLOC1 + (j % N1)] += omega * w[j];
+        for (int b = 0; b < NB; ++b) {
+          const int m = tid + 128 * b, sl = m >> 4, fa = m & 15;
+          float* w = v + 16 * b;
+          if (s == 1 || s == 4) {          // D1[(z,y)][a] -> A1[(z,a)][y];  D4[(a,b)][z] -> A4[(a,z)][b]
+            if (NB == 2 || sl < 8) {
+              tc05::st_row8(opa + off_mn(sl, fa), w);
+              tc05::st_row8(opa + off_mn(sl, fa) + kMStride, w + 8);
+            }
+          } else if (s == 2 || s == 5) {   // D2[(z,a)][b] -> A2[(a,b)][z];  D5[(a,z)][y] -> A5[(z,y)][a]
+            if (NB == 2 || fa < 8) {
+              tc05::st_row8(opa + off_mn(fa, sl), w);
+              tc05::st_row8(opa + off_mn(fa, sl) + kMStride, w + 8);
+            }
+          } else if (s == 3) {             // D3[(a,b)][c] / (lx_a + ly_b + lz_c) -> A3[(a,b)][c]
+            const float sab = lam[sl] + lam[16 + fa];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              w[j] = (sl < N && fa < N && j < N) ? __fdividef(w[j], sab + lam[32 + j]) : 0.f;
+            tc05::st_row8(opa + off_k(m), w);
+            tc05::st_row8(opa + off_k(m) + kKStride, w + 8);
+          } else if constexpr (!M::CARRY) {   // D6[(z,y)][x]: omega * line -> plane accumulators
+            if (sl < N && fa < N) {
+              const int sz = sl / N1, iz = sl % N1, sy = fa / N1, iy = fa % N1;
+              float* acc = ACC + ((pz + sz) & 1) * NP + 2 * sy * NLOC1 + N1 * (iy + N1 * iz);
+#pragma unroll
+              for (int j = 0; j < N; ++j) acc[(j / N1) * NLOC1 + (j % N1)] += omega * w[j];
+            }
           }
         }
       }
@@ -272,12 +366,32 @@ patch_stream_tc05_kernel(const float* __restrict__ Z0, const float* __restrict__
       if (failed) break;
     }
     if (failed) break;
-    // plane pz now has both of its patches of this column
-    flush_plane<N1>(x, ACC + (pz & 1) * NP, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
+    if constexpr (!M::CARRY)   // plane pz now has both of its patches of this column
+      flush_plane<N1>(x, ACC + (pz & 1) * NP, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
   }
   if (!failed) {
-    __syncthreads();
-    flush_plane<N1>(x, ACC + ((nc2 - 1) & 1) * NP, px, py, nc2 - 1, nc0, nc1, cls, x_is_zero, tid);
+    if constexpr (M::CARRY) {   // the last plane has only the last patch's contribution
+#pragma unroll
+      for (int sx = 0; sx < 2; ++sx) {
+        float* dst = x + line_off[sx] + (int64_t)(nc2 - 1) * plane_stride;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float4 o = make_float4(carry[8 * sx + 4 * q], carry[8 * sx + 4 * q + 1], carry[8 * sx + 4 * q + 2],
+                                 carry[8 * sx + 4 * q + 3]);
+          if (!store_cell[sx]) {
+            const float4 old = *reinterpret_cast<const float4*>(dst + 4 * q);
+            o.x += old.x;
+            o.y += old.y;
+            o.z += old.z;
+            o.w += old.w;
+          }
+          *reinterpret_cast<float4*>(dst + 4 * q) = o;
+        }
+      }
+    } else {
+      __syncthreads();
+      flush_plane<N1>(x, ACC + ((nc2 - 1) & 1) * NP, px, py, nc2 - 1, nc0, nc1, cls, x_is_zero, tid);
+    }
   } else if (tid == 0) {
     *fail_flag = 1;
     __threadfence_system();
@@ -300,15 +414,19 @@ static tpss_status launch(tpss_patches* P, float omega, int nrhs, const float* r
   }
   const Level& L = P->ctx->levels[P->level];
   const int nc0 = L.nc[0], nc1 = L.nc[1], nc2 = L.nc[2];
+  const __nv_bfloat16* bop = reinterpret_cast<const __nv_bfloat16*>(P->d_bop);
+  const __nv_bfloat16* B0 = bop;
+  const __nv_bfloat16* B1 = B0 + (size_t)P->npos[0] * 512;
+  const __nv_bfloat16* B2 = B1 + (size_t)P->npos[1] * 512;
   for (int cls = 0; cls < 4; ++cls) {
     const int ax = cls & 1, ay = cls >> 1;
     const int ncolx = ax <= nc0 - 2 ? (nc0 - 2 - ax) / 2 + 1 : 0;
     const int ncoly = ay <= nc1 - 2 ? (nc1 - 2 - ay) / 2 + 1 : 0;
     if (ncolx == 0 || ncoly == 0) continue;
     dim3 grid((unsigned)(ncolx * ncoly), (unsigned)nrhs);
-    patch_stream_tc05_kernel<N><<<grid, kThreads, smem, s>>>(
-        P->d_Z32[0], P->d_Z32[1], P->d_Z32[2], P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r, x, omega, nc0, nc1,
-        nc2, L.ndofs, cls, ncolx, x_is_zero, P->d_fail_flag);
+    patch_stream_tc05_kernel<N><<<grid, kThreads, smem, s>>>(B0, B1, B2, P->d_lam32[0], P->d_lam32[1],
+                                                              P->d_lam32[2], r, x, omega, nc0, nc1, nc2, L.ndofs,
+                                                              cls, ncolx, x_is_zero, P->d_fail_flag);
     TPSS_CHECK_LAUNCH();
   }
   return TPSS_OK;
@@ -316,26 +434,41 @@ static tpss_status launch(tpss_patches* P, float omega, int nrhs, const float* r
 
 }  // namespace tcs
 
+// Per-position B operands of the tcgen05 smoother (BF16, [t][position][Z^T /
+// Z][16 x 16 K-major]) and its failure flag; for BF16 3D vertex patch sets
+// with n <= 16, built once at setup.
+tpss_status tc05_prepare(tpss_patches* P) {
+  if (P->ctx->dim != 3 || P->kind != TPSS_VERTEX_PATCH || P->per_sub || P->n > 16) return TPSS_OK;
+  const size_t per = 2 * 256;   // BF16 elements per position
+  const size_t total = per * (P->npos[0] + P->npos[1] + P->npos[2]);
+  TPSS_TRY(dalloc(&P->d_bop, total * sizeof(__nv_bfloat16)));
+  __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P->d_bop);
+  for (int t = 0; t < 3; ++t) {
+    tcs::prepare_bop_kernel<<<dim3((unsigned)P->npos[t], 2), 256, 0, P->ctx->stream>>>(P->d_Z32[t], P->npos[t], P->n,
+                                                                                        out);
+    TPSS_CHECK_LAUNCH();
+    out += per * P->npos[t];
+  }
+  void* h = nullptr;
+  TPSS_CHECK_CUDA(cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped));
+  P->h_fail_flag = static_cast<int*>(h);
+  *P->h_fail_flag = 0;
+  void* d = nullptr;
+  TPSS_CHECK_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+  P->d_fail_flag = static_cast<int*>(d);
+  return TPSS_OK;
+}
+
 // The additive pass of the tcgen05 column-streaming schedule (all four
 // parity classes); TPSS_EINVAL without launching for shapes it does not
 // cover (the same as the COLUMNS schedule); TPSS_ETIMEOUT if a previous
 // launch on this patch set gave up waiting for its MMAs.
 tpss_status patch_pass_bf16_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
                                  cudaStream_t s) {
-  if (P->ctx->dim != 3 || P->kind != TPSS_VERTEX_PATCH || P->per_sub) return TPSS_EINVAL;
+  if (P->ctx->dim != 3 || P->kind != TPSS_VERTEX_PATCH || P->per_sub || P->d_bop == nullptr) return TPSS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x)) & 15) return TPSS_EINVAL;
   const Level& L = P->ctx->levels[P->level];
   if (L.nc[0] < 2 || L.nc[1] < 2 || L.nc[2] < 2 || nrhs > 65535 || P->n > 16) return TPSS_EINVAL;
-  if (P->h_fail_flag == nullptr) {
-    // a host-visible word the kernel sets if it gives up waiting (read without a device synchronization)
-    void* h = nullptr;
-    TPSS_CHECK_CUDA(cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped));
-    P->h_fail_flag = static_cast<int*>(h);
-    *P->h_fail_flag = 0;
-    void* d = nullptr;
-    TPSS_CHECK_CUDA(cudaHostGetDevicePointer(&d, h, 0));
-    P->d_fail_flag = static_cast<int*>(d);
-  }
   if (*reinterpret_cast<volatile int*>(P->h_fail_flag) != 0) {
     *P->h_fail_flag = 0;
     set_error("BF16 tensor-core smoother: an MMA completion wait expired in an earlier call (its result is invalid)");

@@ -217,6 +217,7 @@ struct tpss_patches {
   int* d_plane_list = nullptr;
   std::vector<int> plane_offsets;
   int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule (BF16 3D vertex: COLUMNS)
+  void* d_bop = nullptr;           // tcgen05 smoother: BF16 B operands per direction and position
   int* h_fail_flag = nullptr;      // tcgen05 smoother: host-mapped word set when an MMA wait expires
   int* d_fail_flag = nullptr;      // its device address
   // per multiplicative color: cells outside the color with a face to it,
@@ -277,6 +278,8 @@ tpss_status patch_pass_bf16_stream(tpss_patches* P, float omega, int nrhs, const
 // if an earlier launch on P gave up waiting for its MMAs)
 tpss_status patch_pass_bf16_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
                                  cudaStream_t s);
+// its per-position operands and failure flag, built at setup (BF16 3D vertex patches)
+tpss_status tc05_prepare(tpss_patches* P);
 
 // ---- smoother_large.cu (3D FP64 vertex patches with n > 16, per-CTA scratch slabs)
 tpss_status patch_large_ctas(int n, int num_sms, int* max_ctas);
