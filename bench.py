@@ -505,8 +505,9 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
     hbm = peaks.get("hbm_gbs", 6800.0)
     nr = len(SEEDS)
     out = {"dtype": prec, "accumulate": "fp32", "per_degree": {}}
-    out["schedule"] = ("column streaming (default; 4 launches, r read and x written once per parity class); "
-                       "colored, plane-by-plane and single-launch atomic schedules timed beside it" if prec == "bf16"
+    out["schedule"] = ("default: tcgen05 column streaming for k >= 4 (4 launches, r read and x written once per "
+                       "parity class), colored launches for k <= 3; colored, plane-by-plane, atomic and both column "
+                       "schedules timed beside it" if prec == "bf16"
                        else "colored launches (default); plane-by-plane schedule timed beside it")
     total_ms = 0.0
     for k in ks:

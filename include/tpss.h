@@ -197,8 +197,8 @@ tpss_status tpss_patches_set_large_cluster(tpss_patches* patches, int ctas);
 
 /* Order of the subdomain solves of the additive smoother (the result is the
  * same sum; the schedules differ in memory traffic).
- *   COLORS (default, except below): one launch per color (2^d for vertex
- *     patches), each over the whole mesh; deterministic.
+ *   COLORS (default, except TCGEN05 below): one launch per color (2^d for
+ *     vertex patches), each over the whole mesh; deterministic.
  *   PLANES (3D vertex patches): plane of patches by plane of patches, the 4
  *     colors of a plane in turn, so that the two cell planes a patch plane
  *     touches stay in L2 across its colors (r and x are read from HBM about
@@ -206,15 +206,16 @@ tpss_status tpss_patches_set_large_cluster(tpss_patches* patches, int ctas);
  *   ATOMIC (3D, BF16 contractions): one launch over all subdomains in
  *     lexicographic order, x accumulated with FP32 atomic adds; the order of
  *     the contributions to a DoF, and so the FP32 rounding, varies between runs.
- *   COLUMNS (3D vertex patches, BF16 contractions; the default there): one
+ *   COLUMNS (3D vertex patches, BF16 contractions): one
  *     CTA per column of patches (p_x, p_y) and right-hand side walks p_z,
  *     staging each cell plane of r once and accumulating each cell plane of x
  *     in FP32 in shared memory until both of its patches in the column are
  *     done; the 4 parity classes of (p_x, p_y) share no cell and are 4
  *     launches; deterministic; x is written without being cleared first.
- *   TCGEN05 (same patch sets): the COLUMNS schedule with the six mode
- *     contractions of each local solve as tcgen05 MMAs (BF16 operands in
- *     shared memory, FP32 accumulators in tensor memory).  Its waits for MMA
+ *   TCGEN05 (same patch sets; the default there for k >= 4): the COLUMNS
+ *     schedule with the six mode contractions of each local solve as tcgen05
+ *     MMAs (BF16 operands in shared memory, FP32 accumulators in tensor
+ *     memory); deterministic.  Its waits for MMA
  *     completion are bounded (about a second); if one expires the kernel
  *     stops, frees its tensor memory, and the next additive smoother call on
  *     the patch set returns TPSS_ETIMEOUT (the earlier result is invalid).

@@ -677,9 +677,10 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
   P->level = level;
   P->kind = kind;
   P->precision = precision;
-  // BF16 3D vertex patches stream columns of patches by default
-  if (precision == TPSS_BF16 && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped)
-    P->additive_schedule = TPSS_ADDITIVE_COLUMNS;
+  // BF16 3D vertex patches: the tcgen05 column walk by default where it is
+  // the fastest measured schedule (n >= 10, k >= 4); colored launches below
+  if (precision == TPSS_BF16 && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped && P->n >= 10)
+    P->additive_schedule = TPSS_ADDITIVE_TCGEN05;
   P->n = kind == TPSS_VERTEX_PATCH ? 2 * n1 : n1;
   const int n = P->n;
   P->nsub = 1;

@@ -166,7 +166,7 @@ __device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, i
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 5)
 patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat16* __restrict__ B1,
                          const __nv_bfloat16* __restrict__ B2, const float* __restrict__ L0,
                          const float* __restrict__ L1, const float* __restrict__ L2, const float* __restrict__ r,
@@ -232,12 +232,23 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
     }
   }
   const int64_t plane_stride = (int64_t)nc0 * nc1 * NLOC1;
+  // k = 7 plane staging: thread t copies 16 bytes at float 4 t of each of the 4 cells
+  int64_t stage_off[4];
+#pragma unroll
+  for (int c2 = 0; c2 < 4; ++c2) stage_off[c2] = ((px + (c2 & 1)) + (int64_t)nc0 * (py + (c2 >> 1))) * NLOC1 + 4 * tid;
 
   for (int pz = 0; pz + 1 < nc2 && !failed; ++pz) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();   // planes pz, pz + 1 and patch pz's z operands staged; patch pz - 1 is done
     if (pz + 2 < nc2) {
-      stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
+      if constexpr (NLOC1 == 4 * kThreads) {
+        const uint32_t d = tc05::smem_u32(SB + ((pz + 2) % 3) * NP) + 16u * tid;
+        const float* src = r + (int64_t)(pz + 2) * plane_stride;
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2) cp16(d + 4u * NLOC1 * c2, src + stage_off[c2]);
+      } else {
+        stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
+      }
       stage_b2(opb + (4 + 2 * ((pz + 1) & 1)) * 512, B2 + (size_t)(pz + 1) * 512, tid);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
@@ -292,7 +303,8 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
     __syncthreads();
     tc05::fence_after_sync();
 
-    for (int s = 1; s <= 6; ++s) {
+#pragma unroll
+    for (int s = 1; s <= 6; ++s) {   // unrolled: every stage's index rotation is resolved at compile time
       if (tid == 0) {
         const uint32_t idesc = tc05::idesc_bf16(128, 16, a_major(s), 0);
         const uint64_t bdesc = tc05::desc(b_base + 512 * b_slot(s, pz & 1), 256, 128);

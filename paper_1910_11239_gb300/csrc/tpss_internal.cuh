@@ -216,7 +216,7 @@ struct tpss_patches {
   // present in plane p_z
   int* d_plane_list = nullptr;
   std::vector<int> plane_offsets;
-  int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule (BF16 3D vertex: COLUMNS)
+  int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule (BF16 3D vertex, k >= 4: TCGEN05)
   void* d_bop = nullptr;           // tcgen05 smoother: BF16 B operands per direction and position
   int* h_fail_flag = nullptr;      // tcgen05 smoother: host-mapped word set when an MMA wait expires
   int* d_fail_flag = nullptr;      // its device address
