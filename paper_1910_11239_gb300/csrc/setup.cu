@@ -677,12 +677,12 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
   P->level = level;
   P->kind = kind;
   P->precision = precision;
-  // BF16 3D vertex patches: the tcgen05 column walk by default where it is
-  // the fastest measured schedule (n >= 10, k >= 4); colored launches below
-  if (precision == TPSS_BF16 && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped && P->n >= 10)
-    P->additive_schedule = TPSS_ADDITIVE_TCGEN05;
   P->n = kind == TPSS_VERTEX_PATCH ? 2 * n1 : n1;
   const int n = P->n;
+  // BF16 3D vertex patches: the tcgen05 column walk by default where it is
+  // the fastest measured schedule (n >= 10, k >= 4); colored launches below
+  if (precision == TPSS_BF16 && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped && n >= 10)
+    P->additive_schedule = TPSS_ADDITIVE_TCGEN05;
   P->nsub = 1;
   for (int t = 0; t < d; ++t) {
     P->npos[t] = kind == TPSS_VERTEX_PATCH ? L.nc[t] - 1 : L.nc[t];
