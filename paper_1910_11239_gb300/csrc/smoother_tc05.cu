@@ -184,7 +184,7 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
   float* ACC = reinterpret_cast<float*>(dsm + M::ACC);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
-  __shared__ float lam[48];
+  __shared__ __align__(16) float lam[64];   // x, y (columns), z of patch p_z in slot 32 + 16 (p_z & 1)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int px = (cls & 1) + 2 * (int)(blockIdx.x % ncolx);
   const int py = (cls >> 1) + 2 * (int)(blockIdx.x / ncolx);
@@ -198,12 +198,16 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
   stage_b2(opb + 0 * 512, B0 + (size_t)px * 512, tid);   // slots 0, 1
   stage_b2(opb + 2 * 512, B1 + (size_t)py * 512, tid);   // slots 2, 3
   stage_b2(opb + 4 * 512, B2, tid);                      // patch 0: slots 4, 5
+  if (tid < N)                                           // patch 0's z eigenvalues
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(tc05::smem_u32(lam + 32 + tid)),
+                 "l"(L2 + tid) : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
   for (int e = tid; e < kOpABytes / 16; e += kThreads) reinterpret_cast<uint4*>(opa)[e] = make_uint4(0, 0, 0, 0);
   if constexpr (!M::CARRY)
     for (int e = tid; e < 2 * NP; e += kThreads) ACC[e] = 0.f;
   if (tid < 32) lam[tid] = (tid < 16) ? (tid < N ? L0[(size_t)px * N + tid] : 0.f)
                                       : (tid - 16 < N ? L1[(size_t)py * N + tid - 16] : 0.f);
+  // (z slots: entries >= N are never read)
   if (tid == 0) tc05::mbar_init(mb, 1);
   if (warp == 0) tc05::alloc(tc05::smem_u32(&tslot), 32);
   tc05::fence_before_sync();
@@ -250,9 +254,13 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
         stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
       }
       stage_b2(opb + (4 + 2 * ((pz + 1) & 1)) * 512, B2 + (size_t)(pz + 1) * 512, tid);
+      if (tid < N)   // the next patch's z eigenvalues
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                     :: "r"(tc05::smem_u32(lam + 32 + 16 * ((pz + 1) & 1) + tid)), "l"(L2 + (size_t)(pz + 1) * N + tid)
+                     : "memory");
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    if (tid < 16) lam[32 + tid] = tid < N ? L2[(size_t)pz * N + tid] : 0.f;
+    const float* lamz = lam + 32 + 16 * (pz & 1);
     // previous values of this thread's line of plane pz (read-modify-write classes)
     float xold[16];
     if constexpr (M::CARRY) {
@@ -356,7 +364,7 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
             const float sab = lam[sl] + lam[16 + fa];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              w[j] = (sl < N && fa < N && j < N) ? __fdividef(w[j], sab + lam[32 + j]) : 0.f;
+              w[j] = (sl < N && fa < N && j < N) ? __fdividef(w[j], sab + lamz[j]) : 0.f;
             tc05::st_row8(opa + off_k(m), w);
             tc05::st_row8(opa + off_k(m) + kKStride, w + 8);
           } else if constexpr (!M::CARRY) {   // D6[(z,y)][x]: omega * line -> plane accumulators
