@@ -393,7 +393,7 @@ def main():
                 "frac": dom["frac_fp64_peak"],
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe; HBM is not binding)",
                 "per": "one smoother call = 8 color launches on 8 RHS",
-                "traffic": TRAFFIC_K7_PER_CALL if kdom == 7 else None,
+                "traffic": TRAFFIC_K7_PER_CALL if (kdom == 7 and NC == 32) else None,
                 "traffic_unit": "bytes per call (dram read + write, ncu)",
                 "algorithmic_bytes": perf.smoother_bytes((NC, NC, NC), kdom, nrhs=nr)}
 
