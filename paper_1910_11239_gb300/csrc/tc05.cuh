@@ -57,17 +57,21 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// One try: the thread may be suspended (up to about 0.1 ms) until the phase
+// completes, so a waiting warp takes few issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done) : "r"(mbar), "r"(parity), "r"(100000u) : "memory");
   return done != 0;
 }
 
 // Wait for the given phase parity with a bound of `limit` clock cycles;
 // false if the bound ran out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long limit) {
+  if (mbar_try_wait(mbar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(mbar, parity)) {
     if (clock64() - t0 > limit) return false;
