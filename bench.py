@@ -535,7 +535,11 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
         for name, sch in (("colors", tpss.ADDITIVE_COLORS), ("planes", tpss.ADDITIVE_PLANES),
                           ("atomic", tpss.ADDITIVE_ATOMIC), ("columns_mma_sync", tpss.ADDITIVE_COLUMNS),
                           ("columns_tcgen05", tpss.ADDITIVE_TCGEN05)):
-            if sch != tpss.ADDITIVE_PLANES and prec != "bf16":
+            allowed = {"bf16": (tpss.ADDITIVE_COLORS, tpss.ADDITIVE_PLANES, tpss.ADDITIVE_ATOMIC,
+                                tpss.ADDITIVE_COLUMNS, tpss.ADDITIVE_TCGEN05),
+                       "tf32": (tpss.ADDITIVE_COLORS, tpss.ADDITIVE_PLANES, tpss.ADDITIVE_TCGEN05)}.get(
+                           prec, (tpss.ADDITIVE_PLANES,))
+            if sch not in allowed:
                 continue
             P.set_additive_schedule(sch)
             P.smooth_additive(OMEGA, b, x, x_is_zero=True, nrhs=nr)
