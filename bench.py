@@ -508,6 +508,8 @@ def run_low_precision_smoother(prec, ks, widths, steps, tpss, workloads, perf, t
     out["schedule"] = ("default: tcgen05 column streaming for k >= 4 (4 launches, r read and x written once per "
                        "parity class), colored launches for k <= 3; colored, plane-by-plane, atomic and both column "
                        "schedules timed beside it" if prec == "bf16"
+                       else "default: tcgen05 column streaming (TF32 operands) for k >= 4, colored launches for "
+                       "k <= 3; colored, plane-by-plane and tcgen05 schedules timed beside it" if prec == "tf32"
                        else "colored launches (default); plane-by-plane schedule timed beside it")
     total_ms = 0.0
     for k in ks:

@@ -212,10 +212,11 @@ tpss_status tpss_patches_set_large_cluster(tpss_patches* patches, int ctas);
  *     in FP32 in shared memory until both of its patches in the column are
  *     done; the 4 parity classes of (p_x, p_y) share no cell and are 4
  *     launches; deterministic; x is written without being cleared first.
- *   TCGEN05 (same patch sets; the default there for k >= 4): the COLUMNS
- *     schedule with the six mode contractions of each local solve as tcgen05
- *     MMAs (BF16 operands in shared memory, FP32 accumulators in tensor
- *     memory); deterministic.  Its waits for MMA
+ *   TCGEN05 (3D vertex patches, k <= 7, BF16 or TF32 contractions; the
+ *     default there for k >= 4): the COLUMNS schedule with the six mode
+ *     contractions of each local solve as tcgen05 MMAs (BF16 or TF32
+ *     operands in shared memory, FP32 accumulators in tensor memory);
+ *     deterministic.  Its waits for MMA
  *     completion are bounded (about a second); if one expires the kernel
  *     stops, frees its tensor memory, and the next additive smoother call on
  *     the patch set returns TPSS_ETIMEOUT (the earlier result is invalid).
@@ -228,6 +229,15 @@ typedef enum {
   TPSS_ADDITIVE_TCGEN05 = 4
 } tpss_additive_schedule;
 tpss_status tpss_patches_set_additive_schedule(tpss_patches* patches, int schedule);
+
+/* Test hook for the failure path of the TCGEN05 schedule (not in the paper):
+ * in the next additive smoother call on this patch set, every CTA waits
+ * once for an mbarrier phase that no MMA completes, with a short bound
+ * (about 1 ms), gives up, frees its tensor memory and sets the failure
+ * flag; that call's x is invalid and the call after it returns
+ * TPSS_ETIMEOUT (and clears the flag).  No GPU fault is involved: the MMAs
+ * themselves complete normally.  TPSS_EINVAL for other patch sets. */
+tpss_status tpss_patches_test_wait_expiry(tpss_patches* patches);
 
 /* ------------------------------------------------------------- smoothers --
  * Additive Schwarz smoother, Alg. 2 with the damping of eq. additiveschwarz:

@@ -679,9 +679,10 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
   P->precision = precision;
   P->n = kind == TPSS_VERTEX_PATCH ? 2 * n1 : n1;
   const int n = P->n;
-  // BF16 3D vertex patches: the tcgen05 column walk by default where it is
-  // the fastest measured schedule (n >= 10, k >= 4); colored launches below
-  if (precision == TPSS_BF16 && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped && n >= 10)
+  // BF16 / TF32 3D vertex patches: the tcgen05 column walk by default where
+  // it is the fastest measured schedule (n >= 10, k >= 4); colored launches below
+  if ((precision == TPSS_BF16 || precision == TPSS_TF32) && d == 3 && kind == TPSS_VERTEX_PATCH && !ctx->mapped &&
+      n >= 10)
     P->additive_schedule = TPSS_ADDITIVE_TCGEN05;
   P->nsub = 1;
   for (int t = 0; t < d; ++t) {
@@ -741,7 +742,8 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
     }
   }
   // operands of the tcgen05 smoother (every direction's FP32 eigenvectors are converted by now)
-  if (!ctx->mapped && precision == TPSS_BF16 && (st = tc05_prepare(P)) != TPSS_OK) return fail(st);
+  if (!ctx->mapped && (precision == TPSS_BF16 || precision == TPSS_TF32) && (st = tc05_prepare(P)) != TPSS_OK)
+    return fail(st);
   const bool large = d == 3 && n > kMaxSharedPatchN;
   if (ctx->mapped) {
     // inverse table already built per cell
@@ -905,6 +907,15 @@ extern "C" tpss_status tpss_patches_set_large_cluster(tpss_patches* P, int ctas)
   TPSS_REQUIRE(ctas == 0 || ctas == 1 || ctas == 2 || ctas == 4 || ctas == 8,
                "tpss_patches_set_large_cluster: ctas must be 0 (automatic), 1, 2, 4 or 8");
   P->large_cluster = ctas;
+  return TPSS_OK;
+}
+
+extern "C" tpss_status tpss_patches_test_wait_expiry(tpss_patches* P) {
+  clear_error();
+  TPSS_REQUIRE(P, "tpss_patches_test_wait_expiry: null patches");
+  TPSS_REQUIRE(P->d_bop != nullptr,
+               "tpss_patches_test_wait_expiry: not a tcgen05 patch set (BF16 or TF32 3D vertex patches)");
+  P->expire_test = 1;
   return TPSS_OK;
 }
 

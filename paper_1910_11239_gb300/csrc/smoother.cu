@@ -326,9 +326,10 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
     return TPSS_OK;
   }
   if constexpr (sizeof(T) == 4) {
-    // BF16 3D vertex patches, column-streaming schedule: writes x itself
-    if (P->precision == TPSS_BF16 && (P->additive_schedule == TPSS_ADDITIVE_COLUMNS ||
-                                      P->additive_schedule == TPSS_ADDITIVE_TCGEN05)) {
+    // BF16 / TF32 3D vertex patches, column-streaming schedule: writes x itself
+    if ((P->precision == TPSS_BF16 && (P->additive_schedule == TPSS_ADDITIVE_COLUMNS ||
+                                       P->additive_schedule == TPSS_ADDITIVE_TCGEN05)) ||
+        (P->precision == TPSS_TF32 && P->additive_schedule == TPSS_ADDITIVE_TCGEN05)) {
       if (!x_is_zero) {
         TPSS_TRY(ensure_level_scratch(ctx, P->level, nrhs));
         T* rb = residual_buffer<T>(L);
@@ -339,8 +340,9 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
       float* xf = reinterpret_cast<float*>(x);
       tpss_status st = TPSS_EINVAL;
       if (P->additive_schedule == TPSS_ADDITIVE_TCGEN05)
-        st = patch_pass_bf16_tc05(P, (float)omega, nrhs, rf, xf, x_is_zero, s);
-      if (st == TPSS_EINVAL) st = patch_pass_bf16_stream(P, (float)omega, nrhs, rf, xf, x_is_zero, s);
+        st = patch_pass_tc05(P, (float)omega, nrhs, rf, xf, x_is_zero, s);
+      if (st == TPSS_EINVAL && P->precision == TPSS_BF16)
+        st = patch_pass_bf16_stream(P, (float)omega, nrhs, rf, xf, x_is_zero, s);
       if (st != TPSS_EINVAL) return st;   // else: shape or alignment not covered, colored launches
       if (!x_is_zero) {                   // r already holds the residual
         const int nc = (int)P->add_offsets.size() - 1;

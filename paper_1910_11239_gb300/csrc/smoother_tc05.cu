@@ -1,6 +1,6 @@
-// Column-streaming BF16 additive vertex-patch smoother on the 5th-generation
-// tensor cores (tcgen05 MMA, accumulators in tensor memory); 3D, mixed
-// precision (not in the paper).
+// Column-streaming BF16 / TF32 additive vertex-patch smoother on the
+// 5th-generation tensor cores (tcgen05 MMA, accumulators in tensor memory);
+// 3D, mixed precision (not in the paper).
 //
 // Schedule: as the COLUMNS schedule (smoother_stream.cu): one CTA per column
 // of vertex patches (p_x, p_y) and right-hand side walks p_z, r staged one
@@ -30,6 +30,11 @@
 // The core matrices of A sit 144 bytes apart along M (not 128) so that these
 // writes are free of shared-memory bank conflicts.
 //
+// TF32 (kind::tf32, K = 8 per MMA): the same walk with FP32 operands rounded
+// to TF32, two MMAs per 16-wide contraction and every operand K-major (a
+// core matrix row holds 4 values); the rotated stages write their values to
+// the next A one by one instead of as MN-major rows.
+//
 // Output: with k = 7 (16 points per direction) a thread's two rows of D6 are
 // the same (y, z) line of the patch's lower and upper cell plane; the upper
 // one is kept in registers until the next patch of the column adds the lower
@@ -50,8 +55,15 @@ namespace tcs {
 constexpr int kThreads = 128;
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 constexpr int kMStride = 144;                     // bytes between core matrices along M
-constexpr int kKStride = 32 * kMStride;           // bytes between the two K halves (256 rows)
-constexpr int kOpABytes = 2 * kKStride;
+constexpr int kKStride = 32 * kMStride;           // bytes between core matrices along K (256 rows)
+
+// per element type: A bytes (2 or 4 core-matrix columns of 8 or 4 values),
+// one 16 x 16 B operand, the B operands of one position (Z^T and Z)
+template <bool TF> struct Op {
+  static constexpr int ABYTES = (TF ? 4 : 2) * kKStride;
+  static constexpr int BBYTES = TF ? 1024 : 512;
+  static constexpr int BPOS = 2 * BBYTES;
+};
 
 // byte offset of row m of a K-major A (K half 0; + kKStride for K half 1)
 __device__ __forceinline__ int off_k(int m) { return (m & 7) * 16 + (m >> 3) * kMStride; }
@@ -61,15 +73,15 @@ __device__ __forceinline__ int off_mn(int slow, int k) {
   return (k & 7) * 16 + slow * 2 * kMStride + (k >> 3) * kKStride;
 }
 
-template <int N>
+template <int N, bool TF>
 struct Smem {
   static constexpr int N1 = N / 2;
   static constexpr int NLOC1 = N1 * N1 * N1;
   static constexpr int NP = 4 * NLOC1;                       // floats of one column plane (4 cells)
   static constexpr bool CARRY = (N == 16);                   // finished lines kept in registers
   static constexpr size_t OPA = 0;
-  static constexpr size_t OPB = kOpABytes;                   // 8 x 512 bytes: operands B
-  static constexpr size_t SB = OPB + 8 * 512;                // 3 staged planes of r (FP32)
+  static constexpr size_t OPB = Op<TF>::ABYTES;              // 8 operands B
+  static constexpr size_t SB = OPB + 8 * Op<TF>::BBYTES;     // 3 staged planes of r (FP32)
   static constexpr size_t ACC = SB + 3 * (size_t)NP * 4;     // 2 plane accumulators (FP32) unless CARRY
   static constexpr size_t BYTES = ACC + (CARRY ? 0 : 2 * (size_t)NP * 4);
 };
@@ -79,7 +91,7 @@ struct Smem {
 __device__ __forceinline__ int b_slot(int s, int q) {
   return s == 1 ? 0 : s == 2 ? 2 : s == 3 ? 4 + 2 * q : s == 4 ? 5 + 2 * q : s == 5 ? 3 : 1;
 }
-// A layout of the MMA of stage s (0 K-major, 1 MN-major)
+// A layout of the BF16 MMA of stage s (0 K-major, 1 MN-major)
 __device__ __forceinline__ int a_major(int s) { return (s == 1 || s == 4) ? 0 : 1; }
 
 // Global B operands: [t][position][apply Z^T (0) / Z (1)][512 bytes], the
@@ -94,6 +106,21 @@ __global__ void prepare_bop_kernel(const float* __restrict__ Z, int npos, int n,
     float v = 0.f;
     if (nn < n && k < n) v = back ? Zp[nn * n + k] : Zp[k * n + nn];
     o[((nn & 7) * 16 + (nn >> 3) * 128 + (k >> 3) * 256 + (k & 7) * 2) / 2] = __float2bfloat16(v);
+  }
+}
+
+// The same for TF32: [t][position][Z^T / Z][1024 bytes], 16 x 16 K-major with
+// core matrices of 8 rows x 4 values, rounded to TF32.
+__global__ void prepare_bop_tf32_kernel(const float* __restrict__ Z, int npos, int n, float* __restrict__ out) {
+  const int p = blockIdx.x, back = blockIdx.y;
+  if (p >= npos) return;
+  const float* Zp = Z + (size_t)p * n * n;
+  float* o = out + ((size_t)p * 2 + back) * 256;
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    const int nn = e >> 4, k = e & 15;
+    float v = 0.f;
+    if (nn < n && k < n) v = back ? Zp[nn * n + k] : Zp[k * n + nn];
+    o[((nn & 7) * 16 + (nn >> 3) * 128 + (k >> 2) * 256 + (k & 3) * 4) / 4] = __uint_as_float(tc05::to_tf32(v));
   }
 }
 
@@ -123,9 +150,36 @@ __device__ __forceinline__ void stage_plane(float* dst, const float* __restrict_
   }
 }
 
-// 1 KB of B operands (two matrices) -> shared memory
-__device__ __forceinline__ void stage_b2(unsigned char* dst, const __nv_bfloat16* src, int tid) {
-  if (tid < 64) cp16(tc05::smem_u32(dst) + 16u * tid, reinterpret_cast<const unsigned char*>(src) + 16 * tid);
+// the B operands of one position (two matrices) -> shared memory
+template <bool TF>
+__device__ __forceinline__ void stage_b2(unsigned char* dst, const unsigned char* src, int tid) {
+  if (tid < Op<TF>::BPOS / 16) cp16(tc05::smem_u32(dst) + 16u * tid, src + 16 * tid);
+}
+
+// row m (16 values along K) of a K-major A
+template <bool TF>
+__device__ __forceinline__ void put_row_k(unsigned char* opa, int m, const float* v) {
+  if constexpr (TF) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tc05::st_row4_tf32(opa + off_k(m) + c * kKStride, v + 4 * c);
+  } else {
+    tc05::st_row8(opa + off_k(m), v);
+    tc05::st_row8(opa + off_k(m) + kKStride, v + 8);
+  }
+}
+// rows 16 slow + j (j = 0..15) at column k of A: MN-major rows (BF16) or
+// one value per row of the K-major TF32 operand
+template <bool TF>
+__device__ __forceinline__ void put_col(unsigned char* opa, int slow, int k, const float* v) {
+  if constexpr (TF) {
+    unsigned char* base = opa + (k & 3) * 4 + (k >> 2) * kKStride;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      *reinterpret_cast<uint32_t*>(base + off_k(16 * slow + j)) = tc05::to_tf32(v[j]);
+  } else {
+    tc05::st_row8(opa + off_mn(slow, k), v);
+    tc05::st_row8(opa + off_mn(slow, k) + kMStride, v + 8);
+  }
 }
 
 __device__ __forceinline__ int first_class(int cx, int cy, int nc0, int nc1) {
@@ -134,12 +188,37 @@ __device__ __forceinline__ int first_class(int cx, int cy, int nc0, int nc1) {
   return xm + 2 * ym;
 }
 
+// The previous values of cell plane cz of x (read-modify-write cells only)
+// -> shared memory, with cp.async, in the element order of flush_plane (each
+// thread later reads only what it copied itself).
 template <int N1>
-__device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, int px, int py, int cz, int nc0,
-                                            int nc1, int cls, int x_is_zero, int tid) {
+__device__ __forceinline__ void prefetch_plane(float* xo, const float* __restrict__ x, int px, int py, int cz,
+                                               int nc0, int nc1, int cls, int x_is_zero, int tid) {
   constexpr int NLOC1 = N1 * N1 * N1;
   constexpr int V = (NLOC1 % 4 == 0) ? 4 : 1;
   constexpr int CH = NLOC1 / V;
+  const uint32_t d = tc05::smem_u32(xo);
+  for (int e = tid; e < 4 * CH; e += kThreads) {
+    const int c2 = e / CH, o = (e % CH) * V;
+    const int cx = px + (c2 & 1), cy = py + (c2 >> 1);
+    if (x_is_zero && first_class(cx, cy, nc0, nc1) == cls) continue;
+    const float* src = x + (cx + (int64_t)nc0 * (cy + (int64_t)nc1 * cz)) * NLOC1 + o;
+    if constexpr (V == 4)
+      cp16(d + 4u * (c2 * NLOC1 + o), src);
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(d + 4u * (c2 * NLOC1 + o)), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// x (plane cz) = acc, or xo + acc for the read-modify-write cells; acc is cleared
+template <int N1>
+__device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, const float* xo, int px, int py,
+                                            int cz, int nc0, int nc1, int cls, int x_is_zero, int tid) {
+  constexpr int NLOC1 = N1 * N1 * N1;
+  constexpr int V = (NLOC1 % 4 == 0) ? 4 : 1;
+  constexpr int CH = NLOC1 / V;
+  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's prefetched values
   for (int e = tid; e < 4 * CH; e += kThreads) {
     const int c2 = e / CH, o = (e % CH) * V;
     const int cx = px + (c2 & 1), cy = py + (c2 >> 1);
@@ -149,7 +228,7 @@ __device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, i
     if constexpr (V == 4) {
       float4 v = *reinterpret_cast<float4*>(a);
       if (!store) {
-        const float4 old = *reinterpret_cast<const float4*>(dst);
+        const float4 old = *reinterpret_cast<const float4*>(xo + c2 * NLOC1 + o);
         v.x += old.x;
         v.y += old.y;
         v.z += old.z;
@@ -159,20 +238,21 @@ __device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, i
       *reinterpret_cast<float4*>(a) = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
       const float v = *a;
-      *dst = store ? v : v + *dst;
+      *dst = store ? v : v + xo[c2 * NLOC1 + o];
       *a = 0.f;
     }
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 5)
-patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat16* __restrict__ B1,
-                         const __nv_bfloat16* __restrict__ B2, const float* __restrict__ L0,
+template <int N, bool TF>
+__global__ void __launch_bounds__(kThreads, TF ? 4 : 5)   // TF32 at k = 7: 51 KB of shared memory, 4 CTAs
+patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned char* __restrict__ B1,
+                         const unsigned char* __restrict__ B2, const float* __restrict__ L0,
                          const float* __restrict__ L1, const float* __restrict__ L2, const float* __restrict__ r,
                          float* __restrict__ x, float omega, int nc0, int nc1, int nc2, int64_t ndofs, int cls,
-                         int ncolx, int x_is_zero, volatile int* fail_flag) {
-  using M = Smem<N>;
+                         int ncolx, int x_is_zero, volatile int* fail_flag, int expire_test) {
+  using M = Smem<N, TF>;
+  constexpr int BB = Op<TF>::BBYTES, BP = Op<TF>::BPOS;
   constexpr int N1 = N / 2;
   constexpr int NLOC1 = M::NLOC1;
   constexpr int NP = M::NP;
@@ -195,14 +275,14 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
   // prologue: planes 0 and 1, the column's x and y operands, patch 0's z operands
   stage_plane<NLOC1>(SB, r, px, py, 0, nc0, nc1, tid);
   stage_plane<NLOC1>(SB + NP, r, px, py, 1, nc0, nc1, tid);
-  stage_b2(opb + 0 * 512, B0 + (size_t)px * 512, tid);   // slots 0, 1
-  stage_b2(opb + 2 * 512, B1 + (size_t)py * 512, tid);   // slots 2, 3
-  stage_b2(opb + 4 * 512, B2, tid);                      // patch 0: slots 4, 5
+  stage_b2<TF>(opb + 0 * BB, B0 + (size_t)px * BP, tid);   // slots 0, 1
+  stage_b2<TF>(opb + 2 * BB, B1 + (size_t)py * BP, tid);   // slots 2, 3
+  stage_b2<TF>(opb + 4 * BB, B2, tid);                     // patch 0: slots 4, 5
   if (tid < N)                                           // patch 0's z eigenvalues
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(tc05::smem_u32(lam + 32 + tid)),
                  "l"(L2 + tid) : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int e = tid; e < kOpABytes / 16; e += kThreads) reinterpret_cast<uint4*>(opa)[e] = make_uint4(0, 0, 0, 0);
+  for (int e = tid; e < Op<TF>::ABYTES / 16; e += kThreads) reinterpret_cast<uint4*>(opa)[e] = make_uint4(0, 0, 0, 0);
   if constexpr (!M::CARRY)
     for (int e = tid; e < 2 * NP; e += kThreads) ACC[e] = 0.f;
   if (tid < 32) lam[tid] = (tid < 16) ? (tid < N ? L0[(size_t)px * N + tid] : 0.f)
@@ -253,7 +333,7 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
       } else {
         stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
       }
-      stage_b2(opb + (4 + 2 * ((pz + 1) & 1)) * 512, B2 + (size_t)(pz + 1) * 512, tid);
+      stage_b2<TF>(opb + (4 + 2 * ((pz + 1) & 1)) * BB, B2 + (size_t)(pz + 1) * BP, tid);
       if (tid < N)   // the next patch's z eigenvalues
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
                      :: "r"(tc05::smem_u32(lam + 32 + 16 * ((pz + 1) & 1) + tid)), "l"(L2 + (size_t)(pz + 1) * N + tid)
@@ -303,25 +383,45 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
           for (int j = 0; j < N; ++j) v[j] = src[(j / N1) * NLOC1 + (j % N1)];
         }
       }
-      tc05::st_row8(opa + off_k(m), v);
-      tc05::st_row8(opa + off_k(m) + kKStride, v + 8);
+      put_row_k<TF>(opa, m, v);
     }
     tc05::fence_proxy_async();
     tc05::fence_before_sync();
     __syncthreads();
     tc05::fence_after_sync();
+    if constexpr (!M::CARRY) {   // r of plane pz (and of the last plane) is consumed: its slots take x
+      prefetch_plane<N1>(SB + (pz % 3) * NP, x, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
+      if (pz + 2 == nc2)
+        prefetch_plane<N1>(SB + ((pz + 1) % 3) * NP, x, px, py, pz + 1, nc0, nc1, cls, x_is_zero, tid);
+    }
 
 #pragma unroll
     for (int s = 1; s <= 6; ++s) {   // unrolled: every stage's index rotation is resolved at compile time
       if (tid == 0) {
-        const uint32_t idesc = tc05::idesc_bf16(128, 16, a_major(s), 0);
-        const uint64_t bdesc = tc05::desc(b_base + 512 * b_slot(s, pz & 1), 256, 128);
+        const uint32_t bslot = b_base + BB * b_slot(s, pz & 1);
+        if constexpr (TF) {   // K = 16 as two MMAs of K = 8 (core-matrix columns 2h, 2h + 1)
+          constexpr uint32_t idesc = tc05::idesc_tf32(128, 16);
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-          tc05::mma(tmem + 16 * b, tc05::desc(a_base + 16 * kMStride * b, kKStride, kMStride), bdesc, idesc, 0);
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              tc05::mma_tf32(tmem + 16 * b,
+                             tc05::desc(a_base + 16 * kMStride * b + 2 * h * kKStride, kKStride, kMStride),
+                             tc05::desc(bslot + 512 * h, 256, 128), idesc, h);
+        } else {
+          const uint32_t idesc = tc05::idesc_bf16(128, 16, a_major(s), 0);
+          const uint64_t bdesc = tc05::desc(bslot, 256, 128);
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            tc05::mma(tmem + 16 * b, tc05::desc(a_base + 16 * kMStride * b, kKStride, kMStride), bdesc, idesc, 0);
+        }
         tc05::commit(mb);
       }
-      const bool ok = tc05::mbar_wait_bounded(mb, phase, kWaitCycles);
+      bool ok = tc05::mbar_wait_bounded(mb, phase, kWaitCycles);
+      // expire_test: after the first MMA has completed, wait (with a short
+      // bound) for the next phase, which no commit completes, so that the
+      // failure path runs with no MMA in flight
+      if (expire_test && pz == 0 && s == 1) ok = ok && tc05::mbar_wait_bounded(mb, phase ^ 1, 2000000LL);
       phase ^= 1;
       tc05::fence_after_sync();
       float v[16 * NB];
@@ -351,22 +451,15 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
           const int m = tid + 128 * b, sl = m >> 4, fa = m & 15;
           float* w = v + 16 * b;
           if (s == 1 || s == 4) {          // D1[(z,y)][a] -> A1[(z,a)][y];  D4[(a,b)][z] -> A4[(a,z)][b]
-            if (NB == 2 || sl < 8) {
-              tc05::st_row8(opa + off_mn(sl, fa), w);
-              tc05::st_row8(opa + off_mn(sl, fa) + kMStride, w + 8);
-            }
+            if (NB == 2 || sl < 8) put_col<TF>(opa, sl, fa, w);
           } else if (s == 2 || s == 5) {   // D2[(z,a)][b] -> A2[(a,b)][z];  D5[(a,z)][y] -> A5[(z,y)][a]
-            if (NB == 2 || fa < 8) {
-              tc05::st_row8(opa + off_mn(fa, sl), w);
-              tc05::st_row8(opa + off_mn(fa, sl) + kMStride, w + 8);
-            }
+            if (NB == 2 || fa < 8) put_col<TF>(opa, fa, sl, w);
           } else if (s == 3) {             // D3[(a,b)][c] / (lx_a + ly_b + lz_c) -> A3[(a,b)][c]
             const float sab = lam[sl] + lam[16 + fa];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               w[j] = (sl < N && fa < N && j < N) ? __fdividef(w[j], sab + lamz[j]) : 0.f;
-            tc05::st_row8(opa + off_k(m), w);
-            tc05::st_row8(opa + off_k(m) + kKStride, w + 8);
+            put_row_k<TF>(opa, m, w);
           } else if constexpr (!M::CARRY) {   // D6[(z,y)][x]: omega * line -> plane accumulators
             if (sl < N && fa < N) {
               const int sz = sl / N1, iz = sl % N1, sy = fa / N1, iy = fa % N1;
@@ -387,7 +480,7 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
     }
     if (failed) break;
     if constexpr (!M::CARRY)   // plane pz now has both of its patches of this column
-      flush_plane<N1>(x, ACC + (pz & 1) * NP, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
+      flush_plane<N1>(x, ACC + (pz & 1) * NP, SB + (pz % 3) * NP, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
   }
   if (!failed) {
     if constexpr (M::CARRY) {   // the last plane has only the last patch's contribution
@@ -410,7 +503,8 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
       }
     } else {
       __syncthreads();
-      flush_plane<N1>(x, ACC + ((nc2 - 1) & 1) * NP, px, py, nc2 - 1, nc0, nc1, cls, x_is_zero, tid);
+      flush_plane<N1>(x, ACC + ((nc2 - 1) & 1) * NP, SB + ((nc2 - 1) % 3) * NP, px, py, nc2 - 1, nc0, nc1, cls,
+                      x_is_zero, tid);
     }
   } else if (tid == 0) {
     *fail_flag = 1;
@@ -422,31 +516,32 @@ patch_stream_tc05_kernel(const __nv_bfloat16* __restrict__ B0, const __nv_bfloat
   if (warp == 0) tc05::dealloc(tmem, 32);
 }
 
-template <int N>
+template <int N, bool TF>
 static tpss_status launch(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
                           cudaStream_t s) {
-  constexpr size_t smem = Smem<N>::BYTES;
+  constexpr size_t smem = Smem<N, TF>::BYTES;
+  constexpr int BP = Op<TF>::BPOS;
   static bool attr = false;
   if (!attr) {
-    TPSS_CHECK_CUDA(cudaFuncSetAttribute(patch_stream_tc05_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+    TPSS_CHECK_CUDA(cudaFuncSetAttribute(patch_stream_tc05_kernel<N, TF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   const Level& L = P->ctx->levels[P->level];
   const int nc0 = L.nc[0], nc1 = L.nc[1], nc2 = L.nc[2];
-  const __nv_bfloat16* bop = reinterpret_cast<const __nv_bfloat16*>(P->d_bop);
-  const __nv_bfloat16* B0 = bop;
-  const __nv_bfloat16* B1 = B0 + (size_t)P->npos[0] * 512;
-  const __nv_bfloat16* B2 = B1 + (size_t)P->npos[1] * 512;
+  const unsigned char* B0 = static_cast<const unsigned char*>(P->d_bop);
+  const unsigned char* B1 = B0 + (size_t)P->npos[0] * BP;
+  const unsigned char* B2 = B1 + (size_t)P->npos[1] * BP;
   for (int cls = 0; cls < 4; ++cls) {
     const int ax = cls & 1, ay = cls >> 1;
     const int ncolx = ax <= nc0 - 2 ? (nc0 - 2 - ax) / 2 + 1 : 0;
     const int ncoly = ay <= nc1 - 2 ? (nc1 - 2 - ay) / 2 + 1 : 0;
     if (ncolx == 0 || ncoly == 0) continue;
     dim3 grid((unsigned)(ncolx * ncoly), (unsigned)nrhs);
-    patch_stream_tc05_kernel<N><<<grid, kThreads, smem, s>>>(B0, B1, B2, P->d_lam32[0], P->d_lam32[1],
+    patch_stream_tc05_kernel<N, TF><<<grid, kThreads, smem, s>>>(B0, B1, B2, P->d_lam32[0], P->d_lam32[1],
                                                               P->d_lam32[2], r, x, omega, nc0, nc1, nc2, L.ndofs,
-                                                              cls, ncolx, x_is_zero, P->d_fail_flag);
+                                                              cls, ncolx, x_is_zero, P->d_fail_flag,
+                                                              P->expire_test);
     TPSS_CHECK_LAUNCH();
   }
   return TPSS_OK;
@@ -454,20 +549,27 @@ static tpss_status launch(tpss_patches* P, float omega, int nrhs, const float* r
 
 }  // namespace tcs
 
-// Per-position B operands of the tcgen05 smoother (BF16, [t][position][Z^T /
-// Z][16 x 16 K-major]) and its failure flag; for BF16 3D vertex patch sets
-// with n <= 16, built once at setup.
+// Per-position B operands of the tcgen05 smoother (BF16 or TF32,
+// [t][position][Z^T / Z][16 x 16 K-major]) and its failure flag; for BF16
+// and TF32 3D vertex patch sets with n <= 16, built once at setup.
 tpss_status tc05_prepare(tpss_patches* P) {
   if (P->ctx->dim != 3 || P->kind != TPSS_VERTEX_PATCH || P->per_sub || P->n > 16) return TPSS_OK;
-  const size_t per = 2 * 256;   // BF16 elements per position
+  if (P->precision != TPSS_BF16 && P->precision != TPSS_TF32) return TPSS_OK;
+  const bool tf = P->precision == TPSS_TF32;
+  const size_t per = 2 * 256;   // elements per position
   const size_t total = per * (P->npos[0] + P->npos[1] + P->npos[2]);
-  TPSS_TRY(dalloc(&P->d_bop, total * sizeof(__nv_bfloat16)));
-  __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(P->d_bop);
+  TPSS_TRY(dalloc(&P->d_bop, total * (tf ? sizeof(float) : sizeof(__nv_bfloat16))));
+  size_t off = 0;
   for (int t = 0; t < 3; ++t) {
-    tcs::prepare_bop_kernel<<<dim3((unsigned)P->npos[t], 2), 256, 0, P->ctx->stream>>>(P->d_Z32[t], P->npos[t], P->n,
-                                                                                        out);
+    const dim3 grid((unsigned)P->npos[t], 2);
+    if (tf)
+      tcs::prepare_bop_tf32_kernel<<<grid, 256, 0, P->ctx->stream>>>(P->d_Z32[t], P->npos[t], P->n,
+                                                                      static_cast<float*>(P->d_bop) + off);
+    else
+      tcs::prepare_bop_kernel<<<grid, 256, 0, P->ctx->stream>>>(P->d_Z32[t], P->npos[t], P->n,
+                                                                 static_cast<__nv_bfloat16*>(P->d_bop) + off);
     TPSS_CHECK_LAUNCH();
-    out += per * P->npos[t];
+    off += per * P->npos[t];
   }
   void* h = nullptr;
   TPSS_CHECK_CUDA(cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped));
@@ -483,27 +585,37 @@ tpss_status tc05_prepare(tpss_patches* P) {
 // parity classes); TPSS_EINVAL without launching for shapes it does not
 // cover (the same as the COLUMNS schedule); TPSS_ETIMEOUT if a previous
 // launch on this patch set gave up waiting for its MMAs.
-tpss_status patch_pass_bf16_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
-                                 cudaStream_t s) {
+tpss_status patch_pass_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
+                            cudaStream_t s) {
   if (P->ctx->dim != 3 || P->kind != TPSS_VERTEX_PATCH || P->per_sub || P->d_bop == nullptr) return TPSS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x)) & 15) return TPSS_EINVAL;
   const Level& L = P->ctx->levels[P->level];
   if (L.nc[0] < 2 || L.nc[1] < 2 || L.nc[2] < 2 || nrhs > 65535 || P->n > 16) return TPSS_EINVAL;
   if (*reinterpret_cast<volatile int*>(P->h_fail_flag) != 0) {
     *P->h_fail_flag = 0;
-    set_error("BF16 tensor-core smoother: an MMA completion wait expired in an earlier call (its result is invalid)");
+    set_error("tcgen05 smoother: an MMA completion wait expired in an earlier call (its result is invalid)");
     return TPSS_ETIMEOUT;
   }
+  struct ClearTest {   // the test hook applies to one call
+    tpss_patches* P;
+    ~ClearTest() { P->expire_test = 0; }
+  } clear_test{P};
+  const bool tf = P->precision == TPSS_TF32;
+#define TPSS_TC05_CASE(n)                                                                                    \
+  case n:                                                                                                    \
+    return tf ? tcs::launch<n, true>(P, omega, nrhs, r, x, x_is_zero, s)                                     \
+              : tcs::launch<n, false>(P, omega, nrhs, r, x, x_is_zero, s);
   switch (P->n) {
-    case 4: return tcs::launch<4>(P, omega, nrhs, r, x, x_is_zero, s);
-    case 6: return tcs::launch<6>(P, omega, nrhs, r, x, x_is_zero, s);
-    case 8: return tcs::launch<8>(P, omega, nrhs, r, x, x_is_zero, s);
-    case 10: return tcs::launch<10>(P, omega, nrhs, r, x, x_is_zero, s);
-    case 12: return tcs::launch<12>(P, omega, nrhs, r, x, x_is_zero, s);
-    case 14: return tcs::launch<14>(P, omega, nrhs, r, x, x_is_zero, s);
-    case 16: return tcs::launch<16>(P, omega, nrhs, r, x, x_is_zero, s);
+    TPSS_TC05_CASE(4)
+    TPSS_TC05_CASE(6)
+    TPSS_TC05_CASE(8)
+    TPSS_TC05_CASE(10)
+    TPSS_TC05_CASE(12)
+    TPSS_TC05_CASE(14)
+    TPSS_TC05_CASE(16)
     default: return TPSS_EINVAL;
   }
+#undef TPSS_TC05_CASE
 }
 
 }  // namespace tpss

@@ -1,10 +1,10 @@
 // Inline-PTX building blocks for the 5th-generation tensor cores (tcgen05:
 // MMA with the accumulator in tensor memory, TMEM allocation and loads) and
-// the mbarrier that tracks MMA completion.  BF16 operands from shared
+// the mbarrier that tracks MMA completion.  BF16 or TF32 operands from shared
 // memory in the canonical no-swizzle layouts, FP32 accumulation.
 //
 // Shared-memory matrix descriptor (no swizzle): a "core matrix" is 8 rows of
-// 16 contiguous bytes (8 BF16).  For a K-major operand a row runs along K;
+// 16 contiguous bytes (8 BF16 or 4 TF32).  For a K-major operand a row runs along K;
 // for an MN-major operand a row runs along M (or N) and the 8 rows are 8
 // consecutive K.  In both cases lbo is the byte distance between core
 // matrices adjacent along K and sbo the distance between core matrices
@@ -38,11 +38,24 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::tf32 (TF32 A and B, FP32 D, dense, both K-major).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // D (TMEM) = A B (+ D if accumulate); issued by one thread.
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
       :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
@@ -124,6 +137,18 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// FP32 -> TF32 (round to nearest, ties away from zero), as FP32 bits
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+// 4 consecutive values -> one 16-byte row of a TF32 core matrix
+__device__ __forceinline__ void st_row4_tf32(unsigned char* dst, const float* v) {
+  *reinterpret_cast<uint4*>(dst) = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
 }
 
 // 8 consecutive values -> one 16-byte row of a core matrix

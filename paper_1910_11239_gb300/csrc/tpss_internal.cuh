@@ -217,9 +217,10 @@ struct tpss_patches {
   int* d_plane_list = nullptr;
   std::vector<int> plane_offsets;
   int additive_schedule = 0;       // FP32-vector 3D additive: tpss_additive_schedule (BF16 3D vertex, k >= 4: TCGEN05)
-  void* d_bop = nullptr;           // tcgen05 smoother: BF16 B operands per direction and position
+  void* d_bop = nullptr;           // tcgen05 smoother: BF16 / TF32 B operands per direction and position
   int* h_fail_flag = nullptr;      // tcgen05 smoother: host-mapped word set when an MMA wait expires
   int* d_fail_flag = nullptr;      // its device address
+  int expire_test = 0;             // test hook: the next tcgen05 call lets its first waits expire
   // per multiplicative color: cells outside the color with a face to it,
   // {cell index, face mask (bit 2t+side: neighbour at -1 / +1 along t)}
   int2* d_flux_list = nullptr;
@@ -274,11 +275,11 @@ tpss_status patch_pass_bf16_atomic(tpss_patches* P, const int* list, int count, 
 // the whole additive pass, x written without clearing when x_is_zero)
 tpss_status patch_pass_bf16_stream(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
                                    cudaStream_t s);
-// ---- smoother_tc05.cu (the same schedule with tcgen05 MMAs; TPSS_ETIMEOUT
-// if an earlier launch on P gave up waiting for its MMAs)
-tpss_status patch_pass_bf16_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
-                                 cudaStream_t s);
-// its per-position operands and failure flag, built at setup (BF16 3D vertex patches)
+// ---- smoother_tc05.cu (the same schedule with tcgen05 MMAs, BF16 or TF32;
+// TPSS_ETIMEOUT if an earlier launch on P gave up waiting for its MMAs)
+tpss_status patch_pass_tc05(tpss_patches* P, float omega, int nrhs, const float* r, float* x, int x_is_zero,
+                            cudaStream_t s);
+// its per-position operands and failure flag, built at setup (BF16 and TF32 3D vertex patches)
 tpss_status tc05_prepare(tpss_patches* P);
 
 // ---- smoother_large.cu (3D FP64 vertex patches with n > 16, per-CTA scratch slabs)

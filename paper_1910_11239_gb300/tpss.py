@@ -65,6 +65,7 @@ SIGNATURES = {
     "tpss_patches_set_mult_residual": [_VP, _I],
     "tpss_patches_set_large_cluster": [_VP, _I],
     "tpss_patches_set_additive_schedule": [_VP, _I],
+    "tpss_patches_test_wait_expiry": [_VP],
     "tpss_smooth_additive": [_VP, _D, _I, _VP, _VP, _I],
     "tpss_smooth_additive_f32": [_VP, _F, _I, _VP, _VP, _I],
     "tpss_smooth_multiplicative": [_VP, _D, _I, _I, _VP, _VP],
@@ -363,6 +364,9 @@ class Patches:
 
     def set_additive_schedule(self, schedule):
         _check(lib().tpss_patches_set_additive_schedule(self.h, schedule))
+
+    def test_wait_expiry(self):
+        _check(lib().tpss_patches_test_wait_expiry(self.h))
 
     def smooth_additive(self, omega, b, x, x_is_zero=False, nrhs=1):
         n = self.problem.ndofs(self.level) * nrhs

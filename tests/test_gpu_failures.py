@@ -55,3 +55,31 @@ def test_context_usable_after_errors():
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
     prob.close()
+
+
+def test_tcgen05_wait_expiry_is_reported_and_the_context_recovers():
+    # the tcgen05 smoother's bounded MMA wait, made to run out by the test
+    # hook (a phase no MMA completes): the call after reports TPSS_ETIMEOUT,
+    # the next one runs normally
+    from gpu_helpers import rel_err
+    from oracle import fastdiag
+    widths = workloads.widths_random(4, 3, seed=7)
+    prob = make(3, 4, widths)
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH, tpss.BF16)
+    P.set_additive_schedule(tpss.ADDITIVE_TCGEN05)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=8)
+    bd = dev(b, torch.float32)
+    x = torch.empty(N, dtype=torch.float32, device="cuda")
+    P.test_wait_expiry()
+    P.smooth_additive(0.7, bd, x, x_is_zero=True)
+    torch.cuda.synchronize()
+    with pytest.raises(tpss.TpssError) as e:
+        P.smooth_additive(0.7, bd, x, x_is_zero=True)
+    assert e.value.status == -5  # TPSS_ETIMEOUT
+    P.smooth_additive(0.7, bd, x, x_is_zero=True)
+    torch.cuda.synchronize()
+    ref = fastdiag.additive_local_sum(widths, 4, True, b.astype(np.float32).astype(np.float64), 0.7)
+    assert rel_err(x.double(), ref) < 5e-2
+    P.close()
+    prob.close()

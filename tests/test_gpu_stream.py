@@ -1,9 +1,10 @@
-"""The column-streaming schedules of the BF16 additive vertex-patch smoother
-(3D): COLUMNS (mma.sync contractions) and TCGEN05 (the same walk with tcgen05
-MMAs and tensor-memory accumulators).  Parity with the FP64 oracle at the
-BF16 bound on ragged meshes (odd and even cell counts, so that every parity
-class is first for some cells), with x = 0 and x != 0, several right-hand
-sides, determinism, and the full 32^3 bench mesh at k = 7."""
+"""The column-streaming schedules of the mixed-precision additive
+vertex-patch smoother (3D): COLUMNS (BF16 mma.sync contractions) and TCGEN05
+(the same walk with tcgen05 MMAs and tensor-memory accumulators, BF16 or
+TF32 operands).  Parity with the FP64 oracle at the BF16 / TF32 bounds on
+ragged meshes (odd and even cell counts, so that every parity class is first
+for some cells), with x = 0 and x != 0, several right-hand sides,
+determinism, and the full 32^3 bench mesh at k = 7."""
 import numpy as np
 import pytest
 import torch
@@ -18,10 +19,13 @@ pytestmark = pytest.mark.gpu
 # relative max-norm errors of a few 1e-3 (the colored schedule's bound, 5e-2,
 # is kept as the bar)
 TOL_BF16 = 5e-2
+# TF32 operands (unit roundoff 2^-11), the same six contractions: the bar of
+# the other TF32 smoothers
+TOL_TF32 = 2e-3
 
 
-def _smooth(prob, k, schedule, b, nrhs, x0=None, omega=0.7):
-    P = prob.setup_patches(0, tpss.VERTEX_PATCH, tpss.BF16)
+def _smooth(prob, k, schedule, b, nrhs, x0=None, omega=0.7, precision=tpss.BF16):
+    P = prob.setup_patches(0, tpss.VERTEX_PATCH, precision)
     if schedule is not None:
         P.set_additive_schedule(schedule)
     x = torch.full((b.size,), float("nan"), dtype=torch.float32, device="cuda")
@@ -130,4 +134,75 @@ def test_columns_full_size_k7(schedule):
     got = _smooth(prob, 7, schedule, b, 1)
     ref = fastdiag.additive_local_sum(widths, 7, True, b.astype(np.float32).astype(np.float64), 0.7)
     assert rel_err(got, ref) < TOL_BF16
+    prob.close()
+
+
+# ---- TF32 operands (tcgen05 kind::tf32, every operand K-major)
+
+@pytest.mark.parametrize("k,cells", [(1, (5, 4, 3)), (2, (3, 6, 5)), (3, (7, 2, 4)), (4, (4, 5, 3)),
+                                     (5, (3, 3, 4)), (6, (2, 3, 3)), (7, (3, 4, 2))])
+def test_tf32_tcgen05_x0_matches_oracle(k, cells):
+    widths = [workloads.widths_random(n, 1, seed=170 + 3 * k + i)[0] for i, n in enumerate(cells)]
+    prob = make(3, k, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=171 + k, nrhs=2)
+    got = _smooth(prob, k, tpss.ADDITIVE_TCGEN05, b, 2, precision=tpss.TF32)
+    for r in range(2):
+        br = b[r * N:(r + 1) * N].astype(np.float32).astype(np.float64)
+        ref = fastdiag.additive_local_sum(widths, k, True, br, 0.7)
+        assert rel_err(got[r * N:(r + 1) * N], ref) < TOL_TF32, r
+    prob.close()
+
+
+@pytest.mark.parametrize("k,cells", [(3, (5, 4, 3)), (7, (3, 3, 2))])
+def test_tf32_tcgen05_nonzero_x_matches_oracle(k, cells):
+    widths = [workloads.widths_random(n, 1, seed=190 + i)[0] for i, n in enumerate(cells)]
+    prob = make(3, k, widths)
+    S = oracle_sipg(widths, k)
+    A = S.assemble().tocsr()
+    N = A.shape[0]
+    b = workloads.rhs_uniform(N, seed=191, nrhs=2)
+    x0 = workloads.rhs_uniform(N, seed=192, nrhs=2)
+    got = _smooth(prob, k, tpss.ADDITIVE_TCGEN05, b, 2, x0=x0, omega=0.3, precision=tpss.TF32)
+    for r in range(2):
+        sl = slice(r * N, (r + 1) * N)
+        bb = b[sl].astype(np.float32).astype(np.float64)
+        xx = x0[sl].astype(np.float32).astype(np.float64)
+        ref = xx + fastdiag.additive_local_sum(widths, k, True, bb - A @ xx, 0.3)
+        assert rel_err(got[sl] - xx, ref - xx) < TOL_TF32, r
+    prob.close()
+
+
+def test_tf32_tcgen05_deterministic_and_close_to_colors():
+    widths = workloads.widths_random(5, 3, seed=195)
+    prob = make(3, 5, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=196, nrhs=3)
+    d1 = _smooth(prob, 5, tpss.ADDITIVE_TCGEN05, b, 3, precision=tpss.TF32)
+    d2 = _smooth(prob, 5, tpss.ADDITIVE_TCGEN05, b, 3, precision=tpss.TF32)
+    assert np.array_equal(d1, d2)
+    col = _smooth(prob, 5, tpss.ADDITIVE_COLORS, b, 3, precision=tpss.TF32)
+    assert rel_err(d1, col) < 2e-3
+    prob.close()
+
+
+@pytest.mark.parametrize("k,expected", [(3, tpss.ADDITIVE_COLORS), (4, tpss.ADDITIVE_TCGEN05)])
+def test_tf32_vertex_default_schedule(k, expected):
+    widths = workloads.widths_random(4, 3, seed=197)
+    prob = make(3, k, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=198)
+    default = _smooth(prob, k, None, b, 1, precision=tpss.TF32)
+    assert np.array_equal(default, _smooth(prob, k, expected, b, 1, precision=tpss.TF32))
+    prob.close()
+
+
+def test_tf32_tcgen05_full_size_k7():
+    widths = workloads.widths_random(32, 3, 2)
+    prob = make(3, 7, widths)
+    N = prob.ndofs(0)
+    b = workloads.rhs_uniform(N, seed=200)
+    got = _smooth(prob, 7, tpss.ADDITIVE_TCGEN05, b, 1, precision=tpss.TF32)
+    ref = fastdiag.additive_local_sum(widths, 7, True, b.astype(np.float32).astype(np.float64), 0.7)
+    assert rel_err(got, ref) < TOL_TF32
     prob.close()
