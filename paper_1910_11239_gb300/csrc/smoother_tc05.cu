@@ -9,10 +9,12 @@
 //
 // Local solve (eq. fastinverse, eq. eigenvectormatvec): the six mode
 // contractions of (Z_z x Z_y x Z_x) Lambda^{-1} (Z_z x Z_y x Z_x)^T are six
-// MMAs D = A B with M = 128 (one or two blocks of 128 rows), N = 16, K = 16,
+// MMAs D = A B with M = 128 (two blocks of 128 rows), N = 16, K = 16,
 // BF16 operands from shared memory, FP32 accumulation in TMEM.  Every index
-// is padded to 16, so the patch tensor has 256 "lines" (slow index s, fast
-// index f, row m = 16 s + f).  A is the tensor with the contracted index as
+// is padded to 16 slots, slot 8 c + i for node i < k + 1 of the patch's cell
+// c (modes take the same slots, mode j at 8 (j / (k+1)) + j % (k+1)), so the
+// patch tensor has 256 "lines" (slow index s, fast index f, row m = 16 s +
+// f) and each cell of the patch owns an 8 x 8 x 8 corner of it.  A is the tensor with the contracted index as
 // K; B is the 1D eigenvector matrix (K-major 16 x 16, zero padded, prepared
 // once per position at setup and staged with cp.async).  After each MMA every
 // thread reads its TMEM rows (row m = thread + 128 b) and writes them back to
@@ -35,12 +37,12 @@
 // core matrix row holds 4 values); the rotated stages write their values to
 // the next A one by one instead of as MN-major rows.
 //
-// Output: with k = 7 (16 points per direction) a thread's two rows of D6 are
-// the same (y, z) line of the patch's lower and upper cell plane; the upper
-// one is kept in registers until the next patch of the column adds the lower
-// one of that plane, and the finished line (two cell rows) goes straight to
-// x.  Other degrees accumulate in FP32 plane buffers in shared memory and
-// write each finished plane.
+// Output: a thread's two rows of D6 (m and m + 128) are the same (y, z) line
+// of the patch's lower and upper cell plane; the upper one is kept in
+// registers until the next patch of the column adds the lower one of that
+// plane, and the finished line (two cell rows of k + 1 values) goes straight
+// to x, which is read (for the read-modify-write classes) and written once
+// per parity class.
 //
 // One thread issues the MMAs; a tcgen05.commit arrives on an mbarrier.  The
 // wait for it is bounded (about a second): on expiry the kernel records the
@@ -73,17 +75,20 @@ __device__ __forceinline__ int off_mn(int slow, int k) {
   return (k & 7) * 16 + slow * 2 * kMStride + (k >> 3) * kKStride;
 }
 
+// node (or mode) of slot sl of a direction with n1 nodes per cell; -1 for padding
+__host__ __device__ __forceinline__ int slot_index(int sl, int n1) {
+  return (sl & 7) < n1 ? (sl >> 3) * n1 + (sl & 7) : -1;
+}
+
 template <int N, bool TF>
 struct Smem {
   static constexpr int N1 = N / 2;
   static constexpr int NLOC1 = N1 * N1 * N1;
   static constexpr int NP = 4 * NLOC1;                       // floats of one column plane (4 cells)
-  static constexpr bool CARRY = (N == 16);                   // finished lines kept in registers
   static constexpr size_t OPA = 0;
   static constexpr size_t OPB = Op<TF>::ABYTES;              // 8 operands B
   static constexpr size_t SB = OPB + 8 * Op<TF>::BBYTES;     // 3 staged planes of r (FP32)
-  static constexpr size_t ACC = SB + 3 * (size_t)NP * 4;     // 2 plane accumulators (FP32) unless CARRY
-  static constexpr size_t BYTES = ACC + (CARRY ? 0 : 2 * (size_t)NP * 4);
+  static constexpr size_t BYTES = SB + 3 * (size_t)NP * 4;
 };
 // B operand slots (pairs as stored per position: Z^T-apply, Z-apply): 0 / 1 x,
 // 2 / 3 y, 4 + 2q / 5 + 2q z of the patch with p_z & 1 == q.  Stage s (1..6)
@@ -95,16 +100,17 @@ __device__ __forceinline__ int b_slot(int s, int q) {
 __device__ __forceinline__ int a_major(int s) { return (s == 1 || s == 4) ? 0 : 1; }
 
 // Global B operands: [t][position][apply Z^T (0) / Z (1)][512 bytes], the
-// 16 x 16 K-major BF16 matrix B[n][k] = Z[k][n] (0) or Z[n][k] (1), Z[node][mode].
+// 16 x 16 K-major BF16 matrix B[n][k] = Z[k][n] (0) or Z[n][k] (1), Z[node][mode],
+// both indices in slots (zero at padding slots).
 __global__ void prepare_bop_kernel(const float* __restrict__ Z, int npos, int n, __nv_bfloat16* __restrict__ out) {
   const int p = blockIdx.x, back = blockIdx.y;
   if (p >= npos) return;
   const float* Zp = Z + (size_t)p * n * n;
   __nv_bfloat16* o = out + ((size_t)p * 2 + back) * 256;
   for (int e = threadIdx.x; e < 256; e += blockDim.x) {
-    const int nn = e >> 4, k = e & 15;
+    const int nn = e >> 4, k = e & 15, in = slot_index(nn, n / 2), ik = slot_index(k, n / 2);
     float v = 0.f;
-    if (nn < n && k < n) v = back ? Zp[nn * n + k] : Zp[k * n + nn];
+    if (in >= 0 && ik >= 0) v = back ? Zp[in * n + ik] : Zp[ik * n + in];
     o[((nn & 7) * 16 + (nn >> 3) * 128 + (k >> 3) * 256 + (k & 7) * 2) / 2] = __float2bfloat16(v);
   }
 }
@@ -117,9 +123,9 @@ __global__ void prepare_bop_tf32_kernel(const float* __restrict__ Z, int npos, i
   const float* Zp = Z + (size_t)p * n * n;
   float* o = out + ((size_t)p * 2 + back) * 256;
   for (int e = threadIdx.x; e < 256; e += blockDim.x) {
-    const int nn = e >> 4, k = e & 15;
+    const int nn = e >> 4, k = e & 15, in = slot_index(nn, n / 2), ik = slot_index(k, n / 2);
     float v = 0.f;
-    if (nn < n && k < n) v = back ? Zp[nn * n + k] : Zp[k * n + nn];
+    if (in >= 0 && ik >= 0) v = back ? Zp[in * n + ik] : Zp[ik * n + in];
     o[((nn & 7) * 16 + (nn >> 3) * 128 + (k >> 2) * 256 + (k & 3) * 4) / 4] = __uint_as_float(tc05::to_tf32(v));
   }
 }
@@ -188,59 +194,39 @@ __device__ __forceinline__ int first_class(int cx, int cy, int nc0, int nc1) {
   return xm + 2 * ym;
 }
 
-// The previous values of cell plane cz of x (read-modify-write cells only)
-// -> shared memory, with cp.async, in the element order of flush_plane (each
-// thread later reads only what it copied itself).
+// n1 consecutive floats (a cell line; 16-byte aligned when n1 % 4 == 0, 8-byte
+// when n1 % 2 == 0) <-> v[0 .. n1)
 template <int N1>
-__device__ __forceinline__ void prefetch_plane(float* xo, const float* __restrict__ x, int px, int py, int cz,
-                                               int nc0, int nc1, int cls, int x_is_zero, int tid) {
-  constexpr int NLOC1 = N1 * N1 * N1;
-  constexpr int V = (NLOC1 % 4 == 0) ? 4 : 1;
-  constexpr int CH = NLOC1 / V;
-  const uint32_t d = tc05::smem_u32(xo);
-  for (int e = tid; e < 4 * CH; e += kThreads) {
-    const int c2 = e / CH, o = (e % CH) * V;
-    const int cx = px + (c2 & 1), cy = py + (c2 >> 1);
-    if (x_is_zero && first_class(cx, cy, nc0, nc1) == cls) continue;
-    const float* src = x + (cx + (int64_t)nc0 * (cy + (int64_t)nc1 * cz)) * NLOC1 + o;
-    if constexpr (V == 4)
-      cp16(d + 4u * (c2 * NLOC1 + o), src);
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(d + 4u * (c2 * NLOC1 + o)), "l"(src) : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// x (plane cz) = acc, or xo + acc for the read-modify-write cells; acc is cleared
-template <int N1>
-__device__ __forceinline__ void flush_plane(float* __restrict__ x, float* acc, const float* xo, int px, int py,
-                                            int cz, int nc0, int nc1, int cls, int x_is_zero, int tid) {
-  constexpr int NLOC1 = N1 * N1 * N1;
-  constexpr int V = (NLOC1 % 4 == 0) ? 4 : 1;
-  constexpr int CH = NLOC1 / V;
-  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's prefetched values
-  for (int e = tid; e < 4 * CH; e += kThreads) {
-    const int c2 = e / CH, o = (e % CH) * V;
-    const int cx = px + (c2 & 1), cy = py + (c2 >> 1);
-    const bool store = x_is_zero && first_class(cx, cy, nc0, nc1) == cls;
-    float* dst = x + (cx + (int64_t)nc0 * (cy + (int64_t)nc1 * cz)) * NLOC1 + o;
-    float* a = acc + c2 * NLOC1 + o;
-    if constexpr (V == 4) {
-      float4 v = *reinterpret_cast<float4*>(a);
-      if (!store) {
-        const float4 old = *reinterpret_cast<const float4*>(xo + c2 * NLOC1 + o);
-        v.x += old.x;
-        v.y += old.y;
-        v.z += old.z;
-        v.w += old.w;
-      }
-      *reinterpret_cast<float4*>(dst) = v;
-      *reinterpret_cast<float4*>(a) = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      const float v = *a;
-      *dst = store ? v : v + xo[c2 * NLOC1 + o];
-      *a = 0.f;
+__device__ __forceinline__ void ld_line(const float* p, float* v) {
+  if constexpr (N1 % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < N1 / 4; ++q) {
+      const float4 a = reinterpret_cast<const float4*>(p)[q];
+      v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
     }
+  } else if constexpr (N1 % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < N1 / 2; ++q) {
+      const float2 a = reinterpret_cast<const float2*>(p)[q];
+      v[2 * q] = a.x; v[2 * q + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < N1; ++q) v[q] = p[q];
+  }
+}
+template <int N1>
+__device__ __forceinline__ void st_line(float* p, const float* v) {
+  if constexpr (N1 % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < N1 / 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else if constexpr (N1 % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < N1 / 2; ++q) reinterpret_cast<float2*>(p)[q] = make_float2(v[2 * q], v[2 * q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N1; ++q) p[q] = v[q];
   }
 }
 
@@ -256,15 +242,13 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
   constexpr int N1 = N / 2;
   constexpr int NLOC1 = M::NLOC1;
   constexpr int NP = M::NP;
-  constexpr int NB = N > 8 ? 2 : 1;   // blocks of 128 rows: slow index < 8 NB
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* opa = dsm + M::OPA;
   unsigned char* opb = dsm + M::OPB;
   float* SB = reinterpret_cast<float*>(dsm + M::SB);
-  float* ACC = reinterpret_cast<float*>(dsm + M::ACC);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
-  __shared__ __align__(16) float lam[64];   // x, y (columns), z of patch p_z in slot 32 + 16 (p_z & 1)
+  __shared__ __align__(16) float lam[64];   // slots of x, y (the column's), z of patch p_z at 32 + 16 (p_z & 1)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int px = (cls & 1) + 2 * (int)(blockIdx.x % ncolx);
   const int py = (cls >> 1) + 2 * (int)(blockIdx.x / ncolx);
@@ -278,16 +262,17 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
   stage_b2<TF>(opb + 0 * BB, B0 + (size_t)px * BP, tid);   // slots 0, 1
   stage_b2<TF>(opb + 2 * BB, B1 + (size_t)py * BP, tid);   // slots 2, 3
   stage_b2<TF>(opb + 4 * BB, B2, tid);                     // patch 0: slots 4, 5
-  if (tid < N)                                           // patch 0's z eigenvalues
+  if (tid < 16 && (tid & 7) < N1)                          // patch 0's z eigenvalues
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(tc05::smem_u32(lam + 32 + tid)),
-                 "l"(L2 + tid) : "memory");
+                 "l"(L2 + slot_index(tid, N1)) : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
   for (int e = tid; e < Op<TF>::ABYTES / 16; e += kThreads) reinterpret_cast<uint4*>(opa)[e] = make_uint4(0, 0, 0, 0);
-  if constexpr (!M::CARRY)
-    for (int e = tid; e < 2 * NP; e += kThreads) ACC[e] = 0.f;
-  if (tid < 32) lam[tid] = (tid < 16) ? (tid < N ? L0[(size_t)px * N + tid] : 0.f)
-                                      : (tid - 16 < N ? L1[(size_t)py * N + tid - 16] : 0.f);
-  // (z slots: entries >= N are never read)
+  if (tid < 32) {
+    const int sl = tid & 15, i = slot_index(sl, N1);
+    lam[tid] = i < 0 ? 0.f : (tid < 16 ? L0[(size_t)px * N + i] : L1[(size_t)py * N + i]);
+  } else if (tid < 64 && ((tid & 7) >= N1)) {
+    lam[tid] = 0.f;   // z padding slots (never written by the copies)
+  }
   if (tid == 0) tc05::mbar_init(mb, 1);
   if (warp == 0) tc05::alloc(tc05::smem_u32(&tslot), 32);
   tc05::fence_before_sync();
@@ -299,21 +284,22 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
   uint32_t phase = 0;
   bool failed = false;
 
-  // CARRY (k = 7): this thread's line (y = tid & 15, local z = tid >> 4) of the
-  // two cells (sx = 0, 1) at (p_x + sx, p_y + y / 8)
-  const int ly = tid & 15, liz = tid >> 4;
+  // this thread's line: y slot tid & 15 (cell row sy, node iy), z node iz =
+  // tid >> 4 of the lower (rows m = tid) and upper (m = tid + 128) cell plane,
+  // in the two cells sx = 0, 1 at (p_x + sx, p_y + sy)
+  const int ly = tid & 15, iz = tid >> 4, sy = ly >> 3, iy = ly & 7;
+  const bool line = iy < N1 && iz < N1;
+  const int lofs = N1 * (iy + N1 * iz);   // the line's offset inside a cell
   float carry[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) carry[j] = 0.f;
-  bool store_cell[2] = {false, false};
-  int64_t line_off[2] = {0, 0};
-  if constexpr (M::CARRY) {
+  bool store_cell[2];
+  int64_t line_off[2];
 #pragma unroll
-    for (int sx = 0; sx < 2; ++sx) {
-      const int cx = px + sx, cy = py + (ly >> 3);
-      store_cell[sx] = x_is_zero && first_class(cx, cy, nc0, nc1) == cls;
-      line_off[sx] = (cx + (int64_t)nc0 * cy) * NLOC1 + 8 * ((ly & 7) + 8 * liz);
-    }
+  for (int sx = 0; sx < 2; ++sx) {
+    const int cx = px + sx, cy = py + sy;
+    store_cell[sx] = x_is_zero && first_class(cx, cy, nc0, nc1) == cls;
+    line_off[sx] = (cx + (int64_t)nc0 * cy) * NLOC1 + lofs;
   }
   const int64_t plane_stride = (int64_t)nc0 * nc1 * NLOC1;
   // k = 7 plane staging: thread t copies 16 bytes at float 4 t of each of the 4 cells
@@ -334,66 +320,41 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
         stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
       }
       stage_b2<TF>(opb + (4 + 2 * ((pz + 1) & 1)) * BB, B2 + (size_t)(pz + 1) * BP, tid);
-      if (tid < N)   // the next patch's z eigenvalues
+      if (tid < 16 && (tid & 7) < N1)   // the next patch's z eigenvalues
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
-                     :: "r"(tc05::smem_u32(lam + 32 + 16 * ((pz + 1) & 1) + tid)), "l"(L2 + (size_t)(pz + 1) * N + tid)
-                     : "memory");
+                     :: "r"(tc05::smem_u32(lam + 32 + 16 * ((pz + 1) & 1) + tid)),
+                        "l"(L2 + (size_t)(pz + 1) * N + slot_index(tid, N1)) : "memory");
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
     const float* lamz = lam + 32 + 16 * (pz & 1);
-    // previous values of this thread's line of plane pz (read-modify-write classes)
+    // previous values of this thread's line of plane pz (read-modify-write cells)
     float xold[16];
-    if constexpr (M::CARRY) {
 #pragma unroll
-      for (int sx = 0; sx < 2; ++sx) {
-        const float* src = x + line_off[sx] + pz * plane_stride;
+    for (int j = 0; j < 16; ++j) xold[j] = 0.f;
+    if (line) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (!store_cell[sx]) v = *reinterpret_cast<const float4*>(src + 4 * q);
-          xold[8 * sx + 4 * q] = v.x;
-          xold[8 * sx + 4 * q + 1] = v.y;
-          xold[8 * sx + 4 * q + 2] = v.z;
-          xold[8 * sx + 4 * q + 3] = v.w;
-        }
-      }
+      for (int sx = 0; sx < 2; ++sx)
+        if (!store_cell[sx]) ld_line<N1>(x + line_off[sx] + pz * plane_stride, xold + 8 * sx);
     }
-    // gather: A0[(z, y)][x] (K-major), zero outside the patch
+    // gather: A0[(z, y)][x] (K-major), zero outside the cells' nodes
     const float* lo = SB + (pz % 3) * NP;
     const float* hi = SB + ((pz + 1) % 3) * NP;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int m = tid + 128 * b, z = m >> 4, y = m & 15;
+    for (int b = 0; b < 2; ++b) {
       float v[16];
-      if constexpr (N1 == 8) {
-        const float* src = (b ? hi : lo) + 2 * (y >> 3) * NLOC1 + 8 * ((y & 7) + 8 * (z & 7));
 #pragma unroll
-        for (int sx = 0; sx < 2; ++sx) {
-          const float4 a0 = *reinterpret_cast<const float4*>(src + sx * NLOC1);
-          const float4 a1 = *reinterpret_cast<const float4*>(src + sx * NLOC1 + 4);
-          v[8 * sx] = a0.x; v[8 * sx + 1] = a0.y; v[8 * sx + 2] = a0.z; v[8 * sx + 3] = a0.w;
-          v[8 * sx + 4] = a1.x; v[8 * sx + 5] = a1.y; v[8 * sx + 6] = a1.z; v[8 * sx + 7] = a1.w;
-        }
-      } else {
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      if (line) {
+        const float* src = (b ? hi : lo) + 2 * sy * NLOC1 + lofs;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.f;
-        if (z < N && y < N) {
-          const float* src = (z >= N1 ? hi : lo) + 2 * (y / N1) * NLOC1 + N1 * ((y % N1) + N1 * (z % N1));
-#pragma unroll
-          for (int j = 0; j < N; ++j) v[j] = src[(j / N1) * NLOC1 + (j % N1)];
-        }
+        for (int sx = 0; sx < 2; ++sx) ld_line<N1>(src + sx * NLOC1, v + 8 * sx);
       }
-      put_row_k<TF>(opa, m, v);
+      put_row_k<TF>(opa, tid + 128 * b, v);
     }
     tc05::fence_proxy_async();
     tc05::fence_before_sync();
     __syncthreads();
     tc05::fence_after_sync();
-    if constexpr (!M::CARRY) {   // r of plane pz (and of the last plane) is consumed: its slots take x
-      prefetch_plane<N1>(SB + (pz % 3) * NP, x, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
-      if (pz + 2 == nc2)
-        prefetch_plane<N1>(SB + ((pz + 1) % 3) * NP, x, px, py, pz + 1, nc0, nc1, cls, x_is_zero, tid);
-    }
 
 #pragma unroll
     for (int s = 1; s <= 6; ++s) {   // unrolled: every stage's index rotation is resolved at compile time
@@ -402,7 +363,7 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
         if constexpr (TF) {   // K = 16 as two MMAs of K = 8 (core-matrix columns 2h, 2h + 1)
           constexpr uint32_t idesc = tc05::idesc_tf32(128, 16);
 #pragma unroll
-          for (int b = 0; b < NB; ++b)
+          for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
               tc05::mma_tf32(tmem + 16 * b,
@@ -412,7 +373,7 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
           const uint32_t idesc = tc05::idesc_bf16(128, 16, a_major(s), 0);
           const uint64_t bdesc = tc05::desc(bslot, 256, 128);
 #pragma unroll
-          for (int b = 0; b < NB; ++b)
+          for (int b = 0; b < 2; ++b)
             tc05::mma(tmem + 16 * b, tc05::desc(a_base + 16 * kMStride * b, kKStride, kMStride), bdesc, idesc, 0);
         }
         tc05::commit(mb);
@@ -424,49 +385,34 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
       if (expire_test && pz == 0 && s == 1) ok = ok && tc05::mbar_wait_bounded(mb, phase ^ 1, 2000000LL);
       phase ^= 1;
       tc05::fence_after_sync();
-      float v[16 * NB];
-      if constexpr (NB == 2) {
-        tc05::ld32(trow, v);
-      } else {
-        tc05::ld16(trow, v);
-      }
-      if (s == 6 && M::CARRY) {
-        // rows: block 0 = line (liz, ly) of plane pz (lower cells), block 1 = plane pz + 1
+      float v[32];
+      tc05::ld32(trow, v);
+      if (s == 6) {
+        // rows: block 0 = the line of plane pz (lower cells), block 1 = plane pz + 1
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           xold[j] += carry[j] + omega * v[j];
           carry[j] = omega * v[16 + j];
         }
+        if (line) {
 #pragma unroll
-        for (int sx = 0; sx < 2; ++sx) {
-          float* dst = x + line_off[sx] + pz * plane_stride;
-          *reinterpret_cast<float4*>(dst) = make_float4(xold[8 * sx], xold[8 * sx + 1], xold[8 * sx + 2],
-                                                        xold[8 * sx + 3]);
-          *reinterpret_cast<float4*>(dst + 4) = make_float4(xold[8 * sx + 4], xold[8 * sx + 5],
-                                                            xold[8 * sx + 6], xold[8 * sx + 7]);
+          for (int sx = 0; sx < 2; ++sx) st_line<N1>(x + line_off[sx] + pz * plane_stride, xold + 8 * sx);
         }
       } else {
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
+        for (int b = 0; b < 2; ++b) {
           const int m = tid + 128 * b, sl = m >> 4, fa = m & 15;
           float* w = v + 16 * b;
           if (s == 1 || s == 4) {          // D1[(z,y)][a] -> A1[(z,a)][y];  D4[(a,b)][z] -> A4[(a,z)][b]
-            if (NB == 2 || sl < 8) put_col<TF>(opa, sl, fa, w);
+            put_col<TF>(opa, sl, fa, w);
           } else if (s == 2 || s == 5) {   // D2[(z,a)][b] -> A2[(a,b)][z];  D5[(a,z)][y] -> A5[(z,y)][a]
-            if (NB == 2 || fa < 8) put_col<TF>(opa, fa, sl, w);
-          } else if (s == 3) {             // D3[(a,b)][c] / (lx_a + ly_b + lz_c) -> A3[(a,b)][c]
+            put_col<TF>(opa, fa, sl, w);
+          } else {                         // D3[(a,b)][c] / (lx_a + ly_b + lz_c) -> A3[(a,b)][c]
             const float sab = lam[sl] + lam[16 + fa];
+            const bool ab = (sl & 7) < N1 && (fa & 7) < N1;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              w[j] = (sl < N && fa < N && j < N) ? __fdividef(w[j], sab + lamz[j]) : 0.f;
+            for (int j = 0; j < 16; ++j) w[j] = (ab && (j & 7) < N1) ? __fdividef(w[j], sab + lamz[j]) : 0.f;
             put_row_k<TF>(opa, m, w);
-          } else if constexpr (!M::CARRY) {   // D6[(z,y)][x]: omega * line -> plane accumulators
-            if (sl < N && fa < N) {
-              const int sz = sl / N1, iz = sl % N1, sy = fa / N1, iy = fa % N1;
-              float* acc = ACC + ((pz + sz) & 1) * NP + 2 * sy * NLOC1 + N1 * (iy + N1 * iz);
-#pragma unroll
-              for (int j = 0; j < N; ++j) acc[(j / N1) * NLOC1 + (j % N1)] += omega * w[j];
-            }
           }
         }
       }
@@ -478,33 +424,19 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
       tc05::fence_after_sync();
       if (failed) break;
     }
-    if (failed) break;
-    if constexpr (!M::CARRY)   // plane pz now has both of its patches of this column
-      flush_plane<N1>(x, ACC + (pz & 1) * NP, SB + (pz % 3) * NP, px, py, pz, nc0, nc1, cls, x_is_zero, tid);
   }
   if (!failed) {
-    if constexpr (M::CARRY) {   // the last plane has only the last patch's contribution
+    // the last plane has only the last patch's contribution
+    if (line) {
 #pragma unroll
       for (int sx = 0; sx < 2; ++sx) {
         float* dst = x + line_off[sx] + (int64_t)(nc2 - 1) * plane_stride;
+        float o[8];
+        if (!store_cell[sx]) ld_line<N1>(dst, o);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float4 o = make_float4(carry[8 * sx + 4 * q], carry[8 * sx + 4 * q + 1], carry[8 * sx + 4 * q + 2],
-                                 carry[8 * sx + 4 * q + 3]);
-          if (!store_cell[sx]) {
-            const float4 old = *reinterpret_cast<const float4*>(dst + 4 * q);
-            o.x += old.x;
-            o.y += old.y;
-            o.z += old.z;
-            o.w += old.w;
-          }
-          *reinterpret_cast<float4*>(dst + 4 * q) = o;
-        }
+        for (int j = 0; j < N1; ++j) o[j] = store_cell[sx] ? carry[8 * sx + j] : o[j] + carry[8 * sx + j];
+        st_line<N1>(dst, o);
       }
-    } else {
-      __syncthreads();
-      flush_plane<N1>(x, ACC + ((nc2 - 1) & 1) * NP, SB + ((nc2 - 1) % 3) * NP, px, py, nc2 - 1, nc0, nc1, cls,
-                      x_is_zero, tid);
     }
   } else if (tid == 0) {
     *fail_flag = 1;
