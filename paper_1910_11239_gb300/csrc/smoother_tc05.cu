@@ -256,9 +256,29 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
   x += (int64_t)blockIdx.y * ndofs;
   const uint32_t mb = tc05::smem_u32(&mbar);
 
+  const int64_t plane_stride = (int64_t)nc0 * nc1 * NLOC1;
+  // k = 7 plane staging: thread t copies 16 bytes at float 4 t of each of the 4
+  // cells (half t & 1 of cell line t / 2); the two halves of the lines with
+  // bit 2 of y set trade places in shared memory, so that the gather's 16-byte
+  // reads of 8 lines hit 8 distinct bank groups
+  int64_t stage_off[4];
+#pragma unroll
+  for (int c2 = 0; c2 < 4; ++c2) stage_off[c2] = ((px + (c2 & 1)) + (int64_t)nc0 * (py + (c2 >> 1))) * NLOC1 + 4 * tid;
+  const uint32_t stage_dst = 16u * ((tid & ~1) | ((tid & 1) ^ ((tid >> 3) & 1)));
+  auto stage_r = [&](int cz) {   // cell plane cz of r -> ring slot cz % 3
+    if constexpr (NLOC1 == 4 * kThreads) {
+      const uint32_t d = tc05::smem_u32(SB + (cz % 3) * NP) + stage_dst;
+      const float* src = r + (int64_t)cz * plane_stride;
+#pragma unroll
+      for (int c2 = 0; c2 < 4; ++c2) cp16(d + 4u * NLOC1 * c2, src + stage_off[c2]);
+    } else {
+      stage_plane<NLOC1>(SB + (cz % 3) * NP, r, px, py, cz, nc0, nc1, tid);
+    }
+  };
+
   // prologue: planes 0 and 1, the column's x and y operands, patch 0's z operands
-  stage_plane<NLOC1>(SB, r, px, py, 0, nc0, nc1, tid);
-  stage_plane<NLOC1>(SB + NP, r, px, py, 1, nc0, nc1, tid);
+  stage_r(0);
+  stage_r(1);
   stage_b2<TF>(opb + 0 * BB, B0 + (size_t)px * BP, tid);   // slots 0, 1
   stage_b2<TF>(opb + 2 * BB, B1 + (size_t)py * BP, tid);   // slots 2, 3
   stage_b2<TF>(opb + 4 * BB, B2, tid);                     // patch 0: slots 4, 5
@@ -301,24 +321,12 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
     store_cell[sx] = x_is_zero && first_class(cx, cy, nc0, nc1) == cls;
     line_off[sx] = (cx + (int64_t)nc0 * cy) * NLOC1 + lofs;
   }
-  const int64_t plane_stride = (int64_t)nc0 * nc1 * NLOC1;
-  // k = 7 plane staging: thread t copies 16 bytes at float 4 t of each of the 4 cells
-  int64_t stage_off[4];
-#pragma unroll
-  for (int c2 = 0; c2 < 4; ++c2) stage_off[c2] = ((px + (c2 & 1)) + (int64_t)nc0 * (py + (c2 >> 1))) * NLOC1 + 4 * tid;
 
   for (int pz = 0; pz + 1 < nc2 && !failed; ++pz) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();   // planes pz, pz + 1 and patch pz's z operands staged; patch pz - 1 is done
     if (pz + 2 < nc2) {
-      if constexpr (NLOC1 == 4 * kThreads) {
-        const uint32_t d = tc05::smem_u32(SB + ((pz + 2) % 3) * NP) + 16u * tid;
-        const float* src = r + (int64_t)(pz + 2) * plane_stride;
-#pragma unroll
-        for (int c2 = 0; c2 < 4; ++c2) cp16(d + 4u * NLOC1 * c2, src + stage_off[c2]);
-      } else {
-        stage_plane<NLOC1>(SB + ((pz + 2) % 3) * NP, r, px, py, pz + 2, nc0, nc1, tid);
-      }
+      stage_r(pz + 2);
       stage_b2<TF>(opb + (4 + 2 * ((pz + 1) & 1)) * BB, B2 + (size_t)(pz + 1) * BP, tid);
       if (tid < 16 && (tid & 7) < N1)   // the next patch's z eigenvalues
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
@@ -346,8 +354,20 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
       for (int j = 0; j < 16; ++j) v[j] = 0.f;
       if (line) {
         const float* src = (b ? hi : lo) + 2 * sy * NLOC1 + lofs;
+        if constexpr (NLOC1 == 4 * kThreads) {   // halves swapped for lines with iy & 4
+          const int sw = (iy >> 2) & 1;
 #pragma unroll
-        for (int sx = 0; sx < 2; ++sx) ld_line<N1>(src + sx * NLOC1, v + 8 * sx);
+          for (int sx = 0; sx < 2; ++sx)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float4 a = *reinterpret_cast<const float4*>(src + sx * NLOC1 + 4 * (h ^ sw));
+              v[8 * sx + 4 * h] = a.x; v[8 * sx + 4 * h + 1] = a.y;
+              v[8 * sx + 4 * h + 2] = a.z; v[8 * sx + 4 * h + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+          for (int sx = 0; sx < 2; ++sx) ld_line<N1>(src + sx * NLOC1, v + 8 * sx);
+        }
       }
       put_row_k<TF>(opa, tid + 128 * b, v);
     }
@@ -399,6 +419,14 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
           for (int sx = 0; sx < 2; ++sx) st_line<N1>(x + line_off[sx] + pz * plane_stride, xold + 8 * sx);
         }
       } else {
+        float lz[16];   // z eigenvalues of this patch (s == 3), four 16-byte reads
+        if (s == 3) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 a = reinterpret_cast<const float4*>(lamz)[q];
+            lz[4 * q] = a.x; lz[4 * q + 1] = a.y; lz[4 * q + 2] = a.z; lz[4 * q + 3] = a.w;
+          }
+        }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           const int m = tid + 128 * b, sl = m >> 4, fa = m & 15;
@@ -411,7 +439,7 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
             const float sab = lam[sl] + lam[16 + fa];
             const bool ab = (sl & 7) < N1 && (fa & 7) < N1;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) w[j] = (ab && (j & 7) < N1) ? __fdividef(w[j], sab + lamz[j]) : 0.f;
+            for (int j = 0; j < 16; ++j) w[j] = (ab && (j & 7) < N1) ? __fdividef(w[j], sab + lz[j]) : 0.f;
             put_row_k<TF>(opa, m, w);
           }
         }
