@@ -508,6 +508,9 @@ static void free_patches(tpss_patches* P) {
   dfree(P->d_plane_list);
   dfree(P->d_bop);
   if (P->h_fail_flag) cudaFreeHost(P->h_fail_flag);
+  if (P->aux_stream) cudaStreamDestroy(P->aux_stream);
+  if (P->fork_event) cudaEventDestroy(P->fork_event);
+  if (P->join_event) cudaEventDestroy(P->join_event);
 }
 
 // Is cell m in a subdomain of multiplicative color `color`?  (The same rule

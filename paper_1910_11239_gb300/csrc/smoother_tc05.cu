@@ -492,17 +492,32 @@ static tpss_status launch(tpss_patches* P, float omega, int nrhs, const float* r
   const unsigned char* B0 = static_cast<const unsigned char*>(P->d_bop);
   const unsigned char* B1 = B0 + (size_t)P->npos[0] * BP;
   const unsigned char* B2 = B1 + (size_t)P->npos[1] * BP;
+  // Two or more right-hand sides: the second half goes to a second stream, so
+  // that its class launches fill the SMs left idle by the last wave of each
+  // class launch of the first half (the halves share no data).
+  const int halves = (nrhs >= 2 && P->aux_stream != nullptr) ? 2 : 1;
+  if (halves == 2) {
+    TPSS_CHECK_CUDA(cudaEventRecord(P->fork_event, s));
+    TPSS_CHECK_CUDA(cudaStreamWaitEvent(P->aux_stream, P->fork_event, 0));
+  }
   for (int cls = 0; cls < 4; ++cls) {
     const int ax = cls & 1, ay = cls >> 1;
     const int ncolx = ax <= nc0 - 2 ? (nc0 - 2 - ax) / 2 + 1 : 0;
     const int ncoly = ay <= nc1 - 2 ? (nc1 - 2 - ay) / 2 + 1 : 0;
     if (ncolx == 0 || ncoly == 0) continue;
-    dim3 grid((unsigned)(ncolx * ncoly), (unsigned)nrhs);
-    patch_stream_tc05_kernel<N, TF><<<grid, kThreads, smem, s>>>(B0, B1, B2, P->d_lam32[0], P->d_lam32[1],
-                                                              P->d_lam32[2], r, x, omega, nc0, nc1, nc2, L.ndofs,
-                                                              cls, ncolx, x_is_zero, P->d_fail_flag,
-                                                              P->expire_test);
-    TPSS_CHECK_LAUNCH();
+    for (int h = 0; h < halves; ++h) {
+      const int r0 = h == 0 ? 0 : nrhs / 2, nr = halves == 1 ? nrhs : (h == 0 ? nrhs / 2 : nrhs - nrhs / 2);
+      const int64_t off = (int64_t)r0 * L.ndofs;
+      dim3 grid((unsigned)(ncolx * ncoly), (unsigned)nr);
+      patch_stream_tc05_kernel<N, TF><<<grid, kThreads, smem, h == 0 ? s : P->aux_stream>>>(
+          B0, B1, B2, P->d_lam32[0], P->d_lam32[1], P->d_lam32[2], r + off, x + off, omega, nc0, nc1, nc2, L.ndofs,
+          cls, ncolx, x_is_zero, P->d_fail_flag, P->expire_test);
+      TPSS_CHECK_LAUNCH();
+    }
+  }
+  if (halves == 2) {
+    TPSS_CHECK_CUDA(cudaEventRecord(P->join_event, P->aux_stream));
+    TPSS_CHECK_CUDA(cudaStreamWaitEvent(s, P->join_event, 0));
   }
   return TPSS_OK;
 }
@@ -538,6 +553,9 @@ tpss_status tc05_prepare(tpss_patches* P) {
   void* d = nullptr;
   TPSS_CHECK_CUDA(cudaHostGetDevicePointer(&d, h, 0));
   P->d_fail_flag = static_cast<int*>(d);
+  TPSS_CHECK_CUDA(cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking));
+  TPSS_CHECK_CUDA(cudaEventCreateWithFlags(&P->fork_event, cudaEventDisableTiming));
+  TPSS_CHECK_CUDA(cudaEventCreateWithFlags(&P->join_event, cudaEventDisableTiming));
   return TPSS_OK;
 }
 
