@@ -174,14 +174,23 @@ __device__ __forceinline__ void put_row_k(unsigned char* opa, int m, const float
   }
 }
 // rows 16 slow + j (j = 0..15) at column k of A: MN-major rows (BF16) or
-// one value per row of the K-major TF32 operand
-template <bool TF>
+// one value per row of the K-major TF32 operand.  ALT: neighbouring threads
+// differ in `slow` (not in k); the threads with bit 2 of slow set write their
+// two 16-byte rows in the other order, so that the 8 rows one store
+// instruction writes per quarter warp fall in 8 distinct bank groups.
+template <bool TF, bool ALT>
 __device__ __forceinline__ void put_col(unsigned char* opa, int slow, int k, const float* v) {
   if constexpr (TF) {
     unsigned char* base = opa + (k & 3) * 4 + (k >> 2) * kKStride;
 #pragma unroll
     for (int j = 0; j < 16; ++j)
       *reinterpret_cast<uint32_t*>(base + off_k(16 * slow + j)) = tc05::to_tf32(v[j]);
+  } else if constexpr (ALT) {
+    const uint4 lo = tc05::pack8(v), hi = tc05::pack8(v + 8);
+    const bool swap = (slow >> 2) & 1;
+    unsigned char* p = opa + off_mn(slow, k);
+    *reinterpret_cast<uint4*>(p + (swap ? kMStride : 0)) = swap ? hi : lo;
+    *reinterpret_cast<uint4*>(p + (swap ? 0 : kMStride)) = swap ? lo : hi;
   } else {
     tc05::st_row8(opa + off_mn(slow, k), v);
     tc05::st_row8(opa + off_mn(slow, k) + kMStride, v + 8);
@@ -432,9 +441,9 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
           const int m = tid + 128 * b, sl = m >> 4, fa = m & 15;
           float* w = v + 16 * b;
           if (s == 1 || s == 4) {          // D1[(z,y)][a] -> A1[(z,a)][y];  D4[(a,b)][z] -> A4[(a,z)][b]
-            put_col<TF>(opa, sl, fa, w);
+            put_col<TF, false>(opa, sl, fa, w);
           } else if (s == 2 || s == 5) {   // D2[(z,a)][b] -> A2[(a,b)][z];  D5[(a,z)][y] -> A5[(z,y)][a]
-            put_col<TF>(opa, fa, sl, w);
+            put_col<TF, true>(opa, fa, sl, w);
           } else {                         // D3[(a,b)][c] / (lx_a + ly_b + lz_c) -> A3[(a,b)][c]
             const float sab = lam[sl] + lam[16 + fa];
             const bool ab = (sl & 7) < N1 && (fa & 7) < N1;

@@ -152,13 +152,11 @@ __device__ __forceinline__ void st_row4_tf32(unsigned char* dst, const float* v)
 }
 
 // 8 consecutive values -> one 16-byte row of a core matrix
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+}
 __device__ __forceinline__ void st_row8(unsigned char* dst, const float* v) {
-  uint4 o;
-  o.x = pack2(v[0], v[1]);
-  o.y = pack2(v[2], v[3]);
-  o.z = pack2(v[4], v[5]);
-  o.w = pack2(v[6], v[7]);
-  *reinterpret_cast<uint4*>(dst) = o;
+  *reinterpret_cast<uint4*>(dst) = pack8(v);
 }
 
 }  // namespace tc05
