@@ -240,7 +240,7 @@ __device__ __forceinline__ void st_line(float* p, const float* v) {
 }
 
 template <int N, bool TF>
-__global__ void __launch_bounds__(kThreads, TF ? 4 : 5)   // TF32 at k = 7: 51 KB of shared memory, 4 CTAs
+__global__ void __launch_bounds__(kThreads, (TF || N == 16) ? 4 : 5)   // k = 7: 4 CTAs (TF32: 51 KB of shared memory; BF16: no spills)
 patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned char* __restrict__ B1,
                          const unsigned char* __restrict__ B2, const float* __restrict__ L0,
                          const float* __restrict__ L1, const float* __restrict__ L2, const float* __restrict__ r,
