@@ -10,6 +10,10 @@
 // to a templated fast-diagonalization routine (gather, Z^T, Lambda^{-1}, Z)
 // and scatter with FP32 atomic adds (overlapping patches of one problem may
 // be processed concurrently; FP32 summation order is therefore not fixed).
+// In BF16 batches, the levels whose patch sets run the tcgen05 column
+// smoother (k >= 4) leave the persistent kernel: each such problem's
+// additive pass runs that deterministic smoother on one of a few side
+// streams, concurrently with the persistent launch for the other problems.
 // Work items are sorted by cost, largest first.  The number of patches per
 // work item is chosen per n by an autotuner that times the candidates at
 // setup.  Operators, transfers and coarse solves are launched per problem
@@ -426,6 +430,7 @@ using namespace tpss;
 struct BatchProb {
   tpss_ctx* ctx = nullptr;
   int L = 0;                          // finest level
+  std::vector<char> tc05;             // per level: smoothed by the tcgen05 column smoother
   int64_t off = 0;                    // offset of the problem's block (nrhs vectors) in concatenated vectors
   std::vector<float*> b, x, r;        // per level, nrhs vectors (finest b/x point into the concatenated buffers)
 };
@@ -459,6 +464,11 @@ struct tpss_batch {
   cudaGraphExec_t graph_exec = nullptr;
   int use_graph = 1;
   int bf16 = 0;                       // 1: BF16 tensor-core persistent smoother
+  int columns = 1;                    // BF16: k >= 4 levels on the tcgen05 column smoother (flags & 4 clears)
+  // side streams of the tcgen05 column smoother passes (fork / join events)
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_join;
+  cudaEvent_t side_fork = nullptr;
   // CG state (FP64, concatenated)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr;
   int64_t* d_off = nullptr;
@@ -483,7 +493,7 @@ static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>&
   for (int p = 0; p < (int)B->probs.size(); ++p) {
     const BatchProb& bp = B->probs[p];
     const int l = bp.L - depth;
-    if (l < 1) continue;
+    if (l < 1 || bp.tc05[l]) continue;
     tpss_patches* P = bp.ctx->mg->patches[l];
     const int n = P->n;
     if (only_n && n != only_n) continue;
@@ -527,6 +537,72 @@ static tpss_status launch_level(tpss_batch* B, const BatchLevelDesc* desc, const
     batch_smooth_simt_kernel<<<grid, kBatchThreads, smem, s>>>(desc, items, nitems, counter, B->omega);
   TPSS_CHECK_LAUNCH();
   return TPSS_OK;
+}
+
+// The additive passes of the problems whose level at this depth uses the
+// tcgen05 column smoother, x += omega sum_j R_j^T A_j^{-1} R_j r (x_is_zero:
+// x holds zeros), spread over the side streams after a fork from the batch
+// stream; side_join makes the batch stream wait for them (issue the
+// persistent launch in between).  fin: the finest level with the caller's
+// vectors.  *forked: whether a join is due.
+static tpss_status side_passes(tpss_batch* B, int depth, bool post, int x_is_zero, bool* forked,
+                               const float* fin_b = nullptr, float* fin_x = nullptr) {
+  *forked = false;
+  bool any = false;
+  for (const BatchProb& bp : B->probs) {
+    const int l = bp.L - depth;
+    any = any || (l >= 1 && bp.tc05[l]);
+  }
+  if (!any) return TPSS_OK;
+  const int K = (int)B->side.size();
+  *forked = true;
+  TPSS_CHECK_CUDA(cudaEventRecord(B->side_fork, B->stream));
+  for (int k = 0; k < K; ++k) TPSS_CHECK_CUDA(cudaStreamWaitEvent(B->side[k], B->side_fork, 0));
+  int next = 0;
+  for (const BatchProb& bp : B->probs) {
+    const int l = bp.L - depth;
+    if (l < 1 || !bp.tc05[l]) continue;
+    tpss_patches* P = bp.ctx->mg->patches[l];
+    const float* r = fin_b ? fin_b + bp.off : (post ? bp.r[l] : bp.b[l]);
+    float* x = fin_x ? fin_x + bp.off : bp.x[l];
+    TPSS_TRY(patch_pass_tc05(P, B->omega, B->nrhs, r, x, x_is_zero, B->side[next]));
+    next = (next + 1) % K;
+  }
+  return TPSS_OK;
+}
+static tpss_status side_join(tpss_batch* B, bool forked) {
+  if (!forked) return TPSS_OK;
+  for (size_t k = 0; k < B->side.size(); ++k) {
+    TPSS_CHECK_CUDA(cudaEventRecord(B->side_join[k], B->side[k]));
+    TPSS_CHECK_CUDA(cudaStreamWaitEvent(B->stream, B->side_join[k], 0));
+  }
+  return TPSS_OK;
+}
+// A tcgen05 pass of the batch gave up waiting for its MMAs (in a replayed
+// graph the per-call check does not run): report it once, clear the flags.
+static tpss_status side_failed(tpss_batch* B) {
+  bool bad = false;
+  for (const BatchProb& bp : B->probs)
+    for (int l = 1; l < (int)bp.tc05.size(); ++l) {
+      tpss_patches* P = bp.ctx->mg->patches[l];
+      if (bp.tc05[l] && P->h_fail_flag && *reinterpret_cast<volatile int*>(P->h_fail_flag) != 0) {
+        *P->h_fail_flag = 0;
+        bad = true;
+      }
+    }
+  if (bad) {
+    set_error("batch: a tcgen05 smoother pass gave up waiting for its MMAs (results invalid)");
+    return TPSS_ETIMEOUT;
+  }
+  return TPSS_OK;
+}
+
+// Does level l of problem bp go through the tcgen05 column smoother?
+static bool uses_tc05(const tpss_batch* B, const BatchProb& bp, int l) {
+  const tpss_patches* P = bp.ctx->mg->patches[l];
+  const Level& L = bp.ctx->levels[l];
+  return B->bf16 && B->columns && P != nullptr && P->d_bop != nullptr && P->additive_schedule == TPSS_ADDITIVE_TCGEN05 &&
+         P->kind == TPSS_VERTEX_PATCH && !P->per_sub && P->n <= 16 && L.nc[0] >= 2 && L.nc[1] >= 2 && L.nc[2] >= 2;
 }
 
 static tpss_status set_descs(tpss_batch* B, int depth) {
@@ -583,8 +659,12 @@ static tpss_status batch_vcycle_rec(tpss_batch* B, int depth) {
   }
   if (!any) return TPSS_OK;
   // pre-smoothing (x = 0, r = b): one persistent launch for all problems
+  // (the tcgen05 levels on the side streams)
+  bool forked = false;
+  TPSS_TRY(side_passes(B, depth, false, 1, &forked));
   TPSS_TRY(launch_level(B, B->d_desc[depth], B->d_items[depth], B->nitems[depth], B->smem[depth],
                         B->grid[depth], B->d_counter + 2 * depth, s));
+  TPSS_TRY(side_join(B, forked));
   for (BatchProb& bp : B->probs) {
     const int l = bp.L - depth;
     if (l < 1) continue;
@@ -599,8 +679,10 @@ static tpss_status batch_vcycle_rec(tpss_batch* B, int depth) {
     TPSS_TRY(apply_operator_t<float>(bp.ctx, l, nr, bp.x[l], bp.r[l], bp.b[l]));
   }
   // post-smoothing with the residual
+  TPSS_TRY(side_passes(B, depth, true, 0, &forked));
   TPSS_TRY(launch_level(B, B->d_desc_post[depth], B->d_items[depth], B->nitems[depth], B->smem[depth],
                         B->grid[depth], B->d_counter + 2 * depth + 1, s));
+  TPSS_TRY(side_join(B, forked));
   return TPSS_OK;
 }
 
@@ -692,6 +774,9 @@ static void free_batch(tpss_batch* B) {
     }
     if (bp.ctx) tpss_destroy(bp.ctx);
   }
+  for (cudaStream_t st : B->side) cudaStreamDestroy(st);
+  for (cudaEvent_t e : B->side_join) cudaEventDestroy(e);
+  if (B->side_fork) cudaEventDestroy(B->side_fork);
   dfree(B->r); dfree(B->z); dfree(B->p); dfree(B->q); dfree(B->zold);
   dfree(B->d_off); dfree(B->d_len); dfree(B->sc); dfree(B->partials);
 }
@@ -719,6 +804,7 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
   B->flexible = 1;
   B->use_graph = (flags & 1) ? 0 : 1;
   B->bf16 = params->precision == TPSS_BF16 ? 1 : 0;
+  B->columns = (flags & 4) ? 0 : 1;
   B->stream = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -743,6 +829,29 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
     B->total = bp.off + bp.ctx->levels[bp.L].ndofs * nrhs;
     for (int l = 0; l <= bp.L; ++l)
       if ((st = ensure_level_scratch(bp.ctx, l, nrhs)) != TPSS_OK) return fail(st);
+    bp.tc05.assign(bp.L + 1, 0);
+    for (int l = 1; l <= bp.L; ++l) bp.tc05[l] = uses_tc05(B, bp, l) ? 1 : 0;
+  }
+  {
+    bool any = false;
+    for (const BatchProb& bp : B->probs)
+      for (char c : bp.tc05) any = any || c;
+    if (any) {
+      const int K = 4;
+      B->side.assign(K, nullptr);
+      B->side_join.assign(K, nullptr);
+      for (int k = 0; k < K; ++k) {
+        if (cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->side_join[k], cudaEventDisableTiming) != cudaSuccess) {
+          set_error("tpss_batch_create: side stream creation failed");
+          return fail(TPSS_ECUDA);
+        }
+      }
+      if (cudaEventCreateWithFlags(&B->side_fork, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("tpss_batch_create: side stream creation failed");
+        return fail(TPSS_ECUDA);
+      }
+    }
   }
   if ((st = dalloc_t(&B->fb, B->total)) != TPSS_OK) return fail(st);
   if ((st = dalloc_t(&B->fx, B->total)) != TPSS_OK) return fail(st);
@@ -923,8 +1032,11 @@ extern "C" tpss_status tpss_batch_smooth_additive(tpss_batch* B, const float* b,
   TPSS_CHECK_CUDA(cudaMemcpyAsync(B->d_desc_fin, B->h_desc_fin.data(), desc.size() * sizeof(BatchLevelDesc),
                                   cudaMemcpyHostToDevice, B->stream));
   TPSS_CHECK_CUDA(cudaMemsetAsync(x, 0, B->total * sizeof(float), B->stream));
-  return launch_level(B, B->d_desc_fin, B->d_items[0], B->nitems[0], B->smem[0], B->grid[0],
-                      B->d_counter + 2 * B->maxdepth, B->stream);
+  bool forked = false;
+  TPSS_TRY(side_passes(B, 0, false, 1, &forked, b, x));
+  TPSS_TRY(launch_level(B, B->d_desc_fin, B->d_items[0], B->nitems[0], B->smem[0], B->grid[0],
+                        B->d_counter + 2 * B->maxdepth, B->stream));
+  return side_join(B, forked);
 }
 
 extern "C" tpss_status tpss_batch_vcycle(tpss_batch* B, const double* b, double* x) {
@@ -936,7 +1048,7 @@ extern "C" tpss_status tpss_batch_vcycle(tpss_batch* B, const double* b, double*
   TPSS_TRY(batch_vcycle(B));
   f32_to_f64_kernel<<<g, 256, 0, B->stream>>>(B->fx, x, B->total);
   TPSS_CHECK_LAUNCH();
-  return TPSS_OK;
+  return side_failed(B);
 }
 
 namespace tpss {
@@ -1016,6 +1128,7 @@ extern "C" tpss_status tpss_batch_pcg_solve(tpss_batch* B, const double* b, doub
     TPSS_CHECK_LAUNCH();
   }
   (void)g;
+  TPSS_TRY(side_failed(B));
   if (nactive > 0) {
     set_error("tpss_batch_pcg_solve: not all systems converged within maxit");
     return TPSS_ENOTCONV;

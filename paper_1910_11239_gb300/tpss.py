@@ -395,7 +395,7 @@ class Batch:
     persistent smoother launch per level, optionally graph-captured."""
 
     def __init__(self, problems, nrhs, omega=0.125, use_graph=True, autotune=True, stream=None,
-                 gamma_hat=1.0, penalty_poly=PENALTY_PAPER, precision=FP32):
+                 gamma_hat=1.0, penalty_poly=PENALTY_PAPER, precision=FP32, columns=True):
         self._keep = []
         descs = (ProblemDesc * len(problems))()
         for i, (degree, widths, nlevels) in enumerate(problems):
@@ -409,7 +409,7 @@ class Batch:
         p = MGParams()
         p.smoother, p.omega, p.precision, p.mult_colors, p.flexible_cg = AVS, omega, precision, 0, 1
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        flags = (0 if use_graph else 1) | (0 if autotune else 2)
+        flags = (0 if use_graph else 1) | (0 if autotune else 2) | (0 if columns else 4)
         h = ctypes.c_void_p()
         _check(lib().tpss_batch_create(descs, len(problems), nrhs, ctypes.byref(p), flags,
                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))

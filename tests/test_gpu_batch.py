@@ -138,13 +138,19 @@ def fine_widths(widths, nlevels):
 BATCH_TOL = {"fp32": 1e-4, "bf16": 5e-2}
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_batch_smoother_large_patches_match_oracle(prec, stream):
-    # each routine is forced by the batch precision: FP32 -> batch_group<n>,
-    # BF16 -> batch_group_bf16<n>; n = 12 and 16 are the k = 5 and k = 7 items
+# (precision, columns): FP32 -> batch_group<n>; BF16 without columns ->
+# batch_group_bf16<n>; BF16 with columns -> the tcgen05 column smoother on the
+# side streams for n = 12, 16 (k = 5, 7) and batch_group_bf16<6> for k = 2
+ROUTES = [("fp32", True), ("bf16", False), ("bf16", True)]
+
+
+@pytest.mark.parametrize("prec,columns", ROUTES)
+def test_batch_smoother_large_patches_match_oracle(prec, columns, stream):
+    # each routine is forced by the batch precision and the columns flag
     from oracle import fastdiag
     with torch.cuda.stream(stream):
-        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec])
+        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec],
+                       columns=columns)
         b = rhs_for(B, 4)
         x = torch.full((B.total,), float("nan"), dtype=torch.float32, device="cuda")
         B.smooth_additive(dev(b, torch.float32), x)
@@ -173,10 +179,11 @@ def _large_hierarchy(p):
     return _LARGE_HIERARCHIES[p]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_batch_vcycle_large_patches_match_oracle(prec, stream):
+@pytest.mark.parametrize("prec,columns", ROUTES)
+def test_batch_vcycle_large_patches_match_oracle(prec, columns, stream):
     with torch.cuda.stream(stream):
-        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec])
+        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.PRECISIONS[prec],
+                       columns=columns)
         b = rhs_for(B, 5)
         x = torch.empty(B.total, dtype=torch.float64, device="cuda")
         B.vcycle(dev(b), x)
@@ -208,4 +215,33 @@ def test_batch_vcycle_every_problem_matches_oracle(stream):
             for r in range(2):
                 seg = slice(info["offset"] + r * n, info["offset"] + (r + 1) * n)
                 assert rel_err(xs[seg], H.precondition(b[seg])) < 1e-4, (p, r)
+        B.close()
+
+
+def test_batch_bf16_columns_deterministic_and_match_single_problem(stream):
+    # with the column route, the k >= 4 problems of a BF16 batch are smoothed
+    # by the same deterministic kernel as the single-problem TCGEN05 schedule:
+    # repeated calls agree bit for bit, and so do the batch and the problem alone
+    with torch.cuda.stream(stream):
+        B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.BF16)
+        b = rhs_for(B, 7)
+        x1 = torch.empty(B.total, dtype=torch.float32, device="cuda")
+        x2 = torch.empty_like(x1)
+        B.smooth_additive(dev(b, torch.float32), x1)
+        B.smooth_additive(dev(b, torch.float32), x2)
+        torch.cuda.synchronize()
+        for p, (k, widths, nl) in enumerate(large_problems()):
+            if k < 4:
+                continue
+            info = B.info(p)
+            n = info["ndofs"]
+            seg = slice(info["offset"], info["offset"] + 2 * n)
+            assert torch.equal(x1[seg], x2[seg])
+            prob = make(3, k, widths, nlevels=nl)
+            P = prob.setup_patches(nl - 1, tpss.VERTEX_PATCH, tpss.BF16)
+            xr = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+            P.smooth_additive(OMEGA, dev(b[seg], torch.float32), xr, x_is_zero=True, nrhs=2)
+            torch.cuda.synchronize()
+            assert torch.equal(x1[seg], xr)
+            prob.close()
         B.close()
