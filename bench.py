@@ -1020,9 +1020,10 @@ def run_batch_one(tpss, workloads, torch, steps, prec, columns=True):
         byt = 8.0 * B.total
         peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
         hbm = json.load(open(peaks)).get("hbm_gbs", 6800.0) if os.path.exists(peaks) else 6800.0
-        n_col = sum(1 for k, _, _ in specs if k >= 4) if out["columns"] else 0
+        # BF16 with columns: every problem's finest level on its own passes (8 launches: 4 classes x 2
+        # RHS halves of the tcgen05 columns for k >= 4, 8 colors below), none left for the persistent kernel
         out["smoother"] = {"dofs_per_s": B.total / (ms / 1e3), "ms_per_call": ms,
-                           "launches_per_call": 1 + 8 * n_col,
+                           "launches_per_call": 8 * len(specs) if out["columns"] else 1,
                            "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
         bd = torch.from_numpy(b).to("cuda")
         x = torch.empty_like(bd)

@@ -11,9 +11,11 @@
 // and scatter with FP32 atomic adds (overlapping patches of one problem may
 // be processed concurrently; FP32 summation order is therefore not fixed).
 // In BF16 batches, the levels whose patch sets run the tcgen05 column
-// smoother (k >= 4) leave the persistent kernel: each such problem's
-// additive pass runs that deterministic smoother on one of a few side
-// streams, concurrently with the persistent launch for the other problems.
+// smoother (k >= 4), and the finest level of the other problems, leave the
+// persistent kernel: each such problem's additive pass runs the library's
+// deterministic per-problem smoother (the tcgen05 column walk, or the
+// colored BF16 launches) on one of a few side streams, concurrently with the
+// persistent launch for the rest.
 // Work items are sorted by cost, largest first.  The number of patches per
 // work item is chosen per n by an autotuner that times the candidates at
 // setup.  Operators, transfers and coarse solves are launched per problem
@@ -430,7 +432,7 @@ using namespace tpss;
 struct BatchProb {
   tpss_ctx* ctx = nullptr;
   int L = 0;                          // finest level
-  std::vector<char> tc05;             // per level: smoothed by the tcgen05 column smoother
+  std::vector<char> route;            // per level: 0 persistent kernel, 1 tcgen05 columns, 2 colored launches
   int64_t off = 0;                    // offset of the problem's block (nrhs vectors) in concatenated vectors
   std::vector<float*> b, x, r;        // per level, nrhs vectors (finest b/x point into the concatenated buffers)
 };
@@ -493,7 +495,7 @@ static tpss_status build_items(tpss_batch* B, int depth, std::vector<BatchItem>&
   for (int p = 0; p < (int)B->probs.size(); ++p) {
     const BatchProb& bp = B->probs[p];
     const int l = bp.L - depth;
-    if (l < 1 || bp.tc05[l]) continue;
+    if (l < 1 || bp.route[l]) continue;
     tpss_patches* P = bp.ctx->mg->patches[l];
     const int n = P->n;
     if (only_n && n != only_n) continue;
@@ -539,9 +541,10 @@ static tpss_status launch_level(tpss_batch* B, const BatchLevelDesc* desc, const
   return TPSS_OK;
 }
 
-// The additive passes of the problems whose level at this depth uses the
-// tcgen05 column smoother, x += omega sum_j R_j^T A_j^{-1} R_j r (x_is_zero:
-// x holds zeros), spread over the side streams after a fork from the batch
+// The additive passes of the problems whose level at this depth leaves the
+// persistent kernel (route 1: tcgen05 column smoother, 2: colored launches),
+// x += omega sum_j R_j^T A_j^{-1} R_j r (x_is_zero: x holds zeros), spread
+// over the side streams after a fork from the batch
 // stream; side_join makes the batch stream wait for them (issue the
 // persistent launch in between).  fin: the finest level with the caller's
 // vectors.  *forked: whether a join is due.
@@ -551,7 +554,7 @@ static tpss_status side_passes(tpss_batch* B, int depth, bool post, int x_is_zer
   bool any = false;
   for (const BatchProb& bp : B->probs) {
     const int l = bp.L - depth;
-    any = any || (l >= 1 && bp.tc05[l]);
+    any = any || (l >= 1 && bp.route[l]);
   }
   if (!any) return TPSS_OK;
   const int K = (int)B->side.size();
@@ -561,11 +564,18 @@ static tpss_status side_passes(tpss_batch* B, int depth, bool post, int x_is_zer
   int next = 0;
   for (const BatchProb& bp : B->probs) {
     const int l = bp.L - depth;
-    if (l < 1 || !bp.tc05[l]) continue;
+    if (l < 1 || !bp.route[l]) continue;
     tpss_patches* P = bp.ctx->mg->patches[l];
     const float* r = fin_b ? fin_b + bp.off : (post ? bp.r[l] : bp.b[l]);
     float* x = fin_x ? fin_x + bp.off : bp.x[l];
-    TPSS_TRY(patch_pass_tc05(P, B->omega, B->nrhs, r, x, x_is_zero, B->side[next]));
+    if (bp.route[l] == 1) {
+      TPSS_TRY(patch_pass_tc05(P, B->omega, B->nrhs, r, x, x_is_zero, B->side[next]));
+    } else {   // one launch per color; x holds zeros or the current iterate
+      for (size_t c = 0; c + 1 < P->add_offsets.size(); ++c) {
+        const int o = P->add_offsets[c], cnt = P->add_offsets[c + 1] - o;
+        TPSS_TRY(patch_pass<float>(P, P->d_add_list + o, cnt, B->omega, B->nrhs, r, x, B->side[next]));
+      }
+    }
     next = (next + 1) % K;
   }
   return TPSS_OK;
@@ -583,9 +593,9 @@ static tpss_status side_join(tpss_batch* B, bool forked) {
 static tpss_status side_failed(tpss_batch* B) {
   bool bad = false;
   for (const BatchProb& bp : B->probs)
-    for (int l = 1; l < (int)bp.tc05.size(); ++l) {
+    for (int l = 1; l < (int)bp.route.size(); ++l) {
       tpss_patches* P = bp.ctx->mg->patches[l];
-      if (bp.tc05[l] && P->h_fail_flag && *reinterpret_cast<volatile int*>(P->h_fail_flag) != 0) {
+      if (bp.route[l] == 1 && P->h_fail_flag && *reinterpret_cast<volatile int*>(P->h_fail_flag) != 0) {
         *P->h_fail_flag = 0;
         bad = true;
       }
@@ -829,13 +839,14 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
     B->total = bp.off + bp.ctx->levels[bp.L].ndofs * nrhs;
     for (int l = 0; l <= bp.L; ++l)
       if ((st = ensure_level_scratch(bp.ctx, l, nrhs)) != TPSS_OK) return fail(st);
-    bp.tc05.assign(bp.L + 1, 0);
-    for (int l = 1; l <= bp.L; ++l) bp.tc05[l] = uses_tc05(B, bp, l) ? 1 : 0;
+    bp.route.assign(bp.L + 1, 0);
+    for (int l = 1; l <= bp.L; ++l)
+      bp.route[l] = uses_tc05(B, bp, l) ? 1 : (B->bf16 && B->columns && l == bp.L) ? 2 : 0;
   }
   {
     bool any = false;
     for (const BatchProb& bp : B->probs)
-      for (char c : bp.tc05) any = any || c;
+      for (char c : bp.route) any = any || c;
     if (any) {
       const int K = 4;
       B->side.assign(K, nullptr);

@@ -139,8 +139,9 @@ BATCH_TOL = {"fp32": 1e-4, "bf16": 5e-2}
 
 
 # (precision, columns): FP32 -> batch_group<n>; BF16 without columns ->
-# batch_group_bf16<n>; BF16 with columns -> the tcgen05 column smoother on the
-# side streams for n = 12, 16 (k = 5, 7) and batch_group_bf16<6> for k = 2
+# batch_group_bf16<n>; BF16 with columns -> per-problem passes on the side
+# streams (tcgen05 columns for n = 12, 16, i.e. k = 5, 7, on every level; the
+# colored BF16 launches for k = 2 on the finest level, batch_group_bf16<6> below)
 ROUTES = [("fp32", True), ("bf16", False), ("bf16", True)]
 
 
@@ -219,9 +220,10 @@ def test_batch_vcycle_every_problem_matches_oracle(stream):
 
 
 def test_batch_bf16_columns_deterministic_and_match_single_problem(stream):
-    # with the column route, the k >= 4 problems of a BF16 batch are smoothed
-    # by the same deterministic kernel as the single-problem TCGEN05 schedule:
-    # repeated calls agree bit for bit, and so do the batch and the problem alone
+    # with the column route, the finest level of every problem of a BF16
+    # batch is smoothed by the same deterministic kernels as the problem alone
+    # (tcgen05 columns for k >= 4, colored launches below): repeated calls
+    # agree bit for bit, and so do the batch and the problem alone
     with torch.cuda.stream(stream):
         B = tpss.Batch(large_problems(), nrhs=2, omega=OMEGA, stream=stream, precision=tpss.BF16)
         b = rhs_for(B, 7)
@@ -231,8 +233,6 @@ def test_batch_bf16_columns_deterministic_and_match_single_problem(stream):
         B.smooth_additive(dev(b, torch.float32), x2)
         torch.cuda.synchronize()
         for p, (k, widths, nl) in enumerate(large_problems()):
-            if k < 4:
-                continue
             info = B.info(p)
             n = info["ndofs"]
             seg = slice(info["offset"], info["offset"] + 2 * n)
