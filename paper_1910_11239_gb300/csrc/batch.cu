@@ -649,24 +649,52 @@ static tpss_status set_descs(tpss_batch* B, int depth) {
   return TPSS_OK;
 }
 
+// Per-problem work f(bp) (operators, transfers, coarse solves: launches on
+// bp.ctx->stream) spread over the side streams between a fork from and a
+// join into the batch stream, so that the problems' launches run side by
+// side instead of one after another; serial on the batch stream without
+// side streams.
+template <typename F>
+static tpss_status on_sides(tpss_batch* B, F&& f) {
+  const int K = (int)B->side.size();
+  if (K == 0) {
+    for (BatchProb& bp : B->probs) TPSS_TRY(f(bp));
+    return TPSS_OK;
+  }
+  TPSS_CHECK_CUDA(cudaEventRecord(B->side_fork, B->stream));
+  for (int k = 0; k < K; ++k) TPSS_CHECK_CUDA(cudaStreamWaitEvent(B->side[k], B->side_fork, 0));
+  int k = 0;
+  for (BatchProb& bp : B->probs) {
+    cudaStream_t keep = bp.ctx->stream;
+    bp.ctx->stream = B->side[k];
+    const tpss_status st = f(bp);
+    bp.ctx->stream = keep;
+    if (st != TPSS_OK) return st;
+    k = (k + 1) % K;
+  }
+  return side_join(B, true);
+}
+
 // One FP32 V-cycle for every problem and right-hand side: fx = MG(0, fb).
 static tpss_status batch_vcycle_rec(tpss_batch* B, int depth) {
   cudaStream_t s = B->stream;
   const int nr = B->nrhs;
   bool any = false;
-  for (BatchProb& bp : B->probs) {
+  for (const BatchProb& bp : B->probs) any = any || bp.L - depth > 0;
+  TPSS_TRY(on_sides(B, [&](BatchProb& bp) -> tpss_status {
     const int l = bp.L - depth;
     if (l == 0) {
       MGState* mg = bp.ctx->mg;
       const int64_t n = bp.ctx->levels[0].ndofs;
       dim3 grid((unsigned)((n * 32 + 255) / 256), nr);
-      batch_dense_mv_kernel<<<grid, 256, 0, s>>>(mg->coarse_inv, bp.b[0], bp.x[0], n);
+      batch_dense_mv_kernel<<<grid, 256, 0, bp.ctx->stream>>>(mg->coarse_inv, bp.b[0], bp.x[0], n);
       TPSS_CHECK_LAUNCH();
     } else if (l > 0) {
-      any = true;
-      TPSS_CHECK_CUDA(cudaMemsetAsync(bp.x[l], 0, (size_t)bp.ctx->levels[l].ndofs * nr * sizeof(float), s));
+      TPSS_CHECK_CUDA(cudaMemsetAsync(bp.x[l], 0, (size_t)bp.ctx->levels[l].ndofs * nr * sizeof(float),
+                                      bp.ctx->stream));
     }
-  }
+    return TPSS_OK;
+  }));
   if (!any) return TPSS_OK;
   // pre-smoothing (x = 0, r = b): one persistent launch for all problems
   // (the tcgen05 levels on the side streams)
@@ -675,19 +703,19 @@ static tpss_status batch_vcycle_rec(tpss_batch* B, int depth) {
   TPSS_TRY(launch_level(B, B->d_desc[depth], B->d_items[depth], B->nitems[depth], B->smem[depth],
                         B->grid[depth], B->d_counter + 2 * depth, s));
   TPSS_TRY(side_join(B, forked));
-  for (BatchProb& bp : B->probs) {
+  TPSS_TRY(on_sides(B, [&](BatchProb& bp) -> tpss_status {
     const int l = bp.L - depth;
-    if (l < 1) continue;
+    if (l < 1) return TPSS_OK;
     TPSS_TRY(apply_operator_t<float>(bp.ctx, l, nr, bp.x[l], bp.r[l], bp.b[l]));
-    TPSS_TRY(restrict_t<float>(bp.ctx, l, nr, bp.r[l], bp.b[l - 1]));
-  }
+    return restrict_t<float>(bp.ctx, l, nr, bp.r[l], bp.b[l - 1]);
+  }));
   TPSS_TRY(batch_vcycle_rec(B, depth + 1));
-  for (BatchProb& bp : B->probs) {
+  TPSS_TRY(on_sides(B, [&](BatchProb& bp) -> tpss_status {
     const int l = bp.L - depth;
-    if (l < 1) continue;
+    if (l < 1) return TPSS_OK;
     TPSS_TRY(prolongate_add_t<float>(bp.ctx, l, nr, bp.x[l - 1], bp.x[l]));
-    TPSS_TRY(apply_operator_t<float>(bp.ctx, l, nr, bp.x[l], bp.r[l], bp.b[l]));
-  }
+    return apply_operator_t<float>(bp.ctx, l, nr, bp.x[l], bp.r[l], bp.b[l]);
+  }));
   // post-smoothing with the residual
   TPSS_TRY(side_passes(B, depth, true, 0, &forked));
   TPSS_TRY(launch_level(B, B->d_desc_post[depth], B->d_items[depth], B->nitems[depth], B->smem[depth],
@@ -844,11 +872,8 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
       bp.route[l] = uses_tc05(B, bp, l) ? 1 : (B->bf16 && B->columns && l == bp.L) ? 2 : 0;
   }
   {
-    bool any = false;
-    for (const BatchProb& bp : B->probs)
-      for (char c : bp.route) any = any || c;
-    if (any) {
-      const int K = 4;
+    {
+      const int K = 4;   // side streams: per-problem passes, operators and transfers run side by side
       B->side.assign(K, nullptr);
       B->side_join.assign(K, nullptr);
       for (int k = 0; k < K; ++k) {
@@ -1105,8 +1130,9 @@ extern "C" tpss_status tpss_batch_pcg_solve(tpss_batch* B, const double* b, doub
   TPSS_TRY(seg_dot(B, B->r, B->z, sc + 0 * S));
   int nactive = (int)std::count(active.begin(), active.end(), 1.0);
   for (int it = 1; it <= maxit && nactive > 0; ++it) {
-    for (BatchProb& bp : B->probs)
-      TPSS_TRY(apply_operator_t<double>(bp.ctx, bp.L, B->nrhs, B->p + bp.off, B->q + bp.off, nullptr));
+    TPSS_TRY(on_sides(B, [&](BatchProb& bp) {
+      return apply_operator_t<double>(bp.ctx, bp.L, B->nrhs, B->p + bp.off, B->q + bp.off, nullptr);
+    }));
     TPSS_TRY(seg_dot(B, B->p, B->q, sc + 1 * S));
     seg_xr_kernel<<<sgrid, 256, 0, s>>>(x, B->r, B->p, B->q, B->d_off, B->d_len, sc, S);
     TPSS_TRY(seg_dot(B, B->r, B->r, sc + 2 * S));
