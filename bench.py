@@ -1027,6 +1027,14 @@ def run_batch_one(tpss, workloads, torch, steps, prec, columns=True):
                            "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_hbm": byt / (ms / 1e3) / 1e9 / hbm}
         bd = torch.from_numpy(b).to("cuda")
         x = torch.empty_like(bd)
+        B.vcycle(bd, x)
+        torch.cuda.synchronize()
+        e0.record(side)
+        for _ in range(steps):
+            B.vcycle(bd, x)
+        e1.record(side)
+        torch.cuda.synchronize()
+        out["vcycle_ms"] = e0.elapsed_time(e1) / steps
         e0.record(side)
         res = B.pcg_solve(bd, x, rtol=1e-8, maxit=100)
         e1.record(side)

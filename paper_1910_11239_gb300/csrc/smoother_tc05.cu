@@ -58,11 +58,17 @@ constexpr int kThreads = 128;
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 constexpr int kMStride = 144;                     // bytes between core matrices along M
 constexpr int kKStride = 32 * kMStride;           // bytes between core matrices along K (256 rows)
+// TF32, the operands written one value per row with rows 16 slow + j, k fixed
+// per thread (stages 1 and 4): core matrices 160 bytes apart along M and
+// 5136 along K, so that a warp's 32 stores (4 k & 3 x 4 k >> 2 x 2 slow) fall
+// in 32 distinct banks; the MMAs of stages 2 and 5 read them with these strides
+constexpr int kMStrideT = 160;
+constexpr int kKStrideT = 32 * kMStrideT + 16;
 
 // per element type: A bytes (2 or 4 core-matrix columns of 8 or 4 values),
 // one 16 x 16 B operand, the B operands of one position (Z^T and Z)
 template <bool TF> struct Op {
-  static constexpr int ABYTES = (TF ? 4 : 2) * kKStride;
+  static constexpr int ABYTES = TF ? 4 * kKStrideT : 2 * kKStride;
   static constexpr int BBYTES = TF ? 1024 : 512;
   static constexpr int BPOS = 2 * BBYTES;
 };
@@ -174,17 +180,21 @@ __device__ __forceinline__ void put_row_k(unsigned char* opa, int m, const float
   }
 }
 // rows 16 slow + j (j = 0..15) at column k of A: MN-major rows (BF16) or
-// one value per row of the K-major TF32 operand.  ALT: neighbouring threads
-// differ in `slow` (not in k); the threads with bit 2 of slow set write their
-// two 16-byte rows in the other order, so that the 8 rows one store
-// instruction writes per quarter warp fall in 8 distinct bank groups.
+// one value per row of the K-major TF32 operand (strides kMStrideT / kKStrideT
+// unless ALT).  ALT: neighbouring threads differ in `slow` (not in k); the
+// BF16 threads with bit 2 of slow set write their two 16-byte rows in the
+// other order, so that the 8 rows one store instruction writes per quarter
+// warp fall in 8 distinct bank groups.
 template <bool TF, bool ALT>
 __device__ __forceinline__ void put_col(unsigned char* opa, int slow, int k, const float* v) {
   if constexpr (TF) {
-    unsigned char* base = opa + (k & 3) * 4 + (k >> 2) * kKStride;
+    constexpr int MS = ALT ? kMStride : kMStrideT, KS = ALT ? kKStride : kKStrideT;
+    unsigned char* base = opa + (k & 3) * 4 + (k >> 2) * KS;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      *reinterpret_cast<uint32_t*>(base + off_k(16 * slow + j)) = tc05::to_tf32(v[j]);
+    for (int j = 0; j < 16; ++j) {
+      const int r = 16 * slow + j;
+      *reinterpret_cast<uint32_t*>(base + (r & 7) * 16 + (r >> 3) * MS) = tc05::to_tf32(v[j]);
+    }
   } else if constexpr (ALT) {
     const uint4 lo = tc05::pack8(v), hi = tc05::pack8(v + 8);
     const bool swap = (slow >> 2) & 1;
@@ -391,12 +401,13 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
         const uint32_t bslot = b_base + BB * b_slot(s, pz & 1);
         if constexpr (TF) {   // K = 16 as two MMAs of K = 8 (core-matrix columns 2h, 2h + 1)
           constexpr uint32_t idesc = tc05::idesc_tf32(128, 16);
+          // A of stages 2 and 5 was written with the strides kMStrideT / kKStrideT
+          const int ms = (s == 2 || s == 5) ? kMStrideT : kMStride, ks = (s == 2 || s == 5) ? kKStrideT : kKStride;
 #pragma unroll
           for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-              tc05::mma_tf32(tmem + 16 * b,
-                             tc05::desc(a_base + 16 * kMStride * b + 2 * h * kKStride, kKStride, kMStride),
+              tc05::mma_tf32(tmem + 16 * b, tc05::desc(a_base + 16 * ms * b + 2 * h * ks, ks, ms),
                              tc05::desc(bslot + 512 * h, 256, 128), idesc, h);
         } else {
           const uint32_t idesc = tc05::idesc_bf16(128, 16, a_major(s), 0);
