@@ -947,9 +947,10 @@ def run_batch(tpss, workloads, perf, torch, steps):
     import numpy as np
     out = {"workload": "48 independent 3D Poisson problems, 12 each of (16^3,k=7), (24^3,k=5), (32^3,k=3), "
                        "(48^3,k=2), random widths, 4 RHS each U[-1,1]; AVS omega 1/8; FP32 V-cycle with one "
-                       "persistent smoother launch per level (BF16: the k >= 4 problems on the tcgen05 column "
-                       "smoother, on side streams beside it; bf16_persistent: every problem in the persistent "
-                       "kernel), CUDA graph, autotuned patches per work item, FP64 flexible PCG to 1e-8"}
+                       "persistent smoother launch per level (BF16: every level on the per-problem smoothers, "
+                       "tcgen05 columns for k >= 4 and colored launches below, on 4 side streams; "
+                       "bf16_persistent: every problem in the persistent kernel), per-problem operators and "
+                       "transfers on the side streams, CUDA graph, FP64 flexible PCG to 1e-8"}
     for prec, key, columns in (("bf16", "bf16", True), ("bf16", "bf16_persistent", False), ("fp32", "fp32", True)):
         out[key] = run_batch_one(tpss, workloads, torch, steps, prec, columns)
     specs = batch_specs(workloads)

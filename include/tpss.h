@@ -412,14 +412,14 @@ tpss_status tpss_ir_solve(tpss_ctx* ctx, const double* b, double* x, double rtol
  * fixed).  The number of patches per work item is autotuned per patch size
  * at creation unless flags & 2; the whole V-cycle is captured as a CUDA graph
  * unless flags & 1 or the stream is the legacy default stream.  With BF16
- * contractions, unless flags & 4, the levels of degree k >= 4 and the finest
- * level of every problem leave the persistent kernel: each such problem's
- * additive pass runs the library's deterministic per-problem smoother (the
- * tcgen05 column walk TPSS_ADDITIVE_TCGEN05 for k >= 4, else the colored
- * launches) on one of four side streams forked from the batch stream,
- * concurrently with the persistent launch for the rest; a tcgen05 pass that
- * gave up waiting for its MMAs is reported as TPSS_ETIMEOUT by the next
- * tpss_batch_vcycle or tpss_batch_pcg_solve.
+ * contractions, unless flags & 4, no level uses the persistent kernel: each
+ * problem's additive pass runs the library's deterministic per-problem
+ * smoother (the tcgen05 column walk TPSS_ADDITIVE_TCGEN05 for k >= 4, else
+ * the colored launches) on one of four side streams forked from the batch
+ * stream, so the problems' launches overlap; a tcgen05 pass that gave up
+ * waiting for its MMAs is reported as TPSS_ETIMEOUT by the next
+ * tpss_batch_vcycle or tpss_batch_pcg_solve.  The per-problem operators,
+ * transfers and coarse solves of every batch run on the same side streams.
  * Vector layout of every batched call: problems one after another, each as
  * nrhs consecutive vectors of its finest level, each problem's block starting
  * on a 16-byte boundary (tpss_batch_info gives offsets; entries between blocks
@@ -435,7 +435,7 @@ tpss_status tpss_batch_info(const tpss_batch* batch, int prob, int64_t* ndofs, i
 tpss_status tpss_batch_summary(const tpss_batch* batch, int64_t* total, int* nsys, int* uses_graph);
 /* Finest level of every problem, x = omega sum_j R_j^T A_j^{-1} R_j b in FP32
  * (Alg. 2 with x = 0), one persistent launch (BF16 batches: the per-problem
- * passes on the side streams); b and x are FP32 device vectors. */
+ * passes on the side streams instead); b and x are FP32 device vectors. */
 tpss_status tpss_batch_smooth_additive(tpss_batch* batch, const float* b, float* x);
 /* x = MG(0, b) for every system (FP64 in and out, FP32 inside). */
 tpss_status tpss_batch_vcycle(tpss_batch* batch, const double* b, double* x);

@@ -10,12 +10,10 @@
 // to a templated fast-diagonalization routine (gather, Z^T, Lambda^{-1}, Z)
 // and scatter with FP32 atomic adds (overlapping patches of one problem may
 // be processed concurrently; FP32 summation order is therefore not fixed).
-// In BF16 batches, the levels whose patch sets run the tcgen05 column
-// smoother (k >= 4), and the finest level of the other problems, leave the
-// persistent kernel: each such problem's additive pass runs the library's
-// deterministic per-problem smoother (the tcgen05 column walk, or the
-// colored BF16 launches) on one of a few side streams, concurrently with the
-// persistent launch for the rest.
+// In BF16 batches every level leaves the persistent kernel: each problem's
+// additive pass runs the library's deterministic per-problem smoother (the
+// tcgen05 column walk for k >= 4, the colored BF16 launches below) on one of
+// a few side streams, so the problems' launches overlap.
 // Work items are sorted by cost, largest first.  The number of patches per
 // work item is chosen per n by an autotuner that times the candidates at
 // setup.  Operators, transfers and coarse solves are launched per problem
@@ -869,7 +867,7 @@ extern "C" tpss_status tpss_batch_create(const tpss_problem_desc* descs, int npr
       if ((st = ensure_level_scratch(bp.ctx, l, nrhs)) != TPSS_OK) return fail(st);
     bp.route.assign(bp.L + 1, 0);
     for (int l = 1; l <= bp.L; ++l)
-      bp.route[l] = uses_tc05(B, bp, l) ? 1 : (B->bf16 && B->columns && l == bp.L) ? 2 : 0;
+      bp.route[l] = uses_tc05(B, bp, l) ? 1 : (B->bf16 && B->columns) ? 2 : 0;
   }
   {
     {

@@ -140,8 +140,8 @@ BATCH_TOL = {"fp32": 1e-4, "bf16": 5e-2}
 
 # (precision, columns): FP32 -> batch_group<n>; BF16 without columns ->
 # batch_group_bf16<n>; BF16 with columns -> per-problem passes on the side
-# streams (tcgen05 columns for n = 12, 16, i.e. k = 5, 7, on every level; the
-# colored BF16 launches for k = 2 on the finest level, batch_group_bf16<6> below)
+# streams on every level (tcgen05 columns for n = 12, 16, i.e. k = 5, 7; the
+# colored BF16 launches for k = 2)
 ROUTES = [("fp32", True), ("bf16", False), ("bf16", True)]
 
 
