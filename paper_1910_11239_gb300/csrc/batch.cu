@@ -333,17 +333,26 @@ batch_smooth_kernel(const BatchLevelDesc* __restrict__ desc, const BatchItem* __
 }
 
 // y_r = Ainv b_r for nrhs vectors (FP64 inverse, FP32 vectors), one warp per row
+// (four right-hand sides per warp and row: the row of A is read once for them)
 __global__ void batch_dense_mv_kernel(const double* __restrict__ A, const float* __restrict__ b, float* __restrict__ y,
-                                      int64_t n) {
+                                      int64_t n, int nrhs) {
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   if (row >= n) return;
-  const float* br = b + (int64_t)blockIdx.y * n;
-  double s = 0.0;
-  for (int64_t c = lane; c < n; c += 32) s = fma(A[row * n + c], (double)br[c], s);
+  const int r0 = 4 * blockIdx.y, nr = nrhs - r0 < 4 ? nrhs - r0 : 4;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t c = lane; c < n; c += 32) {
+    const double a = A[row * n + c];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[(int64_t)blockIdx.y * n + row] = (float)s;
+    for (int q = 0; q < 4; ++q)
+      if (q < nr) s[q] = fma(a, (double)b[(int64_t)(r0 + q) * n + c], s[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+    if (lane == 0 && q < nr) y[(int64_t)(r0 + q) * n + row] = (float)s[q];
+  }
 }
 
 // ------------------------------------------------------------ segmented CG
@@ -684,8 +693,8 @@ static tpss_status batch_vcycle_rec(tpss_batch* B, int depth) {
     if (l == 0) {
       MGState* mg = bp.ctx->mg;
       const int64_t n = bp.ctx->levels[0].ndofs;
-      dim3 grid((unsigned)((n * 32 + 255) / 256), nr);
-      batch_dense_mv_kernel<<<grid, 256, 0, bp.ctx->stream>>>(mg->coarse_inv, bp.b[0], bp.x[0], n);
+      dim3 grid((unsigned)((n * 32 + 255) / 256), (unsigned)((nr + 3) / 4));
+      batch_dense_mv_kernel<<<grid, 256, 0, bp.ctx->stream>>>(mg->coarse_inv, bp.b[0], bp.x[0], n, nr);
       TPSS_CHECK_LAUNCH();
     } else if (l > 0) {
       TPSS_CHECK_CUDA(cudaMemsetAsync(bp.x[l], 0, (size_t)bp.ctx->levels[l].ndofs * nr * sizeof(float),
