@@ -6,6 +6,9 @@
 // of vertex patches (p_x, p_y) and right-hand side walks p_z, r staged one
 // cell plane ahead with cp.async, each cell plane of x written once per
 // parity class of (p_x, p_y) when both of its patches in the column are done.
+// With two or more right-hand sides, the second half runs on a second stream
+// (fork and join by events), so that its class launches fill the SMs that the
+// last wave of each class launch of the first half leaves idle.
 //
 // Local solve (eq. fastinverse, eq. eigenvectormatvec): the six mode
 // contractions of (Z_z x Z_y x Z_x) Lambda^{-1} (Z_z x Z_y x Z_x)^T are six
@@ -14,8 +17,9 @@
 // is padded to 16 slots, slot 8 c + i for node i < k + 1 of the patch's cell
 // c (modes take the same slots, mode j at 8 (j / (k+1)) + j % (k+1)), so the
 // patch tensor has 256 "lines" (slow index s, fast index f, row m = 16 s +
-// f) and each cell of the patch owns an 8 x 8 x 8 corner of it.  A is the tensor with the contracted index as
-// K; B is the 1D eigenvector matrix (K-major 16 x 16, zero padded, prepared
+// f) and each cell of the patch owns an 8 x 8 x 8 corner of it.  A is the
+// tensor with the contracted index as K; B is the 1D eigenvector matrix
+// (K-major 16 x 16, zero padded, prepared
 // once per position at setup and staged with cp.async).  After each MMA every
 // thread reads its TMEM rows (row m = thread + 128 b) and writes them back to
 // shared memory as the next A, rotating the indices so that the next
@@ -29,13 +33,17 @@
 //   A5            --Zx----> D6[(z,y)][x] -> omega * D6, the patch's correction
 //
 // so each thread's TMEM row goes back as two 16-byte rows of core matrices.
-// The core matrices of A sit 144 bytes apart along M (not 128) so that these
-// writes are free of shared-memory bank conflicts.
+// The core matrices of A sit 144 bytes apart along M (not 128), and stages 2
+// and 5 order their two stores by row group, so that these writes are free
+// of shared-memory bank conflicts.  The cell lines of r are staged with the
+// two 16-byte halves of every other group of 4 lines swapped (k = 7), which
+// makes the gather's reads conflict-free too.
 //
 // TF32 (kind::tf32, K = 8 per MMA): the same walk with FP32 operands rounded
 // to TF32, two MMAs per 16-wide contraction and every operand K-major (a
 // core matrix row holds 4 values); the rotated stages write their values to
-// the next A one by one instead of as MN-major rows.
+// the next A one by one instead of as MN-major rows, stages 1 and 4 with
+// core-matrix strides that keep those stores conflict-free.
 //
 // Output: a thread's two rows of D6 (m and m + 128) are the same (y, z) line
 // of the patch's lower and upper cell plane; the upper one is kept in
