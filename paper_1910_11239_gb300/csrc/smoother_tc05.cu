@@ -101,8 +101,8 @@ struct Smem {
   static constexpr int NP = 4 * NLOC1;                       // floats of one column plane (4 cells)
   static constexpr size_t OPA = 0;
   static constexpr size_t OPB = Op<TF>::ABYTES;              // 8 operands B
-  static constexpr size_t SB = OPB + 8 * Op<TF>::BBYTES;     // 3 staged planes of r (FP32)
-  static constexpr size_t BYTES = SB + 3 * (size_t)NP * 4;
+  static constexpr size_t SB = OPB + 8 * Op<TF>::BBYTES;     // 2 staged planes of r (FP32)
+  static constexpr size_t BYTES = SB + 2 * (size_t)NP * 4;
 };
 // B operand slots (pairs as stored per position: Z^T-apply, Z-apply): 0 / 1 x,
 // 2 / 3 y, 4 + 2q / 5 + 2q z of the patch with p_z & 1 == q.  Stage s (1..6)
@@ -258,7 +258,7 @@ __device__ __forceinline__ void st_line(float* p, const float* v) {
 }
 
 template <int N, bool TF>
-__global__ void __launch_bounds__(kThreads, (TF || N == 16) ? 4 : 5)   // k = 7: 4 CTAs (TF32: 51 KB of shared memory; BF16: no spills)
+__global__ void __launch_bounds__(kThreads, TF ? 4 : (N >= 14 ? 5 : 6))   // BF16 k <= 5: 6 CTAs per SM without spills
 patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned char* __restrict__ B1,
                          const unsigned char* __restrict__ B2, const float* __restrict__ L0,
                          const float* __restrict__ L1, const float* __restrict__ L2, const float* __restrict__ r,
@@ -292,14 +292,14 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
 #pragma unroll
   for (int c2 = 0; c2 < 4; ++c2) stage_off[c2] = ((px + (c2 & 1)) + (int64_t)nc0 * (py + (c2 >> 1))) * NLOC1 + 4 * tid;
   const uint32_t stage_dst = 16u * ((tid & ~1) | ((tid & 1) ^ ((tid >> 3) & 1)));
-  auto stage_r = [&](int cz) {   // cell plane cz of r -> ring slot cz % 3
+  auto stage_r = [&](int cz) {   // cell plane cz of r -> ring slot cz % 2
     if constexpr (NLOC1 == 4 * kThreads) {
-      const uint32_t d = tc05::smem_u32(SB + (cz % 3) * NP) + stage_dst;
+      const uint32_t d = tc05::smem_u32(SB + (cz % 2) * NP) + stage_dst;
       const float* src = r + (int64_t)cz * plane_stride;
 #pragma unroll
       for (int c2 = 0; c2 < 4; ++c2) cp16(d + 4u * NLOC1 * c2, src + stage_off[c2]);
     } else {
-      stage_plane<NLOC1>(SB + (cz % 3) * NP, r, px, py, cz, nc0, nc1, tid);
+      stage_plane<NLOC1>(SB + (cz % 2) * NP, r, px, py, cz, nc0, nc1, tid);
     }
   };
 
@@ -353,7 +353,6 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();   // planes pz, pz + 1 and patch pz's z operands staged; patch pz - 1 is done
     if (pz + 2 < nc2) {
-      stage_r(pz + 2);
       stage_b2<TF>(opb + (4 + 2 * ((pz + 1) & 1)) * BB, B2 + (size_t)(pz + 1) * BP, tid);
       if (tid < 16 && (tid & 7) < N1)   // the next patch's z eigenvalues
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
@@ -372,8 +371,8 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
         if (!store_cell[sx]) ld_line<N1>(x + line_off[sx] + pz * plane_stride, xold + 8 * sx);
     }
     // gather: A0[(z, y)][x] (K-major), zero outside the cells' nodes
-    const float* lo = SB + (pz % 3) * NP;
-    const float* hi = SB + ((pz + 1) % 3) * NP;
+    const float* lo = SB + (pz % 2) * NP;
+    const float* hi = SB + ((pz + 1) % 2) * NP;
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       float v[16];
@@ -402,6 +401,10 @@ patch_stream_tc05_kernel(const unsigned char* __restrict__ B0, const unsigned ch
     tc05::fence_before_sync();
     __syncthreads();
     tc05::fence_after_sync();
+    if (pz + 2 < nc2) {   // plane pz is gathered: its slot takes plane pz + 2
+      stage_r(pz + 2);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
 
 #pragma unroll
     for (int s = 1; s <= 6; ++s) {   // unrolled: every stage's index rotation is resolved at compile time
