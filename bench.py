@@ -392,7 +392,7 @@ def main():
                 "achieved": dom["tflops"], "peak": perf.fp64_peak_flops() / 1e12, "unit": "TFLOP/s",
                 "frac": dom["frac_fp64_peak"],
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe; HBM is not binding)",
-                "per": "one smoother call = 8 color launches on 8 RHS",
+                "per": "one smoother call = 8 colors x 2 halves of the 8 RHS (two streams) = 16 launches",
                 "traffic": TRAFFIC_K7_PER_CALL if (kdom == 7 and NC == 32) else None,
                 "traffic_unit": "bytes per call (dram read + write, ncu)",
                 "algorithmic_bytes": perf.smoother_bytes((NC, NC, NC), kdom, nrhs=nr)}
@@ -471,7 +471,8 @@ def main():
 
     if rank == 0:
         print(json.dumps(headline_line(value, ms / args.steps, world, args.steps, nwarm, roofline, e2e, clocks,
-                                       per_k, cpu_res, args.steps * len(ks) * 8)), flush=True)
+                                       per_k, cpu_res, args.steps * len(ks) * 8 * (2 if len(SEEDS) >= 2 else 1))),
+              flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -747,6 +747,13 @@ tpss_status create_patches(tpss_ctx* ctx, int level, int kind, int precision, tp
   // operands of the tcgen05 smoother (every direction's FP32 eigenvectors are converted by now)
   if (!ctx->mapped && (precision == TPSS_BF16 || precision == TPSS_TF32) && (st = tc05_prepare(P)) != TPSS_OK)
     return fail(st);
+  // second stream of the additive passes (second half of the right-hand sides)
+  if (cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->fork_event, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->join_event, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("tpss_setup_patches: stream or event creation failed");
+    return fail(TPSS_ECUDA);
+  }
   const bool large = d == 3 && n > kMaxSharedPatchN;
   if (ctx->mapped) {
     // inverse table already built per cell

@@ -392,10 +392,32 @@ tpss_status smooth_additive_t(tpss_patches* P, T omega, int nrhs, const T* b, T*
     }
     return TPSS_OK;
   }
+  // Two or more right-hand sides: the second half runs on a second stream
+  // (fork and join by events), so that its color launches fill the SMs the
+  // last wave of each color launch of the first half leaves idle; the halves
+  // share no data and each sum keeps its order.  Not for the large 3D vertex
+  // patches, whose CTAs share the patch set's global tensor slabs, nor where
+  // the second half would start off the 16-byte alignment of the first (the
+  // vectorized kernels need it).
   const int nc = (int)P->add_offsets.size() - 1;
+  const bool large = ctx->dim == 3 && P->kind == TPSS_VERTEX_PATCH && P->n > kMaxSharedPatchN;
+  const bool aligned = ((int64_t)(nrhs / 2) * L.ndofs * (int64_t)sizeof(T)) % 16 == 0;
+  const int halves = (nrhs >= 2 && P->aux_stream != nullptr && !large && aligned) ? 2 : 1;
+  if (halves == 2) {
+    TPSS_CHECK_CUDA(cudaEventRecord(P->fork_event, s));
+    TPSS_CHECK_CUDA(cudaStreamWaitEvent(P->aux_stream, P->fork_event, 0));
+  }
   for (int c = 0; c < nc; ++c) {
     const int o = P->add_offsets[c], cnt = P->add_offsets[c + 1] - o;
-    TPSS_TRY(patch_pass<T>(P, P->d_add_list + o, cnt, omega, nrhs, r, x, s));
+    for (int h = 0; h < halves; ++h) {
+      const int r0 = h == 0 ? 0 : nrhs / 2, nr = halves == 1 ? nrhs : (h == 0 ? nrhs / 2 : nrhs - nrhs / 2);
+      const int64_t off = (int64_t)r0 * L.ndofs;
+      TPSS_TRY(patch_pass<T>(P, P->d_add_list + o, cnt, omega, nr, r + off, x + off, h == 0 ? s : P->aux_stream));
+    }
+  }
+  if (halves == 2) {
+    TPSS_CHECK_CUDA(cudaEventRecord(P->join_event, P->aux_stream));
+    TPSS_CHECK_CUDA(cudaStreamWaitEvent(s, P->join_event, 0));
   }
   return TPSS_OK;
 }

@@ -584,9 +584,6 @@ tpss_status tc05_prepare(tpss_patches* P) {
   void* d = nullptr;
   TPSS_CHECK_CUDA(cudaHostGetDevicePointer(&d, h, 0));
   P->d_fail_flag = static_cast<int*>(d);
-  TPSS_CHECK_CUDA(cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking));
-  TPSS_CHECK_CUDA(cudaEventCreateWithFlags(&P->fork_event, cudaEventDisableTiming));
-  TPSS_CHECK_CUDA(cudaEventCreateWithFlags(&P->join_event, cudaEventDisableTiming));
   return TPSS_OK;
 }
 

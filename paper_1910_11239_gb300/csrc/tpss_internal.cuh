@@ -221,7 +221,7 @@ struct tpss_patches {
   int* h_fail_flag = nullptr;      // tcgen05 smoother: host-mapped word set when an MMA wait expires
   int* d_fail_flag = nullptr;      // its device address
   int expire_test = 0;             // test hook: the next tcgen05 call lets its first waits expire
-  cudaStream_t aux_stream = nullptr;   // column smoothers: second half of the right-hand sides
+  cudaStream_t aux_stream = nullptr;   // additive passes: second half of the right-hand sides
   cudaEvent_t fork_event = nullptr, join_event = nullptr;
   // per multiplicative color: cells outside the color with a face to it,
   // {cell index, face mask (bit 2t+side: neighbour at -1 / +1 along t)}
