@@ -55,6 +55,11 @@ def test_null_arguments_rejected_without_gpu(libpath):
     assert b"null" in L.tpss_last_error()
     assert L.tpss_smooth_additive(None, 0.7, 1, None, None, 1) == -1
     assert L.tpss_pcg_solve(None, None, None, 1e-8, 10, None, None, None) == -1
+    # the schedule option, its failure-path test hook and the batch constructor
+    assert L.tpss_patches_set_additive_schedule(None, 4) == -1
+    assert L.tpss_patches_test_wait_expiry(None) == -1
+    assert b"null" in L.tpss_last_error()
+    assert L.tpss_batch_create(None, 1, 1, None, 4, None, None) == -1
 
 
 def test_mapped_mesh_arguments_are_checked_on_the_host(libpath):
