@@ -41,11 +41,12 @@ CONFIG = {"workload": "3D additive vertex-patch Schwarz smoother (fast diagonali
                       "widths U[0.5,1.5]/32, omega 0.7, k=2..7, 8 RHS U[-1,1] batched, x=0 form",
           "cells": [NC, NC, NC], "degrees": KS, "nrhs": len(SEEDS),
           "l2": "inputs larger than L2 (each step streams >= 2.5 GB of vectors and tables)"}
-# DRAM bytes (read + write) of one FP64 smoother call at k=7 (8 color
-# launches, 8 RHS) at the full 32^3 size, from the single-pass ncu capture
-# summarized in profiles/patch_smooth_fp64_32cubed.md (captured again after
-# the kernel's last change, same value); set to None when the kernel changes
-# after that capture.
+# DRAM bytes (read + write) of one FP64 smoother call at k=7 (8 RHS) at the
+# full 32^3 size, from the single-pass ncu capture summarized in
+# profiles/patch_smooth_fp64_32cubed.md (captured again after the kernel's
+# last change, same value; taken with one launch per color, where the call
+# now issues each color as two launches of 4 RHS on two streams, the same
+# CTAs); set to None when the kernel changes after that capture.
 TRAFFIC_K7_PER_CALL = 30.98e9
 
 
