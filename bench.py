@@ -42,11 +42,11 @@ CONFIG = {"workload": "3D additive vertex-patch Schwarz smoother (fast diagonali
           "cells": [NC, NC, NC], "degrees": KS, "nrhs": len(SEEDS),
           "l2": "inputs larger than L2 (each step streams >= 2.5 GB of vectors and tables)"}
 # DRAM bytes (read + write) of one FP64 smoother call at k=7 (8 RHS) at the
-# full 32^3 size, from the single-pass ncu capture summarized in
-# profiles/patch_smooth_fp64_32cubed.md (captured again after the kernel's
-# last change, same value; taken with one launch per color, where the call
-# now issues each color as two launches of 4 RHS on two streams, the same
-# CTAs); set to None when the kernel changes after that capture.
+# full 32^3 size, from a single-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over the call's launches; captured again after the
+# kernel's last change, same value; taken with one launch per color, where
+# the call now issues each color as two launches of 4 RHS on two streams,
+# the same CTAs); set to None when the kernel changes after that capture.
 TRAFFIC_K7_PER_CALL = 30.98e9
 
 
