@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-kernels", action="store_true")
     p.add_argument("--no-distorted", action="store_true")
     p.add_argument("--batch-problems", type=int, default=48, help="use the first N problems of the batch (profiling)")
+    p.add_argument("--batch-persistent", action="store_true",
+                   help="also time the BF16 batch with every level in the persistent kernel")
     p.add_argument("--ks", default=",".join(map(str, KS)))
     p.add_argument("--nc", type=int, default=NC, help="cells per direction (profiling of small cases)")
     p.add_argument("--mixed", default="fp32,tf32,bf16", help="low-precision smoother variants to time")
@@ -462,7 +464,7 @@ def main():
         leg("mg_cg", lambda: run_mgcg(tpss, workloads, torch, MGCG_CASES))
         leg("paper_iterations", lambda: run_paper_iterations(tpss, workloads, perf, torch))
     if not args.no_batch:
-        leg("batched", lambda: run_batch(tpss, workloads, perf, torch, args.steps))
+        leg("batched", lambda: run_batch(tpss, workloads, perf, torch, args.steps, args.batch_persistent))
     if not args.no_kernels:
         leg("kernels", lambda: run_kernels(tpss, workloads, perf, torch, max(3, min(args.steps, 10))))
     if not args.no_high_degree:
@@ -943,9 +945,10 @@ def batch_specs(workloads):
     return out[:BATCH_PROBLEMS]
 
 
-def run_batch(tpss, workloads, perf, torch, steps):
-    """Config 5 for both persistent smoother variants (FP32 SIMT and BF16
-    tensor cores), then the same problems one at a time in FP64."""
+def run_batch(tpss, workloads, perf, torch, steps, persistent_too=False):
+    """Config 5 in BF16 (per-problem smoothers on side streams; with
+    persistent_too also with every level in the persistent kernel) and FP32
+    (persistent kernel), then the same problems one at a time in FP64."""
     import numpy as np
     out = {"workload": "48 independent 3D Poisson problems, 12 each of (16^3,k=7), (24^3,k=5), (32^3,k=3), "
                        "(48^3,k=2), random widths, 4 RHS each U[-1,1]; AVS omega 1/8; FP32 V-cycle with one "
@@ -953,7 +956,9 @@ def run_batch(tpss, workloads, perf, torch, steps):
                        "tcgen05 columns for k >= 4 and colored launches below, on 4 side streams; "
                        "bf16_persistent: every problem in the persistent kernel), per-problem operators and "
                        "transfers on the side streams, CUDA graph, FP64 flexible PCG to 1e-8"}
-    for prec, key, columns in (("bf16", "bf16", True), ("bf16", "bf16_persistent", False), ("fp32", "fp32", True)):
+    variants = [("bf16", "bf16", True)] + ([("bf16", "bf16_persistent", False)] if persistent_too else []) + \
+        [("fp32", "fp32", True)]
+    for prec, key, columns in variants:
         out[key] = run_batch_one(tpss, workloads, torch, steps, prec, columns)
     specs = batch_specs(workloads)
     side = torch.cuda.Stream()
@@ -979,7 +984,7 @@ def run_batch(tpss, workloads, perf, torch, steps):
         out["one_at_a_time_fp64"] = {"time_s": t_fp64 * nrhs,
                                      "measured": f"{len(specs)} problems x 1 RHS, times 4",
                                      "iters_max": int(max(its)), "iters_mean": float(np.mean(its))}
-    for key in ("bf16", "bf16_persistent", "fp32"):
+    for _, key, _ in variants:
         out[key]["speedup_time_to_solution_vs_fp64_one_at_a_time"] = (
             out["one_at_a_time_fp64"]["time_s"] / out[key]["pcg"]["time_s"])
     return out
