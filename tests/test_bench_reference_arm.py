@@ -1,7 +1,7 @@
 """The reference arm of bench.py (the oracle timed on the host) prints one
-JSON line with the contract keys, on a bounded sample (k = 2 only); and the
-GPU arm's contract line, built from stub timings, has its keys and stays a
-few KB."""
+JSON line with the contract keys, on a bounded sample (k = 2 only); the GPU
+arm's contract line, built from stub timings, has its keys and stays a few
+KB; and the batched leg runs the variants its options ask for."""
 import json
 import os
 import subprocess
@@ -54,3 +54,70 @@ def test_headline_line_keys_and_size():
     assert line["impl"] == "tpss" and line["roofline"]["algorithmic_bytes"] > 0
     failed = bench.headline_line(9.6e8, 350.0, 1, 20, 5, roofline, e2e, clocks, per_k, {"error": "boom"}, 960)
     assert failed["cpu_baseline"]["value"] is None and "boom" in failed["cpu_baseline"]["sample"]
+
+
+def test_batched_leg_variants_with_stub_runs():
+    # the batched leg's composition (which variants run, the speedup keys)
+    # with the GPU parts replaced by stubs
+    import contextlib
+    import types
+    import bench
+    from paper_1910_11239_gb300 import workloads
+
+    class Event:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 10.0
+
+    class Tensor:
+        def __init__(self, a):
+            self.a = a
+
+        def to(self, *args, **kwargs):
+            return self
+
+    cuda = types.SimpleNamespace(Stream=lambda: None, stream=lambda s: contextlib.nullcontext(), Event=Event,
+                                 synchronize=lambda: None)
+    torch_stub = types.SimpleNamespace(cuda=cuda, from_numpy=Tensor, empty_like=lambda t: t)
+
+    class Problem:
+        def __init__(self, *args, **kwargs):
+            pass
+
+        def mg_setup(self, *args, **kwargs):
+            pass
+
+        def ndofs(self, level):
+            return 10
+
+        def pcg_solve(self, *args, **kwargs):
+            return {"iters": 40}
+
+        def close(self):
+            pass
+
+    tpss_stub = types.SimpleNamespace(Problem=Problem, FP64=0)
+    calls = []
+
+    def one(tpss, wl, torch, steps, prec, columns=True):
+        calls.append((prec, columns))
+        return {"pcg": {"time_s": 2.0}}
+
+    saved = bench.run_batch_one
+    bench.run_batch_one = one
+    try:
+        out = bench.run_batch(tpss_stub, workloads, None, torch_stub, 3)
+        assert calls == [("bf16", True), ("fp32", True)]
+        assert set(out) == {"workload", "bf16", "fp32", "one_at_a_time_fp64"}
+        calls.clear()
+        out = bench.run_batch(tpss_stub, workloads, None, torch_stub, 3, True)
+        assert calls == [("bf16", True), ("bf16", False), ("fp32", True)]
+        for key in ("bf16", "bf16_persistent", "fp32"):
+            assert out[key]["speedup_time_to_solution_vs_fp64_one_at_a_time"] > 0
+    finally:
+        bench.run_batch_one = saved
